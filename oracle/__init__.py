@@ -1,0 +1,190 @@
+"""Plain FP64 CPU oracle of the seismic-inversion hot path.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers. The product library never
+imports this package, and the two share no code.
+
+The numerical work is in ``acoustic.c`` / ``elastic.c`` (plain scalar C loops in
+FP64); this module compiles them with gcc on first use and marshals numpy
+arrays through ctypes.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["acoustic.c", "elastic.c"]
+_HEADERS = ["oracle.h", "acoustic_fwd_body.h", "elastic_body.h"]
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/liboracle.so`` (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    deps = srcs + [os.path.join(_HERE, h) for h in _HEADERS if os.path.exists(os.path.join(_HERE, h))]
+    if not force and os.path.exists(_LIB_PATH):
+        t = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+class AcousticCfg(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int), ("nx", ctypes.c_int), ("npml", ctypes.c_int),
+        ("order", ctypes.c_int), ("nt", ctypes.c_int), ("nshots", ctypes.c_int),
+        ("src_kind", ctypes.c_int), ("nrec", ctypes.c_int),
+        ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("pml_R", ctypes.c_double), ("pml_vmax", ctypes.c_double), ("pml_f0", ctypes.c_double),
+        ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
+class ElasticCfg(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int), ("nx", ctypes.c_int), ("npml", ctypes.c_int),
+        ("order", ctypes.c_int), ("nt", ctypes.c_int), ("nshots", ctypes.c_int),
+        ("src_kind", ctypes.c_int), ("nrec", ctypes.c_int),
+        ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("pml_R", ctypes.c_double), ("pml_vmax", ctypes.c_double), ("pml_f0", ctypes.c_double),
+        ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
+def _declare(L):
+    P = ctypes.c_void_p
+    L.or_fd_coeffs.argtypes = [ctypes.c_int, P]
+    L.or_fd_coeffs.restype = ctypes.c_int
+    L.or_cpml_profile.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_int, P, P]
+    L.or_cpml_profile.restype = None
+    for name in ("or_acoustic_forward", "or_acoustic_forward_cplx"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.POINTER(AcousticCfg), P, P, P, P]
+        f.restype = ctypes.c_int
+    L.or_acoustic_adjoint.argtypes = [ctypes.POINTER(AcousticCfg), P, P, P, P, P, P, P]
+    L.or_acoustic_adjoint.restype = ctypes.c_int
+    L.or_num_threads.argtypes = []
+    L.or_num_threads.restype = ctypes.c_int
+    if hasattr(L, "or_elastic_forward"):
+        for name in ("or_elastic_forward", "or_elastic_forward_cplx"):
+            f = getattr(L, name)
+            f.argtypes = [ctypes.POINTER(ElasticCfg), P, P, P, P, P, P, P]
+            f.restype = ctypes.c_int
+        L.or_elastic_adjoint.argtypes = [ctypes.POINTER(ElasticCfg), P, P, P, P, P, P, P,
+                                         P, P, P, P, P, P]
+        L.or_elastic_adjoint.restype = ctypes.c_int
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def fd_coeffs(order: int) -> np.ndarray:
+    a = np.zeros(4, dtype=np.float64)
+    if lib().or_fd_coeffs(int(order), _ptr(a)) != 0:
+        raise ValueError(f"unsupported order {order}")
+    return a[: order // 2].copy()
+
+
+def cpml_profile(n_phys, npml, h, dt, R, vmax, f0, half, n_out):
+    a = np.zeros(n_out, dtype=np.float64)
+    b = np.zeros(n_out, dtype=np.float64)
+    lib().or_cpml_profile(int(n_phys), int(npml), float(h), float(dt), float(R), float(vmax),
+                          float(f0), int(half), int(n_out), _ptr(a), _ptr(b))
+    return a, b
+
+
+class _Geom:
+    """Keeps the receiver index arrays alive while the cfg struct points at them."""
+
+    def __init__(self, cls, g, nshots):
+        self.iz = np.ascontiguousarray(g["rec_iz"], dtype=np.int32)
+        self.ix = np.ascontiguousarray(g["rec_ix"], dtype=np.int32)
+        self.cfg = cls(
+            nz=g["nz"], nx=g["nx"], npml=g["npml"], order=g["order"], nt=g["nt"],
+            nshots=nshots, src_kind=g.get("src_kind", 0), nrec=len(self.iz),
+            dz=g["dz"], dx=g["dx"], dt=g["dt"], pml_R=g.get("pml_R", 1e-3),
+            pml_vmax=g.get("pml_vmax", 4500.0), pml_f0=g.get("pml_f0", 10.0),
+            rec_iz=self.iz.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            rec_ix=self.ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+        )
+
+
+def acoustic_forward(g: dict, c, stf, x0, complex_step: bool = False) -> np.ndarray:
+    """Seismograms [nshots][nrec][nt] of the acoustic recursion.
+
+    ``g`` holds the geometry (nz, nx, npml, order, nt, dz, dx, dt, src_kind,
+    pml_R, pml_vmax, pml_f0, rec_iz, rec_ix); c is [nz][nx], stf [S][nt],
+    x0 [S][2] = (x, z) in metres. With ``complex_step`` every input may be
+    complex and the map is evaluated in complex arithmetic.
+    """
+    dt_ = np.complex128 if complex_step else np.float64
+    c = np.ascontiguousarray(c, dtype=dt_)
+    stf = np.ascontiguousarray(np.atleast_2d(stf), dtype=dt_)
+    x0 = np.ascontiguousarray(np.reshape(x0, (-1, 2)), dtype=dt_)
+    S = stf.shape[0]
+    assert x0.shape[0] == S and c.shape == (g["nz"], g["nx"]) and stf.shape[1] == g["nt"]
+    geo = _Geom(AcousticCfg, g, S)
+    seis = np.zeros((S, geo.cfg.nrec, g["nt"]), dtype=dt_)
+    f = lib().or_acoustic_forward_cplx if complex_step else lib().or_acoustic_forward
+    if f(ctypes.byref(geo.cfg), _ptr(c), _ptr(stf), _ptr(x0), _ptr(seis)) != 0:
+        raise ValueError("oracle forward: invalid configuration or source outside the grid")
+    return seis
+
+
+def acoustic_adjoint(g: dict, c, stf, x0, res):
+    """Gradients (dJ/dc [nz][nx], dJ/dstf [S][nt], dJ/dx0 [S][2]) of any
+    misfit whose derivative with respect to the seismograms is ``res``."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    stf = np.ascontiguousarray(np.atleast_2d(stf), dtype=np.float64)
+    x0 = np.ascontiguousarray(np.reshape(x0, (-1, 2)), dtype=np.float64)
+    res = np.ascontiguousarray(res, dtype=np.float64)
+    S = stf.shape[0]
+    geo = _Geom(AcousticCfg, g, S)
+    assert res.shape == (S, geo.cfg.nrec, g["nt"])
+    gc = np.zeros((g["nz"], g["nx"]), dtype=np.float64)
+    gs = np.zeros((S, g["nt"]), dtype=np.float64)
+    gx = np.zeros((S, 2), dtype=np.float64)
+    if lib().or_acoustic_adjoint(ctypes.byref(geo.cfg), _ptr(c), _ptr(stf), _ptr(x0), _ptr(res),
+                                 _ptr(gc), _ptr(gs), _ptr(gx)) != 0:
+        raise ValueError("oracle adjoint: invalid configuration or out of memory")
+    return gc, gs, gx
+
+
+def acoustic_misfit_grad(g: dict, c, stf, x0, observed):
+    """J = 1/2 sum (d - d_obs)^2 over shots, receivers and samples, and its
+    gradients with respect to c, stf and x0."""
+    d = acoustic_forward(g, c, stf, x0)
+    res = d - np.asarray(observed, dtype=np.float64)
+    J = 0.5 * float(np.sum(res * res))
+    gc, gs, gx = acoustic_adjoint(g, c, stf, x0, res)
+    return J, gc, gs, gx
