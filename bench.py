@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the acoustic FWI gradient (forward + adjoint) on GB300.
+
+Workload: 201 x 601 physical grid (+32 CPML cells per side = 265 x 665), 8th
+order in space, dt = 0.8 ms, 3000 steps, 16 Ricker shots (8 Hz), 301
+receivers, checkpoint every 100 steps; seeded dipping-layer model with faults
+(observed data) and its Gaussian-smoothed start model (the gradient is taken
+there). One bench step = one full misfit + gradient evaluation
+(fwi_misfit_grad). Metric: Gcell-steps/s = shots x padded cells x nt / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same per-GPU workload (shots are
+independent; no collective on the data path: weak scaling); rank 0 prints one
+JSON line with the max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FWI Gcell-steps/s (fwd+adjoint), % HBM roofline, batched/learned vs plain"
+UNIT = "Gcell-steps/s"
+
+# Algorithmic HBM bytes per cell-step of each step kernel (FP32): every field
+# streamed once per step, halos assumed cached (kernel table).
+#   forward (recording):  read u^n, u^{n-1}, m; write u^{n+1}          16 B
+#   forward (storing):    + write u^n to the segment slot              20 B
+#   adjoint:              read lam_{n+1}, lam_{n+2}, m, u^n, g; write lam_n, g   28 B
+# plus, per cell inside an x- or z-CPML strip and per active axis:
+#   forward: psi read+write, zeta read+write = 16 B (+4 B psi to the slot when storing)
+#   adjoint: Z read+write, P read+write, stored psi read = 20 B
+BYTES = {"fwd": (16, 16), "store": (20, 20), "adj": (28, 20)}
+
+
+def padded(d):
+    return d["nz"] + 2 * d["npml"], d["nx"] + 2 * d["npml"]
+
+
+def launch_bytes(d, kind):
+    Nz, Nx = padded(d)
+    S = d["stf"].shape[0]
+    cells = Nz * Nx
+    pml_cells = Nz * 2 * d["npml"] + Nx * 2 * d["npml"]  # (cell, axis) pairs in CPML strips
+    base, per_pml = BYTES[kind]
+    return S * (base * cells + per_pml * pml_cells)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(kernel_file):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    src = open(os.path.join(ROOT, "paper_2003_06027_gb300", "csrc", kernel_file), "rb").read()
+    if kv.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        return float(kv["adj_dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", self.gpu, "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, x, local):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(d, shots, nt):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the
+    workload: `shots` shots, `nt` steps, same grid. Returns (Gcell-steps/s,
+    seconds, threads)."""
+    import oracle
+
+    g = dict(nz=d["nz"], nx=d["nx"], npml=d["npml"], order=d["order"], nt=nt, dz=d["dz"], dx=d["dx"],
+             dt=d["dt"], src_kind=d["src_kind"], pml_R=d["pml_R"], pml_vmax=d["pml_vmax"],
+             pml_f0=d["pml_f0"], rec_iz=d["rec_iz"], rec_ix=d["rec_ix"])
+    stf = np.float64(d["stf"][:shots, :nt])
+    x0 = np.float64(d["x0"][:shots])
+    c = np.float64(d["c"])
+    obs = np.zeros((shots, len(d["rec_iz"]), nt))
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.acoustic_misfit_grad(g, c, stf, x0, obs)
+    sec = time.perf_counter() - t0
+    Nz, Nx = padded(d)
+    return shots * Nz * Nx * nt / sec / 1e9, sec, min(oracle.num_threads(), shots)
+
+
+def run_reference(args, ws, rank):
+    """The oracle, timed on the host cores, on bounded samples of the workload."""
+    if rank != 0:
+        return
+    from paper_2003_06027_gb300 import synth
+
+    d = synth.acoustic_fwi()
+    import oracle
+
+    shots = max(1, min(2, oracle.num_threads()))
+    nt = 150
+    for _ in range(args.warmup):
+        cpu_oracle_sample(d, shots, nt)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s, cores = cpu_oracle_sample(d, shots, nt)
+        vals.append(v)
+        secs.append(s)
+    value = statistics.mean(vals)
+    sample = f"{shots} shots x {nt} steps of the 265x665 (padded) 8th-order grid per step, FP64 oracle fwd+adjoint"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(d),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def workload_config(d):
+    Nz, Nx = padded(d)
+    S, nt = d["stf"].shape
+    return {"workload": d["name"] + f"-ckpt{d['ckpt_every']}", "grid_physical": [d["nz"], d["nx"]],
+            "grid_padded": [Nz, Nx], "order": d["order"], "npml": d["npml"], "shots": S, "nt": nt,
+            "receivers": int(len(d["rec_iz"])), "ckpt_every": d["ckpt_every"],
+            "cell_steps_per_step": S * Nz * Nx * nt,
+            "l2": "no explicit flush: each step streams >6 GB (checkpoints + segment slots) through HBM, "
+                  "far more than the 129 MB L2",
+            "parallelism": "shots batched on one GPU; N GPUs = N independent replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+
+    from paper_2003_06027_gb300 import fwi, synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    d = synth.acoustic_fwi()
+    kw = fwi.problem_kwargs(d)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+    c, stf, x0, iz, ix = cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
+    obs = fwi.forward(cu(d["c_true"]), stf, x0, iz, ix, **kw)
+    K = d["ckpt_every"]
+    out = {"misfit": torch.empty(1, dtype=torch.float64, device=dev), "grad": torch.empty_like(c),
+           "grad_stf": torch.empty_like(stf), "grad_x0": torch.empty_like(x0)}
+    Nz, Nx = padded(d)
+    S, nt = d["stf"].shape
+    cell_steps = S * Nz * Nx * nt
+
+    def step():
+        fwi.misfit_grad(c, stf, x0, iz, ix, obs, ckpt_every=K, out=out, **kw)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    kms = {"fwd": [], "store": [], "adj": []}
+    launches = 0
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+        t = fwi.last_timing(local)
+        kms["fwd"].append(t.fwd_step_ms)
+        kms["store"].append(t.store_step_ms)
+        kms["adj"].append(t.adj_step_ms)
+        launches += t.launches
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(ws, e0.elapsed_time(e1) / args.steps, local)
+    value = ws * cell_steps / (ms / 1e3) / 1e9
+
+    # forward only (same workload), for reference beside the gradient
+    for _ in range(2):
+        fwi.forward(c, stf, x0, iz, ix, out=obs, **kw)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    nf = max(3, args.steps // 2)
+    for _ in range(nf):
+        fwi.forward(c, stf, x0, iz, ix, out=obs, **kw)
+    f1.record()
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1) / nf
+
+    # end to end through the same API with host (pinned) buffers
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    h = [pin(d["c"]), pin(d["stf"]), pin(d["x0"]), pin(d["rec_iz"]), pin(d["rec_ix"]), obs.cpu().pin_memory()]
+    hout = {"misfit": torch.empty(1, dtype=torch.float64).pin_memory(), "grad": torch.empty_like(h[0]).pin_memory(),
+            "grad_stf": torch.empty_like(h[1]).pin_memory(), "grad_x0": torch.empty_like(h[2]).pin_memory()}
+    h2d = sum(t.numel() * t.element_size() for t in h)
+    d2h = sum(t.numel() * t.element_size() for t in hout.values())
+    fwi.misfit_grad(*h, ckpt_every=K, out=hout, **kw)
+    barrier(ws)
+    t0 = time.perf_counter()
+    ne = max(3, args.steps // 2)
+    for _ in range(ne):
+        fwi.misfit_grad(*h, ckpt_every=K, out=hout, **kw)
+    e2e_ms = max_over_ranks(ws, (time.perf_counter() - t0) * 1e3 / ne, local)
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (largest device time per step)
+    tot = {k: statistics.mean(v) * nt for k, v in kms.items()}
+    dom = max(tot, key=tot.get)
+    peak, peak_kind = load_peaks()
+    avg_ms = statistics.mean(kms[dom])
+    achieved = launch_bytes(d, dom) / (avg_ms / 1e3) / 1e9
+    kernel_names = {"fwd": "acu_fwd_step<4,record>", "store": "acu_fwd_step<4,store>", "adj": "acu_adj_step<4>"}
+    roof = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind,
+            "traffic": load_traffic("acoustic_kernels.cu") if dom == "adj" else None,
+            "algorithmic_bytes_per_launch": launch_bytes(d, dom), "avg_launch_ms": avg_ms}
+    kernels = {k: {"avg_launch_ms": statistics.mean(v), "algorithmic_GBps": launch_bytes(d, k) / (statistics.mean(v) / 1e3) / 1e9,
+                   "share_of_step": tot[k] / ms} for k, v in kms.items()}
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(d),
+           "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+           "forward": {"value": ws * cell_steps / (fwd_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": fwd_ms},
+           "e2e": {"value": ws * cell_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "clocks": clocks}
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        shots = max(1, min(8, oracle.num_threads()))
+        v, sec, cores = cpu_oracle_sample(d, shots, 150)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{shots} shots x 150 steps of the same 265x665 8th-order grid, "
+                                         f"FP64 oracle fwd+adjoint, {sec:.1f} s"}
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

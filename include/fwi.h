@@ -1,0 +1,147 @@
+/*
+ * fwi.h - C ABI of the GB300 seismic-inversion library (libfwi.so).
+ *
+ * The library implements the hot path of the seismic-inversion method of
+ * Zhu, Xu, Darve & Beroza, "A General Approach to Seismic Inversion with
+ * Automatic Differentiation": explicit time stepping of the 2D acoustic wave
+ * equation u_tt = div(c^2 grad u) + f (Implementation, Eq. acoustic) on a
+ * staggered grid with convolutional PML, receiver sampling, the L2 misfit
+ * J = 1/2 sum_k |U_k - U_k^obs|^2 (Method, after Eq. forward), and its exact
+ * gradient by the adjoint recursion lambda_k = A^T lambda_{k+1} + (U_k - U_k^obs)
+ * (Eq. adjoint-backward) with sum_k lambda_k^T (dA/dtheta) U_{k-1}
+ * (Eq. adjoint-gradient), which the paper's Theorem shows to be identical to
+ * reverse-mode automatic differentiation.
+ *
+ * Conventions shared by every call
+ *   - Arrays are row-major, x (the horizontal index) fastest. The physical
+ *     model is [nz][nx]; npml CPML cells are added OUTSIDE it on all four
+ *     sides. Positions in metres are physical coordinates: x = ix*dx,
+ *     z = iz*dz, with (0,0) the first physical cell.
+ *   - Every array pointer may point to host memory (pageable or pinned) or to
+ *     device memory of the context's device; the library detects which and
+ *     copies host data through its own device workspace. The caller keeps
+ *     ownership of all its arrays; the library never frees them.
+ *   - Calls enqueue work on the given CUDA stream (NULL = legacy default
+ *     stream) and return after the stream has finished the call's work (the
+ *     status of the numerical checks is known only then). Outputs are
+ *     overwritten, never accumulated.
+ *   - FP32 storage and arithmetic for wavefields; FP64 for the misfit and for
+ *     the reductions of the gradient over time segments and shots.
+ *   - Results are deterministic run to run (no floating-point atomics).
+ *   - No call throws; each returns a status, and fwi_last_error() gives a
+ *     message for the calling thread.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FWI_OK = 0,
+  FWI_EINVAL = 1,     /* bad argument: sizes, NULL pointer, position outside the grid */
+  FWI_ECFL = 2,       /* c_max dt sqrt(1/dx^2 + 1/dz^2) sum_k |a_k| > 1 (unstable) */
+  FWI_ENOMEM = 3,     /* device workspace could not be allocated */
+  FWI_ECUDA = 4,      /* a CUDA runtime call failed (message in fwi_last_error) */
+  FWI_EUNSTABLE = 5,  /* non-finite value in the seismograms or the misfit */
+  FWI_ETIMEOUT = 6,   /* reserved: a bounded device wait gave up */
+  FWI_ENOTIMPL = 7    /* combination not supported by this build */
+} fwi_status;
+
+enum { FWI_ACOUSTIC = 0, FWI_ELASTIC = 1 };
+enum { FWI_SRC_POINT = 0, FWI_SRC_GAUSSIAN = 1, FWI_SRC_MOMENT = 2 };
+
+typedef struct fwi_ctx fwi_ctx; /* opaque; owns only its device workspace */
+
+/* Medium and discretisation.
+ * physics  FWI_ACOUSTIC (uses vp = c only) or FWI_ELASTIC (vp, vs, rho).
+ * nz, nx   physical grid, >= 1.   dz, dx  spacing in metres, > 0.
+ * order    spatial order of the staggered first derivative: 4 or 8.
+ * npml     CPML thickness in cells, >= 0 (0 = rigid u = 0 boundary).
+ * pml_R, pml_vmax, pml_f0  CPML constants: target reflection, the velocity
+ *          that sets the damping (a fixed input, not differentiated) and the
+ *          frequency that sets alpha_max = pi f0.
+ * vp, vs, rho  [nz][nx] FP32 fields (m/s, m/s, kg/m^3); acoustic needs vp. */
+typedef struct {
+  int32_t physics;
+  int32_t nz, nx;
+  float dz, dx;
+  int32_t order;
+  int32_t npml;
+  float pml_R, pml_vmax, pml_f0;
+  const float *vp, *vs, *rho;
+} fwi_model;
+
+/* Sources, one per shot.
+ * kind  FWI_SRC_POINT: weight 1/(dx dz) on the cell nearest x0, which must be
+ *       a physical cell. FWI_SRC_GAUSSIAN: the paper's re-parameterisation
+ *       g(t)/(2 pi s^2) exp(-|x - x0|^2 / (2 s^2)), s = dx/2, over the 7 x 7
+ *       cells around the nearest cell (Earthquake Location and Source Time
+ *       Function Retrieval); the 7 x 7 support must lie in the padded grid.
+ * x0    [nshots][2] (x, z) in metres.
+ * stf   [nshots][nt] source time function g(t_n), t_n = n dt.
+ * mt    [nshots][3] moment tensor (Mxx, Mzz, Mxz) for FWI_SRC_MOMENT, else NULL. */
+typedef struct {
+  int32_t nshots;
+  int32_t kind;
+  const float *x0;
+  const float *stf;
+  const float *mt;
+} fwi_sources;
+
+/* Receivers, shared by all shots: physical cell indices iz[r], ix[r]. */
+typedef struct {
+  int32_t nrec;
+  const int32_t *iz, *ix;
+} fwi_receivers;
+
+/* Create a context bound to CUDA device `device`. The workspace is allocated
+ * on first use and grown when a larger problem arrives. */
+fwi_status fwi_create(fwi_ctx **ctx, int device);
+
+/* Free the context and its workspace (waits for its device work). */
+fwi_status fwi_destroy(fwi_ctx *ctx);
+
+/* Forward modelling (Eq. forward): seis[s][r][n] = u^{n+1} at receiver r of
+ * shot s, n = 0..nt-1, u^0 = u^{-1} = 0, source term dt^2 g(t_n) w at step n.
+ * seis: [nshots][nrec][nt] FP32. */
+fwi_status fwi_forward(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
+                       const fwi_receivers *rec, int32_t nt, float dt, float *seis,
+                       void *cuda_stream);
+
+/* Misfit and exact gradient (Eqs. adjoint-backward and adjoint-gradient).
+ * observed   [nshots][nrec][nt] FP32 observed seismograms.
+ * ckpt_every wavefield checkpoint interval K (1..nt); the reverse sweep
+ *            recomputes each K-step segment from its checkpoint.
+ * misfit     J = 1/2 sum_{s,r,n} (seis - observed)^2, one double (host or device).
+ * grad       [nz][nx] dJ/dc (acoustic), or NULL.
+ * grad_stf   [nshots][nt] dJ/dg(t_n), or NULL.
+ * grad_x0    [nshots][2] dJ/dx0 (Gaussian sources; zero for point sources), or NULL.
+ * seis_out   [nshots][nrec][nt] the predicted seismograms, or NULL. */
+fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
+                           const fwi_receivers *rec, int32_t nt, float dt,
+                           const float *observed, int32_t ckpt_every, double *misfit,
+                           float *grad, float *grad_stf, float *grad_x0, float *seis_out,
+                           void *cuda_stream);
+
+/* Timing of the last call, measured with CUDA events recorded on the call's
+ * stream. phase_ms3: [0] forward sweep (with checkpoint saves), [1] reverse
+ * sweep (recompute + adjoint + folds), [2] whole call. kernel_ms3: average
+ * duration of one launch of [0] the recording forward step, [1] the storing
+ * forward step of the recompute, [2] the adjoint step (each averaged over
+ * its back-to-back launches, so launch gaps are included; 0 if none ran).
+ * launches: number of kernels the call launched. Any pointer may be NULL. */
+fwi_status fwi_last_timing(const fwi_ctx *ctx, float *phase_ms3, float *kernel_ms3,
+                           int64_t *launches);
+
+/* Message describing the last error of the calling thread ("" if none). */
+const char *fwi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,568 @@
+// fwi_capi.cu - the C ABI of libfwi (declared in include/fwi.h): context,
+// device workspace, validation, and the orchestration of the time loops.
+//
+// fwi_forward runs the explicit recursion of Eq. forward; fwi_misfit_grad
+// adds the L2 misfit and the reverse sweep of Eqs. adjoint-backward /
+// adjoint-gradient. The reverse sweep needs U_{k-1} at every step; instead of
+// keeping all nt wavefields (the memory limit the paper's Limitations section
+// names), the forward sweep saves the full state every K steps and the
+// reverse sweep recomputes one K-step segment at a time into a slot buffer.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fwi.h"
+#include "fwi_internal.cuh"
+
+namespace fwi {
+cudaError_t launch_acu_fwd(const AcuStep& p, bool record, bool store, cudaStream_t st);
+cudaError_t launch_acu_adj(const AcuStep& p, cudaStream_t st);
+cudaError_t acu_kernels_init();
+cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st);
+cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
+                               double vmax, double f0, float* a, float* b, float* ah, float* bh,
+                               cudaStream_t st);
+cudaError_t launch_src_prep(int S, int kind, const float* x0, const Grid& g, float dx, float dz, int* box,
+                            float* w, int* status, cudaStream_t st);
+cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* start,
+                           int* list, int* status, cudaStream_t st);
+cudaError_t launch_model_check(const float* c, long long n, float coef, int* status, cudaStream_t st);
+cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
+                          int* status, cudaStream_t st);
+cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
+cudaError_t launch_adj_init(const AcuStep& p, float* lam, cudaStream_t st);
+cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st);
+cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st);
+cudaError_t launch_src_grad(const float* part, int S, int nt, double dt2, const float* stf, double inv_sig2,
+                            int kind, float* gstf, float* gx0, cudaStream_t st);
+}  // namespace fwi
+
+using namespace fwi;
+
+namespace {
+
+thread_local std::string g_err;
+
+fwi_status fail(fwi_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+constexpr int MISFIT_BLOCKS = 512;
+
+// Staggered first-derivative weights (the Taylor moment conditions
+// sum_k a_k (2k-1)^(2j-1) = delta_{j1}); exact rationals for orders 4 and 8.
+bool fd_coeffs(int order, float a[4]) {
+  for (int k = 0; k < 4; k++) a[k] = 0.f;
+  if (order == 4) {
+    a[0] = (float)(9.0 / 8.0);
+    a[1] = (float)(-1.0 / 24.0);
+    return true;
+  }
+  if (order == 8) {
+    a[0] = (float)(1225.0 / 1024.0);
+    a[1] = (float)(-245.0 / 3072.0);
+    a[2] = (float)(49.0 / 5120.0);
+    a[3] = (float)(-5.0 / 7168.0);
+    return true;
+  }
+  return false;
+}
+
+struct Plan {
+  Grid g{};
+  int S = 0, nt = 0, nrec = 0, K = 0, nseg = 0, N = 0, kind = 0;
+  bool grad = false;
+  int tablen = 0;
+  // base
+  float *m = nullptr, *tab = nullptr, *c = nullptr, *stf = nullptr, *x0 = nullptr, *src_w = nullptr;
+  int *src_box = nullptr, *rec_in = nullptr, *rec_cell = nullptr, *tstart = nullptr, *tlist = nullptr;
+  float *u[2] = {}, *psix[2] = {}, *psiz[2] = {}, *zetx = nullptr, *zetz = nullptr, *seis = nullptr;
+  int* status = nullptr;
+  // gradient
+  float *res = nullptr, *ckpt = nullptr, *slot = nullptr, *lam[2] = {}, *zx[2] = {}, *zz[2] = {};
+  float *px[2] = {}, *pz[2] = {}, *gpart = nullptr, *src_part = nullptr, *grad_c = nullptr;
+  float *gstf = nullptr, *gx0 = nullptr;
+  double *G = nullptr, *Jpart = nullptr, *J = nullptr;
+  size_t bytes = 0;
+  size_t zero_lo = 0, zero_hi = 0;  // byte range re-zeroed on every call
+};
+
+// Lay the plan out over an arena starting at `base` (nullptr: size only).
+void layout(Plan& P, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = (off + 255) & ~size_t(255);
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t field = (size_t)P.S * (size_t)P.g.slice * sizeof(float);
+  const int ntiles = P.g.ntx * P.g.ntz;
+  P.status = (int*)take(64);
+  P.m = (float*)take((size_t)P.g.slice * 4);
+  P.tab = (float*)take((size_t)8 * P.tablen * 4);
+  P.c = (float*)take((size_t)P.g.nz * P.g.nx * 4);
+  P.stf = (float*)take((size_t)P.S * P.nt * 4);
+  P.x0 = (float*)take((size_t)P.S * 2 * 4);
+  P.src_w = (float*)take((size_t)P.S * SRC_W * SRC_W * 4);
+  P.src_box = (int*)take((size_t)P.S * 2 * 4);
+  P.rec_in = (int*)take((size_t)(P.nrec + 1) * 2 * 4);
+  P.rec_cell = (int*)take((size_t)(P.nrec + 1) * 2 * 4);
+  P.tstart = (int*)take((size_t)(ntiles + 1) * 4);
+  P.tlist = (int*)take((size_t)(P.nrec + 1) * 4);
+  P.seis = (float*)take((size_t)P.S * P.nrec * P.nt * 4 + 4);
+  // fields zeroed on every call (initial conditions)
+  off = (off + 255) & ~size_t(255);
+  P.zero_lo = off;
+  for (int k = 0; k < 2; k++) P.u[k] = (float*)take(field);
+  for (int k = 0; k < 2; k++) P.psix[k] = (float*)take(field);
+  for (int k = 0; k < 2; k++) P.psiz[k] = (float*)take(field);
+  P.zetx = (float*)take(field);
+  P.zetz = (float*)take(field);
+  if (P.grad) {
+    for (int k = 0; k < 2; k++) P.lam[k] = (float*)take(field);
+    for (int k = 0; k < 2; k++) P.zx[k] = (float*)take(field);
+    for (int k = 0; k < 2; k++) P.zz[k] = (float*)take(field);
+    for (int k = 0; k < 2; k++) P.px[k] = (float*)take(field);
+    for (int k = 0; k < 2; k++) P.pz[k] = (float*)take(field);
+    P.gpart = (float*)take(field);
+    P.G = (double*)take((size_t)P.g.slice * 8);
+    P.src_part = (float*)take((size_t)P.S * P.nt * SRC_SLOTS * 3 * 4);
+  }
+  off = (off + 255) & ~size_t(255);
+  P.zero_hi = off;
+  if (P.grad) {
+    P.res = (float*)take((size_t)P.S * P.nrec * P.nt * 4 + 4);
+    P.Jpart = (double*)take((size_t)MISFIT_BLOCKS * 8);
+    P.J = (double*)take(8);
+    P.grad_c = (float*)take((size_t)P.g.nz * P.g.nx * 4);
+    P.gstf = (float*)take((size_t)P.S * P.nt * 4);
+    P.gx0 = (float*)take((size_t)P.S * 2 * 4);
+    P.ckpt = (float*)take(field * 6 * (size_t)P.nseg);
+    P.slot = (float*)take(field * 3 * (size_t)P.K);
+  }
+  P.bytes = (off + 255) & ~size_t(255);
+}
+
+}  // namespace
+
+struct fwi_ctx {
+  int device = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  std::string layout_key;  // layout of the arena's current contents
+  int* h_status = nullptr;  // pinned
+  cudaEvent_t ev[4] = {};
+  std::vector<cudaEvent_t> seg_ev;
+  float phase_ms[3] = {0, 0, 0};
+  float kernel_ms[3] = {0, 0, 0};
+  int64_t launches = 0;
+};
+
+namespace {
+
+// LK: a checked kernel launch, counted (n kernels per launcher call)
+#define LK(n, call)      \
+  do {                   \
+    CK(call);            \
+    ctx->launches += (n); \
+  } while (0)
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(FWI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+fwi_status validate(const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int nt, float dt) {
+  if (!M || !Sv || !R) return fail(FWI_EINVAL, "model, sources and receivers must not be NULL");
+  if (M->physics != FWI_ACOUSTIC) return fail(FWI_ENOTIMPL, "only FWI_ACOUSTIC is implemented in this call");
+  if (M->nz < 1 || M->nx < 1) return fail(FWI_EINVAL, "nz and nx must be >= 1");
+  if (!(M->dz > 0.f) || !(M->dx > 0.f)) return fail(FWI_EINVAL, "dz and dx must be > 0");
+  if (M->order != 4 && M->order != 8) return fail(FWI_EINVAL, "order must be 4 or 8");
+  if (M->npml < 0) return fail(FWI_EINVAL, "npml must be >= 0");
+  if (M->npml > 0 && (!(M->pml_R > 0.f && M->pml_R < 1.f) || !(M->pml_vmax > 0.f) || !(M->pml_f0 >= 0.f)))
+    return fail(FWI_EINVAL, "CPML needs 0 < pml_R < 1, pml_vmax > 0, pml_f0 >= 0");
+  if (!M->vp) return fail(FWI_EINVAL, "vp must not be NULL");
+  if (Sv->nshots < 1) return fail(FWI_EINVAL, "nshots must be >= 1");
+  if (Sv->kind != FWI_SRC_POINT && Sv->kind != FWI_SRC_GAUSSIAN)
+    return fail(FWI_EINVAL, "acoustic sources are FWI_SRC_POINT or FWI_SRC_GAUSSIAN");
+  if (!Sv->x0 || !Sv->stf) return fail(FWI_EINVAL, "x0 and stf must not be NULL");
+  if (R->nrec < 0 || (R->nrec > 0 && (!R->iz || !R->ix))) return fail(FWI_EINVAL, "bad receiver arrays");
+  if (nt < 1) return fail(FWI_EINVAL, "nt must be >= 1");
+  if (!(dt > 0.f)) return fail(FWI_EINVAL, "dt must be > 0");
+  const long long Nz = (long long)M->nz + 2LL * M->npml, Nx = (long long)M->nx + 2LL * M->npml;
+  if (Nz > (1 << 20) || Nx > (1 << 20) || Nz * Nx > (1LL << 31)) return fail(FWI_EINVAL, "grid too large");
+  return FWI_OK;
+}
+
+void make_plan(Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int nt, int K,
+               bool grad) {
+  Grid& g = P.g;
+  g.nz = M->nz;
+  g.nx = M->nx;
+  g.npml = M->npml;
+  g.Nz = M->nz + 2 * M->npml;
+  g.Nx = M->nx + 2 * M->npml;
+  g.ntx = (g.Nx + TILE_X - 1) / TILE_X;
+  g.ntz = (g.Nz + TILE_Z - 1) / TILE_Z;
+  g.pitch = g.ntx * TILE_X + 2 * APRON;
+  g.rows = g.ntz * TILE_Z + 2 * APRON;
+  g.slice = (long long)g.rows * g.pitch;
+  g.off0 = (long long)APRON * g.pitch + APRON;
+  P.S = Sv->nshots;
+  P.nt = nt;
+  P.nrec = R->nrec;
+  P.N = M->order / 2;
+  P.kind = Sv->kind;
+  P.grad = grad;
+  P.K = grad ? K : 0;
+  P.nseg = grad ? (nt + K - 1) / K : 0;
+  P.tablen = std::max(g.ntx * TILE_X, g.ntz * TILE_Z) + 2 * APRON + 2 * TAB_OFF;
+}
+
+std::string plan_key(const Plan& P) {
+  char b[256];
+  snprintf(b, sizeof b, "%d %d %d %d %lld %d %d %d %d %d %d", P.g.Nz, P.g.Nx, P.g.pitch, P.g.rows, P.g.slice,
+           P.S, P.nt, P.nrec, P.K, (int)P.grad, P.tablen);
+  return b;
+}
+
+fwi_status ensure_arena(fwi_ctx* ctx, Plan& P, cudaStream_t st) {
+  layout(P, nullptr);
+  const std::string key = plan_key(P);
+  if (P.bytes > ctx->arena_bytes) {
+    if (ctx->arena) {
+      CK(cudaStreamSynchronize(st));
+      CK(cudaFree(ctx->arena));
+      ctx->arena = nullptr;
+      ctx->arena_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, P.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FWI_ENOMEM, "cannot allocate " + std::to_string(P.bytes) + " bytes of workspace: " +
+                                  cudaGetErrorString(e));
+    }
+    ctx->arena = (char*)p;
+    ctx->arena_bytes = P.bytes;
+    ctx->layout_key.clear();
+  }
+  layout(P, ctx->arena);
+  if (ctx->layout_key != key) {
+    // new layout: every apron and every never-written cell must read as zero
+    CK(cudaMemsetAsync(ctx->arena, 0, P.bytes, st));
+    ctx->layout_key = key;
+  } else {
+    CK(cudaMemsetAsync(ctx->arena + P.zero_lo, 0, P.zero_hi - P.zero_lo, st));
+    CK(cudaMemsetAsync(P.status, 0, 64, st));
+  }
+  return FWI_OK;
+}
+
+// Copy inputs into the workspace and build m, CPML tables, source weights,
+// receiver lists; queue the model checks.
+fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                   float dt, cudaStream_t st, AcuStep& p) {
+  const Grid& g = P.g;
+  CK(cudaMemcpyAsync(P.c, M->vp, (size_t)g.nz * g.nx * 4, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(P.stf, Sv->stf, (size_t)P.S * P.nt * 4, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(P.x0, Sv->x0, (size_t)P.S * 2 * 4, cudaMemcpyDefault, st));
+  if (P.nrec > 0) {
+    CK(cudaMemcpyAsync(P.rec_in, R->iz, (size_t)P.nrec * 4, cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(P.rec_in + P.nrec, R->ix, (size_t)P.nrec * 4, cudaMemcpyDefault, st));
+  }
+  float a[4];
+  fd_coeffs(M->order, a);
+  float sa = 0.f;
+  for (int k = 0; k < 4; k++) sa += fabsf(a[k]);
+  const float coef = dt * sqrtf(1.f / (M->dx * M->dx) + 1.f / (M->dz * M->dz)) * sa;
+  LK(1, launch_model_check(P.c, (long long)g.nz * g.nx, coef, P.status, st));
+  LK(1, launch_pad_model(P.c, g, P.m, st));
+  const int L = P.tablen;
+  float* T = P.tab;
+  LK(1, launch_cpml_tables(g.nx, g.npml, g.Nx, L, M->dx, dt, M->pml_R, M->pml_vmax, M->pml_f0, T, T + L, T + 2 * L,
+                        T + 3 * L, st));
+  LK(1, launch_cpml_tables(g.nz, g.npml, g.Nz, L, M->dz, dt, M->pml_R, M->pml_vmax, M->pml_f0, T + 4 * L, T + 5 * L,
+                        T + 6 * L, T + 7 * L, st));
+  LK(1, launch_src_prep(P.S, P.kind, P.x0, g, M->dx, M->dz, P.src_box, P.src_w, P.status, st));
+  LK(1, launch_rec_csr(P.nrec, P.rec_in, P.rec_in + P.nrec, g, P.rec_cell, P.tstart, P.tlist, P.status, st));
+
+  memset(&p, 0, sizeof p);
+  p.g = g;
+  p.S = P.S;
+  p.N = P.N;
+  p.nt = P.nt;
+  p.nrec = P.nrec;
+  p.inv_dx = 1.f / M->dx;
+  p.inv_dz = 1.f / M->dz;
+  p.dt2 = dt * dt;
+  for (int k = 0; k < 4; k++) p.a[k] = a[k];
+  p.m = P.m;
+  p.ax = T; p.bx = T + L; p.axh = T + 2 * L; p.bxh = T + 3 * L;
+  p.az = T + 4 * L; p.bz = T + 5 * L; p.azh = T + 6 * L; p.bzh = T + 7 * L;
+  p.zetx = P.zetx;
+  p.zetz = P.zetz;
+  p.src_box = P.src_box;
+  p.src_w = P.src_w;
+  p.src_n = P.kind == FWI_SRC_GAUSSIAN ? SRC_W : 1;
+  p.stf = P.stf;
+  p.tile_rec_start = P.tstart;
+  p.tile_rec = P.tlist;
+  p.rec_cell = P.rec_cell;
+  p.seis = P.seis;
+  p.x0 = P.x0;
+  p.dx = M->dx;
+  p.dz = M->dz;
+  (void)ctx;
+  return FWI_OK;
+}
+
+void set_fwd_state(const Plan& P, AcuStep& p, int n) {
+  p.n = n;
+  p.u_cur = P.u[n & 1];
+  p.u_prev = P.u[(n + 1) & 1];
+  p.psix_in = P.psix[n & 1];
+  p.psix_out = P.psix[(n + 1) & 1];
+  p.psiz_in = P.psiz[n & 1];
+  p.psiz_out = P.psiz[(n + 1) & 1];
+}
+
+fwi_status finish_status(fwi_ctx* ctx, const Plan& P, cudaStream_t st) {
+  CK(cudaMemcpyAsync(ctx->h_status, P.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int s = *ctx->h_status;
+  if (s & 16) return fail(FWI_EINVAL, "velocity model must be finite and > 0");
+  if (s & 2) return fail(FWI_EINVAL, "a receiver lies outside the physical grid");
+  if (s & 4) return fail(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
+  if (s & 1) return fail(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
+  if (s & 8) return fail(FWI_EUNSTABLE, "non-finite value in the seismograms or the misfit");
+  return FWI_OK;
+}
+
+void ensure_events(fwi_ctx* ctx, size_t nseg) {
+  for (auto& e : ctx->ev)
+    if (!e) cudaEventCreate(&e);
+  while (ctx->seg_ev.size() < 4 * nseg) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ctx->seg_ev.push_back(e);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_create(fwi_ctx** out, int device) {
+  if (!out) return fail(FWI_EINVAL, "ctx must not be NULL");
+  *out = nullptr;
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(FWI_EINVAL, "no such CUDA device");
+  CK(cudaSetDevice(device));
+  CK(acu_kernels_init());
+  fwi_ctx* c = new fwi_ctx();
+  c->device = device;
+  if (cudaMallocHost((void**)&c->h_status, 64) != cudaSuccess) {
+    delete c;
+    return fail(FWI_ENOMEM, "cannot allocate pinned status word");
+  }
+  *out = c;
+  g_err.clear();
+  return FWI_OK;
+}
+
+fwi_status fwi_destroy(fwi_ctx* ctx) {
+  if (!ctx) return FWI_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->seg_ev) cudaEventDestroy(e);
+  delete ctx;
+  return FWI_OK;
+}
+
+const char* fwi_last_error(void) { return g_err.c_str(); }
+
+fwi_status fwi_last_timing(const fwi_ctx* ctx, float* phase_ms3, float* kernel_ms3, int64_t* launches) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  for (int k = 0; k < 3; k++) {
+    if (phase_ms3) phase_ms3[k] = ctx->phase_ms[k];
+    if (kernel_ms3) kernel_ms3[k] = ctx->kernel_ms[k];
+  }
+  if (launches) *launches = ctx->launches;
+  return FWI_OK;
+}
+
+fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                       int32_t nt, float dt, float* seis, void* stream) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  fwi_status v = validate(M, Sv, R, nt, dt);
+  if (v != FWI_OK) return v;
+  if (!seis && R->nrec > 0) return fail(FWI_EINVAL, "seis must not be NULL");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan P;
+  make_plan(P, M, Sv, R, nt, 0, false);
+  v = ensure_arena(ctx, P, st);
+  if (v != FWI_OK) return v;
+  AcuStep p;
+  ctx->launches = 0;
+  v = prepare(ctx, P, M, Sv, R, dt, st, p);
+  if (v != FWI_OK) return v;
+  ensure_events(ctx, 0);
+  CK(cudaEventRecord(ctx->ev[0], st));
+  for (int n = 0; n < nt; n++) {
+    set_fwd_state(P, p, n);
+    LK(1, launch_acu_fwd(p, true, false, st));
+  }
+  CK(cudaEventRecord(ctx->ev[1], st));
+  const long long ns = (long long)P.S * P.nrec * nt;
+  if (ns > 0) {
+    LK(1, launch_finite_check(P.seis, ns, P.status, st));
+    CK(cudaMemcpyAsync(seis, P.seis, (size_t)ns * 4, cudaMemcpyDefault, st));
+  }
+  CK(cudaEventRecord(ctx->ev[3], st));
+  v = finish_status(ctx, P, st);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
+  ctx->phase_ms[0] = t;
+  ctx->phase_ms[1] = 0.f;
+  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3]);
+  ctx->phase_ms[2] = t;
+  ctx->kernel_ms[0] = ctx->phase_ms[0] / nt;
+  ctx->kernel_ms[1] = 0.f;
+  ctx->kernel_ms[2] = 0.f;
+  if (v == FWI_OK) g_err.clear();
+  return v;
+}
+
+fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                           int32_t nt, float dt, const float* observed, int32_t K, double* misfit, float* grad,
+                           float* grad_stf, float* grad_x0, float* seis_out, void* stream) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  fwi_status v = validate(M, Sv, R, nt, dt);
+  if (v != FWI_OK) return v;
+  if (!observed && R->nrec > 0) return fail(FWI_EINVAL, "observed must not be NULL");
+  if (!misfit) return fail(FWI_EINVAL, "misfit must not be NULL");
+  if (K < 1 || K > nt) return fail(FWI_EINVAL, "ckpt_every must be in [1, nt]");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan P;
+  make_plan(P, M, Sv, R, nt, K, true);
+  v = ensure_arena(ctx, P, st);
+  if (v != FWI_OK) return v;
+  AcuStep p;
+  ctx->launches = 0;
+  v = prepare(ctx, P, M, Sv, R, dt, st, p);
+  if (v != FWI_OK) return v;
+  const long long ns = (long long)P.S * P.nrec * nt;
+  if (ns > 0) CK(cudaMemcpyAsync(P.res, observed, (size_t)ns * 4, cudaMemcpyDefault, st));
+  const size_t field = (size_t)P.S * P.g.slice;
+  ensure_events(ctx, P.nseg);
+
+  // forward sweep with a full-state checkpoint at the start of every segment
+  CK(cudaEventRecord(ctx->ev[0], st));
+  for (int n = 0; n < nt; n++) {
+    if (n % K == 0) {
+      float* ck = P.ckpt + (size_t)(n / K) * 6 * field;
+      const float* src[6] = {P.u[n & 1], P.u[(n + 1) & 1], P.psix[n & 1], P.psiz[n & 1], P.zetx, P.zetz};
+      for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(ck + f * field, src[f], field * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    set_fwd_state(P, p, n);
+    LK(1, launch_acu_fwd(p, true, false, st));
+  }
+  CK(cudaEventRecord(ctx->ev[1], st));
+  if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
+  else CK(cudaMemsetAsync(P.J, 0, 8, st));
+
+  // reverse sweep, segment by segment
+  p.res = P.res;
+  p.gpart = P.gpart;
+  p.src_part = P.src_part;
+  LK(1, launch_adj_init(p, P.lam[nt & 1], st));
+  for (int seg = P.nseg - 1; seg >= 0; seg--) {
+    const int n0 = seg * K, n1 = std::min(nt, n0 + K);
+    const float* ck = P.ckpt + (size_t)seg * 6 * field;
+    float* dst[6] = {P.u[n0 & 1], P.u[(n0 + 1) & 1], P.psix[n0 & 1], P.psiz[n0 & 1], P.zetx, P.zetz};
+    for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(dst[f], ck + f * field, field * 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
+    for (int n = n0; n < n1; n++) {
+      set_fwd_state(P, p, n);
+      float* sl = P.slot + (size_t)(n - n0) * 3 * field;
+      p.slot_u = sl;
+      p.slot_psix = sl + field;
+      p.slot_psiz = sl + 2 * field;
+      LK(1, launch_acu_fwd(p, false, true, st));
+    }
+    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
+    for (int n = n1 - 1; n >= n0; n--) {
+      p.n = n;
+      float* sl = P.slot + (size_t)(n - n0) * 3 * field;
+      p.slot_u = sl;
+      p.slot_psix = sl + field;
+      p.slot_psiz = sl + 2 * field;
+      p.l_cur = P.lam[(n + 1) & 1];
+      p.l_prev = P.lam[n & 1];
+      p.zx_in = P.zx[(n + 1) & 1];
+      p.zx_out = P.zx[n & 1];
+      p.zz_in = P.zz[(n + 1) & 1];
+      p.zz_out = P.zz[n & 1];
+      p.px_in = P.px[(n + 1) & 1];
+      p.px_out = P.px[n & 1];
+      p.pz_in = P.pz[(n + 1) & 1];
+      p.pz_out = P.pz[n & 1];
+      LK(1, launch_acu_adj(p, st));
+    }
+    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
+    LK(1, launch_fold(P.gpart, P.S, P.g.slice, P.G, st));
+  }
+  CK(cudaEventRecord(ctx->ev[2], st));
+  if (grad) {
+    LK(1, launch_grad_c(P.G, P.g, P.c, P.grad_c, st));
+    CK(cudaMemcpyAsync(grad, P.grad_c, (size_t)P.g.nz * P.g.nx * 4, cudaMemcpyDefault, st));
+  }
+  if (grad_stf || grad_x0) {
+    LK(1, launch_src_grad(P.src_part, P.S, nt, (double)dt * dt, P.stf, 1.0 / (0.25 * (double)M->dx * M->dx), P.kind,
+                       P.gstf, P.gx0, st));
+    if (grad_stf) CK(cudaMemcpyAsync(grad_stf, P.gstf, (size_t)P.S * nt * 4, cudaMemcpyDefault, st));
+    if (grad_x0) CK(cudaMemcpyAsync(grad_x0, P.gx0, (size_t)P.S * 2 * 4, cudaMemcpyDefault, st));
+  }
+  if (seis_out && ns > 0) CK(cudaMemcpyAsync(seis_out, P.seis, (size_t)ns * 4, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(misfit, P.J, 8, cudaMemcpyDefault, st));
+  CK(cudaEventRecord(ctx->ev[3], st));
+  v = finish_status(ctx, P, st);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
+  ctx->phase_ms[0] = t;
+  cudaEventElapsedTime(&t, ctx->ev[1], ctx->ev[2]);
+  ctx->phase_ms[1] = t;
+  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3]);
+  ctx->phase_ms[2] = t;
+  ctx->kernel_ms[0] = ctx->phase_ms[0] / nt;
+  float rec = 0.f, adj = 0.f;
+  for (int seg = 0; seg < P.nseg; seg++) {
+    float ta = 0.f;
+    cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 0], ctx->seg_ev[4 * seg + 1]);
+    rec += ta;
+    cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 1], ctx->seg_ev[4 * seg + 2]);
+    adj += ta;
+  }
+  ctx->kernel_ms[1] = rec / nt;
+  ctx->kernel_ms[2] = adj / nt;
+  if (v == FWI_OK) g_err.clear();
+  return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,381 @@
+// prep_kernels.cu - parameter preparation, source/receiver set-up, misfit and
+// gradient reductions of the acoustic path (sm_103a).
+//
+// Steps served: padded model and CPML tables (the coefficient matrix A(theta)
+// of Eq. forward), source weights (point source or the Gaussian
+// re-parameterisation of the Earthquake Location section), receiver lookup,
+// the L2 misfit (Method, J = 1/2 sum |U_k - U_k^obs|^2) in FP64, and the FP64
+// folds of the gradient of Eq. adjoint-gradient over time segments and shots.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fwi_internal.cuh"
+
+namespace fwi {
+
+enum : int { ST_CFL = 1, ST_BADREC = 2, ST_BADSRC = 4, ST_NONFINITE = 8, ST_BADMODEL = 16 };
+
+// m = c^2 on the padded grid with the CPML filled by edge replication; every
+// allocated cell is written (zero outside the padded grid).
+__global__ void k_pad_model_sq(const float* __restrict__ c, Grid g, float* __restrict__ m) {
+  const long long total = (long long)g.rows * g.pitch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / g.pitch), col = (int)(idx - (long long)r * g.pitch);
+    const int i = r - APRON, j = col - APRON;
+    float v = 0.f;
+    if (i >= 0 && i < g.Nz && j >= 0 && j < g.Nx) {
+      const int ci = min(max(i - g.npml, 0), g.nz - 1), cj = min(max(j - g.npml, 0), g.nx - 1);
+      const float cc = c[(long long)ci * g.nx + cj];
+      v = cc * cc;
+    }
+    m[idx] = v;
+  }
+}
+
+// CPML coefficients along one axis (Komatitsch & Martin 2007, cited in the
+// paper's Implementation section): kappa = 1, d(l) = d0 (l/L)^2,
+// d0 = -3 vmax ln R / (2 L), alpha = pi f0 (1 - l/L), b = exp(-(d + alpha) dt),
+// a = d (b - 1) / (d + alpha); l = distance into the layer. Entries outside
+// the padded axis (and half points past its last node) are a = 0, b = 1.
+__global__ void k_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
+                              double vmax, double f0, float* a, float* b, float* ah, float* bh) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= len) return;
+  const int idx = k - TAB_OFF;
+  for (int half = 0; half < 2; half++) {
+    float av = 0.f, bv = 1.f;
+    const bool inside = half ? (idx >= 0 && idx < Npad - 1) : (idx >= 0 && idx < Npad);
+    if (inside && npml > 0) {
+      const double x = idx + (half ? 0.5 : 0.0);
+      double l = 0.0;
+      if (npml - x > l) l = npml - x;
+      if (x - (npml + n_phys - 1) > l) l = x - (npml + n_phys - 1);
+      l *= h;
+      if (l > 0.0) {
+        const double L = npml * h;
+        const double d0 = -3.0 * vmax * log(R) / (2.0 * L);
+        const double d = d0 * (l / L) * (l / L);
+        const double al = M_PI * f0 * (1.0 - l / L);
+        const double bb = exp(-(d + al) * dt);
+        bv = (float)bb;
+        av = (float)(d * (bb - 1.0) / (d + al));
+      }
+    }
+    if (half) {
+      ah[k] = av;
+      bh[k] = bv;
+    } else {
+      a[k] = av;
+      b[k] = bv;
+    }
+  }
+}
+
+// Per-shot source box and weights. Point source: 1/(dx dz) on the nearest
+// physical cell. Gaussian: g/(2 pi s^2) exp(-|x - x0|^2/(2 s^2)), s = dx/2, on
+// the 7 x 7 cells around the nearest cell.
+__global__ void k_src_prep(int S, int kind, const float* __restrict__ x0, Grid g, float dx, float dz,
+                           int* box, float* w, int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const double xr = x0[2 * s], zr = x0[2 * s + 1];
+  const int jc = (int)llround(xr / (double)dx) + g.npml;
+  const int ic = (int)llround(zr / (double)dz) + g.npml;
+  float* ws = w + s * SRC_W * SRC_W;
+  for (int q = 0; q < SRC_W * SRC_W; q++) ws[q] = 0.f;
+  bool ok;
+  if (kind == 0) {
+    ok = isfinite(xr) && isfinite(zr) && ic >= g.npml && ic < g.npml + g.nz && jc >= g.npml &&
+         jc < g.npml + g.nx;
+    if (ok) {
+      box[2 * s] = ic;
+      box[2 * s + 1] = jc;
+      ws[0] = (float)(1.0 / ((double)dx * (double)dz));
+    }
+  } else {
+    ok = isfinite(xr) && isfinite(zr) && ic - 3 >= 0 && ic + 3 < g.Nz && jc - 3 >= 0 && jc + 3 < g.Nx;
+    if (ok) {
+      box[2 * s] = ic - 3;
+      box[2 * s + 1] = jc - 3;
+      const double sg = 0.5 * (double)dx;
+      for (int di = 0; di < SRC_W; di++)
+        for (int dj = 0; dj < SRC_W; dj++) {
+          const double xi = (double)(jc - 3 + dj - g.npml) * dx - xr;
+          const double zi = (double)(ic - 3 + di - g.npml) * dz - zr;
+          ws[di * SRC_W + dj] = (float)(exp(-(xi * xi + zi * zi) / (2.0 * sg * sg)) / (2.0 * M_PI * sg * sg));
+        }
+    }
+  }
+  if (!ok) {
+    box[2 * s] = -1;
+    box[2 * s + 1] = -1;
+    atomicOr(status, ST_BADSRC);
+  }
+}
+
+// Receiver cells and per-tile receiver lists (one block). Receivers outside
+// the physical grid are flagged and never touched by the step kernels.
+__global__ void k_rec_csr(int nrec, const int* __restrict__ iz, const int* __restrict__ ix, Grid g,
+                          int* rec_cell, int* start, int* list, int* status) {
+  const int ntiles = g.ntx * g.ntz;
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+    const int i = iz[r], j = ix[r];
+    if (i >= 0 && i < g.nz && j >= 0 && j < g.nx) {
+      rec_cell[2 * r] = i + g.npml;
+      rec_cell[2 * r + 1] = j + g.npml;
+    } else {
+      rec_cell[2 * r] = -1;
+      rec_cell[2 * r + 1] = -1;
+      atomicOr(status, ST_BADREC);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    int cnt = 0;
+    for (int r = 0; r < nrec; r++) {
+      const int ri = rec_cell[2 * r], rj = rec_cell[2 * r + 1];
+      if (ri >= 0 && (ri / TILE_Z) * g.ntx + rj / TILE_X == t) cnt++;
+    }
+    start[t + 1] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    start[0] = 0;
+    for (int t = 0; t < ntiles; t++) start[t + 1] += start[t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    int pos = start[t];
+    for (int r = 0; r < nrec; r++) {
+      const int ri = rec_cell[2 * r], rj = rec_cell[2 * r + 1];
+      if (ri >= 0 && (ri / TILE_Z) * g.ntx + rj / TILE_X == t) list[pos++] = r;
+    }
+  }
+}
+
+// CFL: c_max dt sqrt(1/dx^2 + 1/dz^2) sum|a_k| <= 1, and c finite and > 0.
+__global__ void k_model_check(const float* __restrict__ c, long long n, float coef, int* status) {
+  __shared__ float smax[1024 / 32];
+  __shared__ int sbad;
+  if (threadIdx.x == 0) sbad = 0;
+  __syncthreads();
+  float mx = 0.f;
+  int bad = 0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = c[i];
+    if (!(v > 0.f) || !isfinite(v)) bad = 1;
+    else mx = fmaxf(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+  if (bad) atomicOr(&sbad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, smax[w]);
+    if (sbad) atomicOr(status, ST_BADMODEL);
+    else if (m * coef > 1.f) atomicOr(status, ST_CFL);
+  }
+}
+
+// Residual r = d - d_obs (in place over the observed copy) and per-block
+// FP64 partial sums of r^2 (fixed reduction tree: deterministic).
+__global__ void k_misfit(const float* __restrict__ seis, float* res, long long n, double* part) {
+  __shared__ double sred[256 / 32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float r = seis[i] - res[i];
+    res[i] = r;
+    acc += (double)r * (double)r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sred[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_misfit_final(const double* part, int nb, double* J, int* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; b++) s += part[b];
+  s *= 0.5;
+  *J = s;
+  if (!isfinite(s)) atomicOr(status, ST_NONFINITE);
+}
+
+__global__ void k_finite_check(const float* __restrict__ a, long long n, int* status) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(a[i])) bad = 1;
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
+}
+
+// Adjoint initial condition: lambda_{nt} = residual of the last sample at the
+// receivers (in receiver order), and its source-parameter partial (index nt-1).
+__global__ void k_adj_init(AcuStep p, float* lam) {
+  const int s = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  const long long sh = (long long)s * p.g.slice + p.g.off0;
+  for (int r = 0; r < p.nrec; r++) {
+    const int ri = p.rec_cell[2 * r], rj = p.rec_cell[2 * r + 1];
+    if (ri < 0) continue;
+    lam[sh + (long long)ri * p.g.pitch + rj] += p.res[((long long)s * p.nrec + r) * p.nt + p.nt - 1];
+  }
+  if (p.src_part == nullptr) return;
+  const int i0 = p.src_box[2 * s], j0 = p.src_box[2 * s + 1], nb = p.src_n;
+  float acc[3] = {0.f, 0.f, 0.f};
+  if (i0 >= 0) {
+    const float xs = p.x0[2 * s], zs = p.x0[2 * s + 1];
+    for (int di = 0; di < nb; di++)
+      for (int dj = 0; dj < nb; dj++) {
+        const float l = lam[sh + (long long)(i0 + di) * p.g.pitch + j0 + dj];
+        const float wl = p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj] * l;
+        acc[0] += wl;
+        acc[1] += wl * ((float)(j0 + dj - p.g.npml) * p.dx - xs);
+        acc[2] += wl * ((float)(i0 + di - p.g.npml) * p.dz - zs);
+      }
+  }
+  float* dst = p.src_part + ((long long)s * p.nt + (p.nt - 1)) * SRC_SLOTS * 3;
+  for (int q = 0; q < SRC_SLOTS * 3; q++) dst[q] = 0.f;
+  dst[0] = acc[0];
+  dst[1] = acc[1];
+  dst[2] = acc[2];
+}
+
+// Segment fold: G (FP64, per padded cell) += sum over shots of the FP32
+// segment partials, which are reset for the next segment.
+__global__ void k_fold(float* gpart, int S, long long slice, double* G) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < slice;
+       i += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < S; s++) {
+      acc += (double)gpart[(long long)s * slice + i];
+      gpart[(long long)s * slice + i] = 0.f;
+    }
+    G[i] += acc;
+  }
+}
+
+// dJ/dc = 2 c dJ/dm, where dJ/dm of a physical cell also collects the CPML
+// cells that replicate it (transpose of the edge padding).
+__global__ void k_grad_c(const double* __restrict__ G, Grid g, const float* __restrict__ c,
+                         float* grad) {
+  const long long n = (long long)g.nz * g.nx;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int iz = (int)(idx / g.nx), ix = (int)(idx - (long long)iz * g.nx);
+    const int i_lo = iz == 0 ? 0 : iz + g.npml;
+    const int i_hi = iz == g.nz - 1 ? g.Nz - 1 : iz + g.npml;
+    const int j_lo = ix == 0 ? 0 : ix + g.npml;
+    const int j_hi = ix == g.nx - 1 ? g.Nx - 1 : ix + g.npml;
+    double acc = 0.0;
+    for (int i = i_lo; i <= i_hi; i++)
+      for (int j = j_lo; j <= j_hi; j++) acc += G[g.off0 + (long long)i * g.pitch + j];
+    grad[idx] = (float)(2.0 * (double)c[idx] * acc);
+  }
+}
+
+// dJ/dg(t_n) = dt^2 sum_i w_i lambda_{n+1}(i);  dJ/dx0 = sum_n g(t_n) dt^2
+// sum_i lambda_{n+1}(i) w_i (x_i - x0) / s^2 (Gaussian sources only).
+__global__ void k_src_grad(const float* __restrict__ part, int S, int nt, double dt2,
+                           const float* __restrict__ stf, double inv_sig2, int kind, float* gstf,
+                           float* gx0) {
+  __shared__ double sred[256 / 32][2];
+  const int s = blockIdx.x;
+  double ax = 0.0, az = 0.0;
+  for (int n = threadIdx.x; n < nt; n += blockDim.x) {
+    const float* q = part + ((long long)s * nt + n) * SRC_SLOTS * 3;
+    double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+    for (int k = 0; k < SRC_SLOTS; k++) {
+      w0 += q[3 * k];
+      w1 += q[3 * k + 1];
+      w2 += q[3 * k + 2];
+    }
+    if (gstf) gstf[(long long)s * nt + n] = (float)(dt2 * w0);
+    const double g = stf[(long long)s * nt + n];
+    ax += g * dt2 * w1 * inv_sig2;
+    az += g * dt2 * w2 * inv_sig2;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sred[threadIdx.x >> 5][0] = ax;
+    sred[threadIdx.x >> 5][1] = az;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && gx0) {
+    double sx = 0.0, sz = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      sx += sred[w][0];
+      sz += sred[w][1];
+    }
+    gx0[2 * s] = kind == 1 ? (float)sx : 0.f;
+    gx0[2 * s + 1] = kind == 1 ? (float)sz : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st) {
+  k_pad_model_sq<<<304, 256, 0, st>>>(c, g, m);
+  return cudaGetLastError();
+}
+cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
+                               double vmax, double f0, float* a, float* b, float* ah, float* bh,
+                               cudaStream_t st) {
+  k_cpml_tables<<<(len + 255) / 256, 256, 0, st>>>(n_phys, npml, Npad, len, h, dt, R, vmax, f0, a, b, ah, bh);
+  return cudaGetLastError();
+}
+cudaError_t launch_src_prep(int S, int kind, const float* x0, const Grid& g, float dx, float dz, int* box,
+                            float* w, int* status, cudaStream_t st) {
+  k_src_prep<<<(S + 127) / 128, 128, 0, st>>>(S, kind, x0, g, dx, dz, box, w, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* start,
+                           int* list, int* status, cudaStream_t st) {
+  k_rec_csr<<<1, 1024, 0, st>>>(nrec, iz, ix, g, rec_cell, start, list, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_model_check(const float* c, long long n, float coef, int* status, cudaStream_t st) {
+  k_model_check<<<1, 1024, 0, st>>>(c, n, coef, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
+                          int* status, cudaStream_t st) {
+  k_misfit<<<nb, 256, 0, st>>>(seis, res, n, part);
+  k_misfit_final<<<1, 32, 0, st>>>(part, nb, J, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st) {
+  k_finite_check<<<304, 256, 0, st>>>(a, n, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_init(const AcuStep& p, float* lam, cudaStream_t st) {
+  k_adj_init<<<p.S, 32, 0, st>>>(p, lam);
+  return cudaGetLastError();
+}
+cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st) {
+  k_fold<<<608, 256, 0, st>>>(gpart, S, slice, G);
+  return cudaGetLastError();
+}
+cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st) {
+  k_grad_c<<<304, 256, 0, st>>>(G, g, c, grad);
+  return cudaGetLastError();
+}
+cudaError_t launch_src_grad(const float* part, int S, int nt, double dt2, const float* stf, double inv_sig2,
+                            int kind, float* gstf, float* gx0, cudaStream_t st) {
+  k_src_grad<<<S, 256, 0, st>>>(part, S, nt, dt2, stf, inv_sig2, kind, gstf, gx0);
+  return cudaGetLastError();
+}
+
+}  // namespace fwi

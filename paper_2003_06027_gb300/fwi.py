@@ -1,0 +1,240 @@
+"""Thin Python binding of libfwi (include/fwi.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels. PyTorch is
+used for device memory and streams. Arrays may be CUDA tensors (device
+pointers are passed as is), or CPU tensors / numpy arrays (host pointers; the
+library copies them through its device workspace). There is no CPU fallback:
+if the library cannot be loaded, the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+FWI_ACOUSTIC, FWI_ELASTIC = 0, 1
+FWI_SRC_POINT, FWI_SRC_GAUSSIAN, FWI_SRC_MOMENT = 0, 1, 2
+STATUS = {0: "FWI_OK", 1: "FWI_EINVAL", 2: "FWI_ECFL", 3: "FWI_ENOMEM", 4: "FWI_ECUDA",
+          5: "FWI_EUNSTABLE", 6: "FWI_ETIMEOUT", 7: "FWI_ENOTIMPL"}
+
+
+class FwiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("physics", ctypes.c_int32), ("nz", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("dz", ctypes.c_float), ("dx", ctypes.c_float), ("order", ctypes.c_int32),
+                ("npml", ctypes.c_int32), ("pml_R", ctypes.c_float), ("pml_vmax", ctypes.c_float),
+                ("pml_f0", ctypes.c_float), ("vp", ctypes.c_void_p), ("vs", ctypes.c_void_p),
+                ("rho", ctypes.c_void_p)]
+
+
+class _Sources(ctypes.Structure):
+    _fields_ = [("nshots", ctypes.c_int32), ("kind", ctypes.c_int32), ("x0", ctypes.c_void_p),
+                ("stf", ctypes.c_void_p), ("mt", ctypes.c_void_p)]
+
+
+class _Receivers(ctypes.Structure):
+    _fields_ = [("nrec", ctypes.c_int32), ("iz", ctypes.c_void_p), ("ix", ctypes.c_void_p)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+_ctx = threading.local()
+
+EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
+           "fwi_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def library(build_if_missing: bool = True):
+    """Load libfwi.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libfwi.so not found at {path}; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            P = ctypes.c_void_p
+            L.fwi_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+            L.fwi_destroy.argtypes = [P]
+            L.fwi_forward.argtypes = [P, ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                      ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P, P]
+            L.fwi_misfit_grad.argtypes = [P, ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                          ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
+                                          ctypes.c_int32, P, P, P, P, P, P]
+            L.fwi_last_timing.argtypes = [P, P, P, P]
+            L.fwi_last_error.restype = ctypes.c_char_p
+            for f in EXPORTS[:-1]:
+                getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise FwiError(st, library().fwi_last_error().decode())
+
+
+def context(device: int = 0):
+    """Per-thread, per-device library context."""
+    ctxs = getattr(_ctx, "ctxs", None)
+    if ctxs is None:
+        ctxs = _ctx.ctxs = {}
+    if device not in ctxs:
+        h = ctypes.c_void_p()
+        _check(library().fwi_create(ctypes.byref(h), int(device)))
+        ctxs[device] = h
+    return ctxs[device]
+
+
+@dataclass
+class Timing:
+    forward_ms: float      # forward sweep (with checkpoint saves)
+    reverse_ms: float      # recompute + adjoint + folds
+    total_ms: float
+    fwd_step_ms: float     # average launch of the recording forward step
+    store_step_ms: float   # average launch of the storing forward step (recompute)
+    adj_step_ms: float     # average launch of the adjoint step
+    launches: int          # kernels launched by the call
+
+
+def last_timing(device: int = 0) -> Timing:
+    ph = (ctypes.c_float * 3)()
+    km = (ctypes.c_float * 3)()
+    n = ctypes.c_int64()
+    _check(library().fwi_last_timing(context(device), ph, km, ctypes.byref(n)))
+    return Timing(ph[0], ph[1], ph[2], km[0], km[1], km[2], int(n.value))
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _arr(x, dtype):
+    """Contiguous array of the given numpy dtype; torch tensors stay torch."""
+    if _is_torch(x):
+        import torch
+
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        return x.detach().to(tdt).contiguous()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _empty_like_place(ref, shape, dtype=np.float32):
+    if _is_torch(ref):
+        import torch
+
+        tdt = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+def _stream(ref, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    if _is_torch(ref) and ref.is_cuda:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream(ref.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _device(ref, device):
+    if device is not None:
+        return int(device)
+    if _is_torch(ref) and ref.is_cuda:
+        return ref.device.index or 0
+    return 0
+
+
+class _Call:
+    """Holds the marshalled arguments (and keeps their buffers alive)."""
+
+    def __init__(self, c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0,
+                 src_kind):
+        self.c = _arr(c, np.float32)
+        self.stf = _arr(stf, np.float32)
+        if self.stf.ndim == 1:
+            self.stf = self.stf.reshape(1, -1)
+        self.x0 = _arr(x0, np.float32).reshape(-1, 2)
+        self.iz = _arr(rec_iz, np.int32).reshape(-1)
+        self.ix = _arr(rec_ix, np.int32).reshape(-1)
+        nz, nx = self.c.shape
+        self.S, self.nt = self.stf.shape
+        self.nrec = self.iz.shape[0]
+        self.model = _Model(FWI_ACOUSTIC, nz, nx, dz, dx, order, npml, pml_R, pml_vmax, pml_f0,
+                            _ptr(self.c), None, None)
+        self.src = _Sources(self.S, src_kind, _ptr(self.x0), _ptr(self.stf), None)
+        self.rec = _Receivers(self.nrec, _ptr(self.iz), _ptr(self.ix))
+
+
+def forward(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
+            pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, out=None, stream=None,
+            device=None):
+    """Seismograms [nshots][nrec][nt] (fwi_forward). nt = stf.shape[-1]."""
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    if out is None:
+        out = _empty_like_place(a.c, (a.S, a.nrec, a.nt))
+    dev = _device(a.c, device)
+    _check(library().fwi_forward(context(dev), ctypes.byref(a.model), ctypes.byref(a.src),
+                                 ctypes.byref(a.rec), a.nt, float(dt), _ptr(out), _stream(a.c, stream)))
+    return out
+
+
+def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20,
+                pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, ckpt_every=100,
+                want_grad=True, want_src=True, want_seis=False, out=None, stream=None, device=None):
+    """(J, dJ/dc, dJ/dstf, dJ/dx0, seis) of J = 1/2 sum (d - d_obs)^2 (fwi_misfit_grad).
+
+    ``out`` may hold preallocated outputs {"misfit", "grad", "grad_stf", "grad_x0", "seis"}.
+    """
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    obs = _arr(observed, np.float32)
+    out = dict(out or {})
+    ref = a.c
+    if "misfit" not in out:
+        out["misfit"] = _empty_like_place(ref, (1,), np.float64)
+    if want_grad and "grad" not in out:
+        out["grad"] = _empty_like_place(ref, tuple(a.c.shape))
+    if want_src and "grad_stf" not in out:
+        out["grad_stf"] = _empty_like_place(ref, (a.S, a.nt))
+    if want_src and "grad_x0" not in out:
+        out["grad_x0"] = _empty_like_place(ref, (a.S, 2))
+    if want_seis and "seis" not in out:
+        out["seis"] = _empty_like_place(ref, (a.S, a.nrec, a.nt))
+    dev = _device(ref, device)
+    K = max(1, min(int(ckpt_every), a.nt))
+    _check(library().fwi_misfit_grad(
+        context(dev), ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
+        float(dt), _ptr(obs), K, _ptr(out["misfit"]), _ptr(out.get("grad")),
+        _ptr(out.get("grad_stf")), _ptr(out.get("grad_x0")), _ptr(out.get("seis")),
+        _stream(ref, stream)))
+    return out["misfit"], out.get("grad"), out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
+def problem_kwargs(d: dict) -> dict:
+    """Keyword arguments of forward()/misfit_grad() from a synth problem dict."""
+    return dict(dx=d["dx"], dz=d["dz"], dt=d["dt"], order=d["order"], npml=d["npml"],
+                pml_R=d["pml_R"], pml_vmax=d["pml_vmax"], pml_f0=d["pml_f0"], src_kind=d["src_kind"])
