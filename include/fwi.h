@@ -128,6 +128,24 @@ fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
                            float *grad, float *grad_stf, float *grad_x0, float *seis_out,
                            void *cuda_stream);
 
+/* Forward modelling that allocates no device memory, for callers that cannot
+ * let a library call cudaMalloc: applications that hand all device memory to
+ * their own allocator and account for every byte, and latency-sensitive loops
+ * that cannot afford the device-wide synchronisation cudaMalloc/cudaFree may
+ * cause. The paper has no counterpart of this call; it computes exactly what
+ * fwi_forward computes, with the same kernels.
+ * Differences from fwi_forward: no context; vp, stf, x0, iz, ix and seis must
+ * be DEVICE pointers on the current device; the working memory is one fixed
+ * 32 MiB device array inside libfwi (held on every GPU where the library is
+ * loaded, until the process exits), so a problem needing more is rejected with
+ * FWI_EINVAL (the message gives the bytes needed). Every call shares that
+ * array and clears the part it uses; calls that overlap on the GPU race and
+ * must be serialised by the caller. The first call on a device resolves the
+ * array's address: make it before any stream capture begins on that device. */
+fwi_status fwi_forward_noalloc(const fwi_model *model, const fwi_sources *src,
+                               const fwi_receivers *rec, int32_t nt, float dt, float *seis,
+                               void *cuda_stream);
+
 /* Timing of the last call, measured with CUDA events recorded on the call's
  * stream. phase_ms3: [0] forward sweep (with checkpoint saves), [1] reverse
  * sweep (recompute + adjoint + folds), [2] whole call. kernel_ms3: average

@@ -39,13 +39,19 @@ cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStr
 cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st);
 cudaError_t launch_src_grad(const float* part, int S, int nt, double dt2, const float* stf, double inv_sig2,
                             int kind, float* gstf, float* gx0, cudaStream_t st);
+void set_last_error(const std::string& msg);
 }  // namespace fwi
 
 using namespace fwi;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+// Lets the other translation units of the library set fwi_last_error().
+void fwi::set_last_error(const std::string& msg) { g_err = msg; }
+
+namespace {
 
 fwi_status fail(fwi_status st, const std::string& msg) {
   g_err = msg;

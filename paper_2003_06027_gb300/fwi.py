@@ -52,7 +52,7 @@ _lib_lock = threading.Lock()
 _ctx = threading.local()
 
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
-           "fwi_last_error"]
+           "fwi_forward_noalloc", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -77,6 +77,9 @@ def library(build_if_missing: bool = True):
                                           ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
                                           ctypes.c_int32, P, P, P, P, P, P]
             L.fwi_last_timing.argtypes = [P, P, P, P]
+            L.fwi_forward_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                              ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
+                                              P]
             L.fwi_last_error.restype = ctypes.c_char_p
             for f in EXPORTS[:-1]:
                 getattr(L, f).restype = ctypes.c_int
@@ -200,6 +203,20 @@ def forward(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1
     dev = _device(a.c, device)
     _check(library().fwi_forward(context(dev), ctypes.byref(a.model), ctypes.byref(a.src),
                                  ctypes.byref(a.rec), a.nt, float(dt), _ptr(out), _stream(a.c, stream)))
+    return out
+
+
+def forward_noalloc(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
+                    pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, out=None, stream=None):
+    """fwi_forward_noalloc: the forward map without any device allocation by
+    the library (for callers whose device memory is fully managed by their own
+    allocator). All arrays must be CUDA tensors on the current device; ``out``
+    (the seismograms) is allocated here by torch when not given."""
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    if out is None:
+        out = _empty_like_place(a.c, (a.S, a.nrec, a.nt))
+    _check(library().fwi_forward_noalloc(ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec),
+                                         a.nt, float(dt), _ptr(out), _stream(a.c, stream)))
     return out
 
 
