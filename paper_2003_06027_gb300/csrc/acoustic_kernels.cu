@@ -1,18 +1,29 @@
-// acoustic_kernels.cu - sm_103a kernels of the acoustic hot path.
+// acoustic_kernels.cu - sm_103a step kernels of the acoustic hot path.
 //
 // One time step of the recursion U_{k+1} = A(theta) U_k + F_k (Method,
 // Eq. forward) for u_tt = div(c^2 grad u) + f (Implementation, Eq. acoustic)
-// on the staggered grid, and one step of its exact transpose
+// on the staggered grid with CPML, and one step of its exact transpose
 // lambda_k = A^T lambda_{k+1} + residual (Eq. adjoint-backward) fused with the
 // gradient correlation lambda^T (dA/dm) U (Eq. adjoint-gradient).
 //
-// Both step kernels are memory bound (no dense contraction): one CTA owns a
-// 64 x 16 tile of one shot, stages the tile plus its halo in shared memory with
-// coalesced float4 loads, evaluates the first-stage half-point fluxes once per
-// half point in shared memory, then the second-stage divergence, and streams
-// each field through HBM once per step. CPML memory variables are read and
-// written only where the damping coefficient is non-zero.
+// Design (memory bound, no dense contraction, so no tensor cores):
+//   * persistent CTAs (grid = resident CTAs of the GPU) walk the tiles of all
+//     shots; a tile is 64 x 32 cells of one shot;
+//   * the wavefield tile with its 8-cell halo and the coefficient tile are
+//     fetched by TMA (cp.async.bulk.tensor) into one of two shared-memory
+//     buffers, so the next tile's fetch overlaps the current tile's work;
+//     the completion wait on the mbarrier is bounded and reports a timeout;
+//   * stage 1 evaluates each half-point flux once (x: q at the half columns
+//     of the tile and its halo; z: a register window over two rows per thread),
+//     stage 2 the divergence, update, sources and receivers;
+//   * per-cell operands that do not need a halo (u^{n-1}, lambda_{n+2}, the
+//     gradient partial) are read with float4 loads issued before the wait, so
+//     their latency overlaps the tile fetch.
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "fwi_internal.cuh"
 
@@ -20,28 +31,94 @@ namespace fwi {
 
 namespace {
 
-constexpr int H = 8;                        // halo of the wavefield tile
-constexpr int SUW = TILE_X + 2 * H;         // 80
-constexpr int SUH = TILE_Z + 2 * H;         // 32
-constexpr int SMW = TILE_X + 12;            // m tile cols [x0-4, x0+TX+8)
-constexpr int SMH = TILE_Z + 9;             // m tile rows [z0-4, z0+TZ+5)
-constexpr int QXW = TILE_X + 8;             // half cols [x0-4, x0+TX+4)
-constexpr int QZH = TILE_Z + 8;             // half rows [z0-4, z0+TZ+4)
-constexpr int NQX = TILE_Z * (QXW / 4);
-constexpr int NQZ = QZH * (TILE_X / 4);
+constexpr int H = 8;                     // wavefield halo (>= 2N-1)
+constexpr int UW = TILE_X + 2 * H;       // 80: wavefield tile width
+constexpr int UH = TILE_Z + 2 * H;       // 48: wavefield tile height
+constexpr int MW = TILE_X + 12;          // 76: m tile cols [x0-4, x0+TX+8)
+constexpr int MH = TILE_Z + 9;           // 41: m tile rows [z0-4, z0+TZ+5)
+constexpr int QXW = TILE_X + 8;          // 72: half cols [x0-4, x0+TX+4)
+constexpr int QZH = TILE_Z + 8;          // 40: half rows [z0-4, z0+TZ+4)
+constexpr int U_BYTES = UW * UH * 4;     // 15360
+constexpr int M_BYTES = MW * MH * 4;     // 12464
+constexpr int M_SLOT = (M_BYTES + 127) / 128 * 128;
+constexpr long long WAIT_SPINS = 1LL << 24;
 
-__device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4s(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Stage a rows x (4*c4n) window of a field whose top-left global cell is
-// (zt, xt) into shared memory (row stride w floats).
-__device__ __forceinline__ void stage(float* dst, int w, const float* __restrict__ src, int pitch,
-                                      int zt, int xt, int nrows, int c4n) {
-  for (int idx = threadIdx.x; idx < nrows * c4n; idx += NTHREADS) {
-    int r = idx / c4n, c4 = idx - r * c4n;
-    float4 v = __ldg(reinterpret_cast<const float4*>(src + (long long)(zt + r) * pitch + (xt + 4 * c4)));
-    st4s(dst + r * w + 4 * c4, v);
-  }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within WAIT_SPINS polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_SPINS; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void unpack12(const float* s, float v[12]) {
+  const float4 a = ld4(s), b = ld4(s + 4), c = ld4(s + 8);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+}
+__device__ __forceinline__ void unpack12_g(const float* s, float v[12]) {
+  const float4 a = ldg4(s), b = ldg4(s + 4), c = ldg4(s + 8);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+}
+__device__ __forceinline__ void f4a(const float4 v, float o[4]) {
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+// float4 stencil accumulation: acc += c (p - m)
+__device__ __forceinline__ void acc4(float4& acc, float c, const float4 p, const float4 m) {
+  acc.x += c * (p.x - m.x); acc.y += c * (p.y - m.y); acc.z += c * (p.z - m.z); acc.w += c * (p.w - m.w);
+}
+
+struct TileId {
+  int s, x0, z0, tx, tz;
+};
+__device__ __forceinline__ TileId tile_of(const Grid& g, int t) {
+  TileId r;
+  r.tx = t % g.ntx;
+  const int q = t / g.ntx;
+  r.tz = q % g.ntz;
+  r.s = q / g.ntz;
+  r.x0 = r.tx * TILE_X;
+  r.z0 = r.tz * TILE_Z;
+  return r;
 }
 
 __device__ __forceinline__ bool tile_pml_x(const Grid& g, int x0) {
@@ -52,547 +129,785 @@ __device__ __forceinline__ bool tile_pml_z(const Grid& g, int z0) {
 }
 
 // Deterministic CTA sum of three floats (fixed shuffle tree, fixed warp order).
-__device__ __forceinline__ void cta_sum3(float v[3], float (*red)[3]) {
+__device__ __forceinline__ void cta_sum3(float v[3], float* red) {
   for (int k = 0; k < 3; k++)
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0)
-    for (int k = 0; k < 3; k++) red[warp][k] = v[k];
+    for (int k = 0; k < 3; k++) red[warp * 3 + k] = v[k];
   __syncthreads();
   if (threadIdx.x == 0)
     for (int k = 0; k < 3; k++) {
       float s = 0.f;
-      for (int w = 0; w < NTHREADS / 32; w++) s += red[w][k];
+      for (int w = 0; w < NTHREADS / 32; w++) s += red[w * 3 + k];
       v[k] = s;
     }
+  __syncthreads();
 }
+
+// Issue the TMA fetches of tile t into one buffer (one elected thread).
+__device__ __forceinline__ void fetch_tile(const CUtensorMap* fmap, const CUtensorMap* mmap, const Grid& g, int S,
+                                           int pair, int t, float* dst_u, float* dst_m, uint64_t* bar) {
+  const TileId id = tile_of(g, t);
+  fence_proxy_async();
+  mbar_expect_tx(bar, U_BYTES + M_BYTES);
+  // allocation coordinates: padded (i, j) -> (i + APRON, j + APRON)
+  tma_3d(dst_u, fmap, id.x0 - H + APRON, id.z0 - H + APRON, pair * S + id.s, bar);
+  tma_2d(dst_m, mmap, id.x0 - 4 + APRON, id.z0 - 4 + APRON, bar);
+}
+
+// Shared memory of the step kernels (every array a multiple of 128 bytes).
+struct FwdSmem {
+  float u[2][UH * UW];
+  float m[2][M_SLOT / 4];
+  float qx[TILE_Z * QXW];
+  float qz[QZH * TILE_X];
+  float red[32];
+  uint64_t bar[2];
+};
+struct AdjSmem {
+  float l[2][UH * UW];
+  float m[2][M_SLOT / 4];
+  float gx[TILE_Z * QXW];
+  float gz[QZH * TILE_X];
+  float imx[TILE_Z * QXW];
+  float imz[QZH * TILE_X];
+  float red[32];
+  uint64_t bar[2];
+};
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Forward step n: u^{n+1} = 2 u^n - u^{n-1} + dt^2 (div(m grad u^n) + f^n) with
-// CPML. RECORD writes the receiver samples; STORE saves u^n and the updated
-// psi (the operands of the gradient correlation) into the segment slot.
+// Forward step n: u^{n+1} = 2 u^n - u^{n-1} + dt^2 (D-(m_half (D+ u^n + psi)) + zeta + f^n)
+// per axis, with psi <- b_h psi + a_h D+u and zeta <- b zeta + a D-(q) (zeta is
+// kept multiplied by dt^2). RECORD writes the receiver samples; STORE keeps
+// p = D+u + psi of every half point (the operand of the gradient correlation).
 template <int N, bool RECORD, bool STORE>
-__global__ void __launch_bounds__(NTHREADS) acu_fwd_step(const AcuStep p) {
-  __shared__ __align__(16) float su[SUH][SUW];
-  __shared__ __align__(16) float sm[SMH][SMW];
-  __shared__ __align__(16) float sqx[TILE_Z][QXW];
-  __shared__ __align__(16) float sqz[QZH][TILE_X];
-
+__global__ void __launch_bounds__(NTHREADS, 3)
+    acu_fwd_step(const __grid_constant__ CUtensorMap tmap_u, const __grid_constant__ CUtensorMap tmap_m,
+                 const AcuStep p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  FwdSmem& sh = *reinterpret_cast<FwdSmem*>(smem_raw);
   const Grid& g = p.g;
-  const int tid = threadIdx.x, s = blockIdx.z;
-  const int x0 = blockIdx.x * TILE_X, z0 = blockIdx.y * TILE_Z;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
-  const long long sh = (long long)s * g.slice + g.off0;
 
-  stage(&su[0][0], SUW, p.u_cur + sh, pitch, z0 - H, x0 - H, SUH, SUW / 4);
-  stage(&sm[0][0], SMW, p.m + g.off0, pitch, z0 - 4, x0 - 4, SMH, SMW / 4);
+  if (tid == 0) {
+    mbar_init(&sh.bar[0], 1);
+    mbar_init(&sh.bar[1], 1);
+    fence_mbar_init();
+  }
   __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < p.ntiles)
+    fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, blockIdx.x, sh.u[0], sh.m[0], &sh.bar[0]);
 
-  const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
-  const float inv_dx = p.inv_dx, inv_dz = p.inv_dz;
+  int it = 0;
+  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
+    const int b = it & 1;
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < p.ntiles)
+      fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, tn, sh.u[b ^ 1], sh.m[b ^ 1], &sh.bar[b ^ 1]);
+    const TileId id = tile_of(g, t);
+    const int x0 = id.x0, z0 = id.z0, s = id.s;
+    const long long base = (long long)s * g.slice + g.off0;
+    float* __restrict__ uprev = p.u + (long long)(p.cur ^ 1) * p.S * g.slice + base;
+    // prefetch u^{n-1} of this thread's 2 x 4 cells
+    const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
+    float4 up[2];
+    up[0] = ldg4(uprev + (long long)zr0 * pitch + xb);
+    up[1] = ldg4(uprev + (long long)(zr0 + 1) * pitch + xb);
+    // small per-tile operands, fetched before the wait as well
+    const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
+    const float stf_n = __ldg(p.stf + (long long)s * p.nt + p.n);
+    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+    int rb = 0, re = 0;
+    if (RECORD) {
+      rb = __ldg(p.thr_rec_start + key);
+      re = __ldg(p.thr_rec_start + key + 1);
+    }
 
-  // Stage 1: q = m_half * (D+ u + psi) at the half points of the tile + halo.
-  for (int it = tid; it < NQX + NQZ; it += NTHREADS) {
-    if (it < NQX) {
-      const int r = it / (QXW / 4), gq = it - r * (QXW / 4);
+    const bool ok = mbar_wait(&sh.bar[b], (it >> 1) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      return;
+    }
+    const float* su = sh.u[b];
+    const float* sm = sh.m[b];
+    const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
+
+    // ---- stage 1a: x fluxes q = m_half (D+u + psi) at 4 half columns of row r
+    auto qx_item = [&](int r, int gq, bool own) {
       const int z = z0 + r, hb = x0 - 4 + 4 * gq;
       float v[12];
-      {
-        const float* row = &su[r + H][4 * gq];
-        float4 a0 = ld4s(row), a1 = ld4s(row + 4), a2 = ld4s(row + 8);
-        v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
-        v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
-        v[8] = a2.x; v[9] = a2.y; v[10] = a2.z; v[11] = a2.w;
-      }
-      float q[4];
+      unpack12(su + (r + H) * UW + 4 * gq, v);
+      const float4 m4 = ld4(sm + (r + 4) * MW + 4 * gq);
+      const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
+      float q[4], pp[4];
 #pragma unroll
       for (int e = 0; e < 4; e++) {
         float gx = 0.f;
 #pragma unroll
-        for (int k = 1; k <= N; k++) gx += p.a[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
-        gx *= inv_dx;
-        const int h = hb + e;
-        float pp = gx;
-        if (pmlx) {
-          const float aa = __ldg(p.axh + h + TAB_OFF);
-          if (aa != 0.f) {
-            const float bb = __ldg(p.bxh + h + TAB_OFF);
-            const long long id = sh + (long long)z * pitch + h;
-            const float ps = bb * p.psix_in[id] + aa * gx;
-            if (h >= x0 && h < x0 + TILE_X && z < g.Nz) {
-              p.psix_out[id] = ps;
-              if (STORE) p.slot_psix[id] = ps;
-            }
-            pp += ps;
-          }
-        }
-        const float mh = 0.5f * (sm[r + 4][4 * gq + e] + sm[r + 4][4 * gq + e + 1]);
-        q[e] = (h >= 0 && h < g.Nx - 1 && z < g.Nz) ? mh * pp : 0.f;
+        for (int k = 1; k <= N; k++) gx += p.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
+        pp[e] = gx;
       }
-      st4s(&sqx[r][4 * gq], make_float4(q[0], q[1], q[2], q[3]));
-    } else {
-      const int k2 = it - NQX;
-      const int hr = k2 / (TILE_X / 4), c = k2 - hr * (TILE_X / 4);
-      const int hz = z0 - 4 + hr, xb = x0 + 4 * c;
+      const long long id0 = base + (long long)z * pitch + hb;
+      if (pmlx) {
+        const float4 a4 = ldg4(p.axh + hb + TAB_OFF);
+        if (a4.x != 0.f || a4.y != 0.f || a4.z != 0.f || a4.w != 0.f) {
+          // psi <- b psi + a g; zero where a = 0 (psi stays zero outside the layer)
+          const float4 b4 = ldg4(p.bxh + hb + TAB_OFF);
+          const float4 po = ld4(p.psix_in + id0);
+          float4 pn;
+          pn.x = b4.x * po.x + a4.x * pp[0]; pn.y = b4.y * po.y + a4.y * pp[1];
+          pn.z = b4.z * po.z + a4.z * pp[2]; pn.w = b4.w * po.w + a4.w * pp[3];
+          if (own && z < g.Nz) st4(p.psix_out + id0, pn);
+          pp[0] += pn.x; pp[1] += pn.y; pp[2] += pn.z; pp[3] += pn.w;
+        }
+      }
+      const bool rowok = z < g.Nz;
+#pragma unroll
+      for (int e = 0; e < 4; e++) q[e] = (rowok && hb + e >= 0 && hb + e < g.Nx - 1) ? (mv[e] + mv[e + 1]) * pp[e] : 0.f;
+      st4(sh.qx + r * QXW + 4 * gq, make_float4(q[0], q[1], q[2], q[3]));
+      if (STORE && own && rowok) st4(p.slot_px + id0, make_float4(pp[0], pp[1], pp[2], pp[3]));
+    };
+    // ---- stage 1b: z fluxes at one half row (the tile's halo rows)
+    auto qz_item = [&](int hr, int c) {
+      const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int k = 1; k <= N; k++) {
-        const float4 wp = ld4s(&su[hr + 4 + k][8 + 4 * c]);
-        const float4 wm = ld4s(&su[hr + 5 - k][8 + 4 * c]);
-        acc.x += p.a[k - 1] * (wp.x - wm.x);
-        acc.y += p.a[k - 1] * (wp.y - wm.y);
-        acc.z += p.a[k - 1] * (wp.z - wm.z);
-        acc.w += p.a[k - 1] * (wp.w - wm.w);
-      }
-      float gz[4] = {acc.x * inv_dz, acc.y * inv_dz, acc.z * inv_dz, acc.w * inv_dz};
-      float pp[4] = {gz[0], gz[1], gz[2], gz[3]};
+      for (int k = 1; k <= N; k++)
+        acc4(acc, p.c1z[k - 1], ld4(su + (hr + 4 + k) * UW + 8 + 4 * c), ld4(su + (hr + 5 - k) * UW + 8 + 4 * c));
+      float pp[4];
+      f4a(acc, pp);
       if (pmlz) {
         const float aa = __ldg(p.azh + hz + TAB_OFF);
         if (aa != 0.f) {
           const float bb = __ldg(p.bzh + hz + TAB_OFF);
-          const bool own = hz >= z0 && hz < z0 + TILE_Z;
-          const long long id = sh + (long long)hz * pitch + xb;
-          const float4 po = *reinterpret_cast<const float4*>(p.psiz_in + id);
-          float4 pn;
-          pn.x = bb * po.x + aa * gz[0];
-          pn.y = bb * po.y + aa * gz[1];
-          pn.z = bb * po.z + aa * gz[2];
-          pn.w = bb * po.w + aa * gz[3];
-          if (own) {
-            // columns beyond Nx are outside the grid: keep them zero
+          const float4 po = *reinterpret_cast<const float4*>(p.psiz_in + base + (long long)hz * pitch + xc);
+          pp[0] += bb * po.x + aa * pp[0]; pp[1] += bb * po.y + aa * pp[1];
+          pp[2] += bb * po.z + aa * pp[2]; pp[3] += bb * po.w + aa * pp[3];
+        }
+      }
+      const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
+      const bool hv = hz >= 0 && hz < g.Nz - 1;
+      const float q0 = (hv && xc + 0 < g.Nx) ? (ma.x + mb.x) * pp[0] : 0.f;
+      const float q1 = (hv && xc + 1 < g.Nx) ? (ma.y + mb.y) * pp[1] : 0.f;
+      const float q2 = (hv && xc + 2 < g.Nx) ? (ma.z + mb.z) * pp[2] : 0.f;
+      const float q3 = (hv && xc + 3 < g.Nx) ? (ma.w + mb.w) * pp[3] : 0.f;
+      st4(sh.qz + hr * TILE_X + 4 * c, make_float4(q0, q1, q2, q3));
+    };
+
+    qx_item(2 * ty, tx + 1, true);
+    qx_item(2 * ty + 1, tx + 1, true);
+    {
+      // own z fluxes at half rows 2ty, 2ty+1 (tile-local) from a (2N+1)-row window
+      float4 w[2 * N + 1];
+#pragma unroll
+      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(su + (2 * ty + H - N + 1 + t2) * UW + 8 + 4 * tx);
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+#pragma unroll
+      for (int k = 1; k <= N; k++) {
+        acc4(a0, p.c1z[k - 1], w[k + N - 1], w[N - k]);
+        acc4(a1, p.c1z[k - 1], w[k + N], w[N - k + 1]);
+      }
+      float pp[2][4];
+      f4a(a0, pp[0]);
+      f4a(a1, pp[1]);
+#pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int hz = zr0 + rr;
+        const long long idz = base + (long long)hz * pitch + xb;
+        if (pmlz) {
+          const float aa = __ldg(p.azh + hz + TAB_OFF);
+          if (aa != 0.f) {
+            const float bb = __ldg(p.bzh + hz + TAB_OFF);
+            const float4 po = *reinterpret_cast<const float4*>(p.psiz_in + idz);
+            float4 pn;
+            pn.x = bb * po.x + aa * pp[rr][0]; pn.y = bb * po.y + aa * pp[rr][1];
+            pn.z = bb * po.z + aa * pp[rr][2]; pn.w = bb * po.w + aa * pp[rr][3];
             if (xb + 0 >= g.Nx) pn.x = 0.f;
             if (xb + 1 >= g.Nx) pn.y = 0.f;
             if (xb + 2 >= g.Nx) pn.z = 0.f;
             if (xb + 3 >= g.Nx) pn.w = 0.f;
-            *reinterpret_cast<float4*>(p.psiz_out + id) = pn;
-            if (STORE) *reinterpret_cast<float4*>(p.slot_psiz + id) = pn;
-          }
-          pp[0] += pn.x; pp[1] += pn.y; pp[2] += pn.z; pp[3] += pn.w;
-        }
-      }
-      const bool hv = hz >= 0 && hz < g.Nz - 1;
-      float q[4];
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const float mh = 0.5f * (sm[hr][4 * c + 4 + e] + sm[hr + 1][4 * c + 4 + e]);
-        q[e] = (hv && xb + e < g.Nx) ? mh * pp[e] : 0.f;
-      }
-      st4s(&sqz[hr][4 * c], make_float4(q[0], q[1], q[2], q[3]));
-    }
-  }
-  __syncthreads();
-
-  // Stage 2: divergence D- q + CPML zeta, leapfrog, source, receivers.
-  const int tx = tid & 15, ty = tid >> 4;
-  const int z = z0 + ty, xb = x0 + 4 * tx;
-  float v[12];
-  {
-    const float* row = &sqx[ty][4 * tx];
-    float4 a0 = ld4s(row), a1 = ld4s(row + 4), a2 = ld4s(row + 8);
-    v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
-    v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
-    v[8] = a2.x; v[9] = a2.y; v[10] = a2.z; v[11] = a2.w;
-  }
-  float4 hz4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int k = 1; k <= N; k++) {
-    const float4 wp = ld4s(&sqz[ty + k + 3][4 * tx]);
-    const float4 wm = ld4s(&sqz[ty - k + 4][4 * tx]);
-    hz4.x += p.a[k - 1] * (wp.x - wm.x);
-    hz4.y += p.a[k - 1] * (wp.y - wm.y);
-    hz4.z += p.a[k - 1] * (wp.z - wm.z);
-    hz4.w += p.a[k - 1] * (wp.w - wm.w);
-  }
-  const float hzv[4] = {hz4.x * inv_dz, hz4.y * inv_dz, hz4.z * inv_dz, hz4.w * inv_dz};
-  const bool zin = z < g.Nz;
-  const float az_ = pmlz ? __ldg(p.az + z + TAB_OFF) : 0.f;
-  const float bz_ = pmlz ? __ldg(p.bz + z + TAB_OFF) : 1.f;
-  float rr[4];
-#pragma unroll
-  for (int e = 0; e < 4; e++) {
-    float hx = 0.f;
-#pragma unroll
-    for (int k = 1; k <= N; k++) hx += p.a[k - 1] * (v[e + k + 3] - v[e - k + 4]);
-    hx *= inv_dx;
-    const int j = xb + e;
-    const bool valid = zin && j < g.Nx;
-    float r = hx + hzv[e];
-    const long long id = sh + (long long)z * pitch + j;
-    if (pmlx) {
-      const float aa = __ldg(p.ax + j + TAB_OFF);
-      if (aa != 0.f) {
-        const float zn = __ldg(p.bx + j + TAB_OFF) * p.zetx[id] + aa * hx;
-        if (valid) p.zetx[id] = zn;
-        r += zn;
-      }
-    }
-    if (az_ != 0.f) {
-      const float zn = bz_ * p.zetz[id] + az_ * hzv[e];
-      if (valid) p.zetz[id] = zn;
-      r += zn;
-    }
-    rr[e] = r;
-  }
-  const float4 uc = ld4s(&su[ty + H][4 * tx + H]);
-  float* upp = p.u_prev + sh + (long long)z * pitch + xb;
-  const float4 uo = *reinterpret_cast<const float4*>(upp);
-  float un[4];
-  un[0] = 2.f * uc.x - uo.x + p.dt2 * rr[0];
-  un[1] = 2.f * uc.y - uo.y + p.dt2 * rr[1];
-  un[2] = 2.f * uc.z - uo.z + p.dt2 * rr[2];
-  un[3] = 2.f * uc.w - uo.w + p.dt2 * rr[3];
-  {
-    // source term dt^2 w g(t_n) on the cells of this tile inside the box
-    const int i0 = p.src_box[2 * s], j0 = p.src_box[2 * s + 1], nb = p.src_n;
-    if (i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0) {
-      const float amp = p.dt2 * p.stf[(long long)s * p.nt + p.n];
-      const int di = z - i0;
-      if (di >= 0 && di < nb) {
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const int dj = xb + e - j0;
-          if (dj >= 0 && dj < nb) un[e] += amp * p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj];
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int e = 0; e < 4; e++)
-    if (!(zin && xb + e < g.Nx)) un[e] = 0.f;
-  *reinterpret_cast<float4*>(upp) = make_float4(un[0], un[1], un[2], un[3]);
-  if (STORE) *reinterpret_cast<float4*>(p.slot_u + sh + (long long)z * pitch + xb) = uc;
-  if (RECORD) {
-    const int t = blockIdx.y * g.ntx + blockIdx.x;
-    const int rb = p.tile_rec_start[t], re = p.tile_rec_start[t + 1];
-    for (int q = rb; q < re; q++) {
-      const int r = p.tile_rec[q];
-      const int ri = p.rec_cell[2 * r], rj = p.rec_cell[2 * r + 1];
-      const int d = rj - xb;
-      if (ri == z && d >= 0 && d < 4) {
-        const float val = d == 0 ? un[0] : (d == 1 ? un[1] : (d == 2 ? un[2] : un[3]));
-        p.seis[((long long)s * p.nrec + r) * p.nt + p.n] = val;
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Adjoint step n (reverse of forward step n, statement by statement):
-//   rbar = dt^2 lambda_{n+1};   hbar = rbar + a (Z + rbar),  Z <- b (Z + rbar)
-//   qbar = D-^T hbar = -D+ hbar (half points)
-//   g_m  += qbar * p^n           (gradient correlation, Eq. adjoint-gradient)
-//   pbar = m_half qbar;  gbar = pbar + a_h (P + pbar),  P <- b_h (P + pbar)
-//   lambda_n = 2 lambda_{n+1} - lambda_{n+2} + D+^T gbar + residual(n-1)
-// The cell gradient receives half of each adjacent half-point correlation.
-struct AdjSmem {
-  float sl[SUH][SUW];      // lambda_{n+1}, halo 8
-  float su[SUH][SUW];      // u^n, halo 8
-  float sm[SMH][SMW];
-  float shx[TILE_Z][SUW];  // hbar_x (CPML tiles)
-  float shz[SUH][SUW];     // hbar_z (CPML tiles)
-  float sgx[TILE_Z][QXW];
-  float sgz[QZH][TILE_X];
-  float simx[TILE_Z][QXW];
-  float simz[QZH][TILE_X];
-  float red[NTHREADS / 32][3];
-};
-
-template <int N>
-__global__ void __launch_bounds__(NTHREADS) acu_adj_step(const AcuStep p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  AdjSmem& S = *reinterpret_cast<AdjSmem*>(smem_raw);
-  auto& sl = S.sl;
-  auto& su = S.su;
-  auto& sm = S.sm;
-  auto& shx = S.shx;
-  auto& shz = S.shz;
-  auto& sgx = S.sgx;
-  auto& sgz = S.sgz;
-  auto& simx = S.simx;
-  auto& simz = S.simz;
-  auto& red = S.red;
-
-  const Grid& g = p.g;
-  const int tid = threadIdx.x, s = blockIdx.z;
-  const int x0 = blockIdx.x * TILE_X, z0 = blockIdx.y * TILE_Z;
-  const int pitch = g.pitch;
-  const long long sh = (long long)s * g.slice + g.off0;
-  const float dt2 = p.dt2, inv_dx = p.inv_dx, inv_dz = p.inv_dz;
-
-  stage(&sl[0][0], SUW, p.l_cur + sh, pitch, z0 - H, x0 - H, SUH, SUW / 4);
-  stage(&su[0][0], SUW, p.slot_u + sh, pitch, z0 - H, x0 - H, SUH, SUW / 4);
-  stage(&sm[0][0], SMW, p.m + g.off0, pitch, z0 - 4, x0 - 4, SMH, SMW / 4);
-  __syncthreads();
-
-  const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
-
-  // Stage 0 (CPML tiles): hbar including the memory variable Z.
-  if (pmlx) {
-    for (int idx = tid; idx < TILE_Z * SUW; idx += NTHREADS) {
-      const int r = idx / SUW, c = idx - r * SUW;
-      const int z = z0 + r, j = x0 - H + c;
-      const float rb = dt2 * sl[r + H][c];
-      float hb = rb;
-      const float aa = __ldg(p.ax + j + TAB_OFF);
-      if (aa != 0.f) {
-        const long long id = sh + (long long)z * pitch + j;
-        const float t = p.zx_in[id] + rb;
-        hb = rb + aa * t;
-        if (c >= H && c < H + TILE_X && z < g.Nz && j < g.Nx) p.zx_out[id] = __ldg(p.bx + j + TAB_OFF) * t;
-      }
-      shx[r][c] = hb;
-    }
-  }
-  if (pmlz) {
-    for (int idx = tid; idx < SUH * TILE_X; idx += NTHREADS) {
-      const int r = idx / TILE_X, c = idx - r * TILE_X;
-      const int z = z0 - H + r, j = x0 + c;
-      const float rb = dt2 * sl[r][c + H];
-      float hb = rb;
-      const float aa = __ldg(p.az + z + TAB_OFF);
-      if (aa != 0.f) {
-        const long long id = sh + (long long)z * pitch + j;
-        const float t = p.zz_in[id] + rb;
-        hb = rb + aa * t;
-        if (r >= H && r < H + TILE_Z && z < g.Nz && j < g.Nx) p.zz_out[id] = __ldg(p.bz + z + TAB_OFF) * t;
-      }
-      shz[r][c + H] = hb;
-    }
-  }
-  __syncthreads();
-  // hbar sources: CPML tiles read the staged hbar, others dt^2 lambda
-  const float* hxb = pmlx ? &shx[0][0] : &sl[H][0];
-  const float hxs = pmlx ? 1.f : dt2;
-  const float* hzb = pmlz ? &shz[0][0] : &sl[0][0];
-  const float hzs = pmlz ? 1.f : dt2;
-
-  // Stage 1: qbar, gradient correlation, gbar at the half points.
-  for (int it = tid; it < NQX + NQZ; it += NTHREADS) {
-    if (it < NQX) {
-      const int r = it / (QXW / 4), gq = it - r * (QXW / 4);
-      const int z = z0 + r, hb = x0 - 4 + 4 * gq;
-      float v[12], w[12];
-      {
-        const float* row = hxb + r * SUW + 4 * gq;
-        float4 a0 = ld4s(row), a1 = ld4s(row + 4), a2 = ld4s(row + 8);
-        v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
-        v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
-        v[8] = a2.x; v[9] = a2.y; v[10] = a2.z; v[11] = a2.w;
-        const float* urow = &su[r + H][4 * gq];
-        a0 = ld4s(urow); a1 = ld4s(urow + 4); a2 = ld4s(urow + 8);
-        w[0] = a0.x; w[1] = a0.y; w[2] = a0.z; w[3] = a0.w;
-        w[4] = a1.x; w[5] = a1.y; w[6] = a1.z; w[7] = a1.w;
-        w[8] = a2.x; w[9] = a2.y; w[10] = a2.z; w[11] = a2.w;
-      }
-      float gb[4], im[4];
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        float dq = 0.f, du = 0.f;
-#pragma unroll
-        for (int k = 1; k <= N; k++) {
-          dq += p.a[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
-          du += p.a[k - 1] * (w[e + 4 + k] - w[e + 5 - k]);
-        }
-        const int h = hb + e;
-        const bool inh = h >= 0 && h < g.Nx - 1 && z < g.Nz;
-        const float qb = inh ? -dq * inv_dx * hxs : 0.f;
-        float px = du * inv_dx;
-        const float mh = 0.5f * (sm[r + 4][4 * gq + e] + sm[r + 4][4 * gq + e + 1]);
-        const float pb = mh * qb;
-        float gbar = pb;
-        if (pmlx) {
-          const float aa = __ldg(p.axh + h + TAB_OFF);
-          if (aa != 0.f) {
-            const long long id = sh + (long long)z * pitch + h;
-            px += p.slot_psix[id];
-            const float t = p.px_in[id] + pb;
-            gbar = pb + aa * t;
-            if (h >= x0 && h < x0 + TILE_X && z < g.Nz) p.px_out[id] = __ldg(p.bxh + h + TAB_OFF) * t;
+            st4(p.psiz_out + idz, pn);
+            pp[rr][0] += pn.x; pp[rr][1] += pn.y; pp[rr][2] += pn.z; pp[rr][3] += pn.w;
           }
         }
-        gb[e] = inh ? gbar : 0.f;
-        im[e] = qb * px;
+        const float4 ma = ld4(sm + (2 * ty + 4 + rr) * MW + 4 * tx + 4);
+        const float4 mb = ld4(sm + (2 * ty + 5 + rr) * MW + 4 * tx + 4);
+        const bool hv = hz < g.Nz - 1;
+        float q[4];
+        q[0] = (hv && xb + 0 < g.Nx) ? (ma.x + mb.x) * pp[rr][0] : 0.f;
+        q[1] = (hv && xb + 1 < g.Nx) ? (ma.y + mb.y) * pp[rr][1] : 0.f;
+        q[2] = (hv && xb + 2 < g.Nx) ? (ma.z + mb.z) * pp[rr][2] : 0.f;
+        q[3] = (hv && xb + 3 < g.Nx) ? (ma.w + mb.w) * pp[rr][3] : 0.f;
+        st4(sh.qz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(q[0], q[1], q[2], q[3]));
+        if (STORE && hz < g.Nz) st4(p.slot_pz + idz, make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3]));
       }
-      st4s(&sgx[r][4 * gq], make_float4(gb[0], gb[1], gb[2], gb[3]));
-      st4s(&simx[r][4 * gq], make_float4(im[0], im[1], im[2], im[3]));
-    } else {
-      const int k2 = it - NQX;
-      const int hr = k2 / (TILE_X / 4), c = k2 - hr * (TILE_X / 4);
-      const int hz = z0 - 4 + hr, xb = x0 + 4 * c;
-      float4 dq = make_float4(0.f, 0.f, 0.f, 0.f), du = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (tid < 128) {
+      const int hr0 = tid >> 4;
+      qz_item(hr0 < 4 ? hr0 : hr0 + 32, tid & 15);
+    } else if (tid < 192) {
+      const int k = tid - 128;
+      qx_item(k >> 1, (k & 1) ? QXW / 4 - 1 : 0, false);
+    }
+    __syncthreads();
+
+    // ---- stage 2: divergence + CPML zeta + leapfrog + source + receivers
+    float hzv[2][4];
+    {
+      float4 w[2 * N + 1];
+#pragma unroll
+      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sh.qz + (2 * ty + 4 - N + t2) * TILE_X + 4 * tx);
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
 #pragma unroll
       for (int k = 1; k <= N; k++) {
-        const float4 hp = ld4s(hzb + (hr + 4 + k) * SUW + 8 + 4 * c);
-        const float4 hm = ld4s(hzb + (hr + 5 - k) * SUW + 8 + 4 * c);
-        const float4 up = ld4s(&su[hr + 4 + k][8 + 4 * c]);
-        const float4 um = ld4s(&su[hr + 5 - k][8 + 4 * c]);
-        const float ak = p.a[k - 1];
-        dq.x += ak * (hp.x - hm.x); dq.y += ak * (hp.y - hm.y);
-        dq.z += ak * (hp.z - hm.z); dq.w += ak * (hp.w - hm.w);
-        du.x += ak * (up.x - um.x); du.y += ak * (up.y - um.y);
-        du.z += ak * (up.z - um.z); du.w += ak * (up.w - um.w);
+        acc4(a0, p.c2z[k - 1], w[k + N - 1], w[N - k]);
+        acc4(a1, p.c2z[k - 1], w[k + N], w[N - k + 1]);
       }
-      const float dqv[4] = {dq.x, dq.y, dq.z, dq.w};
-      const float duv[4] = {du.x, du.y, du.z, du.w};
-      const bool hv = hz >= 0 && hz < g.Nz - 1;
-      const float aa = pmlz ? __ldg(p.azh + hz + TAB_OFF) : 0.f;
-      const float bb = pmlz ? __ldg(p.bzh + hz + TAB_OFF) : 1.f;
-      const bool own = hz >= z0 && hz < z0 + TILE_Z;
-      float gb[4], im[4];
+      f4a(a0, hzv[0]);
+      f4a(a1, hzv[1]);
+    }
+    const int i0 = box.x, j0 = box.y, nb = p.src_n;
+    const bool srcbox = i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0;
+    float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
+    if (pmlx) ax4 = ldg4(p.ax + xb + TAB_OFF);
+    const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
+    if (zx_on) bx4 = ldg4(p.bx + xb + TAB_OFF);
+    float un[2][4];
+#pragma unroll
+    for (int rr = 0; rr < 2; rr++) {
+      const int r = 2 * ty + rr, z = z0 + r;
+      const long long idc0 = base + (long long)z * pitch + xb;
+      float v[12];
+      unpack12(sh.qx + r * QXW + 4 * tx, v);
+      float hxv[4], rv[4];
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        const bool inh = hv && xb + e < g.Nx;
-        const float qb = inh ? -dqv[e] * inv_dz * hzs : 0.f;
-        float pz = duv[e] * inv_dz;
-        const float mh = 0.5f * (sm[hr][4 * c + 4 + e] + sm[hr + 1][4 * c + 4 + e]);
-        const float pb = mh * qb;
-        float gbar = pb;
+        float hx = 0.f;
+#pragma unroll
+        for (int k = 1; k <= N; k++) hx += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
+        hxv[e] = hx;
+        rv[e] = hx + hzv[rr][e];
+      }
+      // CPML zeta (dt^2-scaled) <- b zeta + a h; it stays zero where a = 0 and
+      // outside the grid (h = 0 there), so whole float4 groups are written
+      if (zx_on) {
+        const float4 zo = ld4(p.zetx + idc0);
+        float4 zn;
+        zn.x = bx4.x * zo.x + ax4.x * hxv[0]; zn.y = bx4.y * zo.y + ax4.y * hxv[1];
+        zn.z = bx4.z * zo.z + ax4.z * hxv[2]; zn.w = bx4.w * zo.w + ax4.w * hxv[3];
+        st4(p.zetx + idc0, zn);
+        rv[0] += zn.x; rv[1] += zn.y; rv[2] += zn.z; rv[3] += zn.w;
+      }
+      if (pmlz) {
+        const float aa = __ldg(p.az + z + TAB_OFF);
         if (aa != 0.f) {
-          const long long id = sh + (long long)hz * pitch + xb + e;
-          pz += p.slot_psiz[id];
-          const float t = p.pz_in[id] + pb;
-          gbar = pb + aa * t;
-          if (own && xb + e < g.Nx) p.pz_out[id] = bb * t;
+          const float bb = __ldg(p.bz + z + TAB_OFF);
+          const float4 zo = ld4(p.zetz + idc0);
+          float4 zn;
+          zn.x = bb * zo.x + aa * hzv[rr][0]; zn.y = bb * zo.y + aa * hzv[rr][1];
+          zn.z = bb * zo.z + aa * hzv[rr][2]; zn.w = bb * zo.w + aa * hzv[rr][3];
+          st4(p.zetz + idc0, zn);
+          rv[0] += zn.x; rv[1] += zn.y; rv[2] += zn.z; rv[3] += zn.w;
         }
-        gb[e] = inh ? gbar : 0.f;
-        im[e] = qb * pz;
       }
-      st4s(&sgz[hr][4 * c], make_float4(gb[0], gb[1], gb[2], gb[3]));
-      st4s(&simz[hr][4 * c], make_float4(im[0], im[1], im[2], im[3]));
-    }
-  }
-  __syncthreads();
-
-  // Stage 2: lambda_n and the cell gradient.
-  const int tx = tid & 15, ty = tid >> 4;
-  const int z = z0 + ty, xb = x0 + 4 * tx;
-  float v[12];
-  {
-    const float* row = &sgx[ty][4 * tx];
-    float4 a0 = ld4s(row), a1 = ld4s(row + 4), a2 = ld4s(row + 8);
-    v[0] = a0.x; v[1] = a0.y; v[2] = a0.z; v[3] = a0.w;
-    v[4] = a1.x; v[5] = a1.y; v[6] = a1.z; v[7] = a1.w;
-    v[8] = a2.x; v[9] = a2.y; v[10] = a2.z; v[11] = a2.w;
-  }
-  float4 dz4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 uc = ld4(su + (r + H) * UW + 4 * tx + H);
+      un[rr][0] = 2.f * uc.x - up[rr].x + rv[0];
+      un[rr][1] = 2.f * uc.y - up[rr].y + rv[1];
+      un[rr][2] = 2.f * uc.z - up[rr].z + rv[2];
+      un[rr][3] = 2.f * uc.w - up[rr].w + rv[3];
+      if (srcbox) {
+        const int di = z - i0;
+        if (di >= 0 && di < nb) {
+          const float amp = p.dt2 * stf_n;
 #pragma unroll
-  for (int k = 1; k <= N; k++) {
-    const float4 wp = ld4s(&sgz[ty + k + 3][4 * tx]);
-    const float4 wm = ld4s(&sgz[ty - k + 4][4 * tx]);
-    dz4.x += p.a[k - 1] * (wp.x - wm.x);
-    dz4.y += p.a[k - 1] * (wp.y - wm.y);
-    dz4.z += p.a[k - 1] * (wp.z - wm.z);
-    dz4.w += p.a[k - 1] * (wp.w - wm.w);
-  }
-  const float dzv[4] = {dz4.x * inv_dz, dz4.y * inv_dz, dz4.z * inv_dz, dz4.w * inv_dz};
-  const float4 lc = ld4s(&sl[ty + H][4 * tx + H]);
-  const float lcv[4] = {lc.x, lc.y, lc.z, lc.w};
-  const long long id0 = sh + (long long)z * pitch + xb;
-  const float4 lo = *reinterpret_cast<const float4*>(p.l_prev + id0);
-  const float lov[4] = {lo.x, lo.y, lo.z, lo.w};
-  const float4 gold = *reinterpret_cast<const float4*>(p.gpart + id0);
-  const float goldv[4] = {gold.x, gold.y, gold.z, gold.w};
-  const float4 imzu = ld4s(&simz[ty + 3][4 * tx]);
-  const float4 imzd = ld4s(&simz[ty + 4][4 * tx]);
-  const float imzuv[4] = {imzu.x, imzu.y, imzu.z, imzu.w};
-  const float imzdv[4] = {imzd.x, imzd.y, imzd.z, imzd.w};
-  float ln[4], gn[4];
-  const bool zin = z < g.Nz;
-#pragma unroll
-  for (int e = 0; e < 4; e++) {
-    float dxv = 0.f;
-#pragma unroll
-    for (int k = 1; k <= N; k++) dxv += p.a[k - 1] * (v[e + k + 3] - v[e - k + 4]);
-    dxv *= inv_dx;
-    const bool valid = zin && xb + e < g.Nx;
-    ln[e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[e]) : 0.f;
-    const float gi = 0.5f * (simx[ty][4 * tx + e + 3] + simx[ty][4 * tx + e + 4] + imzuv[e] + imzdv[e]);
-    gn[e] = valid ? goldv[e] + gi : 0.f;
-  }
-  // residual of the sample recorded from u^n (sample n-1)
-  if (p.n >= 1) {
-    const int t = blockIdx.y * g.ntx + blockIdx.x;
-    const int rb = p.tile_rec_start[t], re = p.tile_rec_start[t + 1];
-    for (int q = rb; q < re; q++) {
-      const int r = p.tile_rec[q];
-      const int ri = p.rec_cell[2 * r], rj = p.rec_cell[2 * r + 1];
-      const int d = rj - xb;
-      if (ri == z && d >= 0 && d < 4) {
-        const float rv = p.res[((long long)s * p.nrec + r) * p.nt + p.n - 1];
-#pragma unroll
-        for (int e = 0; e < 4; e++)
-          if (e == d) ln[e] += rv;
-      }
-    }
-  }
-  *reinterpret_cast<float4*>(p.l_prev + id0) = make_float4(ln[0], ln[1], ln[2], ln[3]);
-  *reinterpret_cast<float4*>(p.gpart + id0) = make_float4(gn[0], gn[1], gn[2], gn[3]);
-
-  // source-parameter partials from lambda_n (index n-1): sum w lambda,
-  // sum w lambda (x_i - x0), sum w lambda (z_i - z0); at most 4 tiles touch a box
-  if (p.src_part != nullptr && p.n >= 1) {
-    const int i0 = p.src_box[2 * s], j0 = p.src_box[2 * s + 1], nb = p.src_n;
-    if (i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0) {
-      float acc[3] = {0.f, 0.f, 0.f};
-      const int di = z - i0;
-      if (di >= 0 && di < nb) {
-        const float xs = p.x0[2 * s], zs = p.x0[2 * s + 1];
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-          const int dj = xb + e - j0;
-          if (dj >= 0 && dj < nb) {
-            const float wl = p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj] * ln[e];
-            acc[0] += wl;
-            acc[1] += wl * ((float)(xb + e - g.npml) * p.dx - xs);
-            acc[2] += wl * ((float)(z - g.npml) * p.dz - zs);
+          for (int e = 0; e < 4; e++) {
+            const int dj = xb + e - j0;
+            if (dj >= 0 && dj < nb) un[rr][e] += amp * p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj];
           }
         }
       }
-      cta_sum3(acc, red);
-      if (tid == 0) {
-        const int slot = 2 * (blockIdx.y - i0 / TILE_Z) + (blockIdx.x - j0 / TILE_X);
-        float* dst = p.src_part + (((long long)s * p.nt + (p.n - 1)) * SRC_SLOTS + slot) * 3;
-        dst[0] = acc[0];
-        dst[1] = acc[1];
-        dst[2] = acc[2];
+#pragma unroll
+      for (int e = 0; e < 4; e++)
+        if (!(z < g.Nz && xb + e < g.Nx)) un[rr][e] = 0.f;
+      st4(uprev + (long long)z * pitch + xb, make_float4(un[rr][0], un[rr][1], un[rr][2], un[rr][3]));
+    }
+    if (RECORD) {
+      // receivers of this thread's 2 x 4 cells: (index << 3) | (row << 2) | column
+      for (int q = rb; q < re; q++) {
+        const int code = p.thr_rec[q];
+        const int rc = code >> 3, rr = (code >> 2) & 1, e = code & 3;
+        const float* ur = un[rr];
+        p.seis[((long long)s * p.nrec + rc) * p.nt + p.n] = e == 0 ? ur[0] : (e == 1 ? ur[1] : (e == 2 ? ur[2] : ur[3]));
       }
     }
+    __syncthreads();  // the tile buffer and the flux arrays are free again
   }
 }
 
 // ---------------------------------------------------------------------------
-// Host-side launchers (called from fwi_capi.cu).
-cudaError_t launch_acu_fwd(const AcuStep& p, bool record, bool store, cudaStream_t st) {
-  dim3 grid(p.g.ntx, p.g.ntz, p.S);
+// Adjoint step n (reverse of forward step n, statement by statement; Z is kept
+// divided by dt^2):
+//   hhat = lambda_{n+1} + a (Z + lambda_{n+1}),  Z <- b (Z + lambda_{n+1})
+//   qbar = -dt^2 D+ hhat                         (= D-^T applied to dt^2 hhat)
+//   2 dJ/dm += qbar * p^n at both neighbours of each half point (gradient correlation)
+//   pbar = m_half qbar;  gbar = pbar + a_h (P + pbar),  P <- b_h (P + pbar)
+//   lambda_n = 2 lambda_{n+1} - lambda_{n+2} - D- gbar + residual(sample n-1)
+template <int N>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    acu_adj_step(const __grid_constant__ CUtensorMap tmap_l, const __grid_constant__ CUtensorMap tmap_m,
+                 const AcuStep p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  AdjSmem& sh = *reinterpret_cast<AdjSmem*>(smem_raw);
+  const Grid& g = p.g;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int pitch = g.pitch;
+
+  if (tid == 0) {
+    mbar_init(&sh.bar[0], 1);
+    mbar_init(&sh.bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0 && (int)blockIdx.x < p.ntiles)
+    fetch_tile(&tmap_l, &tmap_m, g, p.S, p.cur, blockIdx.x, sh.l[0], sh.m[0], &sh.bar[0]);
+
+  int it = 0;
+  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
+    const int b = it & 1;
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < p.ntiles)
+      fetch_tile(&tmap_l, &tmap_m, g, p.S, p.cur, tn, sh.l[b ^ 1], sh.m[b ^ 1], &sh.bar[b ^ 1]);
+    const TileId id = tile_of(g, t);
+    const int x0 = id.x0, z0 = id.z0, s = id.s;
+    const long long base = (long long)s * g.slice + g.off0;
+    float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
+    float* __restrict__ gp = p.gpart + base;
+    const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
+    float4 lo[2], go[2];
+    lo[0] = ldg4(lprev + (long long)zr0 * pitch + xb);
+    lo[1] = ldg4(lprev + (long long)(zr0 + 1) * pitch + xb);
+    go[0] = ldg4(gp + (long long)zr0 * pitch + xb);
+    go[1] = ldg4(gp + (long long)(zr0 + 1) * pitch + xb);
+    // stored fluxes p^n of this thread's own half points (x and z)
+    float4 pfx[2], pfz[2];
+    pfx[0] = ldg4(p.slot_px + base + (long long)zr0 * pitch + xb);
+    pfx[1] = ldg4(p.slot_px + base + (long long)(zr0 + 1) * pitch + xb);
+    pfz[0] = ldg4(p.slot_pz + base + (long long)zr0 * pitch + xb);
+    pfz[1] = ldg4(p.slot_pz + base + (long long)(zr0 + 1) * pitch + xb);
+    const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
+    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+    const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
+
+    const bool ok = mbar_wait(&sh.bar[b], (it >> 1) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      return;
+    }
+    const float* sl = sh.l[b];
+    const float* sm = sh.m[b];
+    const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
+
+    // ---- stage 1a: x half points of row r: qbar, correlation, gbar
+    auto x_item = [&](int r, int gq, bool own, bool image, const float4* pre) {
+      const int z = z0 + r, hb = x0 - 4 + 4 * gq;
+      float v[12];
+      unpack12(sl + (r + H) * UW + 4 * gq, v);
+      const long long id0 = base + (long long)z * pitch + hb;
+      if (pmlx) {
+        // hhat = lambda + a (Z + lambda) at the 12 integer points (a = 0 outside the layer)
+        float A[12], Z[12];
+        unpack12_g(p.ax + hb - 4 + TAB_OFF, A);
+        unpack12_g(p.zx_in + id0 - 4, Z);
+#pragma unroll
+        for (int t2 = 0; t2 < 12; t2++) v[t2] += A[t2] * (Z[t2] + v[t2]);
+      }
+      const float4 m4 = ld4(sm + (r + 4) * MW + 4 * gq);
+      const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
+      float pf[4] = {0.f, 0.f, 0.f, 0.f};
+      if (pre) f4a(*pre, pf);
+      else if (image) f4a(ldg4(p.slot_px + id0), pf);
+      const bool rowok = z < g.Nz;
+      float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
+      if (pmlx) a4 = ldg4(p.axh + hb + TAB_OFF);
+      const bool pon = a4.x != 0.f || a4.y != 0.f || a4.z != 0.f || a4.w != 0.f;
+      if (pon) {
+        b4 = ldg4(p.bxh + hb + TAB_OFF);
+        P4 = ld4(p.px_in + id0);
+      }
+      float av[4], bv[4], Pv[4];
+      f4a(a4, av);
+      f4a(b4, bv);
+      f4a(P4, Pv);
+      float gb[4], im[4], Pn[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        float dq = 0.f;
+#pragma unroll
+        for (int k = 1; k <= N; k++) dq += p.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
+        const bool inh = rowok && hb + e >= 0 && hb + e < g.Nx - 1;
+        const float qb = inh ? dq : 0.f;
+        const float pb = (mv[e] + mv[e + 1]) * qb;
+        const float tt = Pv[e] + pb;
+        gb[e] = inh ? pb + av[e] * tt : 0.f;
+        Pn[e] = av[e] != 0.f ? bv[e] * tt : 0.f;  // P stays zero outside the layer
+        im[e] = qb * pf[e];
+      }
+      if (pon && own && rowok) st4(p.px_out + id0, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
+      st4(sh.gx + r * QXW + 4 * gq, make_float4(gb[0], gb[1], gb[2], gb[3]));
+      st4(sh.imx + r * QXW + 4 * gq, make_float4(im[0], im[1], im[2], im[3]));
+    };
+    // hhat at integer row zz of 4 columns from the staged lambda and Z (CPML)
+    auto hhat_row = [&](float4 w, int zz, int xc) -> float4 {
+      if (pmlz) {
+        const float aa = __ldg(p.az + zz + TAB_OFF);
+        if (aa != 0.f) {
+          const float4 Z = *reinterpret_cast<const float4*>(p.zz_in + base + (long long)zz * pitch + xc);
+          w.x += aa * (Z.x + w.x); w.y += aa * (Z.y + w.y); w.z += aa * (Z.z + w.z); w.w += aa * (Z.w + w.w);
+        }
+      }
+      return w;
+    };
+    // ---- stage 1b: one z half row (the tile's halo rows)
+    auto z_item = [&](int hr, int c, bool image) {
+      const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 1; k <= N; k++)
+        acc4(acc, p.c1z[k - 1], hhat_row(ld4(sl + (hr + 4 + k) * UW + 8 + 4 * c), hz + k, xc),
+             hhat_row(ld4(sl + (hr + 5 - k) * UW + 8 + 4 * c), hz - k + 1, xc));
+      float dq[4];
+      f4a(acc, dq);
+      const bool hv = hz >= 0 && hz < g.Nz - 1;
+      const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
+      const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
+      const long long idz = base + (long long)hz * pitch + xc;
+      float pf[4] = {0.f, 0.f, 0.f, 0.f};
+      if (image) f4a(ldg4(p.slot_pz + idz), pf);
+      const float aa = pmlz ? __ldg(p.azh + hz + TAB_OFF) : 0.f;
+      float Pv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (aa != 0.f) f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
+      float gb[4], im[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const bool inh = hv && xc + e < g.Nx;
+        const float qb = inh ? dq[e] : 0.f;
+        const float pb = mhv[e] * qb;
+        gb[e] = inh ? pb + aa * (Pv[e] + pb) : 0.f;
+        im[e] = qb * pf[e];
+      }
+      st4(sh.gz + hr * TILE_X + 4 * c, make_float4(gb[0], gb[1], gb[2], gb[3]));
+      st4(sh.imz + hr * TILE_X + 4 * c, make_float4(im[0], im[1], im[2], im[3]));
+    };
+
+    x_item(2 * ty, tx + 1, true, true, &pfx[0]);
+    x_item(2 * ty + 1, tx + 1, true, true, &pfx[1]);
+    {
+      // own z half rows 2ty, 2ty+1 from a (2N+1)-row window of hhat
+      float4 w[2 * N + 1];
+#pragma unroll
+      for (int t2 = 0; t2 <= 2 * N; t2++)
+        w[t2] = hhat_row(ld4(sl + (2 * ty + H - N + 1 + t2) * UW + 8 + 4 * tx), zr0 - N + 1 + t2, xb);
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+#pragma unroll
+      for (int k = 1; k <= N; k++) {
+        acc4(a0, p.c1z[k - 1], w[k + N - 1], w[N - k]);
+        acc4(a1, p.c1z[k - 1], w[k + N], w[N - k + 1]);
+      }
+      float dq[2][4];
+      f4a(a0, dq[0]);
+      f4a(a1, dq[1]);
+#pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int hz = zr0 + rr;
+        const long long idz = base + (long long)hz * pitch + xb;
+        const bool hv = hz < g.Nz - 1;
+        const float4 ma = ld4(sm + (2 * ty + 4 + rr) * MW + 4 * tx + 4);
+        const float4 mb = ld4(sm + (2 * ty + 5 + rr) * MW + 4 * tx + 4);
+        const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
+        float pf[4];
+        f4a(pfz[rr], pf);
+        const float aa = pmlz ? __ldg(p.azh + hz + TAB_OFF) : 0.f;
+        float Pv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (aa != 0.f) f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
+        const float bb = aa != 0.f ? __ldg(p.bzh + hz + TAB_OFF) : 1.f;
+        float gb[4], im[4], Pn[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const bool inh = hv && xb + e < g.Nx;
+          const float qb = inh ? dq[rr][e] : 0.f;
+          const float pb = mhv[e] * qb;
+          const float tt = Pv[e] + pb;
+          gb[e] = inh ? pb + aa * tt : 0.f;
+          Pn[e] = inh ? bb * tt : 0.f;
+          im[e] = qb * pf[e];
+        }
+        if (aa != 0.f && hz < g.Nz) st4(p.pz_out + idz, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
+        st4(sh.gz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(gb[0], gb[1], gb[2], gb[3]));
+        st4(sh.imz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(im[0], im[1], im[2], im[3]));
+      }
+    }
+    if (tid < 128) {
+      const int hr0 = tid >> 4;
+      const int hr = hr0 < 4 ? hr0 : hr0 + 32;
+      z_item(hr, tid & 15, hr == 3);  // of the halo rows only half row z0-1 feeds this tile's gradient
+    } else if (tid < 192) {
+      const int k = tid - 128;
+      const bool left = (k & 1) == 0;
+      x_item(k >> 1, left ? 0 : QXW / 4 - 1, false, left, nullptr);  // only half column x0-1 feeds the gradient
+    }
+    __syncthreads();
+
+    // ---- stage 2: lambda_n, Z update, gradient, residual, source partials
+    float dzv[2][4];
+    {
+      float4 w[2 * N + 1];
+#pragma unroll
+      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sh.gz + (2 * ty + 4 - N + t2) * TILE_X + 4 * tx);
+      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+#pragma unroll
+      for (int k = 1; k <= N; k++) {
+        acc4(a0, p.c2z[k - 1], w[k + N - 1], w[N - k]);
+        acc4(a1, p.c2z[k - 1], w[k + N], w[N - k + 1]);
+      }
+      f4a(a0, dzv[0]);
+      f4a(a1, dzv[1]);
+    }
+    float imzv[3][4];
+    f4a(ld4(sh.imz + (2 * ty + 3) * TILE_X + 4 * tx), imzv[0]);
+    f4a(ld4(sh.imz + (2 * ty + 4) * TILE_X + 4 * tx), imzv[1]);
+    f4a(ld4(sh.imz + (2 * ty + 5) * TILE_X + 4 * tx), imzv[2]);
+    float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
+    if (pmlx) ax4 = ldg4(p.ax + xb + TAB_OFF);
+    const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
+    if (zx_on) bx4 = ldg4(p.bx + xb + TAB_OFF);
+    float lnew[2][4];
+#pragma unroll
+    for (int rr = 0; rr < 2; rr++) {
+      const int r = 2 * ty + rr, z = z0 + r;
+      const long long idc0 = base + (long long)z * pitch + xb;
+      float v[12];
+      unpack12(sh.gx + r * QXW + 4 * tx, v);
+      float ix8[8];
+      f4a(ld4(sh.imx + r * QXW + 4 * tx), ix8);
+      f4a(ld4(sh.imx + r * QXW + 4 * tx + 4), ix8 + 4);
+      float lcv[4], lov[4], gov[4];
+      const float4 lc4 = ld4(sl + (r + H) * UW + 4 * tx + H);
+      f4a(lc4, lcv);
+      f4a(lo[rr], lov);
+      f4a(go[rr], gov);
+      float gn[4];
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        float dxv = 0.f;
+#pragma unroll
+        for (int k = 1; k <= N; k++) dxv += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
+        const bool valid = z < g.Nz && xb + e < g.Nx;
+        lnew[rr][e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[rr][e]) : 0.f;
+        gn[e] = valid ? gov[e] + (ix8[e + 3] + ix8[e + 4] + imzv[rr][e] + imzv[rr + 1][e]) : 0.f;
+      }
+      // CPML Z (divided by dt^2) <- b (Z + lambda_{n+1}); zero outside the layer and the grid
+      if (zx_on) {
+        const float4 Zo = ld4(p.zx_in + idc0);
+        float4 Zn;
+        Zn.x = ax4.x != 0.f && z < g.Nz ? bx4.x * (Zo.x + lc4.x) : 0.f;
+        Zn.y = ax4.y != 0.f && z < g.Nz ? bx4.y * (Zo.y + lc4.y) : 0.f;
+        Zn.z = ax4.z != 0.f && z < g.Nz ? bx4.z * (Zo.z + lc4.z) : 0.f;
+        Zn.w = ax4.w != 0.f && z < g.Nz ? bx4.w * (Zo.w + lc4.w) : 0.f;
+        st4(p.zx_out + idc0, Zn);
+      }
+      if (pmlz) {
+        const float aa = __ldg(p.az + z + TAB_OFF);
+        if (aa != 0.f) {
+          const float bb = __ldg(p.bz + z + TAB_OFF);
+          const float4 Zo = ld4(p.zz_in + idc0);
+          float4 Zn;
+          Zn.x = xb + 0 < g.Nx ? bb * (Zo.x + lc4.x) : 0.f;
+          Zn.y = xb + 1 < g.Nx ? bb * (Zo.y + lc4.y) : 0.f;
+          Zn.z = xb + 2 < g.Nx ? bb * (Zo.z + lc4.z) : 0.f;
+          Zn.w = xb + 3 < g.Nx ? bb * (Zo.w + lc4.w) : 0.f;
+          st4(p.zz_out + idc0, Zn);
+        }
+      }
+      st4(gp + (long long)z * pitch + xb, make_float4(gn[0], gn[1], gn[2], gn[3]));
+    }
+    if (p.n >= 1) {
+      // residual of the sample recorded from u^n (sample n-1) at this thread's receivers
+      for (int q = rb; q < re; q++) {
+        const int code = p.thr_rec[q];
+        const int rc = code >> 3, rr = (code >> 2) & 1, e = code & 3;
+        const float rv = p.res[((long long)s * p.nrec + rc) * p.nt + p.n - 1];
+#pragma unroll
+        for (int r2 = 0; r2 < 2; r2++)
+#pragma unroll
+          for (int e2 = 0; e2 < 4; e2++)
+            if (r2 == rr && e2 == e) lnew[r2][e2] += rv;
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < 2; rr++)
+      st4(lprev + (long long)(zr0 + rr) * pitch + xb, make_float4(lnew[rr][0], lnew[rr][1], lnew[rr][2], lnew[rr][3]));
+    // source-parameter partials from lambda_n (index n-1): sum w lambda,
+    // sum w lambda (x_i - x0), sum w lambda (z_i - z0); at most 4 tiles touch a box
+    if (p.src_part != nullptr && p.n >= 1) {
+      const int i0 = box.x, j0 = box.y, nb = p.src_n;
+      if (i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0) {
+        float acc[3] = {0.f, 0.f, 0.f};
+        const float xs = p.x0[2 * s], zs = p.x0[2 * s + 1];
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          const int z = zr0 + rr, di = z - i0;
+          if (di >= 0 && di < nb) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const int dj = xb + e - j0;
+              if (dj >= 0 && dj < nb) {
+                const float wl = p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj] * lnew[rr][e];
+                acc[0] += wl;
+                acc[1] += wl * ((float)(xb + e - g.npml) * p.dx - xs);
+                acc[2] += wl * ((float)(z - g.npml) * p.dz - zs);
+              }
+            }
+          }
+        }
+        cta_sum3(acc, sh.red);
+        if (tid == 0) {
+          const int slot = 2 * (id.tz - i0 / TILE_Z) + (id.tx - j0 / TILE_X);
+          float* dst = p.src_part + (((long long)s * p.nt + (p.n - 1)) * SRC_SLOTS + slot) * 3;
+          dst[0] = acc[0];
+          dst[1] = acc[1];
+          dst[2] = acc[2];
+        }
+      }
+    }
+    __syncthreads();  // the tile buffer and the stage arrays are free again
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps, one-time kernel attributes, launchers.
+namespace {
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+bool encode(CUtensorMap* map, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+            const cuuint32_t* box) {
+  EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+std::mutex g_init_mu;
+unsigned long long g_inited = 0;  // bit per device
+int g_grid_fwd[64][2][3], g_grid_adj[64][2];
+
+template <typename K>
+cudaError_t setup_kernel(K k, int smem, int* grid) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, nb = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NTHREADS, smem)) != cudaSuccess) return e;
+  *grid = (nb < 1 ? 1 : nb) * nsm;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_init(int* dev_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  *dev_out = dev;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_init_mu);
+  if (g_inited & (1ull << dev)) return cudaSuccess;
+  const int fs = (int)sizeof(FwdSmem), as = (int)sizeof(AdjSmem);
+  if ((e = setup_kernel(acu_fwd_step<2, false, false>, fs, &g_grid_fwd[dev][0][0])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<2, true, false>, fs, &g_grid_fwd[dev][0][1])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<2, false, true>, fs, &g_grid_fwd[dev][0][2])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<4, false, false>, fs, &g_grid_fwd[dev][1][0])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<4, true, false>, fs, &g_grid_fwd[dev][1][1])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<4, false, true>, fs, &g_grid_fwd[dev][1][2])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_adj_step<2>, as, &g_grid_adj[dev][0])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_adj_step<4>, as, &g_grid_adj[dev][1])) != cudaSuccess) return e;
+  g_inited |= 1ull << dev;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t acu_kernels_init() {
+  int dev;
+  return ensure_init(&dev);
+}
+
+// TMA descriptors for a call: u and lam are [2][S][slice] pairs (lam may be
+// null), mh is one [slice] field.
+cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh) {
+  const cuuint64_t d3[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows, (cuuint64_t)(2 * S)};
+  const cuuint64_t s3[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.slice * 4};
+  const cuuint32_t b3[3] = {(cuuint32_t)UW, (cuuint32_t)UH, 1};
+  const cuuint64_t d2[2] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows};
+  const cuuint64_t s2[1] = {(cuuint64_t)g.pitch * 4};
+  const cuuint32_t b2[2] = {(cuuint32_t)MW, (cuuint32_t)MH};
+  if (!encode(&maps->u, u_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
+  if (!encode(&maps->m, const_cast<float*>(mh), 2, d2, s2, b2)) return cudaErrorInvalidValue;
+  if (lam_pair && !encode(&maps->lam, lam_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ensure_init(&dev);
+  if (e != cudaSuccess) return e;
+  const int v = record ? 1 : (store ? 2 : 0);
+  const int o = p.N == 2 ? 0 : 1;
+  const int grid = std::min(p.ntiles, g_grid_fwd[dev][o][v]);
+  const size_t smem = sizeof(FwdSmem);
   if (p.N == 2) {
-    if (record) acu_fwd_step<2, true, false><<<grid, NTHREADS, 0, st>>>(p);
-    else if (store) acu_fwd_step<2, false, true><<<grid, NTHREADS, 0, st>>>(p);
-    else acu_fwd_step<2, false, false><<<grid, NTHREADS, 0, st>>>(p);
+    if (record) acu_fwd_step<2, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    else if (store) acu_fwd_step<2, false, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    else acu_fwd_step<2, false, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
   } else {
-    if (record) acu_fwd_step<4, true, false><<<grid, NTHREADS, 0, st>>>(p);
-    else if (store) acu_fwd_step<4, false, true><<<grid, NTHREADS, 0, st>>>(p);
-    else acu_fwd_step<4, false, false><<<grid, NTHREADS, 0, st>>>(p);
+    if (record) acu_fwd_step<4, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    else if (store) acu_fwd_step<4, false, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    else acu_fwd_step<4, false, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_acu_adj(const AcuStep& p, cudaStream_t st) {
-  dim3 grid(p.g.ntx, p.g.ntz, p.S);
-  if (p.N == 2) acu_adj_step<2><<<grid, NTHREADS, sizeof(AdjSmem), st>>>(p);
-  else acu_adj_step<4><<<grid, NTHREADS, sizeof(AdjSmem), st>>>(p);
-  return cudaGetLastError();
-}
-
-// The adjoint step stages nine tiles (about 64 KB): opt in to more than the
-// default 48 KB of dynamic shared memory once per device.
-cudaError_t acu_kernels_init() {
-  cudaError_t e = cudaFuncSetAttribute(acu_adj_step<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(AdjSmem));
+cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ensure_init(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(acu_adj_step<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sizeof(AdjSmem));
+  const int grid = std::min(p.ntiles, g_grid_adj[dev][p.N == 2 ? 0 : 1]);
+  const size_t smem = sizeof(AdjSmem);
+  if (p.N == 2) acu_adj_step<2><<<grid, NTHREADS, smem, st>>>(maps.lam, maps.m, p);
+  else acu_adj_step<4><<<grid, NTHREADS, smem, st>>>(maps.lam, maps.m, p);
+  return cudaGetLastError();
 }
 
 }  // namespace fwi

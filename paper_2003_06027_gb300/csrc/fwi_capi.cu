@@ -19,17 +19,18 @@
 #include "fwi_internal.cuh"
 
 namespace fwi {
-cudaError_t launch_acu_fwd(const AcuStep& p, bool record, bool store, cudaStream_t st);
-cudaError_t launch_acu_adj(const AcuStep& p, cudaStream_t st);
+cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
+cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st);
 cudaError_t acu_kernels_init();
+cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh);
 cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st);
 cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
                                double vmax, double f0, float* a, float* b, float* ah, float* bh,
                                cudaStream_t st);
 cudaError_t launch_src_prep(int S, int kind, const float* x0, const Grid& g, float dx, float dz, int* box,
                             float* w, int* status, cudaStream_t st);
-cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* start,
-                           int* list, int* status, cudaStream_t st);
+cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* rec_key,
+                           int* start, int* cursor, int* list, int* status, cudaStream_t st);
 cudaError_t launch_model_check(const float* c, long long n, float coef, int* status, cudaStream_t st);
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
                           int* status, cudaStream_t st);
@@ -86,11 +87,13 @@ struct Plan {
   int tablen = 0;
   // base
   float *m = nullptr, *tab = nullptr, *c = nullptr, *stf = nullptr, *x0 = nullptr, *src_w = nullptr;
-  int *src_box = nullptr, *rec_in = nullptr, *rec_cell = nullptr, *tstart = nullptr, *tlist = nullptr;
-  float *u[2] = {}, *psix[2] = {}, *psiz[2] = {}, *zetx = nullptr, *zetz = nullptr, *seis = nullptr;
+  int *src_box = nullptr, *rec_in = nullptr, *rec_cell = nullptr, *rec_key = nullptr, *tstart = nullptr;
+  int *tcursor = nullptr, *tlist = nullptr;
+  float *u = nullptr;  // [2][S][slice]: pair of wavefield buffers
+  float *psix[2] = {}, *psiz[2] = {}, *zetx = nullptr, *zetz = nullptr, *seis = nullptr;
   int* status = nullptr;
   // gradient
-  float *res = nullptr, *ckpt = nullptr, *slot = nullptr, *lam[2] = {}, *zx[2] = {}, *zz[2] = {};
+  float *res = nullptr, *ckpt = nullptr, *slot = nullptr, *lam = nullptr, *zx[2] = {}, *zz[2] = {};
   float *px[2] = {}, *pz[2] = {}, *gpart = nullptr, *src_part = nullptr, *grad_c = nullptr;
   float *gstf = nullptr, *gx0 = nullptr;
   double *G = nullptr, *Jpart = nullptr, *J = nullptr;
@@ -119,19 +122,21 @@ void layout(Plan& P, char* base) {
   P.src_box = (int*)take((size_t)P.S * 2 * 4);
   P.rec_in = (int*)take((size_t)(P.nrec + 1) * 2 * 4);
   P.rec_cell = (int*)take((size_t)(P.nrec + 1) * 2 * 4);
-  P.tstart = (int*)take((size_t)(ntiles + 1) * 4);
+  P.rec_key = (int*)take((size_t)(P.nrec + 1) * 4);
+  P.tstart = (int*)take((size_t)(ntiles * NTHREADS + 1) * 4);
+  P.tcursor = (int*)take((size_t)(ntiles * NTHREADS + 1) * 4);
   P.tlist = (int*)take((size_t)(P.nrec + 1) * 4);
   P.seis = (float*)take((size_t)P.S * P.nrec * P.nt * 4 + 4);
   // fields zeroed on every call (initial conditions)
   off = (off + 255) & ~size_t(255);
   P.zero_lo = off;
-  for (int k = 0; k < 2; k++) P.u[k] = (float*)take(field);
+  P.u = (float*)take(2 * field);
   for (int k = 0; k < 2; k++) P.psix[k] = (float*)take(field);
   for (int k = 0; k < 2; k++) P.psiz[k] = (float*)take(field);
   P.zetx = (float*)take(field);
   P.zetz = (float*)take(field);
   if (P.grad) {
-    for (int k = 0; k < 2; k++) P.lam[k] = (float*)take(field);
+    P.lam = (float*)take(2 * field);
     for (int k = 0; k < 2; k++) P.zx[k] = (float*)take(field);
     for (int k = 0; k < 2; k++) P.zz[k] = (float*)take(field);
     for (int k = 0; k < 2; k++) P.px[k] = (float*)take(field);
@@ -150,7 +155,7 @@ void layout(Plan& P, char* base) {
     P.gstf = (float*)take((size_t)P.S * P.nt * 4);
     P.gx0 = (float*)take((size_t)P.S * 2 * 4);
     P.ckpt = (float*)take(field * 6 * (size_t)P.nseg);
-    P.slot = (float*)take(field * 3 * (size_t)P.K);
+    P.slot = (float*)take(field * 2 * (size_t)P.K);  // per step: p_x, p_z
   }
   P.bytes = (off + 255) & ~size_t(255);
 }
@@ -299,7 +304,8 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
   LK(1, launch_cpml_tables(g.nz, g.npml, g.Nz, L, M->dz, dt, M->pml_R, M->pml_vmax, M->pml_f0, T + 4 * L, T + 5 * L,
                         T + 6 * L, T + 7 * L, st));
   LK(1, launch_src_prep(P.S, P.kind, P.x0, g, M->dx, M->dz, P.src_box, P.src_w, P.status, st));
-  LK(1, launch_rec_csr(P.nrec, P.rec_in, P.rec_in + P.nrec, g, P.rec_cell, P.tstart, P.tlist, P.status, st));
+  LK(1, launch_rec_csr(P.nrec, P.rec_in, P.rec_in + P.nrec, g, P.rec_cell, P.rec_key, P.tstart, P.tcursor, P.tlist,
+                       P.status, st));
 
   memset(&p, 0, sizeof p);
   p.g = g;
@@ -307,11 +313,19 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
   p.N = P.N;
   p.nt = P.nt;
   p.nrec = P.nrec;
-  p.inv_dx = 1.f / M->dx;
-  p.inv_dz = 1.f / M->dz;
   p.dt2 = dt * dt;
-  for (int k = 0; k < 4; k++) p.a[k] = a[k];
-  p.m = P.m;
+  // forward weights: stage 1 a_k/dx (flux), stage 2 a_k dt^2/dx (dt^2 folded in)
+  for (int k = 0; k < 4; k++) {
+    p.c1x[k] = a[k] / M->dx;
+    p.c1z[k] = a[k] / M->dz;
+    p.c2x[k] = a[k] * p.dt2 / M->dx;
+    p.c2z[k] = a[k] * p.dt2 / M->dz;
+  }
+  p.ntiles = P.S * g.ntx * g.ntz;
+  p.mh = P.m;
+  p.u = P.u;
+  p.lam = P.lam;
+  p.status = P.status;
   p.ax = T; p.bx = T + L; p.axh = T + 2 * L; p.bxh = T + 3 * L;
   p.az = T + 4 * L; p.bz = T + 5 * L; p.azh = T + 6 * L; p.bzh = T + 7 * L;
   p.zetx = P.zetx;
@@ -320,8 +334,8 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
   p.src_w = P.src_w;
   p.src_n = P.kind == FWI_SRC_GAUSSIAN ? SRC_W : 1;
   p.stf = P.stf;
-  p.tile_rec_start = P.tstart;
-  p.tile_rec = P.tlist;
+  p.thr_rec_start = P.tstart;
+  p.thr_rec = P.tlist;
   p.rec_cell = P.rec_cell;
   p.seis = P.seis;
   p.x0 = P.x0;
@@ -331,10 +345,19 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
   return FWI_OK;
 }
 
+// Adjoint weights: stage 1 -a_k dt^2/dx (qbar = -dt^2 D+ hhat), stage 2 a_k/dx.
+void set_adjoint_weights(AcuStep& q, const AcuStep& fwd) {
+  for (int k = 0; k < 4; k++) {
+    q.c1x[k] = -fwd.c2x[k];
+    q.c1z[k] = -fwd.c2z[k];
+    q.c2x[k] = fwd.c1x[k];
+    q.c2z[k] = fwd.c1z[k];
+  }
+}
+
 void set_fwd_state(const Plan& P, AcuStep& p, int n) {
   p.n = n;
-  p.u_cur = P.u[n & 1];
-  p.u_prev = P.u[(n + 1) & 1];
+  p.cur = n & 1;
   p.psix_in = P.psix[n & 1];
   p.psix_out = P.psix[(n + 1) & 1];
   p.psiz_in = P.psiz[n & 1];
@@ -350,6 +373,7 @@ fwi_status finish_status(fwi_ctx* ctx, const Plan& P, cudaStream_t st) {
   if (s & 4) return fail(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
   if (s & 1) return fail(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
   if (s & 8) return fail(FWI_EUNSTABLE, "non-finite value in the seismograms or the misfit");
+  if (s & ST_TIMEOUT) return fail(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");
   return FWI_OK;
 }
 
@@ -427,11 +451,13 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   ctx->launches = 0;
   v = prepare(ctx, P, M, Sv, R, dt, st, p);
   if (v != FWI_OK) return v;
+  AcuMaps maps;
+  CK(acu_make_maps(&maps, P.g, P.S, P.u, nullptr, P.m));
   ensure_events(ctx, 0);
   CK(cudaEventRecord(ctx->ev[0], st));
   for (int n = 0; n < nt; n++) {
     set_fwd_state(P, p, n);
-    LK(1, launch_acu_fwd(p, true, false, st));
+    LK(1, launch_acu_fwd(p, maps, true, false, st));
   }
   CK(cudaEventRecord(ctx->ev[1], st));
   const long long ns = (long long)P.S * P.nrec * nt;
@@ -476,6 +502,8 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   const long long ns = (long long)P.S * P.nrec * nt;
   if (ns > 0) CK(cudaMemcpyAsync(P.res, observed, (size_t)ns * 4, cudaMemcpyDefault, st));
   const size_t field = (size_t)P.S * P.g.slice;
+  AcuMaps maps;
+  CK(acu_make_maps(&maps, P.g, P.S, P.u, P.lam, P.m));
   ensure_events(ctx, P.nseg);
 
   // forward sweep with a full-state checkpoint at the start of every segment
@@ -483,11 +511,12 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   for (int n = 0; n < nt; n++) {
     if (n % K == 0) {
       float* ck = P.ckpt + (size_t)(n / K) * 6 * field;
-      const float* src[6] = {P.u[n & 1], P.u[(n + 1) & 1], P.psix[n & 1], P.psiz[n & 1], P.zetx, P.zetz};
+      const float* src[6] = {P.u + (n & 1) * field, P.u + ((n + 1) & 1) * field, P.psix[n & 1], P.psiz[n & 1],
+                             P.zetx, P.zetz};
       for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(ck + f * field, src[f], field * 4, cudaMemcpyDeviceToDevice, st));
     }
     set_fwd_state(P, p, n);
-    LK(1, launch_acu_fwd(p, true, false, st));
+    LK(1, launch_acu_fwd(p, maps, true, false, st));
   }
   CK(cudaEventRecord(ctx->ev[1], st));
   if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
@@ -497,39 +526,37 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   p.res = P.res;
   p.gpart = P.gpart;
   p.src_part = P.src_part;
-  LK(1, launch_adj_init(p, P.lam[nt & 1], st));
+  AcuStep pa = p;
+  set_adjoint_weights(pa, p);
+  LK(1, launch_adj_init(pa, P.lam + (nt & 1) * field, st));
   for (int seg = P.nseg - 1; seg >= 0; seg--) {
     const int n0 = seg * K, n1 = std::min(nt, n0 + K);
     const float* ck = P.ckpt + (size_t)seg * 6 * field;
-    float* dst[6] = {P.u[n0 & 1], P.u[(n0 + 1) & 1], P.psix[n0 & 1], P.psiz[n0 & 1], P.zetx, P.zetz};
+    float* dst[6] = {P.u + (n0 & 1) * field, P.u + ((n0 + 1) & 1) * field, P.psix[n0 & 1], P.psiz[n0 & 1], P.zetx,
+                     P.zetz};
     for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(dst[f], ck + f * field, field * 4, cudaMemcpyDeviceToDevice, st));
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
     for (int n = n0; n < n1; n++) {
       set_fwd_state(P, p, n);
-      float* sl = P.slot + (size_t)(n - n0) * 3 * field;
-      p.slot_u = sl;
-      p.slot_psix = sl + field;
-      p.slot_psiz = sl + 2 * field;
-      LK(1, launch_acu_fwd(p, false, true, st));
+      p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
+      p.slot_pz = p.slot_px + field;
+      LK(1, launch_acu_fwd(p, maps, false, true, st));
     }
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
     for (int n = n1 - 1; n >= n0; n--) {
-      p.n = n;
-      float* sl = P.slot + (size_t)(n - n0) * 3 * field;
-      p.slot_u = sl;
-      p.slot_psix = sl + field;
-      p.slot_psiz = sl + 2 * field;
-      p.l_cur = P.lam[(n + 1) & 1];
-      p.l_prev = P.lam[n & 1];
-      p.zx_in = P.zx[(n + 1) & 1];
-      p.zx_out = P.zx[n & 1];
-      p.zz_in = P.zz[(n + 1) & 1];
-      p.zz_out = P.zz[n & 1];
-      p.px_in = P.px[(n + 1) & 1];
-      p.px_out = P.px[n & 1];
-      p.pz_in = P.pz[(n + 1) & 1];
-      p.pz_out = P.pz[n & 1];
-      LK(1, launch_acu_adj(p, st));
+      pa.n = n;
+      pa.cur = (n + 1) & 1;  // lambda_{n+1}; lambda_{n+2} -> lambda_n in the other buffer
+      pa.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
+      pa.slot_pz = pa.slot_px + field;
+      pa.zx_in = P.zx[(n + 1) & 1];
+      pa.zx_out = P.zx[n & 1];
+      pa.zz_in = P.zz[(n + 1) & 1];
+      pa.zz_out = P.zz[n & 1];
+      pa.px_in = P.px[(n + 1) & 1];
+      pa.px_out = P.px[n & 1];
+      pa.pz_in = P.pz[(n + 1) & 1];
+      pa.pz_out = P.pz[n & 1];
+      LK(1, launch_acu_adj(pa, maps, st));
     }
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
     LK(1, launch_fold(P.gpart, P.S, P.g.slice, P.G, st));

@@ -32,15 +32,16 @@
 #include "fwi_internal.cuh"
 
 namespace fwi {
-cudaError_t launch_acu_fwd(const AcuStep& p, bool record, bool store, cudaStream_t st);
+cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
+cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh);
 cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st);
 cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
                                double vmax, double f0, float* a, float* b, float* ah, float* bh,
                                cudaStream_t st);
 cudaError_t launch_src_prep(int S, int kind, const float* x0, const Grid& g, float dx, float dz, int* box,
                             float* w, int* status, cudaStream_t st);
-cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* start,
-                           int* list, int* status, cudaStream_t st);
+cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* rec_key,
+                           int* start, int* cursor, int* list, int* status, cudaStream_t st);
 cudaError_t launch_model_check(const float* c, long long n, float coef, int* status, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
 void set_last_error(const std::string& msg);
@@ -142,10 +143,12 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   const size_t field = (size_t)S * (size_t)g.slice * 4;
   const size_t o_status = take(64), o_m = take((size_t)g.slice * 4), o_tab = take((size_t)8 * tablen * 4);
   const size_t o_box = take((size_t)S * 2 * 4), o_w = take((size_t)S * SRC_W * SRC_W * 4);
-  const size_t o_rc = take((size_t)(nrec + 1) * 2 * 4), o_ts = take((size_t)(ntiles + 1) * 4);
+  const size_t o_rc = take((size_t)(nrec + 1) * 2 * 4), o_rk = take((size_t)(nrec + 1) * 4);
+  const size_t o_ts = take((size_t)(ntiles * NTHREADS + 1) * 4), o_tc = take((size_t)(ntiles * NTHREADS + 1) * 4);
   const size_t o_tl = take((size_t)(nrec + 1) * 4);
-  size_t o_f[8];
-  for (int k = 0; k < 8; k++) o_f[k] = take(field);
+  const size_t o_u = take(2 * field);  // wavefield pair, contiguous for its tensor map
+  size_t o_f[6];
+  for (int k = 0; k < 6; k++) o_f[k] = take(field);
   const size_t need = (off + 255) & ~size_t(255);
   if (need > NOALLOC_SCRATCH_BYTES)
     return err(FWI_EINVAL, "problem needs " + std::to_string(need) + " bytes of working memory; the fixed scratch of "
@@ -181,8 +184,8 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
                            T + 5 * tablen, T + 6 * tablen, T + 7 * tablen, st));
   NA_CK(launch_src_prep(S, Sv->kind, Sv->x0, g, M->dx, M->dz, (int*)(base + o_box), (float*)(base + o_w), status,
                         st));
-  NA_CK(launch_rec_csr(nrec, R->iz, R->ix, g, (int*)(base + o_rc), (int*)(base + o_ts), (int*)(base + o_tl),
-                       status, st));
+  NA_CK(launch_rec_csr(nrec, R->iz, R->ix, g, (int*)(base + o_rc), (int*)(base + o_rk), (int*)(base + o_ts),
+                       (int*)(base + o_tc), (int*)(base + o_tl), status, st));
 
   AcuStep p;
   memset(&p, 0, sizeof p);
@@ -191,38 +194,44 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   p.N = M->order / 2;
   p.nt = nt;
   p.nrec = nrec;
-  p.inv_dx = 1.f / M->dx;
-  p.inv_dz = 1.f / M->dz;
   p.dt2 = dt * dt;
-  for (int k = 0; k < 4; k++) p.a[k] = a[k];
-  p.m = (float*)(base + o_m);
+  for (int k = 0; k < 4; k++) {
+    p.c1x[k] = a[k] / M->dx;
+    p.c1z[k] = a[k] / M->dz;
+    p.c2x[k] = a[k] * p.dt2 / M->dx;
+    p.c2z[k] = a[k] * p.dt2 / M->dz;
+  }
+  p.ntiles = S * g.ntx * g.ntz;
+  p.status = status;
+  p.mh = (float*)(base + o_m);
   p.ax = T; p.bx = T + tablen; p.axh = T + 2 * tablen; p.bxh = T + 3 * tablen;
   p.az = T + 4 * tablen; p.bz = T + 5 * tablen; p.azh = T + 6 * tablen; p.bzh = T + 7 * tablen;
-  float* u[2] = {(float*)(base + o_f[0]), (float*)(base + o_f[1])};
-  float* psix[2] = {(float*)(base + o_f[2]), (float*)(base + o_f[3])};
-  float* psiz[2] = {(float*)(base + o_f[4]), (float*)(base + o_f[5])};
-  p.zetx = (float*)(base + o_f[6]);
-  p.zetz = (float*)(base + o_f[7]);
+  p.u = (float*)(base + o_u);
+  float* psix[2] = {(float*)(base + o_f[0]), (float*)(base + o_f[1])};
+  float* psiz[2] = {(float*)(base + o_f[2]), (float*)(base + o_f[3])};
+  p.zetx = (float*)(base + o_f[4]);
+  p.zetz = (float*)(base + o_f[5]);
   p.src_box = (int*)(base + o_box);
   p.src_w = (float*)(base + o_w);
   p.src_n = Sv->kind == FWI_SRC_GAUSSIAN ? SRC_W : 1;
   p.stf = Sv->stf;
-  p.tile_rec_start = (int*)(base + o_ts);
-  p.tile_rec = (int*)(base + o_tl);
+  p.thr_rec_start = (int*)(base + o_ts);
+  p.thr_rec = (int*)(base + o_tl);
   p.rec_cell = (int*)(base + o_rc);
   p.seis = seis;
   p.x0 = Sv->x0;
   p.dx = M->dx;
   p.dz = M->dz;
+  AcuMaps maps;
+  NA_CK(acu_make_maps(&maps, g, S, p.u, nullptr, p.mh));
   for (int n = 0; n < nt; n++) {
     p.n = n;
-    p.u_cur = u[n & 1];
-    p.u_prev = u[(n + 1) & 1];
+    p.cur = n & 1;
     p.psix_in = psix[n & 1];
     p.psix_out = psix[(n + 1) & 1];
     p.psiz_in = psiz[n & 1];
     p.psiz_out = psiz[(n + 1) & 1];
-    NA_CK(launch_acu_fwd(p, true, false, st));
+    NA_CK(launch_acu_fwd(p, maps, true, false, st));
   }
   const long long ns = (long long)S * nrec * nt;
   if (ns > 0) NA_CK(launch_finite_check(seis, ns, status, st));
@@ -234,6 +243,7 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   if (h_status & 4) return err(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
   if (h_status & 1) return err(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
   if (h_status & 8) return err(FWI_EUNSTABLE, "non-finite value in the seismograms");
+  if (h_status & ST_TIMEOUT) return err(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");
   set_last_error("");
   return FWI_OK;
 }

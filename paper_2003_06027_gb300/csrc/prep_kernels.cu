@@ -14,9 +14,9 @@
 
 namespace fwi {
 
-enum : int { ST_CFL = 1, ST_BADREC = 2, ST_BADSRC = 4, ST_NONFINITE = 8, ST_BADMODEL = 16 };
 
-// m = c^2 on the padded grid with the CPML filled by edge replication; every
+// m/2 = c^2/2 on the padded grid with the CPML filled by edge replication
+// (the half-point coefficient is then the sum of two neighbours); every
 // allocated cell is written (zero outside the padded grid).
 __global__ void k_pad_model_sq(const float* __restrict__ c, Grid g, float* __restrict__ m) {
   const long long total = (long long)g.rows * g.pitch;
@@ -28,7 +28,7 @@ __global__ void k_pad_model_sq(const float* __restrict__ c, Grid g, float* __res
     if (i >= 0 && i < g.Nz && j >= 0 && j < g.Nx) {
       const int ci = min(max(i - g.npml, 0), g.nz - 1), cj = min(max(j - g.npml, 0), g.nx - 1);
       const float cc = c[(long long)ci * g.nx + cj];
-      v = cc * cc;
+      v = 0.5f * cc * cc;
     }
     m[idx] = v;
   }
@@ -115,42 +115,72 @@ __global__ void k_src_prep(int S, int kind, const float* __restrict__ x0, Grid g
   }
 }
 
-// Receiver cells and per-tile receiver lists (one block). Receivers outside
-// the physical grid are flagged and never touched by the step kernels.
+// Receiver cells and receiver lists per owning thread (one block of 1024
+// threads). The step kernels give the 2 x 4 cells (rows 2ty..2ty+1, columns
+// 4tx..4tx+3) of a 64 x 32 tile to thread ty*16 + tx, so a receiver belongs to
+// key = (tile of one shot) * NTHREADS + thread; an entry packs the receiver
+// index with the row and column inside that thread's cells. Receivers outside
+// the physical grid are flagged and listed nowhere. Buckets are sorted by
+// receiver index, so the result does not depend on atomic ordering.
 __global__ void k_rec_csr(int nrec, const int* __restrict__ iz, const int* __restrict__ ix, Grid g,
-                          int* rec_cell, int* start, int* list, int* status) {
-  const int ntiles = g.ntx * g.ntz;
+                          int* rec_cell, int* rec_key, int* start, int* cursor, int* list, int* status) {
+  __shared__ int ssum[1024];
+  const int nkeys = g.ntx * g.ntz * NTHREADS;
+  for (int k = threadIdx.x; k <= nkeys; k += blockDim.x) start[k] = 0;
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) cursor[k] = 0;
+  __syncthreads();
   for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
     const int i = iz[r], j = ix[r];
     if (i >= 0 && i < g.nz && j >= 0 && j < g.nx) {
-      rec_cell[2 * r] = i + g.npml;
-      rec_cell[2 * r + 1] = j + g.npml;
+      const int pi = i + g.npml, pj = j + g.npml;
+      rec_cell[2 * r] = pi;
+      rec_cell[2 * r + 1] = pj;
+      const int lr = pi % TILE_Z, lc = pj % TILE_X;
+      const int key = ((pi / TILE_Z) * g.ntx + pj / TILE_X) * NTHREADS + (lr >> 1) * 16 + (lc >> 2);
+      rec_key[r] = key;
+      atomicAdd(&start[key + 1], 1);
     } else {
       rec_cell[2 * r] = -1;
       rec_cell[2 * r + 1] = -1;
+      rec_key[r] = -1;
       atomicOr(status, ST_BADREC);
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-    int cnt = 0;
-    for (int r = 0; r < nrec; r++) {
-      const int ri = rec_cell[2 * r], rj = rec_cell[2 * r + 1];
-      if (ri >= 0 && (ri / TILE_Z) * g.ntx + rj / TILE_X == t) cnt++;
-    }
-    start[t + 1] = cnt;
+  // inclusive scan of start[1..nkeys]: per-thread chunk sums, then a scan of the sums
+  const int chunk = (nkeys + blockDim.x - 1) / blockDim.x;
+  const int lo = 1 + threadIdx.x * chunk, hi = min(nkeys + 1, lo + chunk);
+  int acc = 0;
+  for (int k = lo; k < hi; k++) acc += start[k];
+  ssum[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int t = 1; t < (int)blockDim.x; t++) ssum[t] += ssum[t - 1];
+  __syncthreads();
+  int run = threadIdx.x == 0 ? 0 : ssum[threadIdx.x - 1];
+  for (int k = lo; k < hi; k++) {
+    run += start[k];
+    start[k] = run;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    start[0] = 0;
-    for (int t = 0; t < ntiles; t++) start[t + 1] += start[t];
+  for (int r = threadIdx.x; r < nrec; r += blockDim.x) {
+    const int key = rec_key[r];
+    if (key < 0) continue;
+    const int pi = rec_cell[2 * r], pj = rec_cell[2 * r + 1];
+    const int code = (r << 3) | (((pi % TILE_Z) & 1) << 2) | ((pj % TILE_X) & 3);
+    list[start[key] + atomicAdd(&cursor[key], 1)] = code;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-    int pos = start[t];
-    for (int r = 0; r < nrec; r++) {
-      const int ri = rec_cell[2 * r], rj = rec_cell[2 * r + 1];
-      if (ri >= 0 && (ri / TILE_Z) * g.ntx + rj / TILE_X == t) list[pos++] = r;
+  for (int k = threadIdx.x; k < nkeys; k += blockDim.x) {
+    const int b = start[k], e = start[k + 1];
+    for (int a = b + 1; a < e; a++) {  // insertion sort of a (tiny) bucket
+      const int v = list[a];
+      int q = a - 1;
+      while (q >= b && list[q] > v) {
+        list[q + 1] = list[q];
+        q--;
+      }
+      list[q + 1] = v;
     }
   }
 }
@@ -264,8 +294,10 @@ __global__ void k_fold(float* gpart, int S, long long slice, double* G) {
   }
 }
 
-// dJ/dc = 2 c dJ/dm, where dJ/dm of a physical cell also collects the CPML
-// cells that replicate it (transpose of the edge padding).
+// dJ/dc = 2 c dJ/dm = c G, where G holds 2 dJ/dm (the step kernels add each
+// half-point correlation to both neighbours without the factor 1/2) and a
+// physical cell also collects the CPML cells that replicate it (transpose of
+// the edge padding).
 __global__ void k_grad_c(const double* __restrict__ G, Grid g, const float* __restrict__ c,
                          float* grad) {
   const long long n = (long long)g.nz * g.nx;
@@ -279,7 +311,7 @@ __global__ void k_grad_c(const double* __restrict__ G, Grid g, const float* __re
     double acc = 0.0;
     for (int i = i_lo; i <= i_hi; i++)
       for (int j = j_lo; j <= j_hi; j++) acc += G[g.off0 + (long long)i * g.pitch + j];
-    grad[idx] = (float)(2.0 * (double)c[idx] * acc);
+    grad[idx] = (float)((double)c[idx] * acc);
   }
 }
 
@@ -341,9 +373,9 @@ cudaError_t launch_src_prep(int S, int kind, const float* x0, const Grid& g, flo
   k_src_prep<<<(S + 127) / 128, 128, 0, st>>>(S, kind, x0, g, dx, dz, box, w, status);
   return cudaGetLastError();
 }
-cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* start,
-                           int* list, int* status, cudaStream_t st) {
-  k_rec_csr<<<1, 1024, 0, st>>>(nrec, iz, ix, g, rec_cell, start, list, status);
+cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* rec_key,
+                           int* start, int* cursor, int* list, int* status, cudaStream_t st) {
+  k_rec_csr<<<1, 1024, 0, st>>>(nrec, iz, ix, g, rec_cell, rec_key, start, cursor, list, status);
   return cudaGetLastError();
 }
 cudaError_t launch_model_check(const float* c, long long n, float coef, int* status, cudaStream_t st) {

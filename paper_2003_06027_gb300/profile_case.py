@@ -1,0 +1,49 @@
+"""Small cases of the acoustic gradient for Nsight Compute captures.
+
+    python -m paper_2003_06027_gb300.profile_case --case fwi48-nt20
+
+Each case keeps the benchmark's grid and discretisation (201 x 601 + 32 CPML
+cells, 8th order) but few time steps, so a `--set full` capture of a handful of
+step-kernel launches ends quickly while each launch still touches more data
+than the 129 MB L2 (48 shots: ~40 MB per field).
+"""
+
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+CASES = {
+    # shots, time steps, checkpoint interval
+    "fwi48-nt20": (48, 20, 10),
+    "fwi16-nt20": (16, 20, 10),
+}
+
+
+def main():
+    import torch
+
+    from paper_2003_06027_gb300 import fwi, synth
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="fwi48-nt20", choices=sorted(CASES))
+    ap.add_argument("--repeat", type=int, default=2)
+    args = ap.parse_args()
+    S, nt, K = CASES[args.case]
+    d = synth.acoustic_fwi(nshots=S, nt=nt)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    kw = fwi.problem_kwargs(d)
+    c, stf, x0, iz, ix = cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
+    obs = fwi.forward(cu(d["c_true"]), stf, x0, iz, ix, **kw)
+    for _ in range(args.repeat):
+        J, g, _, _, _ = fwi.misfit_grad(c, stf, x0, iz, ix, obs, ckpt_every=K, **kw)
+    torch.cuda.synchronize()
+    t = fwi.last_timing()
+    print(f"case {args.case}: J = {float(J[0]):.6e}, |grad| = {float(g.norm()):.6e}, "
+          f"fwd {t.fwd_step_ms * 1e3:.1f} us, store {t.store_step_ms * 1e3:.1f} us, adj {t.adj_step_ms * 1e3:.1f} us "
+          f"per launch, {t.launches} launches")
+
+
+if __name__ == "__main__":
+    main()
