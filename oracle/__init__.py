@@ -63,17 +63,6 @@ class AcousticCfg(ctypes.Structure):
     ]
 
 
-class ElasticCfg(ctypes.Structure):
-    _fields_ = [
-        ("nz", ctypes.c_int), ("nx", ctypes.c_int), ("npml", ctypes.c_int),
-        ("order", ctypes.c_int), ("nt", ctypes.c_int), ("nshots", ctypes.c_int),
-        ("src_kind", ctypes.c_int), ("nrec", ctypes.c_int),
-        ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
-        ("pml_R", ctypes.c_double), ("pml_vmax", ctypes.c_double), ("pml_f0", ctypes.c_double),
-        ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
-    ]
-
-
 def _declare(L):
     P = ctypes.c_void_p
     L.or_fd_coeffs.argtypes = [ctypes.c_int, P]
@@ -90,14 +79,14 @@ def _declare(L):
     L.or_acoustic_adjoint.restype = ctypes.c_int
     L.or_num_threads.argtypes = []
     L.or_num_threads.restype = ctypes.c_int
-    if hasattr(L, "or_elastic_forward"):
-        for name in ("or_elastic_forward", "or_elastic_forward_cplx"):
-            f = getattr(L, name)
-            f.argtypes = [ctypes.POINTER(ElasticCfg), P, P, P, P, P, P, P]
-            f.restype = ctypes.c_int
-        L.or_elastic_adjoint.argtypes = [ctypes.POINTER(ElasticCfg), P, P, P, P, P, P, P,
-                                         P, P, P, P, P, P]
-        L.or_elastic_adjoint.restype = ctypes.c_int
+    for name in ("or_elastic_forward", "or_elastic_forward_cplx"):
+        f = getattr(L, name)
+        f.argtypes = [ctypes.POINTER(AcousticCfg), P, P, P, P, P, P, P]
+        f.restype = ctypes.c_int
+    L.or_elastic_snapshot.argtypes = [ctypes.POINTER(AcousticCfg), P, P, P, P, P, P, ctypes.c_int, P]
+    L.or_elastic_snapshot.restype = ctypes.c_int
+    L.or_elastic_adjoint.argtypes = [ctypes.POINTER(AcousticCfg)] + [P] * 12
+    L.or_elastic_adjoint.restype = ctypes.c_int
 
 
 def _ptr(a):
@@ -188,3 +177,62 @@ def acoustic_misfit_grad(g: dict, c, stf, x0, observed):
     J = 0.5 * float(np.sum(res * res))
     gc, gs, gx = acoustic_adjoint(g, c, stf, x0, res)
     return J, gc, gs, gx
+
+
+# ---------------------------------------------------------------- elastic
+def _el_inputs(vp, vs, rho, stf, x0, mt, dt_):
+    vp, vs, rho = (np.ascontiguousarray(a, dtype=dt_) for a in (vp, vs, rho))
+    stf = np.ascontiguousarray(np.atleast_2d(stf), dtype=dt_)
+    x0 = np.ascontiguousarray(np.reshape(x0, (-1, 2)), dtype=dt_)
+    mt = np.ascontiguousarray(np.reshape(mt, (-1, 3)), dtype=dt_)
+    assert x0.shape[0] == stf.shape[0] == mt.shape[0]
+    return vp, vs, rho, stf, x0, mt
+
+
+def elastic_forward(g: dict, vp, vs, rho, stf, x0, mt, complex_step: bool = False) -> np.ndarray:
+    """Seismograms [nshots][2][nrec][nt] (vx, vz of v^{n+1/2}) of the elastic
+    velocity-stress recursion with a moment-tensor source mt [nshots][3]."""
+    dt_ = np.complex128 if complex_step else np.float64
+    vp, vs, rho, stf, x0, mt = _el_inputs(vp, vs, rho, stf, x0, mt, dt_)
+    S = stf.shape[0]
+    geo = _Geom(AcousticCfg, g, S)
+    seis = np.zeros((S, 2, geo.cfg.nrec, g["nt"]), dtype=dt_)
+    f = lib().or_elastic_forward_cplx if complex_step else lib().or_elastic_forward
+    if f(ctypes.byref(geo.cfg), _ptr(vp), _ptr(vs), _ptr(rho), _ptr(stf), _ptr(x0), _ptr(mt), _ptr(seis)) != 0:
+        raise ValueError("oracle elastic forward: invalid configuration or source outside the grid")
+    return seis
+
+
+def elastic_snapshot(g: dict, vp, vs, rho, stf, x0, mt, step: int) -> np.ndarray:
+    """(vx, vz, sxx, szz, sxz) of shot 0 after `step` steps, [5][Nz][Nx]."""
+    vp, vs, rho, stf, x0, mt = _el_inputs(vp, vs, rho, stf, x0, mt, np.float64)
+    geo = _Geom(AcousticCfg, g, stf.shape[0])
+    Nz, Nx = g["nz"] + 2 * g["npml"], g["nx"] + 2 * g["npml"]
+    out = np.zeros((5, Nz, Nx))
+    if lib().or_elastic_snapshot(ctypes.byref(geo.cfg), _ptr(vp), _ptr(vs), _ptr(rho), _ptr(stf), _ptr(x0),
+                                 _ptr(mt), int(step), _ptr(out)) != 0:
+        raise ValueError("oracle elastic snapshot failed")
+    return out
+
+
+def elastic_adjoint(g: dict, vp, vs, rho, stf, x0, mt, res):
+    """(dJ/dlambda, dJ/dmu, dJ/drho, dJ/dstf, dJ/dx0) for residual res [S][2][nrec][nt]."""
+    vp, vs, rho, stf, x0, mt = _el_inputs(vp, vs, rho, stf, x0, mt, np.float64)
+    res = np.ascontiguousarray(res, dtype=np.float64)
+    S = stf.shape[0]
+    geo = _Geom(AcousticCfg, g, S)
+    assert res.shape == (S, 2, geo.cfg.nrec, g["nt"])
+    gl, gm, gr = (np.zeros((g["nz"], g["nx"])) for _ in range(3))
+    gs = np.zeros((S, g["nt"]))
+    gx = np.zeros((S, 2))
+    if lib().or_elastic_adjoint(ctypes.byref(geo.cfg), _ptr(vp), _ptr(vs), _ptr(rho), _ptr(stf), _ptr(x0),
+                                _ptr(mt), _ptr(res), _ptr(gl), _ptr(gm), _ptr(gr), _ptr(gs), _ptr(gx)) != 0:
+        raise ValueError("oracle elastic adjoint failed")
+    return gl, gm, gr, gs, gx
+
+
+def elastic_misfit_grad(g: dict, vp, vs, rho, stf, x0, mt, observed):
+    d = elastic_forward(g, vp, vs, rho, stf, x0, mt)
+    res = d - np.asarray(observed, dtype=np.float64)
+    J = 0.5 * float(np.sum(res * res))
+    return (J,) + elastic_adjoint(g, vp, vs, rho, stf, x0, mt, res)

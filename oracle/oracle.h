@@ -62,6 +62,23 @@ int or_acoustic_adjoint(const or_acoustic_cfg *cfg, const double *c,
                         const double *stf, const double *x0, const double *res,
                         double *grad_c, double *grad_stf, double *grad_x0);
 
+/* Elastic velocity-stress modelling (same geometry struct; src_kind 0 point,
+ * 1 Gaussian spatial weights). vp, vs, rho [nz][nx]; mt [nshots][3] =
+ * (Mxx, Mzz, Mxz); seis [nshots][2][nrec][nt] = (vx, vz) of v^{n+1/2}. */
+int or_elastic_forward(const or_acoustic_cfg *cfg, const double *vp, const double *vs, const double *rho,
+                       const double *stf, const double *x0, const double *mt, double *seis);
+int or_elastic_forward_cplx(const or_acoustic_cfg *cfg, const void *vp, const void *vs, const void *rho,
+                            const void *stf, const void *x0, const void *mt, void *seis);
+/* Fields (vx, vz, sxx, szz, sxz) of shot 0 after `step` steps, [5][Nz][Nx]. */
+int or_elastic_snapshot(const or_acoustic_cfg *cfg, const double *vp, const double *vs, const double *rho,
+                        const double *stf, const double *x0, const double *mt, int step, double *fields);
+/* Exact adjoint: gradients with respect to lambda, mu, rho (summed over
+ * shots), the source time function and x0, for a misfit whose derivative
+ * with respect to seis is res. Any output may be NULL. */
+int or_elastic_adjoint(const or_acoustic_cfg *cfg, const double *vp, const double *vs, const double *rho,
+                       const double *stf, const double *x0, const double *mt, const double *res, double *g_lam,
+                       double *g_mu, double *g_rho, double *g_stf, double *g_x0);
+
 int or_num_threads(void);
 
 #ifdef __cplusplus
