@@ -4,8 +4,9 @@
  * The library implements the hot path of the seismic-inversion method of
  * Zhu, Xu, Darve & Beroza, "A General Approach to Seismic Inversion with
  * Automatic Differentiation": explicit time stepping of the 2D acoustic wave
- * equation u_tt = div(c^2 grad u) + f (Implementation, Eq. acoustic) on a
- * staggered grid with convolutional PML, receiver sampling, the L2 misfit
+ * equation u_tt = div(c^2 grad u) + f (Implementation, Eq. acoustic) and of
+ * the 2D elastic velocity-stress system (Implementation, Eq. elastic) on
+ * staggered grids with convolutional PML, receiver sampling, the L2 misfit
  * J = 1/2 sum_k |U_k - U_k^obs|^2 (Method, after Eq. forward), and its exact
  * gradient by the adjoint recursion lambda_k = A^T lambda_{k+1} + (U_k - U_k^obs)
  * (Eq. adjoint-backward) with sum_k lambda_k^T (dA/dtheta) U_{k-1}
@@ -84,7 +85,11 @@ typedef struct {
  *       Function Retrieval); the 7 x 7 support must lie in the padded grid.
  * x0    [nshots][2] (x, z) in metres.
  * stf   [nshots][nt] source time function g(t_n), t_n = n dt.
- * mt    [nshots][3] moment tensor (Mxx, Mzz, Mxz) for FWI_SRC_MOMENT, else NULL. */
+ * mt    [nshots][3] moment tensor (Mxx, Mzz, Mxz): required for FWI_ELASTIC,
+ *       ignored for FWI_ACOUSTIC. Elastic sources inject sigma <- sigma -
+ *       dt M g(t_n) w into the stresses at step n (g is the moment rate), with
+ *       point or Gaussian weights w on the normal-stress grid and on the shear
+ *       grid (offset by half a cell); FWI_SRC_MOMENT means Gaussian weights. */
 typedef struct {
   int32_t nshots;
   int32_t kind;
@@ -93,7 +98,9 @@ typedef struct {
   const float *mt;
 } fwi_sources;
 
-/* Receivers, shared by all shots: physical cell indices iz[r], ix[r]. */
+/* Receivers, shared by all shots: physical cell indices iz[r], ix[r]. An
+ * elastic receiver records vx at (iz, ix+1/2) and vz at (iz+1/2, ix), the
+ * staggered velocity nodes of its cell. */
 typedef struct {
   int32_t nrec;
   const int32_t *iz, *ix;
@@ -106,22 +113,27 @@ fwi_status fwi_create(fwi_ctx **ctx, int device);
 /* Free the context and its workspace (waits for its device work). */
 fwi_status fwi_destroy(fwi_ctx *ctx);
 
-/* Forward modelling (Eq. forward): seis[s][r][n] = u^{n+1} at receiver r of
- * shot s, n = 0..nt-1, u^0 = u^{-1} = 0, source term dt^2 g(t_n) w at step n.
- * seis: [nshots][nrec][nt] FP32. */
+/* Forward modelling (Eq. forward).
+ * Acoustic: seis[s][r][n] = u^{n+1} at receiver r of shot s, n = 0..nt-1,
+ *   u^0 = u^{-1} = 0, source term dt^2 g(t_n) w at step n; seis [nshots][nrec][nt].
+ * Elastic: seis[s][c][r][n] = component c (0 vx, 1 vz) of v^{n+1/2} at receiver
+ *   r; v^{-1/2} = 0, sigma^0 = 0; seis [nshots][2][nrec][nt].
+ * FP32. */
 fwi_status fwi_forward(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
                        const fwi_receivers *rec, int32_t nt, float dt, float *seis,
                        void *cuda_stream);
 
 /* Misfit and exact gradient (Eqs. adjoint-backward and adjoint-gradient).
- * observed   [nshots][nrec][nt] FP32 observed seismograms.
+ * observed   FP32 observed seismograms, shaped like seis of fwi_forward.
  * ckpt_every wavefield checkpoint interval K (1..nt); the reverse sweep
  *            recomputes each K-step segment from its checkpoint.
  * misfit     J = 1/2 sum_{s,r,n} (seis - observed)^2, one double (host or device).
- * grad       [nz][nx] dJ/dc (acoustic), or NULL.
+ * grad       acoustic: [nz][nx] dJ/dc; elastic: [3][nz][nx] the partial
+ *            derivatives dJ/dlambda, dJ/dmu, dJ/drho (lambda = rho (vp^2 - 2 vs^2),
+ *            mu = rho vs^2, the paper's elastic inversion parameters); or NULL.
  * grad_stf   [nshots][nt] dJ/dg(t_n), or NULL.
  * grad_x0    [nshots][2] dJ/dx0 (Gaussian sources; zero for point sources), or NULL.
- * seis_out   [nshots][nrec][nt] the predicted seismograms, or NULL. */
+ * seis_out   the predicted seismograms (shaped like observed), or NULL. */
 fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
                            const fwi_receivers *rec, int32_t nt, float dt,
                            const float *observed, int32_t ckpt_every, double *misfit,

@@ -16,12 +16,14 @@
 #include <vector>
 
 #include "../../include/fwi.h"
+#include "fwi_host.h"
 #include "fwi_internal.cuh"
 
 namespace fwi {
 cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
 cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st);
 cudaError_t acu_kernels_init();
+cudaError_t ela_kernels_init();
 cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh);
 cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st);
 cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
@@ -38,8 +40,8 @@ cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaSt
 cudaError_t launch_adj_init(const AcuStep& p, float* lam, cudaStream_t st);
 cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st);
 cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st);
-cudaError_t launch_src_grad(const float* part, int S, int nt, double dt2, const float* stf, double inv_sig2,
-                            int kind, float* gstf, float* gx0, cudaStream_t st);
+cudaError_t launch_src_grad(const float* part, int S, int nt, int nslots, double scale, const float* stf,
+                            double inv_sig2, int kind, float* gstf, float* gx0, cudaStream_t st);
 void set_last_error(const std::string& msg);
 }  // namespace fwi
 
@@ -162,19 +164,6 @@ void layout(Plan& P, char* base) {
 
 }  // namespace
 
-struct fwi_ctx {
-  int device = 0;
-  char* arena = nullptr;
-  size_t arena_bytes = 0;
-  std::string layout_key;  // layout of the arena's current contents
-  int* h_status = nullptr;  // pinned
-  cudaEvent_t ev[4] = {};
-  std::vector<cudaEvent_t> seg_ev;
-  float phase_ms[3] = {0, 0, 0};
-  float kernel_ms[3] = {0, 0, 0};
-  int64_t launches = 0;
-};
-
 namespace {
 
 // LK: a checked kernel launch, counted (n kernels per launcher call)
@@ -247,34 +236,10 @@ std::string plan_key(const Plan& P) {
 
 fwi_status ensure_arena(fwi_ctx* ctx, Plan& P, cudaStream_t st) {
   layout(P, nullptr);
-  const std::string key = plan_key(P);
-  if (P.bytes > ctx->arena_bytes) {
-    if (ctx->arena) {
-      CK(cudaStreamSynchronize(st));
-      CK(cudaFree(ctx->arena));
-      ctx->arena = nullptr;
-      ctx->arena_bytes = 0;
-    }
-    void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, P.bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(FWI_ENOMEM, "cannot allocate " + std::to_string(P.bytes) + " bytes of workspace: " +
-                                  cudaGetErrorString(e));
-    }
-    ctx->arena = (char*)p;
-    ctx->arena_bytes = P.bytes;
-    ctx->layout_key.clear();
-  }
+  const std::string key = "acoustic " + plan_key(P);
+  fwi_status v = arena_acquire(ctx, P.bytes, key, P.zero_lo, P.zero_hi, st);
+  if (v != FWI_OK) return v;
   layout(P, ctx->arena);
-  if (ctx->layout_key != key) {
-    // new layout: every apron and every never-written cell must read as zero
-    CK(cudaMemsetAsync(ctx->arena, 0, P.bytes, st));
-    ctx->layout_key = key;
-  } else {
-    CK(cudaMemsetAsync(ctx->arena + P.zero_lo, 0, P.zero_hi - P.zero_lo, st));
-    CK(cudaMemsetAsync(P.status, 0, 64, st));
-  }
   return FWI_OK;
 }
 
@@ -364,20 +329,63 @@ void set_fwd_state(const Plan& P, AcuStep& p, int n) {
   p.psiz_out = P.psiz[(n + 1) & 1];
 }
 
-fwi_status finish_status(fwi_ctx* ctx, const Plan& P, cudaStream_t st) {
-  CK(cudaMemcpyAsync(ctx->h_status, P.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+fwi_status finish_status(fwi_ctx* ctx, const Plan& P, cudaStream_t st) { return finish_status_dev(ctx, P.status, st); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host helpers shared with the elastic orchestration (fwi_host.h)
+fwi_status fwi::host_fail(fwi_status st, const std::string& msg) { return fail(st, msg); }
+
+// Make the context arena at least `bytes` large. A new layout (key) zeroes the
+// whole arena (aprons and never-written cells must read as zero); the same
+// layout re-zeroes only [zero_lo, zero_hi) (the initial conditions) and the
+// status word at offset 0.
+fwi_status fwi::arena_acquire(fwi_ctx* ctx, size_t bytes, const std::string& key, size_t zero_lo, size_t zero_hi,
+                              cudaStream_t st) {
+  if (bytes > ctx->arena_bytes) {
+    if (ctx->arena) {
+      CK(cudaStreamSynchronize(st));
+      CK(cudaFree(ctx->arena));
+      ctx->arena = nullptr;
+      ctx->arena_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FWI_ENOMEM, "cannot allocate " + std::to_string(bytes) + " bytes of workspace: " +
+                                  cudaGetErrorString(e));
+    }
+    ctx->arena = (char*)p;
+    ctx->arena_bytes = bytes;
+    ctx->layout_key.clear();
+  }
+  if (ctx->layout_key != key) {
+    CK(cudaMemsetAsync(ctx->arena, 0, bytes, st));
+    ctx->layout_key = key;
+  } else {
+    CK(cudaMemsetAsync(ctx->arena + zero_lo, 0, zero_hi - zero_lo, st));
+    CK(cudaMemsetAsync(ctx->arena, 0, 64, st));
+  }
+  return FWI_OK;
+}
+
+// Read the device status word (one sync) and turn it into a status code.
+fwi_status fwi::finish_status_dev(fwi_ctx* ctx, const int* d_status, cudaStream_t st) {
+  CK(cudaMemcpyAsync(ctx->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int s = *ctx->h_status;
-  if (s & 16) return fail(FWI_EINVAL, "velocity model must be finite and > 0");
-  if (s & 2) return fail(FWI_EINVAL, "a receiver lies outside the physical grid");
-  if (s & 4) return fail(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
-  if (s & 1) return fail(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
-  if (s & 8) return fail(FWI_EUNSTABLE, "non-finite value in the seismograms or the misfit");
+  if (s & ST_BADMODEL) return fail(FWI_EINVAL, "the medium must be finite with vp > 0, rho > 0, vp^2 >= 2 vs^2");
+  if (s & ST_BADREC) return fail(FWI_EINVAL, "a receiver lies outside the physical grid");
+  if (s & ST_BADSRC) return fail(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
+  if (s & ST_CFL) return fail(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
+  if (s & ST_NONFINITE) return fail(FWI_EUNSTABLE, "non-finite value in the seismograms or the misfit");
   if (s & ST_TIMEOUT) return fail(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");
   return FWI_OK;
 }
 
-void ensure_events(fwi_ctx* ctx, size_t nseg) {
+void fwi::ensure_events(fwi_ctx* ctx, size_t nseg) {
   for (auto& e : ctx->ev)
     if (!e) cudaEventCreate(&e);
   while (ctx->seg_ev.size() < 4 * nseg) {
@@ -386,8 +394,6 @@ void ensure_events(fwi_ctx* ctx, size_t nseg) {
     ctx->seg_ev.push_back(e);
   }
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -399,6 +405,7 @@ fwi_status fwi_create(fwi_ctx** out, int device) {
   if (device < 0 || device >= n) return fail(FWI_EINVAL, "no such CUDA device");
   CK(cudaSetDevice(device));
   CK(acu_kernels_init());
+  CK(ela_kernels_init());
   fwi_ctx* c = new fwi_ctx();
   c->device = device;
   if (cudaMallocHost((void**)&c->h_status, 64) != cudaSuccess) {
@@ -438,6 +445,7 @@ fwi_status fwi_last_timing(const fwi_ctx* ctx, float* phase_ms3, float* kernel_m
 fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
                        int32_t nt, float dt, float* seis, void* stream) {
   if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (M && M->physics == FWI_ELASTIC) return ela_forward(ctx, M, Sv, R, nt, dt, seis, stream);
   fwi_status v = validate(M, Sv, R, nt, dt);
   if (v != FWI_OK) return v;
   if (!seis && R->nrec > 0) return fail(FWI_EINVAL, "seis must not be NULL");
@@ -484,6 +492,8 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
                            int32_t nt, float dt, const float* observed, int32_t K, double* misfit, float* grad,
                            float* grad_stf, float* grad_x0, float* seis_out, void* stream) {
   if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (M && M->physics == FWI_ELASTIC)
+    return ela_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, seis_out, stream);
   fwi_status v = validate(M, Sv, R, nt, dt);
   if (v != FWI_OK) return v;
   if (!observed && R->nrec > 0) return fail(FWI_EINVAL, "observed must not be NULL");
@@ -567,7 +577,7 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     CK(cudaMemcpyAsync(grad, P.grad_c, (size_t)P.g.nz * P.g.nx * 4, cudaMemcpyDefault, st));
   }
   if (grad_stf || grad_x0) {
-    LK(1, launch_src_grad(P.src_part, P.S, nt, (double)dt * dt, P.stf, 1.0 / (0.25 * (double)M->dx * M->dx), P.kind,
+    LK(1, launch_src_grad(P.src_part, P.S, nt, SRC_SLOTS, (double)dt * dt, P.stf, 1.0 / (0.25 * (double)M->dx * M->dx), P.kind,
                        P.gstf, P.gx0, st));
     if (grad_stf) CK(cudaMemcpyAsync(grad_stf, P.gstf, (size_t)P.S * nt * 4, cudaMemcpyDefault, st));
     if (grad_x0) CK(cudaMemcpyAsync(grad_x0, P.gx0, (size_t)P.S * 2 * 4, cudaMemcpyDefault, st));

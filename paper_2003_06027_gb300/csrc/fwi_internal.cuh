@@ -85,4 +85,41 @@ struct AcuStep {
   int* status;
 };
 
+// Everything one elastic step kernel needs (passed by value). Node sets on the
+// padded grid (index (i, j) of each field's storage): normal stresses and
+// lambda, lambda+2mu at (i, j); vx and bx at (i, j+1/2); vz and bz at
+// (i+1/2, j); sxz and mu_xz at (i+1/2, j+1/2).
+constexpr int ELA_SLOTS = 8;  // source partial slots: 4 tiles x (normal box, shear box)
+struct EleStep {
+  Grid g;
+  int S, N, n, nt, nrec;
+  float cx[4], cz[4];     // a_k/dx, a_k/dz
+  float dt;
+  const float *bx, *bz, *lam, *lp2m, *mxz;   // [slice] medium on the nodes (zero outside)
+  const float *ax, *bxt, *axh, *bxh, *az, *bzt, *azh, *bzh;  // CPML tables
+  // forward state ([S][slice] each)
+  float *vx, *vz, *sxx, *szz, *sxz;
+  float* psi[8];          // CPML memory variables, node-local, updated in place
+  // moment-tensor sources: boxes on the normal and shear grids
+  const int *box_n, *box_s;   // [S][2], -1 if invalid
+  const float *w_n, *w_s;     // [S][49]
+  int src_n;
+  const float* stf;           // [S][nt]
+  const float* mt;            // [S][3] (Mxx, Mzz, Mxz)
+  // receivers (vx, vz nodes of the receiver cell), per owning thread
+  const int *thr_rec_start, *thr_rec;
+  float* seis;                // [S][2][nrec][nt]
+  // forward values kept for the reverse sweep (STORE): fx, fz, ex, ez, exz
+  float* slot[5];
+  // adjoint state
+  float *Vx, *Vz, *Sxx, *Szz, *Sxz;
+  const float* Min[8];
+  float* Mout[8];
+  const float* res;           // [S][2][nrec][nt]
+  float *g_lam, *g_mu, *g_mxz, *g_bx, *g_bz;  // [S][slice] FP32 segment partials
+  float* src_part;            // [S][nt][ELA_SLOTS][3]
+  const float* x0;
+  float dx, dz;
+};
+
 }  // namespace fwi

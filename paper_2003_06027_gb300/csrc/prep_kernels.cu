@@ -315,26 +315,28 @@ __global__ void k_grad_c(const double* __restrict__ G, Grid g, const float* __re
   }
 }
 
-// dJ/dg(t_n) = dt^2 sum_i w_i lambda_{n+1}(i);  dJ/dx0 = sum_n g(t_n) dt^2
-// sum_i lambda_{n+1}(i) w_i (x_i - x0) / s^2 (Gaussian sources only).
-__global__ void k_src_grad(const float* __restrict__ part, int S, int nt, double dt2,
-                           const float* __restrict__ stf, double inv_sig2, int kind, float* gstf,
-                           float* gx0) {
+// Source-parameter gradients from the per-step partials (nslots per step,
+// each (sum w a, sum w a (x_i - x0), sum w a (z_i - z0)) of the adjoint field
+// a at the source support): dJ/dg(t_n) = scale * sum_slots part0, and for
+// Gaussian sources dJ/dx0 = sum_n g(t_n) scale sum_slots part1 / s^2 (z alike).
+// Acoustic: scale = dt^2 (a = lambda_{n+1}); elastic: scale = -dt (a = M : sigma-bar^{n+1}).
+__global__ void k_src_grad(const float* __restrict__ part, int S, int nt, int nslots, double scale,
+                           const float* __restrict__ stf, double inv_sig2, int kind, float* gstf, float* gx0) {
   __shared__ double sred[256 / 32][2];
   const int s = blockIdx.x;
   double ax = 0.0, az = 0.0;
   for (int n = threadIdx.x; n < nt; n += blockDim.x) {
-    const float* q = part + ((long long)s * nt + n) * SRC_SLOTS * 3;
+    const float* q = part + ((long long)s * nt + n) * nslots * 3;
     double w0 = 0.0, w1 = 0.0, w2 = 0.0;
-    for (int k = 0; k < SRC_SLOTS; k++) {
+    for (int k = 0; k < nslots; k++) {
       w0 += q[3 * k];
       w1 += q[3 * k + 1];
       w2 += q[3 * k + 2];
     }
-    if (gstf) gstf[(long long)s * nt + n] = (float)(dt2 * w0);
+    if (gstf) gstf[(long long)s * nt + n] = (float)(scale * w0);
     const double g = stf[(long long)s * nt + n];
-    ax += g * dt2 * w1 * inv_sig2;
-    az += g * dt2 * w2 * inv_sig2;
+    ax += g * scale * w1 * inv_sig2;
+    az += g * scale * w2 * inv_sig2;
   }
   for (int o = 16; o > 0; o >>= 1) {
     ax += __shfl_xor_sync(0xffffffffu, ax, o);
@@ -404,9 +406,9 @@ cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float*
   k_grad_c<<<304, 256, 0, st>>>(G, g, c, grad);
   return cudaGetLastError();
 }
-cudaError_t launch_src_grad(const float* part, int S, int nt, double dt2, const float* stf, double inv_sig2,
-                            int kind, float* gstf, float* gx0, cudaStream_t st) {
-  k_src_grad<<<S, 256, 0, st>>>(part, S, nt, dt2, stf, inv_sig2, kind, gstf, gx0);
+cudaError_t launch_src_grad(const float* part, int S, int nt, int nslots, double scale, const float* stf,
+                            double inv_sig2, int kind, float* gstf, float* gx0, cudaStream_t st) {
+  k_src_grad<<<S, 256, 0, st>>>(part, S, nt, nslots, scale, stf, inv_sig2, kind, gstf, gx0);
   return cudaGetLastError();
 }
 

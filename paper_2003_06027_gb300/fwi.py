@@ -251,6 +251,69 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
     return out["misfit"], out.get("grad"), out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
 
 
+class _ECall:
+    """Marshalled arguments of an elastic call."""
+
+    def __init__(self, vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax,
+                 pml_f0, src_kind):
+        self.vp, self.vs, self.rho = (_arr(a, np.float32) for a in (vp, vs, rho))
+        self.stf = _arr(stf, np.float32)
+        if self.stf.ndim == 1:
+            self.stf = self.stf.reshape(1, -1)
+        self.x0 = _arr(x0, np.float32).reshape(-1, 2)
+        self.mt = _arr(mt, np.float32).reshape(-1, 3)
+        self.iz = _arr(rec_iz, np.int32).reshape(-1)
+        self.ix = _arr(rec_ix, np.int32).reshape(-1)
+        nz, nx = self.vp.shape
+        self.S, self.nt = self.stf.shape
+        self.nrec = self.iz.shape[0]
+        self.model = _Model(FWI_ELASTIC, nz, nx, dz, dx, order, npml, pml_R, pml_vmax, pml_f0,
+                            _ptr(self.vp), _ptr(self.vs), _ptr(self.rho))
+        self.src = _Sources(self.S, src_kind, _ptr(self.x0), _ptr(self.stf), _ptr(self.mt))
+        self.rec = _Receivers(self.nrec, _ptr(self.iz), _ptr(self.ix))
+
+
+def forward_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20,
+                    pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_GAUSSIAN, out=None,
+                    stream=None, device=None):
+    """Elastic seismograms [nshots][2][nrec][nt] (vx, vz) (fwi_forward, FWI_ELASTIC)."""
+    a = _ECall(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0,
+               src_kind)
+    if out is None:
+        out = _empty_like_place(a.vp, (a.S, 2, a.nrec, a.nt))
+    dev = _device(a.vp, device)
+    _check(library().fwi_forward(context(dev), ctypes.byref(a.model), ctypes.byref(a.src),
+                                 ctypes.byref(a.rec), a.nt, float(dt), _ptr(out), _stream(a.vp, stream)))
+    return out
+
+
+def misfit_grad_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4,
+                        npml=20, pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_GAUSSIAN,
+                        ckpt_every=100, want_src=True, want_seis=False, out=None, stream=None,
+                        device=None):
+    """(J, [dJ/dlambda, dJ/dmu, dJ/drho] [3][nz][nx], dJ/dstf, dJ/dx0, seis) (fwi_misfit_grad, FWI_ELASTIC)."""
+    a = _ECall(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0,
+               src_kind)
+    obs = _arr(observed, np.float32)
+    out = dict(out or {})
+    ref = a.vp
+    nz, nx = a.vp.shape
+    out.setdefault("misfit", _empty_like_place(ref, (1,), np.float64))
+    out.setdefault("grad", _empty_like_place(ref, (3, nz, nx)))
+    if want_src:
+        out.setdefault("grad_stf", _empty_like_place(ref, (a.S, a.nt)))
+        out.setdefault("grad_x0", _empty_like_place(ref, (a.S, 2)))
+    if want_seis:
+        out.setdefault("seis", _empty_like_place(ref, (a.S, 2, a.nrec, a.nt)))
+    dev = _device(ref, device)
+    K = max(1, min(int(ckpt_every), a.nt))
+    _check(library().fwi_misfit_grad(
+        context(dev), ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
+        float(dt), _ptr(obs), K, _ptr(out["misfit"]), _ptr(out.get("grad")), _ptr(out.get("grad_stf")),
+        _ptr(out.get("grad_x0")), _ptr(out.get("seis")), _stream(ref, stream)))
+    return out["misfit"], out["grad"], out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
 def problem_kwargs(d: dict) -> dict:
     """Keyword arguments of forward()/misfit_grad() from a synth problem dict."""
     return dict(dx=d["dx"], dz=d["dz"], dt=d["dt"], order=d["order"], npml=d["npml"],

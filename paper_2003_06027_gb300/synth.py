@@ -152,3 +152,57 @@ def random_acoustic(seed: int, nz: int, nx: int, nt: int, nshots: int, order: in
         rec_iz=rng.integers(0, nz, nrec).astype(np.int32),
         rec_ix=rng.integers(0, nx, nrec).astype(np.int32), ckpt_every=max(1, nt // 4),
     )
+
+
+def double_couple(phi: np.ndarray) -> np.ndarray:
+    """2D double-couple moment tensors (Mxx, Mzz, Mxz) = (-sin 2phi, sin 2phi, cos 2phi)."""
+    return np.stack([-np.sin(2 * phi), np.sin(2 * phi), np.cos(2 * phi)], axis=1)
+
+
+MOMENT_SCALE = 1e12  # N m per unit moment-tensor entry: keeps seismograms O(0.1-1) m/s in FP32
+
+
+def elastic_layered(nshots: int = 32, nt: int = 4000, seed: int = 3) -> dict:
+    """300 x 800 elastic problem: dx = 5 m, dt = 0.5 ms, 4000 steps, 4th order,
+    32 CPML cells; seeded dipping layers (no faults) with vp 1800-4500 m/s,
+    vs = vp / 1.73, Gardner density; ``nshots`` Gaussian (sigma = dx/2)
+    moment-tensor sources at depths 400-1200 m with random double-couple
+    mechanisms and a 10 Hz Ricker moment rate; 200 receivers at iz = 2 every 4
+    cells recording vx and vz."""
+    nz, nx, dx, dt, f0 = 300, 800, 5.0, 0.5e-3, 10.0
+    vp = layered_model(seed, nz, nx, dx, vmin=1800.0, vmax=4500.0, n_faults=0)
+    vs = (vp / 1.73).astype(np.float32)
+    rho = gardner_density(vp)
+    rng = np.random.default_rng(seed + 100)
+    xs = rng.uniform(40, nx - 40, nshots) * dx
+    zs = rng.uniform(400.0, 1200.0, nshots)
+    mt = (double_couple(rng.uniform(0, np.pi, nshots)) * MOMENT_SCALE).astype(np.float32)
+    stf = np.tile(ricker(f0, dt, nt), (nshots, 1))
+    return dict(
+        name=f"elastic-300x800-o4-nt{nt}-{nshots}shots", nz=nz, nx=nx, dz=dx, dx=dx, dt=dt, nt=nt, order=4,
+        npml=32, pml_R=1e-5, pml_vmax=4500.0, pml_f0=f0, src_kind=1, vp=vp, vs=vs, rho=rho, stf=stf,
+        x0=np.stack([xs, zs], axis=1).astype(np.float32), mt=mt,
+        rec_iz=np.full(200, 2, dtype=np.int32), rec_ix=np.arange(0, 800, 4, dtype=np.int32), ckpt_every=100,
+    )
+
+
+def random_elastic(seed: int, nz: int, nx: int, nt: int, nshots: int, order: int, npml: int,
+                   src_kind: int = 1, nrec: int = 7, dx: float = 10.0, dt: float = 1e-3,
+                   f0: float = 15.0) -> dict:
+    """Small seeded heterogeneous elastic problem for parity tests."""
+    rng = np.random.default_rng(seed)
+    vp = smooth((2600.0 + 600.0 * rng.random((nz, nx))).astype(np.float32), 1.5)
+    vs = (vp / (1.6 + 0.3 * rng.random((nz, nx)))).astype(np.float32)
+    rho = (310.0 * vp.astype(np.float64) ** 0.25 * (1 + 0.1 * rng.random((nz, nx)))).astype(np.float32)
+    stf = np.stack([ricker(f0 * (1.0 + 0.2 * s), dt, nt) for s in range(nshots)])
+    margin = 0 if src_kind == 0 else max(0, 4 - npml)
+    xs = rng.uniform(margin, nx - 1 - margin, nshots) * dx
+    zs = rng.uniform(margin, nz - 1 - margin, nshots) * dx
+    mt = (rng.standard_normal((nshots, 3)) * MOMENT_SCALE).astype(np.float32)
+    return dict(
+        name=f"elastic-rand-{nz}x{nx}-o{order}-nt{nt}", nz=nz, nx=nx, dz=dx, dx=dx, dt=dt, nt=nt, order=order,
+        npml=npml, pml_R=1e-3, pml_vmax=4500.0, pml_f0=f0, src_kind=src_kind, vp=vp, vs=vs, rho=rho,
+        stf=stf.astype(np.float32), x0=np.stack([xs, zs], axis=1).astype(np.float32), mt=mt,
+        rec_iz=rng.integers(0, nz, nrec).astype(np.int32), rec_ix=rng.integers(0, nx, nrec).astype(np.int32),
+        ckpt_every=max(1, nt // 4),
+    )
