@@ -37,13 +37,12 @@ UNIT = "Gcell-steps/s"
 
 # Algorithmic HBM bytes per cell-step of each step kernel (FP32): every field
 # streamed once per step, halos assumed cached (kernel table).
-#   forward (recording):  read u^n, u^{n-1}, m; write u^{n+1}          16 B
-#   forward (storing):    + write u^n to the segment slot              20 B
-#   adjoint:              read lam_{n+1}, lam_{n+2}, m, u^n, g; write lam_n, g   28 B
-# plus, per cell inside an x- or z-CPML strip and per active axis:
-#   forward: psi read+write, zeta read+write = 16 B (+4 B psi to the slot when storing)
-#   adjoint: Z read+write, P read+write, stored psi read = 20 B
-BYTES = {"fwd": (16, 16), "store": (20, 20), "adj": (28, 20)}
+#   forward (recording):  read u^n, u^{n-1}, m; write u^{n+1}                         16 B
+#   forward (storing):    + write the fluxes p_x, p_z to the segment slot             24 B
+#   adjoint:              read lam_{n+1}, lam_{n+2}, m, p_x, p_z, g; write lam_n, g   32 B
+# plus, per cell inside an x- or z-CPML strip and per active axis, 16 B:
+#   forward psi and zeta read+write; adjoint Z and P read+write.
+BYTES = {"fwd": (16, 16), "store": (24, 16), "adj": (32, 16)}
 
 
 def padded(d):
@@ -141,6 +140,69 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def elastic_measure(steps):
+    """fwd+adjoint and forward throughput of the 300 x 800 elastic workload
+    (32 moment-tensor shots, 4000 steps, 4th order, checkpoint every 100)."""
+    import torch
+
+    from paper_2003_06027_gb300 import fwi, synth
+
+    d = synth.elastic_layered()
+    kw = fwi.problem_kwargs(d)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    args = [cu(d[k]) for k in ("vp", "vs", "rho", "stf", "x0", "mt", "rec_iz", "rec_ix")]
+    obs = fwi.forward_elastic(*args, **kw)
+    Nz, Nx = padded(d)
+    S, nt = d["stf"].shape
+    cs = S * Nz * Nx * nt
+    fwi.misfit_grad_elastic(*args, obs, ckpt_every=d["ckpt_every"], **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fwi.misfit_grad_elastic(*args, obs, ckpt_every=d["ckpt_every"], **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    t = fwi.last_timing()
+    e0.record()
+    for _ in range(steps):
+        fwi.forward_elastic(*args, out=obs, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    fms = e0.elapsed_time(e1) / steps
+    return {"workload": d["name"] + "-ckpt100", "value": cs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "forward": {"value": cs / (fms / 1e3) / 1e9, "ms_per_step": fms},
+            "cell_steps_per_step": cs, "step_launch_ms": {"fwd_vel+str": t.fwd_step_ms,
+                                                          "recompute_vel+str": t.store_step_ms,
+                                                          "adjoint_str+vel": t.adj_step_ms}}
+
+
+def acoustic_xl_measure(peak):
+    """Per-launch HBM bandwidth of the acoustic step kernels when one step's
+    working set (256 shots x 265 x 665 cells, ~1 GB per step) is far larger
+    than L2: the same discretisation as the headline workload, 300 steps."""
+    import torch
+
+    from paper_2003_06027_gb300 import fwi, synth
+
+    d = synth.acoustic_xl(nshots=256, nt=300)
+    kw = fwi.problem_kwargs(d)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    c, stf, x0, iz, ix = cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
+    obs = fwi.forward(c, stf, x0, iz, ix, **kw)
+    for _ in range(2):
+        fwi.misfit_grad(c, stf, x0, iz, ix, obs, ckpt_every=100, **kw)
+    torch.cuda.synchronize()
+    t = fwi.last_timing()
+    out = {"workload": d["name"] + "-ckpt100", "shots": 256, "nt": 300,
+           "working_set_per_step_MB": round(5 * 256 * (265 * 665) * 4 / 1e6)}
+    for k, ms in (("fwd", t.fwd_step_ms), ("store", t.store_step_ms), ("adj", t.adj_step_ms)):
+        gbs = launch_bytes(d, k) / (ms / 1e3) / 1e9
+        out[k] = {"avg_launch_ms": ms, "algorithmic_GBps": gbs, "frac": gbs / peak}
+    return out
 
 
 def dist_setup():
@@ -243,6 +305,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the elastic and 256-shot measurements")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -347,6 +410,9 @@ def main():
            "e2e": {"value": ws * cell_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "clocks": clocks}
+    if not args.no_extra:
+        res["elastic"] = elastic_measure(2)
+        res["acoustic_xl"] = acoustic_xl_measure(peak)
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
 

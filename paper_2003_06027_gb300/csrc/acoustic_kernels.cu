@@ -168,6 +168,7 @@ struct FwdSmem {
 struct AdjSmem {
   float l[2][UH * UW];
   float m[2][M_SLOT / 4];
+  float hz[UH * TILE_X];  // z-CPML tiles: lambda + a_z (Z_z + lambda) at the staged rows, own columns
   float gx[TILE_Z * QXW];
   float gz[QZH * TILE_X];
   float imx[TILE_Z * QXW];
@@ -510,6 +511,24 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const float* sl = sh.l[b];
     const float* sm = sh.m[b];
     const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
+    // z-direction hhat for the whole staged height: in z-CPML tiles it is
+    // formed once here (coalesced Z loads), elsewhere it is lambda itself
+    if (pmlz) {
+      for (int k = tid; k < UH * (TILE_X / 4); k += NTHREADS) {
+        const int row = k >> 4, c = k & 15;
+        const int zz = z0 - H + row;
+        float4 w = ld4(sl + row * UW + 8 + 4 * c);
+        const float aa = __ldg(p.az + zz + TAB_OFF);
+        if (aa != 0.f) {
+          const float4 Z = *reinterpret_cast<const float4*>(p.zz_in + base + (long long)zz * pitch + x0 + 4 * c);
+          w.x += aa * (Z.x + w.x); w.y += aa * (Z.y + w.y); w.z += aa * (Z.z + w.z); w.w += aa * (Z.w + w.w);
+        }
+        st4(sh.hz + row * TILE_X + 4 * c, w);
+      }
+      __syncthreads();
+    }
+    const float* hzb = pmlz ? sh.hz : sl + 8;  // element (row, own column c) at hzb[row * hzs + c]
+    const int hzs = pmlz ? TILE_X : UW;
 
     // ---- stage 1a: x half points of row r: qbar, correlation, gbar
     auto x_item = [&](int r, int gq, bool own, bool image, const float4* pre) {
@@ -560,25 +579,13 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       st4(sh.gx + r * QXW + 4 * gq, make_float4(gb[0], gb[1], gb[2], gb[3]));
       st4(sh.imx + r * QXW + 4 * gq, make_float4(im[0], im[1], im[2], im[3]));
     };
-    // hhat at integer row zz of 4 columns from the staged lambda and Z (CPML)
-    auto hhat_row = [&](float4 w, int zz, int xc) -> float4 {
-      if (pmlz) {
-        const float aa = __ldg(p.az + zz + TAB_OFF);
-        if (aa != 0.f) {
-          const float4 Z = *reinterpret_cast<const float4*>(p.zz_in + base + (long long)zz * pitch + xc);
-          w.x += aa * (Z.x + w.x); w.y += aa * (Z.y + w.y); w.z += aa * (Z.z + w.z); w.w += aa * (Z.w + w.w);
-        }
-      }
-      return w;
-    };
     // ---- stage 1b: one z half row (the tile's halo rows)
     auto z_item = [&](int hr, int c, bool image) {
       const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int k = 1; k <= N; k++)
-        acc4(acc, p.c1z[k - 1], hhat_row(ld4(sl + (hr + 4 + k) * UW + 8 + 4 * c), hz + k, xc),
-             hhat_row(ld4(sl + (hr + 5 - k) * UW + 8 + 4 * c), hz - k + 1, xc));
+        acc4(acc, p.c1z[k - 1], ld4(hzb + (hr + 4 + k) * hzs + 4 * c), ld4(hzb + (hr + 5 - k) * hzs + 4 * c));
       float dq[4];
       f4a(acc, dq);
       const bool hv = hz >= 0 && hz < g.Nz - 1;
@@ -609,8 +616,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       // own z half rows 2ty, 2ty+1 from a (2N+1)-row window of hhat
       float4 w[2 * N + 1];
 #pragma unroll
-      for (int t2 = 0; t2 <= 2 * N; t2++)
-        w[t2] = hhat_row(ld4(sl + (2 * ty + H - N + 1 + t2) * UW + 8 + 4 * tx), zr0 - N + 1 + t2, xb);
+      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(hzb + (2 * ty + H - N + 1 + t2) * hzs + 4 * tx);
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
 #pragma unroll
       for (int k = 1; k <= N; k++) {
