@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "fwi_internal.cuh"
+#include "tma.cuh"
 
 namespace fwi {
 
@@ -41,48 +42,6 @@ constexpr int QZH = TILE_Z + 8;          // 40: half rows [z0-4, z0+TZ+4)
 constexpr int U_BYTES = UW * UH * 4;     // 15360
 constexpr int M_BYTES = MW * MH * 4;     // 12464
 constexpr int M_SLOT = (M_BYTES + 127) / 128 * 128;
-constexpr long long WAIT_SPINS = 1LL << 24;
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: false if the phase did not complete within WAIT_SPINS polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < WAIT_SPINS; i++)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void tma_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -105,20 +64,6 @@ __device__ __forceinline__ void f4a(const float4 v, float o[4]) {
 // float4 stencil accumulation: acc += c (p - m)
 __device__ __forceinline__ void acc4(float4& acc, float c, const float4 p, const float4 m) {
   acc.x += c * (p.x - m.x); acc.y += c * (p.y - m.y); acc.z += c * (p.z - m.z); acc.w += c * (p.w - m.w);
-}
-
-struct TileId {
-  int s, x0, z0, tx, tz;
-};
-__device__ __forceinline__ TileId tile_of(const Grid& g, int t) {
-  TileId r;
-  r.tx = t % g.ntx;
-  const int q = t / g.ntx;
-  r.tz = q % g.ntz;
-  r.s = q / g.ntz;
-  r.x0 = r.tx * TILE_X;
-  r.z0 = r.tz * TILE_Z;
-  return r;
 }
 
 __device__ __forceinline__ bool tile_pml_x(const Grid& g, int x0) {
@@ -148,7 +93,7 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* red) {
 // Issue the TMA fetches of tile t into one buffer (one elected thread).
 __device__ __forceinline__ void fetch_tile(const CUtensorMap* fmap, const CUtensorMap* mmap, const Grid& g, int S,
                                            int pair, int t, float* dst_u, float* dst_m, uint64_t* bar) {
-  const TileId id = tile_of(g, t);
+  const TileId id = tile_decode(g, t);
   fence_proxy_async();
   mbar_expect_tx(bar, U_BYTES + M_BYTES);
   // allocation coordinates: padded (i, j) -> (i + APRON, j + APRON)
@@ -209,7 +154,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     const int tn = t + gridDim.x;
     if (tid == 0 && tn < p.ntiles)
       fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, tn, sh.u[b ^ 1], sh.m[b ^ 1], &sh.bar[b ^ 1]);
-    const TileId id = tile_of(g, t);
+    const TileId id = tile_decode(g, t);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
     float* __restrict__ uprev = p.u + (long long)(p.cur ^ 1) * p.S * g.slice + base;
@@ -230,7 +175,10 @@ __global__ void __launch_bounds__(NTHREADS, 3)
 
     const bool ok = mbar_wait(&sh.bar[b], (it >> 1) & 1);
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      if (tid == 0) {
+        atomicOr(p.status, ST_TIMEOUT);
+        tma_drain(sh.bar, it, tn < p.ntiles);
+      }
       return;
     }
     const float* su = sh.u[b];
@@ -482,7 +430,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const int tn = t + gridDim.x;
     if (tid == 0 && tn < p.ntiles)
       fetch_tile(&tmap_l, &tmap_m, g, p.S, p.cur, tn, sh.l[b ^ 1], sh.m[b ^ 1], &sh.bar[b ^ 1]);
-    const TileId id = tile_of(g, t);
+    const TileId id = tile_decode(g, t);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
     float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
@@ -505,7 +453,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 
     const bool ok = mbar_wait(&sh.bar[b], (it >> 1) & 1);
     if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      if (tid == 0) {
+        atomicOr(p.status, ST_TIMEOUT);
+        tma_drain(sh.bar, it, tn < p.ntiles);
+      }
       return;
     }
     const float* sl = sh.l[b];
@@ -797,35 +748,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 // Host side: tensor maps, one-time kernel attributes, launchers.
 namespace {
 
-typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encoder() {
-  static EncodeTiled fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiled>(f);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
-
-bool encode(CUtensorMap* map, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-            const cuuint32_t* box) {
-  EncodeTiled fn = encoder();
-  if (!fn) return false;
-  const cuuint32_t es[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
-}
-
 std::mutex g_init_mu;
 unsigned long long g_inited = 0;  // bit per device
 int g_grid_fwd[64][2][3], g_grid_adj[64][2];
@@ -879,9 +801,9 @@ cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, fl
   const cuuint64_t d2[2] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows};
   const cuuint64_t s2[1] = {(cuuint64_t)g.pitch * 4};
   const cuuint32_t b2[2] = {(cuuint32_t)MW, (cuuint32_t)MH};
-  if (!encode(&maps->u, u_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
-  if (!encode(&maps->m, const_cast<float*>(mh), 2, d2, s2, b2)) return cudaErrorInvalidValue;
-  if (lam_pair && !encode(&maps->lam, lam_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
+  if (!tma_host::encode(&maps->u, u_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
+  if (!tma_host::encode(&maps->m, const_cast<float*>(mh), 2, d2, s2, b2)) return cudaErrorInvalidValue;
+  if (lam_pair && !tma_host::encode(&maps->lam, lam_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 

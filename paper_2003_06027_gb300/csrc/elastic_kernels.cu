@@ -10,16 +10,22 @@
 // buoyancies (ela_str_adj, ela_vel_adj).
 //
 // Every update is a first-order staggered stencil (memory bound, no tensor
-// cores). One CTA owns a 64 x 32 tile of one shot; the fields it needs with a
-// halo are staged in shared memory with coalesced float4 loads; each thread
+// cores). Persistent CTAs walk the 64 x 32 tiles of all shots; the fields a
+// tile needs with a halo are fetched by TMA (cp.async.bulk.tensor, one box per
+// field) into one of two shared-memory buffers, so the next tile's fetch
+// overlaps the current tile's work (bounded mbarrier waits report a timeout);
+// per-node operands without a halo are loaded before the wait. Each thread
 // updates 2 rows x 4 columns. CPML memory variables are node-local in the
 // forward (updated in place) and double-buffered in the adjoint, where their
 // values are needed at halo nodes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "fwi_internal.cuh"
+#include "tma.cuh"
 
 namespace fwi {
 
@@ -187,22 +193,86 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* red) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Persistent-walk skeleton shared by the four kernels: buffer b of iteration it
+// holds tile t; the fetch of the next tile is issued before this one is used.
+#define ELA_WALK_BEGIN(FETCH)                                                      \
+  const int ntiles = p.S * g.ntx * g.ntz;                                        \
+  if (tid == 0) {                                                                \
+    mbar_init(&bar[0], 1);                                                       \
+    mbar_init(&bar[1], 1);                                                       \
+    fence_mbar_init();                                                           \
+  }                                                                              \
+  __syncthreads();                                                               \
+  if (tid == 0 && (int)blockIdx.x < ntiles) FETCH(blockIdx.x, 0);                \
+  int it = 0;                                                                    \
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {                   \
+    const int b = it & 1;                                                        \
+    if (tid == 0 && t + (int)gridDim.x < ntiles) FETCH(t + (int)gridDim.x, b ^ 1); \
+    const TileId id = tile_decode(g, t);                                         \
+    const int s = id.s, x0 = id.x0, z0 = id.z0;                                  \
+    const long long base = (long long)s * g.slice + g.off0;
+
+#define ELA_WAIT()                                          \
+  {                                                         \
+    const bool ok_ = mbar_wait(&bar[b], (it >> 1) & 1);     \
+    if (__syncthreads_or(!ok_)) {                           \
+      if (tid == 0) {                                       \
+        atomicOr(p.status, ST_TIMEOUT);                     \
+        tma_drain(bar, it, t + (int)gridDim.x < ntiles);    \
+      }                                                     \
+      return;                                               \
+    }                                                       \
+  }
+
+#define ELA_WALK_END() \
+  __syncthreads();     \
+  }
+
 // Velocity half step: v^{n+1/2} = v^{n-1/2} + dt b (div sigma^n + CPML).
+// Tile buffer: sxx rows [z0, z0+32) cols [x0-4, x0+68); szz rows [z0-4, z0+36)
+// cols [x0, x0+64); sxz rows [z0-4, z0+36) cols [x0-4, x0+68).
+constexpr int VEL_BUF = TILE_Z * W72 + H40 * TILE_X + H40 * W72;
 template <int N, bool RECORD, bool STORE>
-__global__ void __launch_bounds__(NTHREADS) ela_vel_step(const EleStep p) {
-  __shared__ __align__(16) float s_xx[TILE_Z * W72];  // rows [z0, z0+32), cols [x0-4, x0+68)
-  __shared__ __align__(16) float s_zz[H40 * TILE_X];  // rows [z0-4, z0+36), cols [x0, x0+64)
-  __shared__ __align__(16) float s_xz[H40 * W72];     // rows [z0-4, z0+36), cols [x0-4, x0+68)
+__global__ void __launch_bounds__(NTHREADS, 2)
+    ela_vel_step(const __grid_constant__ CUtensorMap m_xx, const __grid_constant__ CUtensorMap m_zz,
+                 const __grid_constant__ CUtensorMap m_xz, const EleStep p) {
+  extern __shared__ __align__(128) float smem_e[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_e + 2 * VEL_BUF);
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int s = blockIdx.z, x0 = blockIdx.x * TILE_X, z0 = blockIdx.y * TILE_Z;
-  const long long base = (long long)s * g.slice + g.off0;
   const int pitch = g.pitch;
-  stage<TILE_Z, W72>(s_xx, p.sxx + base, pitch, z0, x0 - 4);
-  stage<H40, TILE_X>(s_zz, p.szz + base, pitch, z0 - 4, x0);
-  stage<H40, W72>(s_xz, p.sxz + base, pitch, z0 - 4, x0 - 4);
-  __syncthreads();
-  const int xb = x0 + 4 * tx;
+  auto fetch = [&](int tt, int bb) {
+    const TileId f = tile_decode(g, tt);
+    float* d = smem_e + bb * VEL_BUF;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[bb], VEL_BUF * 4);
+    tma_3d(d, &m_xx, f.x0 - 4 + APRON, f.z0 + APRON, f.s, &bar[bb]);
+    tma_3d(d + TILE_Z * W72, &m_zz, f.x0 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    tma_3d(d + TILE_Z * W72 + H40 * TILE_X, &m_xz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+  };
+  ELA_WALK_BEGIN(fetch)
+  const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
+  // per-node operands of this thread's 2 x 4 nodes
+  float4 vo[2], wo[2], bxv[2], bzv[2];
+#pragma unroll
+  for (int rr = 0; rr < 2; rr++) {
+    const long long id = base + (long long)(zr0 + rr) * pitch + xb;
+    const long long im = g.off0 + (long long)(zr0 + rr) * pitch + xb;
+    vo[rr] = ld4(p.vx + id);
+    wo[rr] = ld4(p.vz + id);
+    bxv[rr] = ldg4(p.bx + im);
+    bzv[rr] = ldg4(p.bz + im);
+  }
+  int rb = 0, re = 0;
+  if (RECORD) {
+    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+    rb = __ldg(p.thr_rec_start + key);
+    re = __ldg(p.thr_rec_start + key + 1);
+  }
+  ELA_WAIT()
+  const float* s_xx = smem_e + b * VEL_BUF;
+  const float* s_zz = s_xx + TILE_Z * W72;
+  const float* s_xz = s_zz + H40 * TILE_X;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   float d2[2][4], d4[2][4];
   {
@@ -228,17 +298,17 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_step(const EleStep p) {
     cpml_z4(pz, p.az, p.bzt, z, p.psi[1], id, d2[rr]);
     cpml_x4(px, p.ax, p.bxt, xb, p.psi[2], id, d3);
     cpml_z4(pz, p.azh, p.bzh, z, p.psi[3], id, d4[rr]);
-    float fx[4], fz[4], bxv[4], bzv[4], vo[4], wo[4];
-    f4a(ldg4(p.bx + g.off0 + (long long)z * pitch + xb), bxv);
-    f4a(ldg4(p.bz + g.off0 + (long long)z * pitch + xb), bzv);
-    f4a(ld4(p.vx + id), vo);
-    f4a(ld4(p.vz + id), wo);
+    float fx[4], fz[4], bxa[4], bza[4], voa[4], woa[4];
+    f4a(bxv[rr], bxa);
+    f4a(bzv[rr], bza);
+    f4a(vo[rr], voa);
+    f4a(wo[rr], woa);
 #pragma unroll
     for (int e = 0; e < 4; e++) {
       fx[e] = d1[e] + d2[rr][e];
       fz[e] = d3[e] + d4[rr][e];
-      vxn[rr][e] = vo[e] + p.dt * bxv[e] * fx[e];  // buoyancy is zero outside the vx nodes
-      vzn[rr][e] = wo[e] + p.dt * bzv[e] * fz[e];
+      vxn[rr][e] = voa[e] + p.dt * bxa[e] * fx[e];  // buoyancy is zero outside the vx nodes
+      vzn[rr][e] = woa[e] + p.dt * bza[e] * fz[e];
     }
     st4(p.vx + id, a4f(vxn[rr]));
     st4(p.vz + id, a4f(vzn[rr]));
@@ -248,42 +318,62 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_step(const EleStep p) {
     }
   }
   if (RECORD) {
-    const int key = (blockIdx.y * g.ntx + blockIdx.x) * NTHREADS + tid;
-    const int rb = p.thr_rec_start[key], re = p.thr_rec_start[key + 1];
     for (int q = rb; q < re; q++) {
       const int code = p.thr_rec[q];
       const int rc = code >> 3, rr = (code >> 2) & 1, e = code & 3;
-      float a = 0.f, b = 0.f;
+      float va = 0.f, vb = 0.f;
 #pragma unroll
       for (int r2 = 0; r2 < 2; r2++)
 #pragma unroll
         for (int e2 = 0; e2 < 4; e2++)
           if (r2 == rr && e2 == e) {
-            a = vxn[r2][e2];
-            b = vzn[r2][e2];
+            va = vxn[r2][e2];
+            vb = vzn[r2][e2];
           }
       const long long o = ((long long)s * 2 * p.nrec + rc) * p.nt + p.n;
-      p.seis[o] = a;
-      p.seis[o + (long long)p.nrec * p.nt] = b;
+      p.seis[o] = va;
+      p.seis[o + (long long)p.nrec * p.nt] = vb;
     }
   }
+  ELA_WALK_END()
 }
 
 // ---------------------------------------------------------------------------
 // Stress half step: sigma^{n+1} = sigma^n + dt C (grad v^{n+1/2} + CPML) - dt M g_n w.
+// Tile buffer: vx and vz, rows [z0-4, z0+36), cols [x0-4, x0+68).
+constexpr int STR_BUF = 2 * H40 * W72;
 template <int N, bool STORE>
-__global__ void __launch_bounds__(NTHREADS) ela_str_step(const EleStep p) {
-  __shared__ __align__(16) float s_vx[H40 * W72];  // rows [z0-4, z0+36), cols [x0-4, x0+68)
-  __shared__ __align__(16) float s_vz[H40 * W72];
+__global__ void __launch_bounds__(NTHREADS, 2)
+    ela_str_step(const __grid_constant__ CUtensorMap m_vx, const __grid_constant__ CUtensorMap m_vz, const EleStep p) {
+  extern __shared__ __align__(128) float smem_e[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_e + 2 * STR_BUF);
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int s = blockIdx.z, x0 = blockIdx.x * TILE_X, z0 = blockIdx.y * TILE_Z;
-  const long long base = (long long)s * g.slice + g.off0;
   const int pitch = g.pitch;
-  stage<H40, W72>(s_vx, p.vx + base, pitch, z0 - 4, x0 - 4);
-  stage<H40, W72>(s_vz, p.vz + base, pitch, z0 - 4, x0 - 4);
-  __syncthreads();
-  const int xb = x0 + 4 * tx;
+  auto fetch = [&](int tt, int bb) {
+    const TileId f = tile_decode(g, tt);
+    float* d = smem_e + bb * STR_BUF;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[bb], STR_BUF * 4);
+    tma_3d(d, &m_vx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    tma_3d(d + H40 * W72, &m_vz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+  };
+  ELA_WALK_BEGIN(fetch)
+  const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
+  float4 so[2][3];
+#pragma unroll
+  for (int rr = 0; rr < 2; rr++) {
+    const long long id = base + (long long)(zr0 + rr) * pitch + xb;
+    so[rr][0] = ld4(p.sxx + id);
+    so[rr][1] = ld4(p.szz + id);
+    so[rr][2] = ld4(p.sxz + id);
+  }
+  const int2 bn = __ldg(reinterpret_cast<const int2*>(p.box_n) + s);
+  const int2 bs = __ldg(reinterpret_cast<const int2*>(p.box_s) + s);
+  const float g_n = __ldg(p.stf + (long long)s * p.nt + p.n);
+  ELA_WAIT()
+  const float* s_vx = smem_e + b * STR_BUF;
+  const float* s_vz = s_vx + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   float d6[2][4], d7[2][4];
   {
@@ -293,10 +383,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_step(const EleStep p) {
     load_win<N, W72>(s_vx, 2 * ty + 5 - N, 4 * tx + 4, W);  // vx rows around shear half rows
     zwin<N>(p.cz, W, d7[0], d7[1]);
   }
-  const int2 bn = __ldg(reinterpret_cast<const int2*>(p.box_n) + s);
-  const int2 bs = __ldg(reinterpret_cast<const int2*>(p.box_s) + s);
   const int nb = p.src_n;
-  const float g_n = p.stf[(long long)s * p.nt + p.n];
   const float Mxx = p.mt[3 * s], Mzz = p.mt[3 * s + 1], Mxz = p.mt[3 * s + 2];
 #pragma unroll
   for (int rr = 0; rr < 2; rr++) {
@@ -318,9 +405,9 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_step(const EleStep p) {
     f4a(ldg4(p.lam + im), la);
     f4a(ldg4(p.lp2m + im), lp);
     f4a(ldg4(p.mxz + im), mx);
-    f4a(ld4(p.sxx + id), sx);
-    f4a(ld4(p.szz + id), sz);
-    f4a(ld4(p.sxz + id), sh);
+    f4a(so[rr][0], sx);
+    f4a(so[rr][1], sz);
+    f4a(so[rr][2], sh);
 #pragma unroll
     for (int e = 0; e < 4; e++) {
       exz[e] = d7[rr][e] + d8[e];
@@ -358,6 +445,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_step(const EleStep p) {
       st4(p.slot[4] + id, a4f(exz));
     }
   }
+  ELA_WALK_END()
 }
 
 // ---------------------------------------------------------------------------
@@ -366,32 +454,52 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_step(const EleStep p) {
 // v^{n+1/2}), adds the residual of sample n, updates the memory adjoints
 // M5..M8 and accumulates the lambda, mu and mu_xz correlations and the
 // source-parameter partials of step n.
+constexpr int ADJA_BUF = 3 * H40 * W72;  // Sbar xx, zz, xz: rows [z0-4, z0+36), cols [x0-4, x0+68)
+constexpr int ADJA_SCR = 2 * TILE_Z * W72 + 2 * H40 * TILE_X + 32;
 template <int N>
-__global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
-  extern __shared__ __align__(16) float smem_e[];
-  float* s_Sxx = smem_e;                      // [H40][W72] rows [z0-4,..), cols [x0-4,..)
-  float* s_Szz = s_Sxx + H40 * W72;
-  float* s_Sxz = s_Szz + H40 * W72;
-  float* d_vx = s_Sxz + H40 * W72;            // [TILE_Z][W72] normal nodes, own rows
+__global__ void __launch_bounds__(NTHREADS, 2)
+    ela_str_adj(const __grid_constant__ CUtensorMap m_Sxx, const __grid_constant__ CUtensorMap m_Szz,
+                const __grid_constant__ CUtensorMap m_Sxz, const EleStep p) {
+  extern __shared__ __align__(128) float smem_e[];
+  float* d_vx = smem_e + 2 * ADJA_BUF;        // [TILE_Z][W72] normal nodes, own rows
   float* d_vz = d_vx + TILE_Z * W72;          // [H40][TILE_X] normal nodes, own cols
   float* d_vxz = d_vz + H40 * TILE_X;         // [H40][TILE_X] shear nodes, own cols
   float* d_vzx = d_vxz + H40 * TILE_X;        // [TILE_Z][W72] shear nodes, own rows
   float* red = d_vzx + TILE_Z * W72;          // [32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + 32);
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int s = blockIdx.z, x0 = blockIdx.x * TILE_X, z0 = blockIdx.y * TILE_Z;
-  const long long base = (long long)s * g.slice + g.off0;
   const int pitch = g.pitch;
-  stage<H40, W72>(s_Sxx, p.Sxx + base, pitch, z0 - 4, x0 - 4);
-  stage<H40, W72>(s_Szz, p.Szz + base, pitch, z0 - 4, x0 - 4);
-  stage<H40, W72>(s_Sxz, p.Sxz + base, pitch, z0 - 4, x0 - 4);
-  __syncthreads();
+  auto fetch = [&](int tt, int bb) {
+    const TileId f = tile_decode(g, tt);
+    float* d = smem_e + bb * ADJA_BUF;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[bb], ADJA_BUF * 4);
+    tma_3d(d, &m_Sxx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    tma_3d(d + H40 * W72, &m_Szz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    tma_3d(d + 2 * H40 * W72, &m_Sxz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+  };
+  ELA_WALK_BEGIN(fetch)
+  const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
+  float4 vpre[2][2];
+#pragma unroll
+  for (int rr = 0; rr < 2; rr++) {
+    const long long id = base + (long long)(zr0 + rr) * pitch + xb;
+    vpre[rr][0] = ld4(p.Vx + id);
+    vpre[rr][1] = ld4(p.Vz + id);
+  }
+  const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+  const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
+  ELA_WAIT()
+  const float* s_Sxx = smem_e + b * ADJA_BUF;
+  const float* s_Szz = s_Sxx + H40 * W72;
+  const float* s_Sxz = s_Szz + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
   constexpr int NA = TILE_Z * (W72 / 4), NB = H40 * (TILE_X / 4);
-  for (int it = tid; it < 2 * NA + 2 * NB; it += NTHREADS) {
-    if (it < NA) {  // (a) strain-x adjoint at normal nodes, own rows, columns [x0-4, x0+68)
-      const int r = it / (W72 / 4), gq = it - r * (W72 / 4);
+  for (int k4 = tid; k4 < 2 * NA + 2 * NB; k4 += NTHREADS) {
+    if (k4 < NA) {  // (a) strain-x adjoint at normal nodes, own rows, columns [x0-4, x0+68)
+      const int r = k4 / (W72 / 4), gq = k4 - r * (W72 / 4);
       const int z = z0 + r, j = x0 - 4 + 4 * gq;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float sx[4], sz[4], la[4], lp[4], t[4], d[4];
@@ -403,8 +511,8 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
       for (int e = 0; e < 4; e++) t[e] = dt * (lp[e] * sx[e] + la[e] * sz[e]);
       cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[4], p.Mout[4], id, gq >= 1 && gq <= 16, t, d);
       st4(d_vx + r * W72 + 4 * gq, a4f(d));
-    } else if (it < NA + NB) {  // (b) strain-z adjoint at normal nodes, rows [z0-4, z0+36), own cols
-      const int k = it - NA, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    } else if (k4 < NA + NB) {  // (b) strain-z adjoint at normal nodes, rows [z0-4, z0+36), own cols
+      const int k = k4 - NA, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
       const int z = z0 - 4 + hr, j = x0 + 4 * c;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float sx[4], sz[4], la[4], lp[4], t[4], d[4];
@@ -416,8 +524,8 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
       for (int e = 0; e < 4; e++) t[e] = dt * (la[e] * sx[e] + lp[e] * sz[e]);
       cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[5], p.Mout[5], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
       st4(d_vz + hr * TILE_X + 4 * c, a4f(d));
-    } else if (it < NA + 2 * NB) {  // (c) shear strain adjoint (z part) at shear nodes, all rows, own cols
-      const int k = it - NA - NB, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    } else if (k4 < NA + 2 * NB) {  // (c) shear strain adjoint (z part) at shear nodes, all rows, own cols
+      const int k = k4 - NA - NB, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
       const int z = z0 - 4 + hr, j = x0 + 4 * c;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float sh[4], mx[4], t[4], d[4];
@@ -428,7 +536,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
       cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[6], p.Mout[6], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
       st4(d_vxz + hr * TILE_X + 4 * c, a4f(d));
     } else {  // (d) shear strain adjoint (x part) at shear nodes, own rows, columns [x0-4, x0+68)
-      const int k = it - NA - 2 * NB, r = k / (W72 / 4), gq = k - r * (W72 / 4);
+      const int k = k4 - NA - 2 * NB, r = k / (W72 / 4), gq = k - r * (W72 / 4);
       const int z = z0 + r, j = x0 - 4 + 4 * gq;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float sh[4], mx[4], t[4], d[4];
@@ -441,7 +549,6 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
     }
   }
   __syncthreads();
-  const int xb = x0 + 4 * tx;
   float zx[2][4], zz[2][4];
   {
     float4 W[2 * N + 1];
@@ -456,8 +563,8 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
     const int r = 2 * ty + rr, z = z0 + r;
     const long long id = base + (long long)z * pitch + xb;
     float v[12], vxb[4], vzb[4];
-    f4a(ld4(p.Vx + id), vxb);
-    f4a(ld4(p.Vz + id), vzb);
+    f4a(vpre[rr][0], vxb);
+    f4a(vpre[rr][1], vzb);
     seg12(d_vx + r * W72 + 4 * tx, v);
 #pragma unroll
     for (int e = 0; e < 4; e++) vxb[e] -= plus12<N>(p.cx, v, e) + zx[rr][e];
@@ -470,8 +577,6 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
       if (!(z < g.Nz - 1 && xb + e < g.Nx)) vzb[e] = 0.f;
     }
     // residual of sample n at this thread's receivers
-    const int key = (blockIdx.y * g.ntx + blockIdx.x) * NTHREADS + tid;
-    const int rb = p.thr_rec_start[key], re = p.thr_rec_start[key + 1];
     for (int q = rb; q < re; q++) {
       const int code = p.thr_rec[q];
       if (((code >> 2) & 1) != rr) continue;
@@ -540,7 +645,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
       }
       cta_sum3(acc, red);
       if (tid == 0) {
-        const int slot = 4 * which + 2 * ((int)blockIdx.y - bx2.x / TILE_Z) + ((int)blockIdx.x - bx2.y / TILE_X);
+        const int slot = 4 * which + 2 * (id.tz - bx2.x / TILE_Z) + (id.tx - bx2.y / TILE_X);
         float* dst = p.src_part + (((long long)s * p.nt + p.n) * ELA_SLOTS + slot) * 3;
         dst[0] = acc[0];
         dst[1] = acc[1];
@@ -548,6 +653,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
       }
     }
   }
+  ELA_WALK_END()
 }
 
 // ---------------------------------------------------------------------------
@@ -555,29 +661,47 @@ __global__ void __launch_bounds__(NTHREADS) ela_str_adj(const EleStep p) {
 // v^{n+1/2}) flows through to v^{n-1/2}; its image is added to Sbar (which
 // becomes the adjoint of sigma^n), the memory adjoints M1..M4 are updated and
 // the buoyancy correlations accumulated.
+constexpr int ADJB_BUF = 2 * H40 * W72;  // Vbar x, z: rows [z0-4, z0+36), cols [x0-4, x0+68)
+constexpr int ADJB_SCR = 2 * TILE_Z * W72 + 2 * H40 * TILE_X;
 template <int N>
-__global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
-  extern __shared__ __align__(16) float smem_e[];
-  float* s_Vx = smem_e;                       // [H40][W72]
-  float* s_Vz = s_Vx + H40 * W72;
-  float* d_sxx = s_Vz + H40 * W72;            // [TILE_Z][W72] vx nodes, own rows
+__global__ void __launch_bounds__(NTHREADS, 2)
+    ela_vel_adj(const __grid_constant__ CUtensorMap m_Vx, const __grid_constant__ CUtensorMap m_Vz, const EleStep p) {
+  extern __shared__ __align__(128) float smem_e[];
+  float* d_sxx = smem_e + 2 * ADJB_BUF;       // [TILE_Z][W72] vx nodes, own rows
   float* d_sxz = d_sxx + TILE_Z * W72;        // [H40][TILE_X] vx nodes, own cols
   float* d_szz = d_sxz + H40 * TILE_X;        // [H40][TILE_X] vz nodes, own cols
   float* d_sxzx = d_szz + H40 * TILE_X;       // [TILE_Z][W72] vz nodes, own rows
+  uint64_t* bar = reinterpret_cast<uint64_t*>(d_sxzx + TILE_Z * W72);
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int s = blockIdx.z, x0 = blockIdx.x * TILE_X, z0 = blockIdx.y * TILE_Z;
-  const long long base = (long long)s * g.slice + g.off0;
   const int pitch = g.pitch;
-  stage<H40, W72>(s_Vx, p.Vx + base, pitch, z0 - 4, x0 - 4);
-  stage<H40, W72>(s_Vz, p.Vz + base, pitch, z0 - 4, x0 - 4);
-  __syncthreads();
+  auto fetch = [&](int tt, int bb) {
+    const TileId f = tile_decode(g, tt);
+    float* d = smem_e + bb * ADJB_BUF;
+    fence_proxy_async();
+    mbar_expect_tx(&bar[bb], ADJB_BUF * 4);
+    tma_3d(d, &m_Vx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    tma_3d(d + H40 * W72, &m_Vz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+  };
+  ELA_WALK_BEGIN(fetch)
+  const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
+  float4 spre[2][3];
+#pragma unroll
+  for (int rr = 0; rr < 2; rr++) {
+    const long long id = base + (long long)(zr0 + rr) * pitch + xb;
+    spre[rr][0] = ld4(p.Sxx + id);
+    spre[rr][1] = ld4(p.Szz + id);
+    spre[rr][2] = ld4(p.Sxz + id);
+  }
+  ELA_WAIT()
+  const float* s_Vx = smem_e + b * ADJB_BUF;
+  const float* s_Vz = s_Vx + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
   constexpr int NA = TILE_Z * (W72 / 4), NB = H40 * (TILE_X / 4);
-  for (int it = tid; it < 2 * NA + 2 * NB; it += NTHREADS) {
-    if (it < NA) {  // (a) at vx nodes, own rows, columns [x0-4, x0+68): psi1 adjoint (x)
-      const int r = it / (W72 / 4), gq = it - r * (W72 / 4);
+  for (int k4 = tid; k4 < 2 * NA + 2 * NB; k4 += NTHREADS) {
+    if (k4 < NA) {  // (a) at vx nodes, own rows, columns [x0-4, x0+68): psi1 adjoint (x)
+      const int r = k4 / (W72 / 4), gq = k4 - r * (W72 / 4);
       const int z = z0 + r, j = x0 - 4 + 4 * gq;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float v[4], b[4], t[4], d[4];
@@ -587,8 +711,8 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
       for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
       cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[0], p.Mout[0], id, gq >= 1 && gq <= 16, t, d);
       st4(d_sxx + r * W72 + 4 * gq, a4f(d));
-    } else if (it < NA + NB) {  // (b) at vx nodes, rows [z0-4, z0+36), own cols: psi2 adjoint (z)
-      const int k = it - NA, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    } else if (k4 < NA + NB) {  // (b) at vx nodes, rows [z0-4, z0+36), own cols: psi2 adjoint (z)
+      const int k = k4 - NA, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
       const int z = z0 - 4 + hr, j = x0 + 4 * c;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float v[4], b[4], t[4], d[4];
@@ -598,8 +722,8 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
       for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
       cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[1], p.Mout[1], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
       st4(d_sxz + hr * TILE_X + 4 * c, a4f(d));
-    } else if (it < NA + 2 * NB) {  // (c) at vz nodes, rows [z0-4, z0+36), own cols: psi4 adjoint (z)
-      const int k = it - NA - NB, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    } else if (k4 < NA + 2 * NB) {  // (c) at vz nodes, rows [z0-4, z0+36), own cols: psi4 adjoint (z)
+      const int k = k4 - NA - NB, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
       const int z = z0 - 4 + hr, j = x0 + 4 * c;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float v[4], b[4], t[4], d[4];
@@ -610,7 +734,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
       cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[3], p.Mout[3], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
       st4(d_szz + hr * TILE_X + 4 * c, a4f(d));
     } else {  // (d) at vz nodes, own rows, columns [x0-4, x0+68): psi3 adjoint (x)
-      const int k = it - NA - 2 * NB, r = k / (W72 / 4), gq = k - r * (W72 / 4);
+      const int k = k4 - NA - 2 * NB, r = k / (W72 / 4), gq = k - r * (W72 / 4);
       const int z = z0 + r, j = x0 - 4 + 4 * gq;
       const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
       float v[4], b[4], t[4], d[4];
@@ -623,7 +747,6 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
     }
   }
   __syncthreads();
-  const int xb = x0 + 4 * tx;
   float zs[2][4], zh[2][4];
   {
     float4 W[2 * N + 1];
@@ -637,9 +760,9 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
     const int r = 2 * ty + rr, z = z0 + r;
     const long long id = base + (long long)z * pitch + xb;
     float v[12], sx[4], sz[4], sh[4];
-    f4a(ld4(p.Sxx + id), sx);
-    f4a(ld4(p.Szz + id), sz);
-    f4a(ld4(p.Sxz + id), sh);
+    f4a(spre[rr][0], sx);
+    f4a(spre[rr][1], sz);
+    f4a(spre[rr][2], sh);
     seg12(d_sxx + r * W72 + 4 * tx, v);
 #pragma unroll
     for (int e = 0; e < 4; e++) sx[e] -= minus12<N>(p.cx, v, e);
@@ -673,6 +796,7 @@ __global__ void __launch_bounds__(NTHREADS) ela_vel_adj(const EleStep p) {
     st4(p.g_bx + id, a4f(gbx));
     st4(p.g_bz + id, a4f(gbz));
   }
+  ELA_WALK_END()
 }
 
 // ---------------------------------------------------------------------------
@@ -872,57 +996,129 @@ __global__ void k_ela_grad(const double* __restrict__ G, Grid g, const float* __
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// launchers: one-time kernel attributes and occupancy-sized persistent grids
+// per device, tensor maps per call.
 namespace {
-constexpr size_t ADJ_A_SMEM = sizeof(float) * (3 * H40 * W72 + 2 * TILE_Z * W72 + 2 * H40 * TILE_X + 32);
-constexpr size_t ADJ_B_SMEM = sizeof(float) * (2 * H40 * W72 + 2 * TILE_Z * W72 + 2 * H40 * TILE_X);
+constexpr size_t VEL_SMEM = sizeof(float) * 2 * VEL_BUF + 2 * sizeof(uint64_t);
+constexpr size_t STR_SMEM = sizeof(float) * 2 * STR_BUF + 2 * sizeof(uint64_t);
+constexpr size_t ADJ_A_SMEM = sizeof(float) * (2 * ADJA_BUF + ADJA_SCR) + 2 * sizeof(uint64_t);
+constexpr size_t ADJ_B_SMEM = sizeof(float) * (2 * ADJB_BUF + ADJB_SCR) + 2 * sizeof(uint64_t);
+
+std::mutex g_ela_mu;
+unsigned long long g_ela_inited = 0;  // bit per device
+// [device][order 4/8][variant]: vel (plain, record, store), str (plain, store), adjA, adjB
+int g_ela_grid[64][2][7];
+
+template <typename K>
+cudaError_t ela_setup(K k, size_t smem, int* grid) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, nb = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NTHREADS, smem)) != cudaSuccess) return e;
+  *grid = (nb < 1 ? 1 : nb) * nsm;
+  return cudaSuccess;
+}
+
+template <int N>
+cudaError_t ela_setup_order(int* gr) {
+  cudaError_t e;
+  if ((e = ela_setup(ela_vel_step<N, false, false>, VEL_SMEM, &gr[0])) != cudaSuccess) return e;
+  if ((e = ela_setup(ela_vel_step<N, true, false>, VEL_SMEM, &gr[1])) != cudaSuccess) return e;
+  if ((e = ela_setup(ela_vel_step<N, false, true>, VEL_SMEM, &gr[2])) != cudaSuccess) return e;
+  if ((e = ela_setup(ela_str_step<N, false>, STR_SMEM, &gr[3])) != cudaSuccess) return e;
+  if ((e = ela_setup(ela_str_step<N, true>, STR_SMEM, &gr[4])) != cudaSuccess) return e;
+  if ((e = ela_setup(ela_str_adj<N>, ADJ_A_SMEM, &gr[5])) != cudaSuccess) return e;
+  return ela_setup(ela_vel_adj<N>, ADJ_B_SMEM, &gr[6]);
+}
+
+cudaError_t ela_ensure_init(int* dev_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  *dev_out = dev;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_ela_mu);
+  if (g_ela_inited & (1ull << dev)) return cudaSuccess;
+  if ((e = ela_setup_order<2>(g_ela_grid[dev][0])) != cudaSuccess) return e;
+  if ((e = ela_setup_order<4>(g_ela_grid[dev][1])) != cudaSuccess) return e;
+  g_ela_inited |= 1ull << dev;
+  return cudaSuccess;
+}
+
+int ela_grid(const EleStep& p, int dev, int variant) {
+  return std::min(p.S * p.g.ntx * p.g.ntz, g_ela_grid[dev][p.N == 2 ? 0 : 1][variant]);
+}
 }  // namespace
 
 cudaError_t ela_kernels_init() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(ela_str_adj<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_A_SMEM)))
-    return e;
-  if ((e = cudaFuncSetAttribute(ela_str_adj<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_A_SMEM)))
-    return e;
-  if ((e = cudaFuncSetAttribute(ela_vel_adj<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_B_SMEM)))
-    return e;
-  return cudaFuncSetAttribute(ela_vel_adj<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ADJ_B_SMEM);
+  int dev;
+  return ela_ensure_init(&dev);
 }
 
-cudaError_t launch_ela_vel(const EleStep& p, bool record, bool store, cudaStream_t st) {
-  dim3 grid(p.g.ntx, p.g.ntz, p.S);
+// TMA descriptors for a call over the five forward fields f = (vx, vz, sxx,
+// szz, sxz) and, if a is not null, the five adjoint fields in the same order;
+// each field is [S][rows][pitch].
+cudaError_t ela_make_maps(EleMaps* maps, const Grid& g, int S, float* const* f, float* const* a) {
+  const cuuint64_t d3[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows, (cuuint64_t)S};
+  const cuuint64_t s3[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.slice * 4};
+  const cuuint32_t bxx[3] = {(cuuint32_t)W72, (cuuint32_t)TILE_Z, 1};
+  const cuuint32_t bzz[3] = {(cuuint32_t)TILE_X, (cuuint32_t)H40, 1};
+  const cuuint32_t bfull[3] = {(cuuint32_t)W72, (cuuint32_t)H40, 1};
+  bool ok = tma_host::encode(&maps->vx, f[0], 3, d3, s3, bfull) && tma_host::encode(&maps->vz, f[1], 3, d3, s3, bfull) &&
+            tma_host::encode(&maps->sxx, f[2], 3, d3, s3, bxx) && tma_host::encode(&maps->szz, f[3], 3, d3, s3, bzz) &&
+            tma_host::encode(&maps->sxz, f[4], 3, d3, s3, bfull);
+  if (ok && a)
+    ok = tma_host::encode(&maps->Vx, a[0], 3, d3, s3, bfull) && tma_host::encode(&maps->Vz, a[1], 3, d3, s3, bfull) &&
+         tma_host::encode(&maps->Sxx, a[2], 3, d3, s3, bfull) && tma_host::encode(&maps->Szz, a[3], 3, d3, s3, bfull) &&
+         tma_host::encode(&maps->Sxz, a[4], 3, d3, s3, bfull);
+  return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_ela_vel(const EleStep& p, const EleMaps& m, bool record, bool store, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ela_ensure_init(&dev);
+  if (e != cudaSuccess) return e;
+  const int grid = ela_grid(p, dev, record ? 1 : (store ? 2 : 0));
   if (p.N == 2) {
-    if (record) ela_vel_step<2, true, false><<<grid, NTHREADS, 0, st>>>(p);
-    else if (store) ela_vel_step<2, false, true><<<grid, NTHREADS, 0, st>>>(p);
-    else ela_vel_step<2, false, false><<<grid, NTHREADS, 0, st>>>(p);
+    if (record) ela_vel_step<2, true, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    else if (store) ela_vel_step<2, false, true><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    else ela_vel_step<2, false, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
   } else {
-    if (record) ela_vel_step<4, true, false><<<grid, NTHREADS, 0, st>>>(p);
-    else if (store) ela_vel_step<4, false, true><<<grid, NTHREADS, 0, st>>>(p);
-    else ela_vel_step<4, false, false><<<grid, NTHREADS, 0, st>>>(p);
+    if (record) ela_vel_step<4, true, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    else if (store) ela_vel_step<4, false, true><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    else ela_vel_step<4, false, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_ela_str(const EleStep& p, bool store, cudaStream_t st) {
-  dim3 grid(p.g.ntx, p.g.ntz, p.S);
+cudaError_t launch_ela_str(const EleStep& p, const EleMaps& m, bool store, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ela_ensure_init(&dev);
+  if (e != cudaSuccess) return e;
+  const int grid = ela_grid(p, dev, store ? 4 : 3);
   if (p.N == 2) {
-    if (store) ela_str_step<2, true><<<grid, NTHREADS, 0, st>>>(p);
-    else ela_str_step<2, false><<<grid, NTHREADS, 0, st>>>(p);
+    if (store) ela_str_step<2, true><<<grid, NTHREADS, STR_SMEM, st>>>(m.vx, m.vz, p);
+    else ela_str_step<2, false><<<grid, NTHREADS, STR_SMEM, st>>>(m.vx, m.vz, p);
   } else {
-    if (store) ela_str_step<4, true><<<grid, NTHREADS, 0, st>>>(p);
-    else ela_str_step<4, false><<<grid, NTHREADS, 0, st>>>(p);
+    if (store) ela_str_step<4, true><<<grid, NTHREADS, STR_SMEM, st>>>(m.vx, m.vz, p);
+    else ela_str_step<4, false><<<grid, NTHREADS, STR_SMEM, st>>>(m.vx, m.vz, p);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_ela_adj(const EleStep& p, cudaStream_t st) {
-  dim3 grid(p.g.ntx, p.g.ntz, p.S);
+cudaError_t launch_ela_adj(const EleStep& p, const EleMaps& m, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ela_ensure_init(&dev);
+  if (e != cudaSuccess) return e;
+  const int ga = ela_grid(p, dev, 5), gb = ela_grid(p, dev, 6);
   if (p.N == 2) {
-    ela_str_adj<2><<<grid, NTHREADS, ADJ_A_SMEM, st>>>(p);
-    ela_vel_adj<2><<<grid, NTHREADS, ADJ_B_SMEM, st>>>(p);
+    ela_str_adj<2><<<ga, NTHREADS, ADJ_A_SMEM, st>>>(m.Sxx, m.Szz, m.Sxz, p);
+    ela_vel_adj<2><<<gb, NTHREADS, ADJ_B_SMEM, st>>>(m.Vx, m.Vz, p);
   } else {
-    ela_str_adj<4><<<grid, NTHREADS, ADJ_A_SMEM, st>>>(p);
-    ela_vel_adj<4><<<grid, NTHREADS, ADJ_B_SMEM, st>>>(p);
+    ela_str_adj<4><<<ga, NTHREADS, ADJ_A_SMEM, st>>>(m.Sxx, m.Szz, m.Sxz, p);
+    ela_vel_adj<4><<<gb, NTHREADS, ADJ_B_SMEM, st>>>(m.Vx, m.Vz, p);
   }
   return cudaGetLastError();
 }

@@ -22,9 +22,10 @@
 #include "fwi_internal.cuh"
 
 namespace fwi {
-cudaError_t launch_ela_vel(const EleStep& p, bool record, bool store, cudaStream_t st);
-cudaError_t launch_ela_str(const EleStep& p, bool store, cudaStream_t st);
-cudaError_t launch_ela_adj(const EleStep& p, cudaStream_t st);
+cudaError_t ela_make_maps(EleMaps* maps, const Grid& g, int S, float* const* f, float* const* a);
+cudaError_t launch_ela_vel(const EleStep& p, const EleMaps& m, bool record, bool store, cudaStream_t st);
+cudaError_t launch_ela_str(const EleStep& p, const EleMaps& m, bool store, cudaStream_t st);
+cudaError_t launch_ela_adj(const EleStep& p, const EleMaps& m, cudaStream_t st);
 cudaError_t launch_ela_medium(const float* vp, const float* vs, const float* rho, const Grid& g, float* lam,
                               float* lp2m, float* bx, float* bz, float* mxz, float* mu_pad, cudaStream_t st);
 cudaError_t launch_ela_src_prep(int S, int kind, const float* x0, const Grid& g, float dx, float dz, int* box_n,
@@ -279,6 +280,7 @@ fwi_status ela_prepare(fwi_ctx* ctx, EPlan& P, const fwi_model* M, const fwi_sou
   p.x0 = P.x0;
   p.dx = M->dx;
   p.dz = M->dz;
+  p.status = P.status;
   (void)ctx;
   return FWI_OK;
 }
@@ -300,12 +302,14 @@ fwi_status ela_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   ctx->launches = 0;
   v = ela_prepare(ctx, P, M, Sv, R, dt, st, p);
   if (v != FWI_OK) return v;
+  EleMaps maps;
+  ECK(ela_make_maps(&maps, P.g, P.S, P.f, nullptr));
   ensure_events(ctx, 0);
   ECK(cudaEventRecord(ctx->ev[0], st));
   for (int n = 0; n < nt; n++) {
     p.n = n;
-    ELK(1, launch_ela_vel(p, true, false, st));
-    ELK(1, launch_ela_str(p, false, st));
+    ELK(1, launch_ela_vel(p, maps, true, false, st));
+    ELK(1, launch_ela_str(p, maps, false, st));
   }
   ECK(cudaEventRecord(ctx->ev[1], st));
   const long long ns = (long long)P.S * 2 * P.nrec * nt;
@@ -346,6 +350,8 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   ctx->launches = 0;
   v = ela_prepare(ctx, P, M, Sv, R, dt, st, p);
   if (v != FWI_OK) return v;
+  EleMaps maps;
+  ECK(ela_make_maps(&maps, P.g, P.S, P.f, P.a));
   const long long ns = (long long)P.S * 2 * P.nrec * nt;
   if (ns > 0) ECK(cudaMemcpyAsync(P.res, observed, (size_t)ns * 4, cudaMemcpyDefault, st));
   const size_t field = (size_t)P.S * P.g.slice;
@@ -360,8 +366,8 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
         ECK(cudaMemcpyAsync(ck + f * field, P.f[f], field * 4, cudaMemcpyDeviceToDevice, st));
     }
     p.n = n;
-    ELK(1, launch_ela_vel(p, true, false, st));
-    ELK(1, launch_ela_str(p, false, st));
+    ELK(1, launch_ela_vel(p, maps, true, false, st));
+    ELK(1, launch_ela_str(p, maps, false, st));
   }
   ECK(cudaEventRecord(ctx->ev[1], st));
   if (ns > 0) ELK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
@@ -389,8 +395,8 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     for (int n = n0; n < n1; n++) {
       p.n = n;
       for (int k = 0; k < 5; k++) p.slot[k] = P.slot + ((size_t)(n - n0) * 5 + k) * field;
-      ELK(1, launch_ela_vel(p, false, true, st));
-      ELK(1, launch_ela_str(p, true, st));
+      ELK(1, launch_ela_vel(p, maps, false, true, st));
+      ELK(1, launch_ela_str(p, maps, true, st));
     }
     ECK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
     for (int n = n1 - 1; n >= n0; n--) {
@@ -401,7 +407,7 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
         p.Min[k] = P.M[in][k];
         p.Mout[k] = P.M[out][k];
       }
-      ELK(2, launch_ela_adj(p, st));
+      ELK(2, launch_ela_adj(p, maps, st));
     }
     ECK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
     ELK(1, launch_ela_fold(P.gp, P.S, P.g.slice, P.G, st));

@@ -36,6 +36,28 @@ struct Grid {
   long long off0;     // offset of padded cell (0,0)
 };
 
+// Tile t of a persistent walk over all shots: t = (s * ntz + tz) * ntx + tx.
+struct TileId {
+  int s, x0, z0, tx, tz;
+};
+__device__ __forceinline__ TileId tile_decode(const Grid& g, int t) {
+  TileId r;
+  r.tx = t % g.ntx;
+  const int q = t / g.ntx;
+  r.tz = q % g.ntz;
+  r.s = q / g.ntz;
+  r.x0 = r.tx * TILE_X;
+  r.z0 = r.tz * TILE_Z;
+  return r;
+}
+
+// TMA descriptors of one elastic call: 3D maps over [S][rows][pitch] of each
+// field, with the box each kernel stages.
+struct EleMaps {
+  CUtensorMap sxx, szz, sxz, vx, vz;   // forward fields
+  CUtensorMap Sxx, Szz, Sxz, Vx, Vz;   // adjoint fields
+};
+
 // TMA descriptors of one call: the wavefield pair [2][S] (forward), the
 // adjoint pair [2][S], and the half-coefficient field m/2.
 struct AcuMaps {
@@ -120,6 +142,7 @@ struct EleStep {
   float* src_part;            // [S][nt][ELA_SLOTS][3]
   const float* x0;
   float dx, dz;
+  int* status;                // ST_* bits (a timed-out tile wait sets ST_TIMEOUT)
 };
 
 }  // namespace fwi
