@@ -9,7 +9,7 @@
 // Design (memory bound, no dense contraction, so no tensor cores):
 //   * persistent CTAs (grid = resident CTAs of the GPU) walk the tiles of all
 //     shots; a tile is 64 x 32 cells of one shot;
-//   * the wavefield tile with its 8-cell halo and the coefficient tile are
+//   * the stencil operand tiles with their 8-cell halo and the coefficient tile are
 //     fetched by TMA (cp.async.bulk.tensor) into one of two shared-memory
 //     buffers, so the next tile's fetch overlaps the current tile's work;
 //     the completion wait on the mbarrier is bounded and reports a timeout;
@@ -42,18 +42,14 @@ constexpr int QZH = TILE_Z + 8;          // 40: half rows [z0-4, z0+TZ+4)
 constexpr int U_BYTES = UW * UH * 4;     // 15360
 constexpr int M_BYTES = MW * MH * 4;     // 12464
 constexpr int M_SLOT = (M_BYTES + 127) / 128 * 128;
+constexpr int XS_BYTES = TILE_Z * UW * 4;  // 10240: adjoint x operand tile
+constexpr int ZS_BYTES = UH * TILE_X * 4;  // 12288: adjoint z operand tile
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void unpack12(const float* s, float v[12]) {
   const float4 a = ld4(s), b = ld4(s + 4), c = ld4(s + 8);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-  v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
-}
-__device__ __forceinline__ void unpack12_g(const float* s, float v[12]) {
-  const float4 a = ldg4(s), b = ldg4(s + 4), c = ldg4(s + 8);
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
   v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
@@ -71,6 +67,27 @@ __device__ __forceinline__ bool tile_pml_x(const Grid& g, int x0) {
 }
 __device__ __forceinline__ bool tile_pml_z(const Grid& g, int z0) {
   return g.npml > 0 && (z0 - H < g.npml || z0 + TILE_Z + H > g.npml + g.nz - 1);
+}
+
+// Tiles that leave hhat behind for the next adjoint step: those whose own
+// columns (rows) lie in the stencil reach of a CPML tile (itself or a neighbour).
+__device__ __forceinline__ bool tile_writes_hx(const Grid& g, int tx) {
+  bool w = false;
+#pragma unroll
+  for (int d = -1; d <= 1; d++) {
+    const int t2 = tx + d;
+    w = w || (t2 >= 0 && t2 < g.ntx && tile_pml_x(g, t2 * TILE_X));
+  }
+  return w;
+}
+__device__ __forceinline__ bool tile_writes_hz(const Grid& g, int tz) {
+  bool w = false;
+#pragma unroll
+  for (int d = -1; d <= 1; d++) {
+    const int t2 = tz + d;
+    w = w || (t2 >= 0 && t2 < g.ntz && tile_pml_z(g, t2 * TILE_Z));
+  }
+  return w;
 }
 
 // Deterministic CTA sum of three floats (fixed shuffle tree, fixed warp order).
@@ -111,15 +128,15 @@ struct FwdSmem {
   uint64_t bar[2];
 };
 struct AdjSmem {
-  float l[2][UH * UW];
-  float m[2][M_SLOT / 4];
-  float hz[UH * TILE_X];  // z-CPML tiles: lambda + a_z (Z_z + lambda) at the staged rows, own columns
+  float xs[TILE_Z * UW];     // x stencil operand (lambda or Hx): own rows, cols [x0-H, x0+TX+H)
+  float zs[UH * TILE_X];     // z stencil operand (lambda or Hz): rows [z0-H, z0+TZ+H), own cols
+  float m[M_SLOT / 4];
   float gx[TILE_Z * QXW];
   float gz[QZH * TILE_X];
-  float imx[TILE_Z * QXW];
-  float imz[QZH * TILE_X];
+  float imz[(NTHREADS / 16 + 1) * TILE_X];  // image at half row z0-1 and at each thread row's lower half row
+  float imx[TILE_Z];                        // image at half column x0-1 of every row
   float red[32];
-  uint64_t bar[2];
+  uint64_t bar;
 };
 
 }  // namespace
@@ -405,96 +422,76 @@ __global__ void __launch_bounds__(NTHREADS, 3)
 //   2 dJ/dm += qbar * p^n at both neighbours of each half point (gradient correlation)
 //   pbar = m_half qbar;  gbar = pbar + a_h (P + pbar),  P <- b_h (P + pbar)
 //   lambda_n = 2 lambda_{n+1} - lambda_{n+2} - D- gbar + residual(sample n-1)
+// hhat is needed with an N-cell halo, so the step that produces lambda_{n+1}
+// also leaves hhat behind: every tile within one tile of a CPML tile writes
+// Hx = (1 + a_x) lambda + a_x Zx and Hz likewise at its own cells, and a CPML
+// tile fetches its x (z) stencil operand from Hx (Hz) instead of lambda. Z is
+// then read and written only by the thread that owns the cell.
 template <int N>
-__global__ void __launch_bounds__(NTHREADS, 2)
-    acu_adj_step(const __grid_constant__ CUtensorMap tmap_l, const __grid_constant__ CUtensorMap tmap_m,
-                 const AcuStep p) {
+__global__ void __launch_bounds__(NTHREADS, 3)
+    acu_adj_step(const __grid_constant__ CUtensorMap tmap_lx, const __grid_constant__ CUtensorMap tmap_lz,
+                 const __grid_constant__ CUtensorMap tmap_hx, const __grid_constant__ CUtensorMap tmap_hz,
+                 const __grid_constant__ CUtensorMap tmap_m, const AcuStep p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   AdjSmem& sh = *reinterpret_cast<AdjSmem*>(smem_raw);
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
 
+  // one operand buffer: the next tile's fetch is issued once stage 1 of this
+  // tile (its last reader) is done, and overlaps stage 2
+  auto fetch = [&](int tt) {
+    const TileId f = tile_decode(g, tt);
+    const int plane = p.cur * p.S + f.s;
+    const CUtensorMap* xm = tile_pml_x(g, f.x0) ? &tmap_hx : &tmap_lx;
+    const CUtensorMap* zm = tile_pml_z(g, f.z0) ? &tmap_hz : &tmap_lz;
+    fence_proxy_async();
+    mbar_expect_tx(&sh.bar, XS_BYTES + ZS_BYTES + M_BYTES);
+    tma_3d(sh.xs, xm, f.x0 - H + APRON, f.z0 + APRON, plane, &sh.bar);
+    tma_3d(sh.zs, zm, f.x0 + APRON, f.z0 - H + APRON, plane, &sh.bar);
+    tma_2d(sh.m, &tmap_m, f.x0 - 4 + APRON, f.z0 - 4 + APRON, &sh.bar);
+  };
+
   if (tid == 0) {
-    mbar_init(&sh.bar[0], 1);
-    mbar_init(&sh.bar[1], 1);
+    mbar_init(&sh.bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < p.ntiles)
-    fetch_tile(&tmap_l, &tmap_m, g, p.S, p.cur, blockIdx.x, sh.l[0], sh.m[0], &sh.bar[0]);
+  if (tid == 0 && (int)blockIdx.x < p.ntiles) fetch(blockIdx.x);
 
   int it = 0;
   for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
-    const int b = it & 1;
     const int tn = t + gridDim.x;
-    if (tid == 0 && tn < p.ntiles)
-      fetch_tile(&tmap_l, &tmap_m, g, p.S, p.cur, tn, sh.l[b ^ 1], sh.m[b ^ 1], &sh.bar[b ^ 1]);
     const TileId id = tile_decode(g, t);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
-    float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
-    float* __restrict__ gp = p.gpart + base;
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
-    float4 lo[2], go[2];
-    lo[0] = ldg4(lprev + (long long)zr0 * pitch + xb);
-    lo[1] = ldg4(lprev + (long long)(zr0 + 1) * pitch + xb);
-    go[0] = ldg4(gp + (long long)zr0 * pitch + xb);
-    go[1] = ldg4(gp + (long long)(zr0 + 1) * pitch + xb);
-    // stored fluxes p^n of this thread's own half points (x and z)
+    // stored fluxes p^n of this thread's own half points (x and z), fetched before the wait
     float4 pfx[2], pfz[2];
     pfx[0] = ldg4(p.slot_px + base + (long long)zr0 * pitch + xb);
     pfx[1] = ldg4(p.slot_px + base + (long long)(zr0 + 1) * pitch + xb);
     pfz[0] = ldg4(p.slot_pz + base + (long long)zr0 * pitch + xb);
     pfz[1] = ldg4(p.slot_pz + base + (long long)(zr0 + 1) * pitch + xb);
-    const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
-    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
-    const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
 
-    const bool ok = mbar_wait(&sh.bar[b], (it >> 1) & 1);
+    const bool ok = mbar_wait(&sh.bar, it & 1);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.status, ST_TIMEOUT);
-        tma_drain(sh.bar, it, tn < p.ntiles);
+        mbar_wait(&sh.bar, it & 1);  // let a late copy land before the CTA exits
       }
       return;
     }
-    const float* sl = sh.l[b];
-    const float* sm = sh.m[b];
+    const float* sx = sh.xs;  // [TILE_Z][UW]: x operand, cols [x0-H, x0+TX+H)
+    const float* sz = sh.zs;  // [UH][TILE_X]: z operand, rows [z0-H, z0+TZ+H)
+    const float* sm = sh.m;
     const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
-    // z-direction hhat for the whole staged height: in z-CPML tiles it is
-    // formed once here (coalesced Z loads), elsewhere it is lambda itself
-    if (pmlz) {
-      for (int k = tid; k < UH * (TILE_X / 4); k += NTHREADS) {
-        const int row = k >> 4, c = k & 15;
-        const int zz = z0 - H + row;
-        float4 w = ld4(sl + row * UW + 8 + 4 * c);
-        const float aa = __ldg(p.az + zz + TAB_OFF);
-        if (aa != 0.f) {
-          const float4 Z = *reinterpret_cast<const float4*>(p.zz_in + base + (long long)zz * pitch + x0 + 4 * c);
-          w.x += aa * (Z.x + w.x); w.y += aa * (Z.y + w.y); w.z += aa * (Z.z + w.z); w.w += aa * (Z.w + w.w);
-        }
-        st4(sh.hz + row * TILE_X + 4 * c, w);
-      }
-      __syncthreads();
-    }
-    const float* hzb = pmlz ? sh.hz : sl + 8;  // element (row, own column c) at hzb[row * hzs + c]
-    const int hzs = pmlz ? TILE_X : UW;
 
     // ---- stage 1a: x half points of row r: qbar, correlation, gbar
-    auto x_item = [&](int r, int gq, bool own, bool image, const float4* pre) {
+    auto x_item = [&](int r, int gq, bool own, bool image, const float4* pre, float im[4]) {
       const int z = z0 + r, hb = x0 - 4 + 4 * gq;
       float v[12];
-      unpack12(sl + (r + H) * UW + 4 * gq, v);
+      unpack12(sx + r * UW + 4 * gq, v);
       const long long id0 = base + (long long)z * pitch + hb;
-      if (pmlx) {
-        // hhat = lambda + a (Z + lambda) at the 12 integer points (a = 0 outside the layer)
-        float A[12], Z[12];
-        unpack12_g(p.ax + hb - 4 + TAB_OFF, A);
-        unpack12_g(p.zx_in + id0 - 4, Z);
-#pragma unroll
-        for (int t2 = 0; t2 < 12; t2++) v[t2] += A[t2] * (Z[t2] + v[t2]);
-      }
       const float4 m4 = ld4(sm + (r + 4) * MW + 4 * gq);
       const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
       float pf[4] = {0.f, 0.f, 0.f, 0.f};
@@ -502,9 +499,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       else if (image) f4a(ldg4(p.slot_px + id0), pf);
       const bool rowok = z < g.Nz;
       float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
-      if (pmlx) a4 = ldg4(p.axh + hb + TAB_OFF);
-      const bool pon = a4.x != 0.f || a4.y != 0.f || a4.z != 0.f || a4.w != 0.f;
-      if (pon) {
+      if (pmlx) {  // one round trip: tables and P together
+        a4 = ldg4(p.axh + hb + TAB_OFF);
         b4 = ldg4(p.bxh + hb + TAB_OFF);
         P4 = ld4(p.px_in + id0);
       }
@@ -512,7 +508,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       f4a(a4, av);
       f4a(b4, bv);
       f4a(P4, Pv);
-      float gb[4], im[4], Pn[4];
+      float gb[4], Pn[4];
 #pragma unroll
       for (int e = 0; e < 4; e++) {
         float dq = 0.f;
@@ -526,28 +522,31 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         Pn[e] = av[e] != 0.f ? bv[e] * tt : 0.f;  // P stays zero outside the layer
         im[e] = qb * pf[e];
       }
-      if (pon && own && rowok) st4(p.px_out + id0, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
+      if (pmlx && own && rowok && (av[0] != 0.f || av[1] != 0.f || av[2] != 0.f || av[3] != 0.f))
+        st4(p.px_out + id0, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
       st4(sh.gx + r * QXW + 4 * gq, make_float4(gb[0], gb[1], gb[2], gb[3]));
-      st4(sh.imx + r * QXW + 4 * gq, make_float4(im[0], im[1], im[2], im[3]));
     };
     // ---- stage 1b: one z half row (the tile's halo rows)
     auto z_item = [&](int hr, int c, bool image) {
       const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
+      const long long idz = base + (long long)hz * pitch + xc;
+      float pf[4] = {0.f, 0.f, 0.f, 0.f};
+      if (image) f4a(ldg4(p.slot_pz + idz), pf);
+      float aa = 0.f;
+      float Pv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (pmlz) {
+        aa = __ldg(p.azh + hz + TAB_OFF);
+        f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
+      }
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int k = 1; k <= N; k++)
-        acc4(acc, p.c1z[k - 1], ld4(hzb + (hr + 4 + k) * hzs + 4 * c), ld4(hzb + (hr + 5 - k) * hzs + 4 * c));
+        acc4(acc, p.c1z[k - 1], ld4(sz + (hr + 4 + k) * TILE_X + 4 * c), ld4(sz + (hr + 5 - k) * TILE_X + 4 * c));
       float dq[4];
       f4a(acc, dq);
       const bool hv = hz >= 0 && hz < g.Nz - 1;
       const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
       const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
-      const long long idz = base + (long long)hz * pitch + xc;
-      float pf[4] = {0.f, 0.f, 0.f, 0.f};
-      if (image) f4a(ldg4(p.slot_pz + idz), pf);
-      const float aa = pmlz ? __ldg(p.azh + hz + TAB_OFF) : 0.f;
-      float Pv[4] = {0.f, 0.f, 0.f, 0.f};
-      if (aa != 0.f) f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
       float gb[4], im[4];
 #pragma unroll
       for (int e = 0; e < 4; e++) {
@@ -558,16 +557,28 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         im[e] = qb * pf[e];
       }
       st4(sh.gz + hr * TILE_X + 4 * c, make_float4(gb[0], gb[1], gb[2], gb[3]));
-      st4(sh.imz + hr * TILE_X + 4 * c, make_float4(im[0], im[1], im[2], im[3]));
+      if (image) st4(sh.imz + 4 * c, make_float4(im[0], im[1], im[2], im[3]));
     };
 
-    x_item(2 * ty, tx + 1, true, true, &pfx[0]);
-    x_item(2 * ty + 1, tx + 1, true, true, &pfx[1]);
+    // own x half points xb+e+1/2 of rows 2ty, 2ty+1: their images stay in registers
+    float imx[2][4], imz[2][4];
+    x_item(2 * ty, tx + 1, true, true, &pfx[0], imx[0]);
+    x_item(2 * ty + 1, tx + 1, true, true, &pfx[1], imx[1]);
     {
       // own z half rows 2ty, 2ty+1 from a (2N+1)-row window of hhat
+      float aa[2] = {0.f, 0.f}, bb[2] = {1.f, 1.f};
+      float4 Pz[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+      if (pmlz) {
+#pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          aa[rr] = __ldg(p.azh + zr0 + rr + TAB_OFF);
+          bb[rr] = __ldg(p.bzh + zr0 + rr + TAB_OFF);
+          Pz[rr] = *reinterpret_cast<const float4*>(p.pz_in + base + (long long)(zr0 + rr) * pitch + xb);
+        }
+      }
       float4 w[2 * N + 1];
 #pragma unroll
-      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(hzb + (2 * ty + H - N + 1 + t2) * hzs + 4 * tx);
+      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sz + (2 * ty + H - N + 1 + t2) * TILE_X + 4 * tx);
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
 #pragma unroll
       for (int k = 1; k <= N; k++) {
@@ -585,27 +596,25 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         const float4 ma = ld4(sm + (2 * ty + 4 + rr) * MW + 4 * tx + 4);
         const float4 mb = ld4(sm + (2 * ty + 5 + rr) * MW + 4 * tx + 4);
         const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
-        float pf[4];
+        float pf[4], Pv[4];
         f4a(pfz[rr], pf);
-        const float aa = pmlz ? __ldg(p.azh + hz + TAB_OFF) : 0.f;
-        float Pv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (aa != 0.f) f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
-        const float bb = aa != 0.f ? __ldg(p.bzh + hz + TAB_OFF) : 1.f;
-        float gb[4], im[4], Pn[4];
+        f4a(Pz[rr], Pv);
+        float gb[4], Pn[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
           const bool inh = hv && xb + e < g.Nx;
           const float qb = inh ? dq[rr][e] : 0.f;
           const float pb = mhv[e] * qb;
           const float tt = Pv[e] + pb;
-          gb[e] = inh ? pb + aa * tt : 0.f;
-          Pn[e] = inh ? bb * tt : 0.f;
-          im[e] = qb * pf[e];
+          gb[e] = inh ? pb + aa[rr] * tt : 0.f;
+          Pn[e] = inh ? bb[rr] * tt : 0.f;
+          imz[rr][e] = qb * pf[e];
         }
-        if (aa != 0.f && hz < g.Nz) st4(p.pz_out + idz, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
+        if (aa[rr] != 0.f && hz < g.Nz) st4(p.pz_out + idz, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
         st4(sh.gz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(gb[0], gb[1], gb[2], gb[3]));
-        st4(sh.imz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(im[0], im[1], im[2], im[3]));
       }
+      // half row 2ty+1 is the upper neighbour of the next thread row's cells
+      st4(sh.imz + (ty + 1) * TILE_X + 4 * tx, make_float4(imz[1][0], imz[1][1], imz[1][2], imz[1][3]));
     }
     if (tid < 128) {
       const int hr0 = tid >> 4;
@@ -614,11 +623,33 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     } else if (tid < 192) {
       const int k = tid - 128;
       const bool left = (k & 1) == 0;
-      x_item(k >> 1, left ? 0 : QXW / 4 - 1, false, left, nullptr);  // only half column x0-1 feeds the gradient
+      float im[4];
+      x_item(k >> 1, left ? 0 : QXW / 4 - 1, false, left, nullptr, im);  // only half column x0-1 feeds the gradient
+      if (left) sh.imx[k >> 1] = im[3];
+    }
+    // lambda_{n+1} at the own cells, from a stencil tile that holds lambda itself
+    float4 lc[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; rr++) {
+      const int r = 2 * ty + rr;
+      if (!pmlx) lc[rr] = ld4(sx + r * UW + H + 4 * tx);
+      else if (!pmlz) lc[rr] = ld4(sz + (r + H) * TILE_X + 4 * tx);
+      else lc[rr] = ldg4(p.lam + (long long)p.cur * p.S * g.slice + base + (long long)(z0 + r) * pitch + xb);
     }
     __syncthreads();
+    if (tid == 0 && tn < p.ntiles) fetch(tn);  // the operand buffer is free
 
-    // ---- stage 2: lambda_n, Z update, gradient, residual, source partials
+    // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
+    float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
+    float* __restrict__ gp = p.gpart + base;
+    float4 lo[2], go[2];
+    lo[0] = ldg4(lprev + (long long)zr0 * pitch + xb);
+    lo[1] = ldg4(lprev + (long long)(zr0 + 1) * pitch + xb);
+    go[0] = ldg4(gp + (long long)zr0 * pitch + xb);
+    go[1] = ldg4(gp + (long long)(zr0 + 1) * pitch + xb);
+    const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
+    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+    const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
     float dzv[2][4];
     {
       float4 w[2 * N + 1];
@@ -633,27 +664,23 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       f4a(a0, dzv[0]);
       f4a(a1, dzv[1]);
     }
-    float imzv[3][4];
-    f4a(ld4(sh.imz + (2 * ty + 3) * TILE_X + 4 * tx), imzv[0]);
-    f4a(ld4(sh.imz + (2 * ty + 4) * TILE_X + 4 * tx), imzv[1]);
-    f4a(ld4(sh.imz + (2 * ty + 5) * TILE_X + 4 * tx), imzv[2]);
-    float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
-    if (pmlx) ax4 = ldg4(p.ax + xb + TAB_OFF);
-    const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
-    if (zx_on) bx4 = ldg4(p.bx + xb + TAB_OFF);
+    // image of the half row above (2ty-1) and of the half column left of the thread (xb-1/2)
+    float imzu[4];
+    f4a(ld4(sh.imz + ty * TILE_X + 4 * tx), imzu);
+    float imxl[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; rr++) {
+      const float up = __shfl_up_sync(0xffffffffu, imx[rr][3], 1, 16);
+      imxl[rr] = tx == 0 ? sh.imx[2 * ty + rr] : up;
+    }
     float lnew[2][4];
 #pragma unroll
     for (int rr = 0; rr < 2; rr++) {
       const int r = 2 * ty + rr, z = z0 + r;
-      const long long idc0 = base + (long long)z * pitch + xb;
       float v[12];
       unpack12(sh.gx + r * QXW + 4 * tx, v);
-      float ix8[8];
-      f4a(ld4(sh.imx + r * QXW + 4 * tx), ix8);
-      f4a(ld4(sh.imx + r * QXW + 4 * tx + 4), ix8 + 4);
       float lcv[4], lov[4], gov[4];
-      const float4 lc4 = ld4(sl + (r + H) * UW + 4 * tx + H);
-      f4a(lc4, lcv);
+      f4a(lc[rr], lcv);
       f4a(lo[rr], lov);
       f4a(go[rr], gov);
       float gn[4];
@@ -664,30 +691,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         for (int k = 1; k <= N; k++) dxv += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
         const bool valid = z < g.Nz && xb + e < g.Nx;
         lnew[rr][e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[rr][e]) : 0.f;
-        gn[e] = valid ? gov[e] + (ix8[e + 3] + ix8[e + 4] + imzv[rr][e] + imzv[rr + 1][e]) : 0.f;
-      }
-      // CPML Z (divided by dt^2) <- b (Z + lambda_{n+1}); zero outside the layer and the grid
-      if (zx_on) {
-        const float4 Zo = ld4(p.zx_in + idc0);
-        float4 Zn;
-        Zn.x = ax4.x != 0.f && z < g.Nz ? bx4.x * (Zo.x + lc4.x) : 0.f;
-        Zn.y = ax4.y != 0.f && z < g.Nz ? bx4.y * (Zo.y + lc4.y) : 0.f;
-        Zn.z = ax4.z != 0.f && z < g.Nz ? bx4.z * (Zo.z + lc4.z) : 0.f;
-        Zn.w = ax4.w != 0.f && z < g.Nz ? bx4.w * (Zo.w + lc4.w) : 0.f;
-        st4(p.zx_out + idc0, Zn);
-      }
-      if (pmlz) {
-        const float aa = __ldg(p.az + z + TAB_OFF);
-        if (aa != 0.f) {
-          const float bb = __ldg(p.bz + z + TAB_OFF);
-          const float4 Zo = ld4(p.zz_in + idc0);
-          float4 Zn;
-          Zn.x = xb + 0 < g.Nx ? bb * (Zo.x + lc4.x) : 0.f;
-          Zn.y = xb + 1 < g.Nx ? bb * (Zo.y + lc4.y) : 0.f;
-          Zn.z = xb + 2 < g.Nx ? bb * (Zo.z + lc4.z) : 0.f;
-          Zn.w = xb + 3 < g.Nx ? bb * (Zo.w + lc4.w) : 0.f;
-          st4(p.zz_out + idc0, Zn);
-        }
+        const float ixl = e == 0 ? imxl[rr] : imx[rr][e - 1];
+        const float izu = rr == 0 ? imzu[e] : imz[0][e];
+        gn[e] = valid ? gov[e] + (ixl + imx[rr][e] + izu + imz[rr][e]) : 0.f;
       }
       st4(gp + (long long)z * pitch + xb, make_float4(gn[0], gn[1], gn[2], gn[3]));
     }
@@ -704,9 +710,50 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             if (r2 == rr && e2 == e) lnew[r2][e2] += rv;
       }
     }
+    const bool wx = tile_writes_hx(g, id.tx), wz = tile_writes_hz(g, id.tz);
+    float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
+    if (pmlx) {
+      ax4 = ldg4(p.ax + xb + TAB_OFF);
+      bx4 = ldg4(p.bx + xb + TAB_OFF);
+    }
+    const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
 #pragma unroll
-    for (int rr = 0; rr < 2; rr++)
-      st4(lprev + (long long)(zr0 + rr) * pitch + xb, make_float4(lnew[rr][0], lnew[rr][1], lnew[rr][2], lnew[rr][3]));
+    for (int rr = 0; rr < 2; rr++) {
+      const int z = zr0 + rr;
+      const long long idc0 = base + (long long)z * pitch + xb;
+      const float4 l4 = make_float4(lnew[rr][0], lnew[rr][1], lnew[rr][2], lnew[rr][3]);
+      st4(lprev + (long long)z * pitch + xb, l4);
+      // CPML Z (divided by dt^2) <- b (Z + lambda_{n+1}); zero outside the layer and the grid
+      float4 Zx = make_float4(0.f, 0.f, 0.f, 0.f), Zz = Zx;
+      if (zx_on) {
+        const float4 Zo = ld4(p.zx_in + idc0);
+        Zx.x = ax4.x != 0.f && z < g.Nz ? bx4.x * (Zo.x + lc[rr].x) : 0.f;
+        Zx.y = ax4.y != 0.f && z < g.Nz ? bx4.y * (Zo.y + lc[rr].y) : 0.f;
+        Zx.z = ax4.z != 0.f && z < g.Nz ? bx4.z * (Zo.z + lc[rr].z) : 0.f;
+        Zx.w = ax4.w != 0.f && z < g.Nz ? bx4.w * (Zo.w + lc[rr].w) : 0.f;
+        st4(p.zx_out + idc0, Zx);
+      }
+      float az = 0.f;
+      if (pmlz) {
+        az = __ldg(p.az + z + TAB_OFF);
+        if (az != 0.f) {
+          const float bz = __ldg(p.bz + z + TAB_OFF);
+          const float4 Zo = ld4(p.zz_in + idc0);
+          Zz.x = xb + 0 < g.Nx ? bz * (Zo.x + lc[rr].x) : 0.f;
+          Zz.y = xb + 1 < g.Nx ? bz * (Zo.y + lc[rr].y) : 0.f;
+          Zz.z = xb + 2 < g.Nx ? bz * (Zo.z + lc[rr].z) : 0.f;
+          Zz.w = xb + 3 < g.Nx ? bz * (Zo.w + lc[rr].w) : 0.f;
+          st4(p.zz_out + idc0, Zz);
+        }
+      }
+      // hhat of step n-1 (lambda_n with the updated Z); equal to lambda_n outside the layer
+      if (wx)
+        st4(p.hx_out + idc0, make_float4(l4.x + ax4.x * (Zx.x + l4.x), l4.y + ax4.y * (Zx.y + l4.y),
+                                         l4.z + ax4.z * (Zx.z + l4.z), l4.w + ax4.w * (Zx.w + l4.w)));
+      if (wz)
+        st4(p.hz_out + idc0, make_float4(l4.x + az * (Zz.x + l4.x), l4.y + az * (Zz.y + l4.y),
+                                         l4.z + az * (Zz.z + l4.z), l4.w + az * (Zz.w + l4.w)));
+    }
     // source-parameter partials from lambda_n (index n-1): sum w lambda,
     // sum w lambda (x_i - x0), sum w lambda (z_i - z0); at most 4 tiles touch a box
     if (p.src_part != nullptr && p.n >= 1) {
@@ -740,7 +787,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         }
       }
     }
-    __syncthreads();  // the tile buffer and the stage arrays are free again
+    __syncthreads();  // the stage arrays are free again
   }
 }
 
@@ -792,9 +839,9 @@ cudaError_t acu_kernels_init() {
   return ensure_init(&dev);
 }
 
-// TMA descriptors for a call: u and lam are [2][S][slice] pairs (lam may be
-// null), mh is one [slice] field.
-cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh) {
+// TMA descriptors for a call: u is the [2][S][slice] wavefield pair, mh one
+// [slice] field.
+cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, const float* mh) {
   const cuuint64_t d3[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows, (cuuint64_t)(2 * S)};
   const cuuint64_t s3[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.slice * 4};
   const cuuint32_t b3[3] = {(cuuint32_t)UW, (cuuint32_t)UH, 1};
@@ -803,7 +850,6 @@ cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, fl
   const cuuint32_t b2[2] = {(cuuint32_t)MW, (cuuint32_t)MH};
   if (!tma_host::encode(&maps->u, u_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
   if (!tma_host::encode(&maps->m, const_cast<float*>(mh), 2, d2, s2, b2)) return cudaErrorInvalidValue;
-  if (lam_pair && !tma_host::encode(&maps->lam, lam_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
@@ -827,14 +873,29 @@ cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, b
   return cudaGetLastError();
 }
 
+// Adjoint operand maps: lambda and the hhat pairs Hx, Hz, each [2][S][slice],
+// with the x-operand box (own rows, 80 columns) and the z-operand box (48 rows,
+// own columns).
+cudaError_t acu_make_adj_maps(AcuMaps* maps, const Grid& g, int S, float* lam_pair, float* hx_pair, float* hz_pair) {
+  const cuuint64_t d3[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.rows, (cuuint64_t)(2 * S)};
+  const cuuint64_t s3[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.slice * 4};
+  const cuuint32_t bx[3] = {(cuuint32_t)UW, (cuuint32_t)TILE_Z, 1};
+  const cuuint32_t bz[3] = {(cuuint32_t)TILE_X, (cuuint32_t)UH, 1};
+  const bool ok = tma_host::encode(&maps->lx, lam_pair, 3, d3, s3, bx) &&
+                  tma_host::encode(&maps->lz, lam_pair, 3, d3, s3, bz) &&
+                  tma_host::encode(&maps->hx, hx_pair, 3, d3, s3, bx) &&
+                  tma_host::encode(&maps->hz, hz_pair, 3, d3, s3, bz);
+  return ok ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st) {
   int dev;
   cudaError_t e = ensure_init(&dev);
   if (e != cudaSuccess) return e;
   const int grid = std::min(p.ntiles, g_grid_adj[dev][p.N == 2 ? 0 : 1]);
   const size_t smem = sizeof(AdjSmem);
-  if (p.N == 2) acu_adj_step<2><<<grid, NTHREADS, smem, st>>>(maps.lam, maps.m, p);
-  else acu_adj_step<4><<<grid, NTHREADS, smem, st>>>(maps.lam, maps.m, p);
+  if (p.N == 2) acu_adj_step<2><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p);
+  else acu_adj_step<4><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,8 @@ cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, b
 cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st);
 cudaError_t acu_kernels_init();
 cudaError_t ela_kernels_init();
-cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh);
+cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, const float* mh);
+cudaError_t acu_make_adj_maps(AcuMaps* maps, const Grid& g, int S, float* lam_pair, float* hx_pair, float* hz_pair);
 cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st);
 cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
                                double vmax, double f0, float* a, float* b, float* ah, float* bh,
@@ -37,7 +38,7 @@ cudaError_t launch_model_check(const float* c, long long n, float coef, int* sta
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
                           int* status, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
-cudaError_t launch_adj_init(const AcuStep& p, float* lam, cudaStream_t st);
+cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st);
 cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st);
 cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st);
 cudaError_t launch_src_grad(const float* part, int S, int nt, int nslots, double scale, const float* stf,
@@ -97,6 +98,7 @@ struct Plan {
   // gradient
   float *res = nullptr, *ckpt = nullptr, *slot = nullptr, *lam = nullptr, *zx[2] = {}, *zz[2] = {};
   float *px[2] = {}, *pz[2] = {}, *gpart = nullptr, *src_part = nullptr, *grad_c = nullptr;
+  float *hx = nullptr, *hz = nullptr;  // [2][S][slice] hhat pairs of the adjoint CPML tiles
   float *gstf = nullptr, *gx0 = nullptr;
   double *G = nullptr, *Jpart = nullptr, *J = nullptr;
   size_t bytes = 0;
@@ -143,6 +145,8 @@ void layout(Plan& P, char* base) {
     for (int k = 0; k < 2; k++) P.zz[k] = (float*)take(field);
     for (int k = 0; k < 2; k++) P.px[k] = (float*)take(field);
     for (int k = 0; k < 2; k++) P.pz[k] = (float*)take(field);
+    P.hx = (float*)take(2 * field);
+    P.hz = (float*)take(2 * field);
     P.gpart = (float*)take(field);
     P.G = (double*)take((size_t)P.g.slice * 8);
     P.src_part = (float*)take((size_t)P.S * P.nt * SRC_SLOTS * 3 * 4);
@@ -460,7 +464,7 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   v = prepare(ctx, P, M, Sv, R, dt, st, p);
   if (v != FWI_OK) return v;
   AcuMaps maps;
-  CK(acu_make_maps(&maps, P.g, P.S, P.u, nullptr, P.m));
+  CK(acu_make_maps(&maps, P.g, P.S, P.u, P.m));
   ensure_events(ctx, 0);
   CK(cudaEventRecord(ctx->ev[0], st));
   for (int n = 0; n < nt; n++) {
@@ -513,7 +517,8 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   if (ns > 0) CK(cudaMemcpyAsync(P.res, observed, (size_t)ns * 4, cudaMemcpyDefault, st));
   const size_t field = (size_t)P.S * P.g.slice;
   AcuMaps maps;
-  CK(acu_make_maps(&maps, P.g, P.S, P.u, P.lam, P.m));
+  CK(acu_make_maps(&maps, P.g, P.S, P.u, P.m));
+  CK(acu_make_adj_maps(&maps, P.g, P.S, P.lam, P.hx, P.hz));
   ensure_events(ctx, P.nseg);
 
   // forward sweep with a full-state checkpoint at the start of every segment
@@ -538,7 +543,7 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   p.src_part = P.src_part;
   AcuStep pa = p;
   set_adjoint_weights(pa, p);
-  LK(1, launch_adj_init(pa, P.lam + (nt & 1) * field, st));
+  LK(1, launch_adj_init(pa, P.lam + (nt & 1) * field, P.hx + (nt & 1) * field, P.hz + (nt & 1) * field, st));
   for (int seg = P.nseg - 1; seg >= 0; seg--) {
     const int n0 = seg * K, n1 = std::min(nt, n0 + K);
     const float* ck = P.ckpt + (size_t)seg * 6 * field;
@@ -566,6 +571,8 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       pa.px_out = P.px[n & 1];
       pa.pz_in = P.pz[(n + 1) & 1];
       pa.pz_out = P.pz[n & 1];
+      pa.hx_out = P.hx + (n & 1) * field;
+      pa.hz_out = P.hz + (n & 1) * field;
       LK(1, launch_acu_adj(pa, maps, st));
     }
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));

@@ -59,11 +59,12 @@ struct EleMaps {
 };
 
 // TMA descriptors of one call: the wavefield pair [2][S] (forward), the
-// adjoint pair [2][S], and the half-coefficient field m/2.
+// half-coefficient field m/2, and the adjoint operand pairs [2][S].
 struct AcuMaps {
   CUtensorMap u;
-  CUtensorMap lam;
   CUtensorMap m;
+  CUtensorMap lx, lz;   // adjoint: lambda pair, x-operand and z-operand boxes
+  CUtensorMap hx, hz;   // adjoint: hhat pairs (CPML tiles)
 };
 
 // Everything one acoustic step kernel needs (passed by value).
@@ -99,6 +100,7 @@ struct AcuStep {
   float* lam;             // [2][S][slice]
   const float *zx_in, *zz_in, *px_in, *pz_in;   // Z (scaled by 1/dt^2) and P
   float *zx_out, *zz_out, *px_out, *pz_out;
+  float *hx_out, *hz_out;  // hhat of the next (earlier) step, written near the CPML: [S][slice]
   const float* res;       // [S][nrec][nt] residual seis - observed
   float* gpart;           // [S][slice] FP32 partial of 2 dJ/dm per padded cell
   float* src_part;        // [S][nt][SRC_SLOTS][3]

@@ -33,7 +33,7 @@
 
 namespace fwi {
 cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
-cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, float* lam_pair, const float* mh);
+cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, const float* mh);
 cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st);
 cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h, double dt, double R,
                                double vmax, double f0, float* a, float* b, float* ah, float* bh,
@@ -223,7 +223,7 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   p.dx = M->dx;
   p.dz = M->dz;
   AcuMaps maps;
-  NA_CK(acu_make_maps(&maps, g, S, p.u, nullptr, p.mh));
+  NA_CK(acu_make_maps(&maps, g, S, p.u, p.mh));
   for (int n = 0; n < nt; n++) {
     p.n = n;
     p.cur = n & 1;

@@ -250,14 +250,18 @@ __global__ void k_finite_check(const float* __restrict__ a, long long n, int* st
 
 // Adjoint initial condition: lambda_{nt} = residual of the last sample at the
 // receivers (in receiver order), and its source-parameter partial (index nt-1).
-__global__ void k_adj_init(AcuStep p, float* lam) {
+__global__ void k_adj_init(AcuStep p, float* lam, float* hx, float* hz) {
   const int s = blockIdx.x;
   if (threadIdx.x != 0) return;
   const long long sh = (long long)s * p.g.slice + p.g.off0;
   for (int r = 0; r < p.nrec; r++) {
     const int ri = p.rec_cell[2 * r], rj = p.rec_cell[2 * r + 1];
     if (ri < 0) continue;
-    lam[sh + (long long)ri * p.g.pitch + rj] += p.res[((long long)s * p.nrec + r) * p.nt + p.nt - 1];
+    const long long c = sh + (long long)ri * p.g.pitch + rj;
+    const float rv = p.res[((long long)s * p.nrec + r) * p.nt + p.nt - 1];
+    lam[c] += rv;
+    hx[c] += rv;  // hhat = lambda at a receiver (never inside the CPML layer)
+    hz[c] += rv;
   }
   if (p.src_part == nullptr) return;
   const int i0 = p.src_box[2 * s], j0 = p.src_box[2 * s + 1], nb = p.src_n;
@@ -394,8 +398,8 @@ cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaSt
   k_finite_check<<<304, 256, 0, st>>>(a, n, status);
   return cudaGetLastError();
 }
-cudaError_t launch_adj_init(const AcuStep& p, float* lam, cudaStream_t st) {
-  k_adj_init<<<p.S, 32, 0, st>>>(p, lam);
+cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st) {
+  k_adj_init<<<p.S, 32, 0, st>>>(p, lam, hx, hz);
   return cudaGetLastError();
 }
 cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st) {
