@@ -42,6 +42,10 @@ constexpr int QZH = TILE_Z + 8;          // 40: half rows [z0-4, z0+TZ+4)
 constexpr int U_BYTES = UW * UH * 4;     // 15360
 constexpr int M_BYTES = MW * MH * 4;     // 12464
 constexpr int M_SLOT = (M_BYTES + 127) / 128 * 128;
+#ifndef FWI_FWD_CTAS
+#define FWI_FWD_CTAS 4
+#endif
+constexpr int FWD_CTAS = FWI_FWD_CTAS;     // resident forward CTAs per SM the registers are sized for
 constexpr int XS_BYTES = TILE_Z * UW * 4;  // 10240: adjoint x operand tile
 constexpr int ZS_BYTES = UH * TILE_X * 4;  // 12288: adjoint z operand tile
 
@@ -120,12 +124,12 @@ __device__ __forceinline__ void fetch_tile(const CUtensorMap* fmap, const CUtens
 
 // Shared memory of the step kernels (every array a multiple of 128 bytes).
 struct FwdSmem {
-  float u[2][UH * UW];
-  float m[2][M_SLOT / 4];
+  float u[UH * UW];
+  float m[M_SLOT / 4];
   float qx[TILE_Z * QXW];
   float qz[QZH * TILE_X];
   float red[32];
-  uint64_t bar[2];
+  uint64_t bar;
 };
 struct AdjSmem {
   float xs[TILE_Z * UW];     // x stencil operand (lambda or Hx): own rows, cols [x0-H, x0+TX+H)
@@ -147,7 +151,7 @@ struct AdjSmem {
 // kept multiplied by dt^2). RECORD writes the receiver samples; STORE keeps
 // p = D+u + psi of every half point (the operand of the gradient correlation).
 template <int N, bool RECORD, bool STORE>
-__global__ void __launch_bounds__(NTHREADS, 3)
+__global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     acu_fwd_step(const __grid_constant__ CUtensorMap tmap_u, const __grid_constant__ CUtensorMap tmap_m,
                  const AcuStep p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -156,21 +160,19 @@ __global__ void __launch_bounds__(NTHREADS, 3)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
 
+  // one operand buffer: the next tile's fetch is issued once stage 1 of this
+  // tile (its last reader) is done, and overlaps stage 2
   if (tid == 0) {
-    mbar_init(&sh.bar[0], 1);
-    mbar_init(&sh.bar[1], 1);
+    mbar_init(&sh.bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < p.ntiles)
-    fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, blockIdx.x, sh.u[0], sh.m[0], &sh.bar[0]);
+    fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, blockIdx.x, sh.u, sh.m, &sh.bar);
 
   int it = 0;
   for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
-    const int b = it & 1;
     const int tn = t + gridDim.x;
-    if (tid == 0 && tn < p.ntiles)
-      fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, tn, sh.u[b ^ 1], sh.m[b ^ 1], &sh.bar[b ^ 1]);
     const TileId id = tile_decode(g, t);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
@@ -190,16 +192,16 @@ __global__ void __launch_bounds__(NTHREADS, 3)
       re = __ldg(p.thr_rec_start + key + 1);
     }
 
-    const bool ok = mbar_wait(&sh.bar[b], (it >> 1) & 1);
+    const bool ok = mbar_wait(&sh.bar, it & 1);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.status, ST_TIMEOUT);
-        tma_drain(sh.bar, it, tn < p.ntiles);
+        mbar_wait(&sh.bar, it & 1);  // let a late copy land before the CTA exits
       }
       return;
     }
-    const float* su = sh.u[b];
-    const float* sm = sh.m[b];
+    const float* su = sh.u;
+    const float* sm = sh.m;
     const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
 
     // ---- stage 1a: x fluxes q = m_half (D+u + psi) at 4 half columns of row r
@@ -319,7 +321,12 @@ __global__ void __launch_bounds__(NTHREADS, 3)
       const int k = tid - 128;
       qx_item(k >> 1, (k & 1) ? QXW / 4 - 1 : 0, false);
     }
+    // u^n at the own cells, read before the operand buffer is refilled
+    float4 ucur[2];
+    ucur[0] = ld4(su + (2 * ty + H) * UW + 4 * tx + H);
+    ucur[1] = ld4(su + (2 * ty + 1 + H) * UW + 4 * tx + H);
     __syncthreads();
+    if (tid == 0 && tn < p.ntiles) fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, tn, sh.u, sh.m, &sh.bar);
 
     // ---- stage 2: divergence + CPML zeta + leapfrog + source + receivers
     float hzv[2][4];
@@ -380,7 +387,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           rv[0] += zn.x; rv[1] += zn.y; rv[2] += zn.z; rv[3] += zn.w;
         }
       }
-      const float4 uc = ld4(su + (r + H) * UW + 4 * tx + H);
+      const float4 uc = ucur[rr];
       un[rr][0] = 2.f * uc.x - up[rr].x + rv[0];
       un[rr][1] = 2.f * uc.y - up[rr].y + rv[1];
       un[rr][2] = 2.f * uc.z - up[rr].z + rv[2];
@@ -410,7 +417,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         p.seis[((long long)s * p.nrec + rc) * p.nt + p.n] = e == 0 ? ur[0] : (e == 1 ? ur[1] : (e == 2 ? ur[2] : ur[3]));
       }
     }
-    __syncthreads();  // the tile buffer and the flux arrays are free again
+    __syncthreads();  // the flux arrays are free again
   }
 }
 
