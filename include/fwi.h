@@ -168,6 +168,20 @@ fwi_status fwi_forward_noalloc(const fwi_model *model, const fwi_sources *src,
 fwi_status fwi_last_timing(const fwi_ctx *ctx, float *phase_ms3, float *kernel_ms3,
                            int64_t *launches);
 
+/* Elastic gradient in the velocity parametrisation: the chain rule through
+ * lambda = rho (vp^2 - 2 vs^2) and mu = rho vs^2 (Implementation, elastic
+ * wave equation) applied to the grad output of fwi_misfit_grad:
+ *   dJ/dvp  = 2 rho vp dJ/dlambda
+ *   dJ/dvs  = 2 rho vs (dJ/dmu - 2 dJ/dlambda)
+ *   dJ/drho = (vp^2 - 2 vs^2) dJ/dlambda + vs^2 dJ/dmu + dJ/drho (lambda, mu fixed)
+ * vp, vs, rho  [n] device arrays (the model of the fwi_misfit_grad call).
+ * grad_lame    [3][n] device array (dJ/dlambda, dJ/dmu, dJ/drho).
+ * grad_vel     [3][n] device array receiving (dJ/dvp, dJ/dvs, dJ/drho); may be grad_lame.
+ * Asynchronous on cuda_stream; FWI_EINVAL on a NULL pointer or n < 0. */
+fwi_status fwi_elastic_velocity_grad(const float *vp, const float *vs, const float *rho,
+                                     const float *grad_lame, float *grad_vel, int64_t n,
+                                     void *cuda_stream);
+
 /* Message describing the last error of the calling thread ("" if none). */
 const char *fwi_last_error(void);
 

@@ -236,3 +236,15 @@ def elastic_misfit_grad(g: dict, vp, vs, rho, stf, x0, mt, observed):
     res = d - np.asarray(observed, dtype=np.float64)
     J = 0.5 * float(np.sum(res * res))
     return (J,) + elastic_adjoint(g, vp, vs, rho, stf, x0, mt, res)
+
+
+def elastic_velocity_grad(vp, vs, rho, g_lam, g_mu, g_rho):
+    """(dJ/dvp, dJ/dvs, dJ/drho) from the Lame-parameter gradient, by the chain
+    rule through lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2 (Implementation,
+    elastic wave equation: the inversion parameters are lambda, mu, rho)."""
+    vp, vs, rho = (np.asarray(a, np.float64) for a in (vp, vs, rho))
+    dl_dvp, dl_dvs, dl_drho = 2 * rho * vp, -4 * rho * vs, vp ** 2 - 2 * vs ** 2
+    dm_dvs, dm_drho = 2 * rho * vs, vs ** 2
+    return (g_lam * dl_dvp,
+            g_lam * dl_dvs + g_mu * dm_dvs,
+            g_lam * dl_drho + g_mu * dm_drho + g_rho)

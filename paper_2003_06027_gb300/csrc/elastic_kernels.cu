@@ -995,6 +995,18 @@ __global__ void k_ela_grad(const double* __restrict__ G, Grid g, const float* __
   }
 }
 
+// Chain rule from (lambda, mu, rho) to (vp, vs, rho) per cell; in place allowed.
+__global__ void k_ela_velocity_grad(const float* __restrict__ vp, const float* __restrict__ vs,
+                                    const float* __restrict__ rho, const float* gin, float* gout, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float a = vp[i], b = vs[i], r = rho[i];
+    const float gl = gin[i], gm = gin[n + i], gr = gin[2 * n + i];
+    gout[i] = 2.f * r * a * gl;
+    gout[n + i] = 2.f * r * b * (gm - 2.f * gl);
+    gout[2 * n + i] = (a * a - 2.f * b * b) * gl + b * b * gm + gr;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers: one-time kernel attributes and occupancy-sized persistent grids
 // per device, tensor maps per call.
@@ -1142,6 +1154,13 @@ cudaError_t launch_ela_fold(float* const* parts, int S, long long slice, double*
   Parts5 p5;
   for (int f = 0; f < 5; f++) p5.f[f] = parts[f];
   k_ela_fold<<<608, 256, 0, st>>>(p5, S, slice, G);
+  return cudaGetLastError();
+}
+cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
+                                     float* gout, long long n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + 255) / 256, 1216);
+  k_ela_velocity_grad<<<(int)blocks, 256, 0, st>>>(vp, vs, rho, gin, gout, n);
   return cudaGetLastError();
 }
 cudaError_t launch_ela_grad(const double* G, const Grid& g, const float* mxz, const float* mu_pad, const float* bx,

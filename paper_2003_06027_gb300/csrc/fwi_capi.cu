@@ -38,6 +38,8 @@ cudaError_t launch_model_check(const float* c, long long n, float coef, int* sta
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
                           int* status, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
+cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
+                                     float* gout, long long n, cudaStream_t st);
 cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st);
 cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st);
 cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st);
@@ -435,6 +437,16 @@ fwi_status fwi_destroy(fwi_ctx* ctx) {
 }
 
 const char* fwi_last_error(void) { return g_err.c_str(); }
+
+fwi_status fwi_elastic_velocity_grad(const float* vp, const float* vs, const float* rho, const float* grad_lame,
+                                     float* grad_vel, int64_t n, void* stream) {
+  if (n < 0) return fail(FWI_EINVAL, "n must be >= 0");
+  if (n > 0 && (!vp || !vs || !rho || !grad_lame || !grad_vel))
+    return fail(FWI_EINVAL, "vp, vs, rho, grad_lame and grad_vel must not be NULL");
+  CK(launch_ela_velocity_grad(vp, vs, rho, grad_lame, grad_vel, n, (cudaStream_t)stream));
+  g_err.clear();
+  return FWI_OK;
+}
 
 fwi_status fwi_last_timing(const fwi_ctx* ctx, float* phase_ms3, float* kernel_ms3, int64_t* launches) {
   if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");

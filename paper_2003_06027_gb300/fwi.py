@@ -52,7 +52,7 @@ _lib_lock = threading.Lock()
 _ctx = threading.local()
 
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
-           "fwi_forward_noalloc", "fwi_last_error"]
+           "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -80,6 +80,7 @@ def library(build_if_missing: bool = True):
             L.fwi_forward_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
                                               ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
                                               P]
+            L.fwi_elastic_velocity_grad.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
             L.fwi_last_error.restype = ctypes.c_char_p
             for f in EXPORTS[:-1]:
                 getattr(L, f).restype = ctypes.c_int
@@ -312,6 +313,24 @@ def misfit_grad_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, observed, *, d
         float(dt), _ptr(obs), K, _ptr(out["misfit"]), _ptr(out.get("grad")), _ptr(out.get("grad_stf")),
         _ptr(out.get("grad_x0")), _ptr(out.get("seis")), _stream(ref, stream)))
     return out["misfit"], out["grad"], out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
+def elastic_velocity_grad(vp, vs, rho, grad_lame, out=None, stream=None):
+    """(dJ/dvp, dJ/dvs, dJ/drho) [3][nz][nx] from the (dJ/dlambda, dJ/dmu, dJ/drho)
+    output of misfit_grad_elastic (fwi_elastic_velocity_grad). CUDA tensors on
+    one device; ``out`` may be ``grad_lame`` itself."""
+    vp, vs, rho = (_arr(a, np.float32) for a in (vp, vs, rho))
+    gl = _arr(grad_lame, np.float32)
+    if not (_is_torch(vp) and vp.is_cuda):
+        raise ValueError("elastic_velocity_grad takes CUDA tensors")
+    n = vp.numel()
+    if gl.numel() != 3 * n or vs.numel() != n or rho.numel() != n:
+        raise ValueError("grad_lame must hold 3 fields shaped like vp")
+    if out is None:
+        out = _empty_like_place(vp, (3,) + tuple(vp.shape))
+    _check(library().fwi_elastic_velocity_grad(_ptr(vp), _ptr(vs), _ptr(rho), _ptr(gl), _ptr(out), n,
+                                               _stream(vp, stream)))
+    return out
 
 
 def problem_kwargs(d: dict) -> dict:

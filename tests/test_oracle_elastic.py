@@ -209,3 +209,29 @@ def test_zero_residual_zero_gradient():
     obs = oracle.elastic_forward(g, vp, vs, rho, stf, x0, mt)
     J, gl, gm, gr, gs, gx = oracle.elastic_misfit_grad(g, vp, vs, rho, stf, x0, mt, obs)
     assert J == 0 and not np.any(gl) and not np.any(gm) and not np.any(gr) and not np.any(gs)
+
+
+def test_velocity_gradient_vs_complex_step():
+    """The chain rule to (vp, vs, rho) against complex-step derivatives taken in
+    the velocity parametrisation itself (the oracle forward is evaluated with a
+    complex vp, vs or rho, so lambda and mu carry the perturbation through the
+    medium set-up of the scheme)."""
+    nz, nx, nt = 14, 18, 100
+    g = _geom(nz, nx, nt, order=4, npml=5, src_kind=1, rec=([0, 6, 13], [2, 17, 9]))
+    vp, vs, rho = _medium(21, nz, nx)
+    x0 = np.array([[81.3, 64.9]])
+    mt = np.array([[0.3, -0.9, 0.7]])
+    stf = synth.ricker(24.0, 1e-3, nt, dtype=np.float64)[None]
+    obs = oracle.elastic_forward(g, *_medium(22, nz, nx), stf, x0, mt)
+    J, gl, gm, gr, _, _ = oracle.elastic_misfit_grad(g, vp, vs, rho, stf, x0, mt, obs)
+    gvp, gvs, grho = oracle.elastic_velocity_grad(vp, vs, rho, gl, gm, gr)
+    h = 1e-30
+    rng = np.random.default_rng(23)
+    for k, grad in enumerate((gvp, gvs, grho)):
+        dirn = rng.standard_normal((nz, nx)) * (vp, vs, rho)[k] * 1e-2
+        args = [a.astype(np.complex128) for a in (vp, vs, rho)]
+        args[k] = args[k] + 1j * h * dirn
+        d = oracle.elastic_forward(g, *args, stf, x0, mt, complex_step=True)
+        r = d - obs
+        cs = (0.5 * np.sum(r * r)).imag / h
+        assert np.sum(grad * dirn) == pytest.approx(cs, rel=1e-9), k
