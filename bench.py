@@ -69,7 +69,8 @@ def load_peaks():
 
 def load_traffic(kernel_file):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source is unchanged since the counters were taken."""
+    source (its file and the two headers it includes) is unchanged since the
+    counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -78,8 +79,10 @@ def load_traffic(kernel_file):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    src = open(os.path.join(ROOT, "paper_2003_06027_gb300", "csrc", kernel_file), "rb").read()
-    if kv.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    h = hashlib.sha256()
+    for f in (kernel_file, "tma.cuh", "fwi_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2003_06027_gb300", "csrc", f), "rb").read())
+    if kv.get("source_sha256") != h.hexdigest():
         return None
     try:
         return float(kv["adj_dram_bytes_per_launch_full"])

@@ -49,7 +49,7 @@ typedef enum {
   FWI_ENOMEM = 3,     /* device workspace could not be allocated */
   FWI_ECUDA = 4,      /* a CUDA runtime call failed (message in fwi_last_error) */
   FWI_EUNSTABLE = 5,  /* non-finite value in the seismograms or the misfit */
-  FWI_ETIMEOUT = 6,   /* reserved: a bounded device wait gave up */
+  FWI_ETIMEOUT = 6,   /* a bounded device wait gave up (results invalid; context usable) */
   FWI_ENOTIMPL = 7    /* combination not supported by this build */
 } fwi_status;
 
@@ -181,6 +181,16 @@ fwi_status fwi_last_timing(const fwi_ctx *ctx, float *phase_ms3, float *kernel_m
 fwi_status fwi_elastic_velocity_grad(const float *vp, const float *vs, const float *rho,
                                      const float *grad_lame, float *grad_vel, int64_t n,
                                      void *cuda_stream);
+
+/* Self-test of the failure detection inside the step kernels. Every step
+ * kernel waits for its tile copies on an mbarrier with a bound (2^24 polls or
+ * 1 s, whichever comes first), after which it records a timeout that the call
+ * returns as FWI_ETIMEOUT. This call runs that same wait, in one thread on the
+ * context's device, on a barrier whose expected bytes no copy will deliver.
+ * Returns FWI_ETIMEOUT when the wait gave up as designed (the expected result),
+ * with the time it waited in *waited_ns (may be NULL); the device and the
+ * context stay usable. Synchronous; allocates and frees 16 bytes. */
+fwi_status fwi_selftest_wait_timeout(fwi_ctx *ctx, int64_t *waited_ns);
 
 /* Message describing the last error of the calling thread ("" if none). */
 const char *fwi_last_error(void);

@@ -799,6 +799,22 @@ __global__ void __launch_bounds__(NTHREADS, 3)
 }
 
 // ---------------------------------------------------------------------------
+// Self-test of the bounded wait: one thread waits, as a step kernel waits for
+// its tile, on an mbarrier whose 16 expected bytes no copy will ever deliver.
+__global__ void k_selftest_wait(int* status, unsigned long long* waited_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_expect_tx(&bar, 16);
+    const unsigned long long t0 = global_ns();
+    const bool ok = mbar_wait(&bar, 0);
+    *waited_ns = global_ns() - t0;
+    *status = ok ? 0 : ST_TIMEOUT;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side: tensor maps, one-time kernel attributes, launchers.
 namespace {
 
@@ -840,6 +856,11 @@ cudaError_t ensure_init(int* dev_out) {
 }
 
 }  // namespace
+
+cudaError_t launch_selftest_wait(int* status, unsigned long long* waited_ns, cudaStream_t st) {
+  k_selftest_wait<<<1, 32, 0, st>>>(status, waited_ns);
+  return cudaGetLastError();
+}
 
 cudaError_t acu_kernels_init() {
   int dev;

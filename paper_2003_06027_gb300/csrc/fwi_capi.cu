@@ -38,6 +38,7 @@ cudaError_t launch_model_check(const float* c, long long n, float coef, int* sta
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
                           int* status, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
+cudaError_t launch_selftest_wait(int* status, unsigned long long* waited_ns, cudaStream_t st);
 cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
                                      float* gout, long long n, cudaStream_t st);
 cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st);
@@ -382,12 +383,12 @@ fwi_status fwi::finish_status_dev(fwi_ctx* ctx, const int* d_status, cudaStream_
   CK(cudaMemcpyAsync(ctx->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const int s = *ctx->h_status;
+  if (s & ST_TIMEOUT) return fail(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");  // first: later results are invalid
   if (s & ST_BADMODEL) return fail(FWI_EINVAL, "the medium must be finite with vp > 0, rho > 0, vp^2 >= 2 vs^2");
   if (s & ST_BADREC) return fail(FWI_EINVAL, "a receiver lies outside the physical grid");
   if (s & ST_BADSRC) return fail(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
   if (s & ST_CFL) return fail(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
   if (s & ST_NONFINITE) return fail(FWI_EUNSTABLE, "non-finite value in the seismograms or the misfit");
-  if (s & ST_TIMEOUT) return fail(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");
   return FWI_OK;
 }
 
@@ -446,6 +447,25 @@ fwi_status fwi_elastic_velocity_grad(const float* vp, const float* vs, const flo
   CK(launch_ela_velocity_grad(vp, vs, rho, grad_lame, grad_vel, n, (cudaStream_t)stream));
   g_err.clear();
   return FWI_OK;
+}
+
+fwi_status fwi_selftest_wait_timeout(fwi_ctx* ctx, int64_t* waited_ns) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  CK(cudaSetDevice(ctx->device));
+  void* buf = nullptr;
+  CK(cudaMalloc(&buf, 16));
+  int* dst = reinterpret_cast<int*>(buf);
+  unsigned long long* dns = reinterpret_cast<unsigned long long*>(static_cast<char*>(buf) + 8);
+  cudaError_t e = launch_selftest_wait(dst, dns, 0);
+  int st = 0;
+  unsigned long long ns = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, dst, sizeof st, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&ns, dns, sizeof ns, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(FWI_ECUDA, std::string("selftest: ") + cudaGetErrorString(e));
+  if (waited_ns) *waited_ns = (int64_t)ns;
+  if (st & ST_TIMEOUT) return fail(FWI_ETIMEOUT, "device wait gave up as designed (self-test)");
+  return fail(FWI_ECUDA, "self-test: a wait that cannot complete reported completion");
 }
 
 fwi_status fwi_last_timing(const fwi_ctx* ctx, float* phase_ms3, float* kernel_ms3, int64_t* launches) {

@@ -11,7 +11,8 @@
 
 namespace fwi {
 
-constexpr long long WAIT_SPINS = 1LL << 24;  // bound on mbarrier polls before a kernel reports a timeout
+constexpr long long WAIT_SPINS = 1LL << 24;           // bound on mbarrier polls before a kernel reports a timeout
+constexpr unsigned long long WAIT_NS = 1000000000ull;  // and on the wall time of one wait (1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -32,10 +33,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: false if the phase did not complete within WAIT_SPINS polls.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false if the phase did not complete within WAIT_SPINS polls or
+// WAIT_NS nanoseconds, whichever comes first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < WAIT_SPINS; i++)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long i = 0; i < WAIT_SPINS; i++) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0 && global_ns() - t0 > WAIT_NS) return false;
+  }
   return false;
 }
 // After a timed-out wait: one more bounded wait on each copy this CTA may still

@@ -52,7 +52,7 @@ _lib_lock = threading.Lock()
 _ctx = threading.local()
 
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
-           "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_last_error"]
+           "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -81,6 +81,7 @@ def library(build_if_missing: bool = True):
                                               ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
                                               P]
             L.fwi_elastic_velocity_grad.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
+            L.fwi_selftest_wait_timeout.argtypes = [P, P]
             L.fwi_last_error.restype = ctypes.c_char_p
             for f in EXPORTS[:-1]:
                 getattr(L, f).restype = ctypes.c_int
@@ -331,6 +332,14 @@ def elastic_velocity_grad(vp, vs, rho, grad_lame, out=None, stream=None):
     _check(library().fwi_elastic_velocity_grad(_ptr(vp), _ptr(vs), _ptr(rho), _ptr(gl), _ptr(out), n,
                                                _stream(vp, stream)))
     return out
+
+
+def selftest_wait_timeout(device: int = 0):
+    """(status, waited_ns) of fwi_selftest_wait_timeout: FWI_ETIMEOUT is the
+    expected status (the bounded device wait gave up as designed)."""
+    ns = ctypes.c_int64()
+    st = library().fwi_selftest_wait_timeout(context(device), ctypes.byref(ns))
+    return int(st), int(ns.value)
 
 
 def problem_kwargs(d: dict) -> dict:

@@ -262,3 +262,17 @@ def test_fwi_full_size_sampled(fwi_lib, fwi_problem):
     fd = (Jo(c0 + eps * dirn) - Jo(c0 - eps * dirn)) / (2 * eps)
     gd = float(np.sum(np.float64(gg2) * dirn))
     assert abs(gd - fd) <= GRAD_TOL * abs(fd), (gd, fd)
+
+
+def test_bounded_wait_gives_up_and_context_survives(fwi_lib):
+    """The step kernels' bounded tile wait, run on a barrier that nothing
+    completes, gives up after about a second with FWI_ETIMEOUT; the context
+    then still computes a correct forward."""
+    from paper_2003_06027_gb300 import fwi
+
+    st, ns = fwi.selftest_wait_timeout(0)
+    assert st == 6, (st, fwi.library().fwi_last_error())  # FWI_ETIMEOUT
+    assert 0.5e9 < ns < 5e9, ns
+    d = synth.random_acoustic(23, 20, 24, 60, 1, 4, 4, nrec=4)
+    do = oracle.acoustic_forward(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(gpu_forward(d), do) <= SEIS_TOL
