@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "fwi_internal.cuh"
 #include "tma.cuh"
@@ -237,7 +238,8 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
 #pragma unroll
       for (int e = 0; e < 4; e++) q[e] = (rowok && hb + e >= 0 && hb + e < g.Nx - 1) ? (mv[e] + mv[e + 1]) * pp[e] : 0.f;
       st4(sh.qx + r * QXW + 4 * gq, make_float4(q[0], q[1], q[2], q[3]));
-      if (STORE && own && rowok) st4(p.slot_px + id0, make_float4(pp[0], pp[1], pp[2], pp[3]));
+      // every own row is written (zero beyond the grid): the adjoint multiplies these by zero there
+      if (STORE && own) st4(p.slot_px + id0, rowok ? make_float4(pp[0], pp[1], pp[2], pp[3]) : make_float4(0.f, 0.f, 0.f, 0.f));
     };
     // ---- stage 1b: z fluxes at one half row (the tile's halo rows)
     auto qz_item = [&](int hr, int c) {
@@ -311,7 +313,9 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         q[2] = (hv && xb + 2 < g.Nx) ? (ma.z + mb.z) * pp[rr][2] : 0.f;
         q[3] = (hv && xb + 3 < g.Nx) ? (ma.w + mb.w) * pp[rr][3] : 0.f;
         st4(sh.qz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(q[0], q[1], q[2], q[3]));
-        if (STORE && hz < g.Nz) st4(p.slot_pz + idz, make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3]));
+        if (STORE)
+          st4(p.slot_pz + idz, hz < g.Nz ? make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3])
+                                         : make_float4(0.f, 0.f, 0.f, 0.f));
       }
     }
     if (tid < 128) {
@@ -488,313 +492,321 @@ __global__ void __launch_bounds__(NTHREADS, 3)
       }
       return;
     }
-    const float* sx = sh.xs;  // [TILE_Z][UW]: x operand, cols [x0-H, x0+TX+H)
-    const float* sz = sh.zs;  // [UH][TILE_X]: z operand, rows [z0-H, z0+TZ+H)
-    const float* sm = sh.m;
-    const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
+    // the tile body, compiled twice: with the grid-edge masks, and without them for
+    // tiles whose stencils and halo stay strictly inside the padded grid
+    auto tile_body = [&](auto edge_c) {
+      constexpr bool EDGE = decltype(edge_c)::value;
+      const float* sx = sh.xs;  // [TILE_Z][UW]: x operand, cols [x0-H, x0+TX+H)
+      const float* sz = sh.zs;  // [UH][TILE_X]: z operand, rows [z0-H, z0+TZ+H)
+      const float* sm = sh.m;
+      const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
 
-    // ---- stage 1a: x half points of row r: qbar, correlation, gbar
-    auto x_item = [&](int r, int gq, bool own, bool image, const float4* pre, float im[4]) {
-      const int z = z0 + r, hb = x0 - 4 + 4 * gq;
-      float v[12];
-      unpack12(sx + r * UW + 4 * gq, v);
-      const long long id0 = base + (long long)z * pitch + hb;
-      const float4 m4 = ld4(sm + (r + 4) * MW + 4 * gq);
-      const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
-      float pf[4] = {0.f, 0.f, 0.f, 0.f};
-      if (pre) f4a(*pre, pf);
-      else if (image) f4a(ldg4(p.slot_px + id0), pf);
-      const bool rowok = z < g.Nz;
-      float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
-      if (pmlx) {  // one round trip: tables and P together
-        a4 = ldg4(p.axh + hb + TAB_OFF);
-        b4 = ldg4(p.bxh + hb + TAB_OFF);
-        P4 = ld4(p.px_in + id0);
-      }
-      float av[4], bv[4], Pv[4];
-      f4a(a4, av);
-      f4a(b4, bv);
-      f4a(P4, Pv);
-      float gb[4], Pn[4];
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        float dq = 0.f;
-#pragma unroll
-        for (int k = 1; k <= N; k++) dq += p.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
-        const bool inh = rowok && hb + e >= 0 && hb + e < g.Nx - 1;
-        const float qb = inh ? dq : 0.f;
-        const float pb = (mv[e] + mv[e + 1]) * qb;
-        const float tt = Pv[e] + pb;
-        gb[e] = inh ? pb + av[e] * tt : 0.f;
-        Pn[e] = av[e] != 0.f ? bv[e] * tt : 0.f;  // P stays zero outside the layer
-        im[e] = qb * pf[e];
-      }
-      if (pmlx && own && rowok && (av[0] != 0.f || av[1] != 0.f || av[2] != 0.f || av[3] != 0.f))
-        st4(p.px_out + id0, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
-      st4(sh.gx + r * QXW + 4 * gq, make_float4(gb[0], gb[1], gb[2], gb[3]));
-    };
-    // ---- stage 1b: one z half row (the tile's halo rows)
-    auto z_item = [&](int hr, int c, bool image) {
-      const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
-      const long long idz = base + (long long)hz * pitch + xc;
-      float pf[4] = {0.f, 0.f, 0.f, 0.f};
-      if (image) f4a(ldg4(p.slot_pz + idz), pf);
-      float aa = 0.f;
-      float Pv[4] = {0.f, 0.f, 0.f, 0.f};
-      if (pmlz) {
-        aa = __ldg(p.azh + hz + TAB_OFF);
-        f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
-      }
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int k = 1; k <= N; k++)
-        acc4(acc, p.c1z[k - 1], ld4(sz + (hr + 4 + k) * TILE_X + 4 * c), ld4(sz + (hr + 5 - k) * TILE_X + 4 * c));
-      float dq[4];
-      f4a(acc, dq);
-      const bool hv = hz >= 0 && hz < g.Nz - 1;
-      const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
-      const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
-      float gb[4], im[4];
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const bool inh = hv && xc + e < g.Nx;
-        const float qb = inh ? dq[e] : 0.f;
-        const float pb = mhv[e] * qb;
-        gb[e] = inh ? pb + aa * (Pv[e] + pb) : 0.f;
-        im[e] = qb * pf[e];
-      }
-      st4(sh.gz + hr * TILE_X + 4 * c, make_float4(gb[0], gb[1], gb[2], gb[3]));
-      if (image) st4(sh.imz + 4 * c, make_float4(im[0], im[1], im[2], im[3]));
-    };
-
-    // own x half points xb+e+1/2 of rows 2ty, 2ty+1: their images stay in registers
-    float imx[2][4], imz[2][4];
-    x_item(2 * ty, tx + 1, true, true, &pfx[0], imx[0]);
-    x_item(2 * ty + 1, tx + 1, true, true, &pfx[1], imx[1]);
-    {
-      // own z half rows 2ty, 2ty+1 from a (2N+1)-row window of hhat
-      float aa[2] = {0.f, 0.f}, bb[2] = {1.f, 1.f};
-      float4 Pz[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-      if (pmlz) {
-#pragma unroll
-        for (int rr = 0; rr < 2; rr++) {
-          aa[rr] = __ldg(p.azh + zr0 + rr + TAB_OFF);
-          bb[rr] = __ldg(p.bzh + zr0 + rr + TAB_OFF);
-          Pz[rr] = *reinterpret_cast<const float4*>(p.pz_in + base + (long long)(zr0 + rr) * pitch + xb);
+      // ---- stage 1a: x half points of row r: qbar, correlation, gbar
+      auto x_item = [&](int r, int gq, bool own, bool image, const float4* pre, float im[4]) {
+        const int z = z0 + r, hb = x0 - 4 + 4 * gq;
+        float v[12];
+        unpack12(sx + r * UW + 4 * gq, v);
+        const long long id0 = base + (long long)z * pitch + hb;
+        const float4 m4 = ld4(sm + (r + 4) * MW + 4 * gq);
+        const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
+        float pf[4] = {0.f, 0.f, 0.f, 0.f};
+        if (pre) f4a(*pre, pf);
+        else if (image && (!EDGE || hb >= 0)) f4a(ldg4(p.slot_px + id0), pf);  // the apron holds no flux
+        const bool rowok = !EDGE || z < g.Nz;
+        float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
+        if (pmlx) {  // one round trip: tables and P together
+          a4 = ldg4(p.axh + hb + TAB_OFF);
+          b4 = ldg4(p.bxh + hb + TAB_OFF);
+          P4 = ld4(p.px_in + id0);
         }
-      }
-      float4 w[2 * N + 1];
-#pragma unroll
-      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sz + (2 * ty + H - N + 1 + t2) * TILE_X + 4 * tx);
-      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-#pragma unroll
-      for (int k = 1; k <= N; k++) {
-        acc4(a0, p.c1z[k - 1], w[k + N - 1], w[N - k]);
-        acc4(a1, p.c1z[k - 1], w[k + N], w[N - k + 1]);
-      }
-      float dq[2][4];
-      f4a(a0, dq[0]);
-      f4a(a1, dq[1]);
-#pragma unroll
-      for (int rr = 0; rr < 2; rr++) {
-        const int hz = zr0 + rr;
-        const long long idz = base + (long long)hz * pitch + xb;
-        const bool hv = hz < g.Nz - 1;
-        const float4 ma = ld4(sm + (2 * ty + 4 + rr) * MW + 4 * tx + 4);
-        const float4 mb = ld4(sm + (2 * ty + 5 + rr) * MW + 4 * tx + 4);
-        const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
-        float pf[4], Pv[4];
-        f4a(pfz[rr], pf);
-        f4a(Pz[rr], Pv);
+        float av[4], bv[4], Pv[4];
+        f4a(a4, av);
+        f4a(b4, bv);
+        f4a(P4, Pv);
         float gb[4], Pn[4];
-#pragma unroll
+  #pragma unroll
         for (int e = 0; e < 4; e++) {
-          const bool inh = hv && xb + e < g.Nx;
-          const float qb = inh ? dq[rr][e] : 0.f;
-          const float pb = mhv[e] * qb;
+          float dq = 0.f;
+  #pragma unroll
+          for (int k = 1; k <= N; k++) dq += p.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
+          const bool inh = !EDGE || (rowok && hb + e >= 0 && hb + e < g.Nx - 1);
+          const float qb = inh ? dq : 0.f;
+          const float pb = (mv[e] + mv[e + 1]) * qb;
           const float tt = Pv[e] + pb;
-          gb[e] = inh ? pb + aa[rr] * tt : 0.f;
-          Pn[e] = inh ? bb[rr] * tt : 0.f;
-          imz[rr][e] = qb * pf[e];
+          gb[e] = inh ? pb + av[e] * tt : 0.f;
+          Pn[e] = av[e] != 0.f ? bv[e] * tt : 0.f;  // P stays zero outside the layer
+          im[e] = qb * pf[e];
         }
-        if (aa[rr] != 0.f && hz < g.Nz) st4(p.pz_out + idz, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
-        st4(sh.gz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(gb[0], gb[1], gb[2], gb[3]));
-      }
-      // half row 2ty+1 is the upper neighbour of the next thread row's cells
-      st4(sh.imz + (ty + 1) * TILE_X + 4 * tx, make_float4(imz[1][0], imz[1][1], imz[1][2], imz[1][3]));
-    }
-    if (tid < 128) {
-      const int hr0 = tid >> 4;
-      const int hr = hr0 < 4 ? hr0 : hr0 + 32;
-      z_item(hr, tid & 15, hr == 3);  // of the halo rows only half row z0-1 feeds this tile's gradient
-    } else if (tid < 192) {
-      const int k = tid - 128;
-      const bool left = (k & 1) == 0;
-      float im[4];
-      x_item(k >> 1, left ? 0 : QXW / 4 - 1, false, left, nullptr, im);  // only half column x0-1 feeds the gradient
-      if (left) sh.imx[k >> 1] = im[3];
-    }
-    // lambda_{n+1} at the own cells, from a stencil tile that holds lambda itself
-    float4 lc[2];
-#pragma unroll
-    for (int rr = 0; rr < 2; rr++) {
-      const int r = 2 * ty + rr;
-      if (!pmlx) lc[rr] = ld4(sx + r * UW + H + 4 * tx);
-      else if (!pmlz) lc[rr] = ld4(sz + (r + H) * TILE_X + 4 * tx);
-      else lc[rr] = ldg4(p.lam + (long long)p.cur * p.S * g.slice + base + (long long)(z0 + r) * pitch + xb);
-    }
-    __syncthreads();
-    if (tid == 0 && tn < p.ntiles) fetch(tn);  // the operand buffer is free
+        if (pmlx && own && rowok && (av[0] != 0.f || av[1] != 0.f || av[2] != 0.f || av[3] != 0.f))
+          st4(p.px_out + id0, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
+        st4(sh.gx + r * QXW + 4 * gq, make_float4(gb[0], gb[1], gb[2], gb[3]));
+      };
+      // ---- stage 1b: one z half row (the tile's halo rows)
+      auto z_item = [&](int hr, int c, bool image) {
+        const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
+        const long long idz = base + (long long)hz * pitch + xc;
+        float pf[4] = {0.f, 0.f, 0.f, 0.f};
+        if (image && (!EDGE || hz >= 0)) f4a(ldg4(p.slot_pz + idz), pf);
+        float aa = 0.f;
+        float Pv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (pmlz) {
+          aa = __ldg(p.azh + hz + TAB_OFF);
+          f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
+        }
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  #pragma unroll
+        for (int k = 1; k <= N; k++)
+          acc4(acc, p.c1z[k - 1], ld4(sz + (hr + 4 + k) * TILE_X + 4 * c), ld4(sz + (hr + 5 - k) * TILE_X + 4 * c));
+        float dq[4];
+        f4a(acc, dq);
+        const bool hv = !EDGE || (hz >= 0 && hz < g.Nz - 1);
+        const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
+        const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
+        float gb[4], im[4];
+  #pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const bool inh = !EDGE || (hv && xc + e < g.Nx);
+          const float qb = inh ? dq[e] : 0.f;
+          const float pb = mhv[e] * qb;
+          gb[e] = inh ? pb + aa * (Pv[e] + pb) : 0.f;
+          im[e] = qb * pf[e];
+        }
+        st4(sh.gz + hr * TILE_X + 4 * c, make_float4(gb[0], gb[1], gb[2], gb[3]));
+        if (image) st4(sh.imz + 4 * c, make_float4(im[0], im[1], im[2], im[3]));
+      };
 
-    // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
-    float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
-    float* __restrict__ gp = p.gpart + base;
-    float4 lo[2], go[2];
-    lo[0] = ldg4(lprev + (long long)zr0 * pitch + xb);
-    lo[1] = ldg4(lprev + (long long)(zr0 + 1) * pitch + xb);
-    go[0] = ldg4(gp + (long long)zr0 * pitch + xb);
-    go[1] = ldg4(gp + (long long)(zr0 + 1) * pitch + xb);
-    const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
-    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
-    const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
-    float dzv[2][4];
-    {
-      float4 w[2 * N + 1];
-#pragma unroll
-      for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sh.gz + (2 * ty + 4 - N + t2) * TILE_X + 4 * tx);
-      float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
-#pragma unroll
-      for (int k = 1; k <= N; k++) {
-        acc4(a0, p.c2z[k - 1], w[k + N - 1], w[N - k]);
-        acc4(a1, p.c2z[k - 1], w[k + N], w[N - k + 1]);
+      // own x half points xb+e+1/2 of rows 2ty, 2ty+1: their images stay in registers
+      float imx[2][4], imz[2][4];
+      x_item(2 * ty, tx + 1, true, true, &pfx[0], imx[0]);
+      x_item(2 * ty + 1, tx + 1, true, true, &pfx[1], imx[1]);
+      {
+        // own z half rows 2ty, 2ty+1 from a (2N+1)-row window of hhat
+        float aa[2] = {0.f, 0.f}, bb[2] = {1.f, 1.f};
+        float4 Pz[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+        if (pmlz) {
+  #pragma unroll
+          for (int rr = 0; rr < 2; rr++) {
+            aa[rr] = __ldg(p.azh + zr0 + rr + TAB_OFF);
+            bb[rr] = __ldg(p.bzh + zr0 + rr + TAB_OFF);
+            Pz[rr] = *reinterpret_cast<const float4*>(p.pz_in + base + (long long)(zr0 + rr) * pitch + xb);
+          }
+        }
+        float4 w[2 * N + 1];
+  #pragma unroll
+        for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sz + (2 * ty + H - N + 1 + t2) * TILE_X + 4 * tx);
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+  #pragma unroll
+        for (int k = 1; k <= N; k++) {
+          acc4(a0, p.c1z[k - 1], w[k + N - 1], w[N - k]);
+          acc4(a1, p.c1z[k - 1], w[k + N], w[N - k + 1]);
+        }
+        float dq[2][4];
+        f4a(a0, dq[0]);
+        f4a(a1, dq[1]);
+  #pragma unroll
+        for (int rr = 0; rr < 2; rr++) {
+          const int hz = zr0 + rr;
+          const long long idz = base + (long long)hz * pitch + xb;
+          const bool hv = !EDGE || hz < g.Nz - 1;
+          const float4 ma = ld4(sm + (2 * ty + 4 + rr) * MW + 4 * tx + 4);
+          const float4 mb = ld4(sm + (2 * ty + 5 + rr) * MW + 4 * tx + 4);
+          const float mhv[4] = {ma.x + mb.x, ma.y + mb.y, ma.z + mb.z, ma.w + mb.w};
+          float pf[4], Pv[4];
+          f4a(pfz[rr], pf);
+          f4a(Pz[rr], Pv);
+          float gb[4], Pn[4];
+  #pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const bool inh = !EDGE || (hv && xb + e < g.Nx);
+            const float qb = inh ? dq[rr][e] : 0.f;
+            const float pb = mhv[e] * qb;
+            const float tt = Pv[e] + pb;
+            gb[e] = inh ? pb + aa[rr] * tt : 0.f;
+            Pn[e] = inh ? bb[rr] * tt : 0.f;
+            imz[rr][e] = qb * pf[e];
+          }
+          if (aa[rr] != 0.f && (!EDGE || hz < g.Nz)) st4(p.pz_out + idz, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
+          st4(sh.gz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(gb[0], gb[1], gb[2], gb[3]));
+        }
+        // half row 2ty+1 is the upper neighbour of the next thread row's cells
+        st4(sh.imz + (ty + 1) * TILE_X + 4 * tx, make_float4(imz[1][0], imz[1][1], imz[1][2], imz[1][3]));
       }
-      f4a(a0, dzv[0]);
-      f4a(a1, dzv[1]);
-    }
-    // image of the half row above (2ty-1) and of the half column left of the thread (xb-1/2)
-    float imzu[4];
-    f4a(ld4(sh.imz + ty * TILE_X + 4 * tx), imzu);
-    float imxl[2];
-#pragma unroll
-    for (int rr = 0; rr < 2; rr++) {
-      const float up = __shfl_up_sync(0xffffffffu, imx[rr][3], 1, 16);
-      imxl[rr] = tx == 0 ? sh.imx[2 * ty + rr] : up;
-    }
-    float lnew[2][4];
-#pragma unroll
-    for (int rr = 0; rr < 2; rr++) {
-      const int r = 2 * ty + rr, z = z0 + r;
-      float v[12];
-      unpack12(sh.gx + r * QXW + 4 * tx, v);
-      float lcv[4], lov[4], gov[4];
-      f4a(lc[rr], lcv);
-      f4a(lo[rr], lov);
-      f4a(go[rr], gov);
-      float gn[4];
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        float dxv = 0.f;
-#pragma unroll
-        for (int k = 1; k <= N; k++) dxv += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
-        const bool valid = z < g.Nz && xb + e < g.Nx;
-        lnew[rr][e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[rr][e]) : 0.f;
-        const float ixl = e == 0 ? imxl[rr] : imx[rr][e - 1];
-        const float izu = rr == 0 ? imzu[e] : imz[0][e];
-        gn[e] = valid ? gov[e] + (ixl + imx[rr][e] + izu + imz[rr][e]) : 0.f;
+      if (tid < 128) {
+        const int hr0 = tid >> 4;
+        const int hr = hr0 < 4 ? hr0 : hr0 + 32;
+        z_item(hr, tid & 15, hr == 3);  // of the halo rows only half row z0-1 feeds this tile's gradient
+      } else if (tid < 192) {
+        const int k = tid - 128;
+        const bool left = (k & 1) == 0;
+        float im[4];
+        x_item(k >> 1, left ? 0 : QXW / 4 - 1, false, left, nullptr, im);  // only half column x0-1 feeds the gradient
+        if (left) sh.imx[k >> 1] = im[3];
       }
-      st4(gp + (long long)z * pitch + xb, make_float4(gn[0], gn[1], gn[2], gn[3]));
-    }
-    if (p.n >= 1) {
-      // residual of the sample recorded from u^n (sample n-1) at this thread's receivers
-      for (int q = rb; q < re; q++) {
-        const int code = p.thr_rec[q];
-        const int rc = code >> 3, rr = (code >> 2) & 1, e = code & 3;
-        const float rv = p.res[((long long)s * p.nrec + rc) * p.nt + p.n - 1];
-#pragma unroll
-        for (int r2 = 0; r2 < 2; r2++)
-#pragma unroll
-          for (int e2 = 0; e2 < 4; e2++)
-            if (r2 == rr && e2 == e) lnew[r2][e2] += rv;
+      // lambda_{n+1} at the own cells, from a stencil tile that holds lambda itself
+      float4 lc[2];
+  #pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int r = 2 * ty + rr;
+        if (!pmlx) lc[rr] = ld4(sx + r * UW + H + 4 * tx);
+        else if (!pmlz) lc[rr] = ld4(sz + (r + H) * TILE_X + 4 * tx);
+        else lc[rr] = ldg4(p.lam + (long long)p.cur * p.S * g.slice + base + (long long)(z0 + r) * pitch + xb);
       }
-    }
-    const bool wx = tile_writes_hx(g, id.tx), wz = tile_writes_hz(g, id.tz);
-    float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
-    if (pmlx) {
-      ax4 = ldg4(p.ax + xb + TAB_OFF);
-      bx4 = ldg4(p.bx + xb + TAB_OFF);
-    }
-    const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
-#pragma unroll
-    for (int rr = 0; rr < 2; rr++) {
-      const int z = zr0 + rr;
-      const long long idc0 = base + (long long)z * pitch + xb;
-      const float4 l4 = make_float4(lnew[rr][0], lnew[rr][1], lnew[rr][2], lnew[rr][3]);
-      st4(lprev + (long long)z * pitch + xb, l4);
-      // CPML Z (divided by dt^2) <- b (Z + lambda_{n+1}); zero outside the layer and the grid
-      float4 Zx = make_float4(0.f, 0.f, 0.f, 0.f), Zz = Zx;
-      if (zx_on) {
-        const float4 Zo = ld4(p.zx_in + idc0);
-        Zx.x = ax4.x != 0.f && z < g.Nz ? bx4.x * (Zo.x + lc[rr].x) : 0.f;
-        Zx.y = ax4.y != 0.f && z < g.Nz ? bx4.y * (Zo.y + lc[rr].y) : 0.f;
-        Zx.z = ax4.z != 0.f && z < g.Nz ? bx4.z * (Zo.z + lc[rr].z) : 0.f;
-        Zx.w = ax4.w != 0.f && z < g.Nz ? bx4.w * (Zo.w + lc[rr].w) : 0.f;
-        st4(p.zx_out + idc0, Zx);
+      __syncthreads();
+      if (tid == 0 && tn < p.ntiles) fetch(tn);  // the operand buffer is free
+
+      // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
+      float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
+      float* __restrict__ gp = p.gpart + base;
+      float4 lo[2], go[2];
+      lo[0] = ldg4(lprev + (long long)zr0 * pitch + xb);
+      lo[1] = ldg4(lprev + (long long)(zr0 + 1) * pitch + xb);
+      go[0] = ldg4(gp + (long long)zr0 * pitch + xb);
+      go[1] = ldg4(gp + (long long)(zr0 + 1) * pitch + xb);
+      const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
+      const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+      const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
+      float dzv[2][4];
+      {
+        float4 w[2 * N + 1];
+  #pragma unroll
+        for (int t2 = 0; t2 <= 2 * N; t2++) w[t2] = ld4(sh.gz + (2 * ty + 4 - N + t2) * TILE_X + 4 * tx);
+        float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+  #pragma unroll
+        for (int k = 1; k <= N; k++) {
+          acc4(a0, p.c2z[k - 1], w[k + N - 1], w[N - k]);
+          acc4(a1, p.c2z[k - 1], w[k + N], w[N - k + 1]);
+        }
+        f4a(a0, dzv[0]);
+        f4a(a1, dzv[1]);
       }
-      float az = 0.f;
-      if (pmlz) {
-        az = __ldg(p.az + z + TAB_OFF);
-        if (az != 0.f) {
-          const float bz = __ldg(p.bz + z + TAB_OFF);
-          const float4 Zo = ld4(p.zz_in + idc0);
-          Zz.x = xb + 0 < g.Nx ? bz * (Zo.x + lc[rr].x) : 0.f;
-          Zz.y = xb + 1 < g.Nx ? bz * (Zo.y + lc[rr].y) : 0.f;
-          Zz.z = xb + 2 < g.Nx ? bz * (Zo.z + lc[rr].z) : 0.f;
-          Zz.w = xb + 3 < g.Nx ? bz * (Zo.w + lc[rr].w) : 0.f;
-          st4(p.zz_out + idc0, Zz);
+      // image of the half row above (2ty-1) and of the half column left of the thread (xb-1/2)
+      float imzu[4];
+      f4a(ld4(sh.imz + ty * TILE_X + 4 * tx), imzu);
+      float imxl[2];
+  #pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const float up = __shfl_up_sync(0xffffffffu, imx[rr][3], 1, 16);
+        imxl[rr] = tx == 0 ? sh.imx[2 * ty + rr] : up;
+      }
+      float lnew[2][4];
+  #pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int r = 2 * ty + rr, z = z0 + r;
+        float v[12];
+        unpack12(sh.gx + r * QXW + 4 * tx, v);
+        float lcv[4], lov[4], gov[4];
+        f4a(lc[rr], lcv);
+        f4a(lo[rr], lov);
+        f4a(go[rr], gov);
+        float gn[4];
+  #pragma unroll
+        for (int e = 0; e < 4; e++) {
+          float dxv = 0.f;
+  #pragma unroll
+          for (int k = 1; k <= N; k++) dxv += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
+          const bool valid = !EDGE || (z < g.Nz && xb + e < g.Nx);
+          lnew[rr][e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[rr][e]) : 0.f;
+          const float ixl = e == 0 ? imxl[rr] : imx[rr][e - 1];
+          const float izu = rr == 0 ? imzu[e] : imz[0][e];
+          gn[e] = valid ? gov[e] + (ixl + imx[rr][e] + izu + imz[rr][e]) : 0.f;
+        }
+        st4(gp + (long long)z * pitch + xb, make_float4(gn[0], gn[1], gn[2], gn[3]));
+      }
+      if (p.n >= 1) {
+        // residual of the sample recorded from u^n (sample n-1) at this thread's receivers
+        for (int q = rb; q < re; q++) {
+          const int code = p.thr_rec[q];
+          const int rc = code >> 3, rr = (code >> 2) & 1, e = code & 3;
+          const float rv = p.res[((long long)s * p.nrec + rc) * p.nt + p.n - 1];
+  #pragma unroll
+          for (int r2 = 0; r2 < 2; r2++)
+  #pragma unroll
+            for (int e2 = 0; e2 < 4; e2++)
+              if (r2 == rr && e2 == e) lnew[r2][e2] += rv;
         }
       }
-      // hhat of step n-1 (lambda_n with the updated Z); equal to lambda_n outside the layer
-      if (wx)
-        st4(p.hx_out + idc0, make_float4(l4.x + ax4.x * (Zx.x + l4.x), l4.y + ax4.y * (Zx.y + l4.y),
-                                         l4.z + ax4.z * (Zx.z + l4.z), l4.w + ax4.w * (Zx.w + l4.w)));
-      if (wz)
-        st4(p.hz_out + idc0, make_float4(l4.x + az * (Zz.x + l4.x), l4.y + az * (Zz.y + l4.y),
-                                         l4.z + az * (Zz.z + l4.z), l4.w + az * (Zz.w + l4.w)));
-    }
-    // source-parameter partials from lambda_n (index n-1): sum w lambda,
-    // sum w lambda (x_i - x0), sum w lambda (z_i - z0); at most 4 tiles touch a box
-    if (p.src_part != nullptr && p.n >= 1) {
-      const int i0 = box.x, j0 = box.y, nb = p.src_n;
-      if (i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0) {
-        float acc[3] = {0.f, 0.f, 0.f};
-        const float xs = p.x0[2 * s], zs = p.x0[2 * s + 1];
-#pragma unroll
-        for (int rr = 0; rr < 2; rr++) {
-          const int z = zr0 + rr, di = z - i0;
-          if (di >= 0 && di < nb) {
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-              const int dj = xb + e - j0;
-              if (dj >= 0 && dj < nb) {
-                const float wl = p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj] * lnew[rr][e];
-                acc[0] += wl;
-                acc[1] += wl * ((float)(xb + e - g.npml) * p.dx - xs);
-                acc[2] += wl * ((float)(z - g.npml) * p.dz - zs);
+      const bool wx = tile_writes_hx(g, id.tx), wz = tile_writes_hz(g, id.tz);
+      float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
+      if (pmlx) {
+        ax4 = ldg4(p.ax + xb + TAB_OFF);
+        bx4 = ldg4(p.bx + xb + TAB_OFF);
+      }
+      const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
+  #pragma unroll
+      for (int rr = 0; rr < 2; rr++) {
+        const int z = zr0 + rr;
+        const long long idc0 = base + (long long)z * pitch + xb;
+        const float4 l4 = make_float4(lnew[rr][0], lnew[rr][1], lnew[rr][2], lnew[rr][3]);
+        st4(lprev + (long long)z * pitch + xb, l4);
+        // CPML Z (divided by dt^2) <- b (Z + lambda_{n+1}); zero outside the layer and the grid
+        float4 Zx = make_float4(0.f, 0.f, 0.f, 0.f), Zz = Zx;
+        if (zx_on) {
+          const float4 Zo = ld4(p.zx_in + idc0);
+          Zx.x = ax4.x != 0.f && (!EDGE || z < g.Nz) ? bx4.x * (Zo.x + lc[rr].x) : 0.f;
+          Zx.y = ax4.y != 0.f && (!EDGE || z < g.Nz) ? bx4.y * (Zo.y + lc[rr].y) : 0.f;
+          Zx.z = ax4.z != 0.f && (!EDGE || z < g.Nz) ? bx4.z * (Zo.z + lc[rr].z) : 0.f;
+          Zx.w = ax4.w != 0.f && (!EDGE || z < g.Nz) ? bx4.w * (Zo.w + lc[rr].w) : 0.f;
+          st4(p.zx_out + idc0, Zx);
+        }
+        float az = 0.f;
+        if (pmlz) {
+          az = __ldg(p.az + z + TAB_OFF);
+          if (az != 0.f) {
+            const float bz = __ldg(p.bz + z + TAB_OFF);
+            const float4 Zo = ld4(p.zz_in + idc0);
+            Zz.x = (!EDGE || xb + 0 < g.Nx) ? bz * (Zo.x + lc[rr].x) : 0.f;
+            Zz.y = (!EDGE || xb + 1 < g.Nx) ? bz * (Zo.y + lc[rr].y) : 0.f;
+            Zz.z = (!EDGE || xb + 2 < g.Nx) ? bz * (Zo.z + lc[rr].z) : 0.f;
+            Zz.w = (!EDGE || xb + 3 < g.Nx) ? bz * (Zo.w + lc[rr].w) : 0.f;
+            st4(p.zz_out + idc0, Zz);
+          }
+        }
+        // hhat of step n-1 (lambda_n with the updated Z); equal to lambda_n outside the layer
+        if (wx)
+          st4(p.hx_out + idc0, make_float4(l4.x + ax4.x * (Zx.x + l4.x), l4.y + ax4.y * (Zx.y + l4.y),
+                                           l4.z + ax4.z * (Zx.z + l4.z), l4.w + ax4.w * (Zx.w + l4.w)));
+        if (wz)
+          st4(p.hz_out + idc0, make_float4(l4.x + az * (Zz.x + l4.x), l4.y + az * (Zz.y + l4.y),
+                                           l4.z + az * (Zz.z + l4.z), l4.w + az * (Zz.w + l4.w)));
+      }
+      // source-parameter partials from lambda_n (index n-1): sum w lambda,
+      // sum w lambda (x_i - x0), sum w lambda (z_i - z0); at most 4 tiles touch a box
+      if (p.src_part != nullptr && p.n >= 1) {
+        const int i0 = box.x, j0 = box.y, nb = p.src_n;
+        if (i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0) {
+          float acc[3] = {0.f, 0.f, 0.f};
+          const float xs = p.x0[2 * s], zs = p.x0[2 * s + 1];
+  #pragma unroll
+          for (int rr = 0; rr < 2; rr++) {
+            const int z = zr0 + rr, di = z - i0;
+            if (di >= 0 && di < nb) {
+  #pragma unroll
+              for (int e = 0; e < 4; e++) {
+                const int dj = xb + e - j0;
+                if (dj >= 0 && dj < nb) {
+                  const float wl = p.src_w[s * SRC_W * SRC_W + di * SRC_W + dj] * lnew[rr][e];
+                  acc[0] += wl;
+                  acc[1] += wl * ((float)(xb + e - g.npml) * p.dx - xs);
+                  acc[2] += wl * ((float)(z - g.npml) * p.dz - zs);
+                }
               }
             }
           }
-        }
-        cta_sum3(acc, sh.red);
-        if (tid == 0) {
-          const int slot = 2 * (id.tz - i0 / TILE_Z) + (id.tx - j0 / TILE_X);
-          float* dst = p.src_part + (((long long)s * p.nt + (p.n - 1)) * SRC_SLOTS + slot) * 3;
-          dst[0] = acc[0];
-          dst[1] = acc[1];
-          dst[2] = acc[2];
+          cta_sum3(acc, sh.red);
+          if (tid == 0) {
+            const int slot = 2 * (id.tz - i0 / TILE_Z) + (id.tx - j0 / TILE_X);
+            float* dst = p.src_part + (((long long)s * p.nt + (p.n - 1)) * SRC_SLOTS + slot) * 3;
+            dst[0] = acc[0];
+            dst[1] = acc[1];
+            dst[2] = acc[2];
+          }
         }
       }
-    }
-    __syncthreads();  // the stage arrays are free again
+      __syncthreads();  // the stage arrays are free again
+    };
+    const bool edge = x0 < 4 || x0 + TILE_X + 5 > g.Nx || z0 < 4 || z0 + TILE_Z + 5 > g.Nz;
+    if (edge) tile_body(std::true_type{});
+    else tile_body(std::false_type{});
   }
 }
 

@@ -97,7 +97,8 @@ inline bool encode(CUtensorMap* map, void* base, int rank, const cuuint64_t* dim
             const cuuint32_t* box) {
   EncodeTiled fn = encoder();
   if (!fn) return false;
-  const cuuint32_t es[3] = {1, 1, 1};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  if (rank < 1 || rank > 5) return false;
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
