@@ -208,6 +208,28 @@ def acoustic_xl_measure(peak):
     return out
 
 
+def batched_measure(n_inst=8):
+    """Batched vs plain per-shot gradient sweeps over the first ``n_inst``
+    instances of the seeded uneven workload (seed 4; grids 128..512 x
+    128..1024, nt 1000..4000, 4..16 shots). The batched sweep's (streams,
+    checkpoint interval) comes from the autotuner run on the same instances."""
+    from paper_2003_06027_gb300 import batch, synth
+
+    inst = batch.prepare([synth.uneven_instance(4, i) for i in range(n_inst)])
+    cells = sum(i.cell_steps for i in inst)
+    best, table = batch.autotune(inst, workers=(1, 2, 4, 8), ckpt=(100,))
+    _, _, tb = batch.sweep(inst, "batched", *best)
+    batch.sweep(inst, "plain", ckpt_every=100)
+    _, _, tp = batch.sweep(inst, "plain", ckpt_every=100)
+    return {"workload": f"uneven-seed4-{n_inst}-instances", "cell_steps_per_sweep": cells,
+            "batched": {"value": cells / tb / 1e9, "unit": UNIT, "s_per_sweep": tb, "streams": best[0],
+                        "ckpt_every": best[1]},
+            "plain_per_shot": {"value": cells / tp / 1e9, "unit": UNIT, "s_per_sweep": tp},
+            "speedup": tp / tb,
+            "autotune_s": {f"{w}x{k}": t for (w, k), t in table.items()},
+            "timing": "host wall time per sweep, device idle before and after (each call ends synchronised)"}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -399,8 +421,11 @@ def main():
     avg_ms = statistics.mean(kms[dom])
     achieved = launch_bytes(d, dom) / (avg_ms / 1e3) / 1e9
     kernel_names = {"fwd": "acu_fwd_step<4,record>", "store": "acu_fwd_step<4,store>", "adj": "acu_adj_step<4>"}
+    groups = min(4, S)
     roof = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind,
+            "frac": achieved / peak, "peak_source": peak_kind, "launches_per_step": groups,
+            "note": f"one step of the kernel is {groups} concurrent launches (one per shot group, own stream); "
+                    "achieved = the step's algorithmic bytes / the step's duration, traffic likewise per step",
             "traffic": load_traffic("acoustic_kernels.cu") if dom == "adj" else None,
             "algorithmic_bytes_per_launch": launch_bytes(d, dom), "avg_launch_ms": avg_ms}
     kernels = {k: {"avg_launch_ms": statistics.mean(v), "algorithmic_GBps": launch_bytes(d, k) / (statistics.mean(v) / 1e3) / 1e9,
@@ -416,6 +441,7 @@ def main():
     if not args.no_extra:
         res["elastic"] = elastic_measure(2)
         res["acoustic_xl"] = acoustic_xl_measure(peak)
+        res["batched_uneven"] = batched_measure()
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
 

@@ -161,10 +161,13 @@ fwi_status fwi_forward_noalloc(const fwi_model *model, const fwi_sources *src,
 /* Timing of the last call, measured with CUDA events recorded on the call's
  * stream. phase_ms3: [0] forward sweep (with checkpoint saves), [1] reverse
  * sweep (recompute + adjoint + folds), [2] whole call. kernel_ms3: average
- * duration of one launch of [0] the recording forward step, [1] the storing
- * forward step of the recompute, [2] the adjoint step (each averaged over
- * its back-to-back launches, so launch gaps are included; 0 if none ran).
- * launches: number of kernels the call launched. Any pointer may be NULL. */
+ * duration of one time step of [0] the recording forward step, [1] the storing
+ * forward step of the recompute (with the checkpoint restores), [2] the
+ * adjoint step; 0 if none ran. Acoustic calls split the shots into up to 4
+ * groups whose launches run concurrently on internal streams (forked from and
+ * joined to the call's stream), so one step is one launch per group, and the
+ * step time includes launch gaps. launches: number of kernels the call
+ * launched. Any pointer may be NULL. */
 fwi_status fwi_last_timing(const fwi_ctx *ctx, float *phase_ms3, float *kernel_ms3,
                            int64_t *launches);
 

@@ -1,0 +1,206 @@
+"""Batched FWI over many independent inversion instances of uneven grid size.
+
+Two ways to run the same gradient sweep (J_i and dJ_i/dc_i of every instance i):
+
+* ``plain``: the per-shot scheme of the paper's multi-GPU experiment
+  (Performance Benchmarking: shots split across devices, gradients summed): one
+  instance after the other, one shot per fwi_misfit_grad call, on one stream,
+  the per-shot gradients summed.
+* ``batched``: every instance's shots in one fwi_misfit_grad call (shots are a
+  batch axis of every step kernel), and W instances in flight at once, each on
+  its own CUDA stream and library context (a pool of W persistent host threads,
+  one per stream; the library call releases the GIL). Instances are handed out
+  largest first.
+
+``autotune`` measures a sweep on the instances themselves for each candidate
+(W, checkpoint interval K) and keeps the fastest. Both modes compute the same
+gradients (up to the order of the shot sum), so an FWI loop reaches the same
+misfit in the same number of iterations; what differs is GPU time per iteration.
+All wave propagation and all gradients run in the library's kernels; the model
+update and the plain mode's shot sum are torch element-wise operations.
+"""
+
+from __future__ import annotations
+
+import threading
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import fwi
+
+
+@dataclass
+class Instance:
+    name: str
+    c: torch.Tensor          # [nz][nx] current model (updated in place by fwi_iterations)
+    stf: torch.Tensor        # [S][nt]
+    x0: torch.Tensor         # [S][2]
+    rec_iz: torch.Tensor
+    rec_ix: torch.Tensor
+    observed: torch.Tensor   # [S][nrec][nt]
+    kw: dict
+    cell_steps: int          # S * padded cells * nt: one forward sweep
+
+    @property
+    def shots(self) -> int:
+        return int(self.stf.shape[0])
+
+
+def prepare(problems, device=0) -> list:
+    """Device copies of synth problem dicts, with observed data from each true model."""
+    dev = torch.device("cuda", device)
+    out = []
+    for d in problems:
+        cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+        kw = fwi.problem_kwargs(d)
+        c, stf, x0, iz, ix = cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
+        obs = fwi.forward(cu(d["c_true"]), stf, x0, iz, ix, **kw)
+        S, nt = d["stf"].shape
+        cells = S * (d["nz"] + 2 * d["npml"]) * (d["nx"] + 2 * d["npml"]) * nt
+        out.append(Instance(d["name"], c, stf, x0, iz, ix, obs, kw, cells))
+    torch.cuda.synchronize(dev)
+    return out
+
+
+def _grad_batched(inst: Instance, K: int):
+    J, g, _, _, _ = fwi.misfit_grad(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed,
+                                    ckpt_every=K, want_src=False, **inst.kw)
+    return J, g
+
+
+def _grad_per_shot(inst: Instance, K: int):
+    J = None
+    g = None
+    for s in range(inst.shots):
+        Js, gs, _, _, _ = fwi.misfit_grad(inst.c, inst.stf[s:s + 1], inst.x0[s:s + 1], inst.rec_iz, inst.rec_ix,
+                                          inst.observed[s:s + 1], ckpt_every=K, want_src=False, **inst.kw)
+        J = Js if J is None else J + Js
+        g = gs if g is None else g + gs
+    return J, g
+
+
+class _Pool:
+    """W persistent host threads, each with its own CUDA stream and library
+    context (so its device arena is reused from sweep to sweep)."""
+
+    def __init__(self, workers: int, device: int):
+        import queue
+
+        self.q = queue.Queue()
+        self.device = device
+        self.threads = [threading.Thread(target=self._loop, daemon=True) for _ in range(workers)]
+        for t in self.threads:
+            t.start()
+
+    def _loop(self):
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream()
+        while True:
+            job = self.q.get()
+            if job is None:
+                fwi.release_context()
+                self.q.task_done()
+                return
+            fn, done = job
+            try:
+                with torch.cuda.stream(stream):
+                    fn()
+                stream.synchronize()
+            except Exception as e:  # surfaced by run()
+                done.append(e)
+            self.q.task_done()
+
+    def run(self, fns):
+        errors = []
+        for fn in fns:
+            self.q.put((fn, errors))
+        self.q.join()
+        if errors:
+            raise errors[0]
+
+    def close(self):
+        for _ in self.threads:
+            self.q.put(None)
+        self.q.join()
+
+
+_pools = {}
+
+
+def pool(workers: int, device: int = 0) -> _Pool:
+    key = (workers, device)
+    if key not in _pools:
+        _pools[key] = _Pool(workers, device)
+    return _pools[key]
+
+
+def close_pools():
+    """Stop the worker threads and free their library contexts."""
+    for k in list(_pools):
+        _pools.pop(k).close()
+
+
+def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 100):
+    """One gradient sweep over all instances; returns ([J_i], [g_i], seconds).
+    The time is host wall time with the device idle on both sides (every
+    library call ends with a stream synchronisation)."""
+    n = len(instances)
+    Js, gs = [None] * n, [None] * n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if mode == "plain":
+        for i, inst in enumerate(instances):
+            Js[i], gs[i] = _grad_per_shot(inst, min(ckpt_every, int(inst.stf.shape[1])))
+    elif mode == "batched":
+        def job(i):
+            def fn():
+                inst = instances[i]
+                Js[i], gs[i] = _grad_batched(inst, min(ckpt_every, int(inst.stf.shape[1])))
+            return fn
+
+        order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
+        pool(max(1, min(workers, n)), torch.cuda.current_device()).run([job(i) for i in order])
+    else:
+        raise ValueError(f"unknown mode {mode!r}")
+    torch.cuda.synchronize()
+    return Js, gs, time.perf_counter() - t0
+
+
+def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200)):
+    """Pick (workers, ckpt_every) by timing one batched sweep per candidate on
+    the given instances (the first call of each candidate also sizes the
+    per-thread arenas, so each candidate is run twice and the second run counts).
+    The pools of the losing worker counts are closed, freeing their arenas."""
+    best = None
+    table = {}
+    dev = torch.cuda.current_device()
+    for W in workers:
+        prev = best
+        for K in ckpt:
+            sweep(instances, "batched", W, K)
+            _, _, t = sweep(instances, "batched", W, K)
+            table[(W, K)] = t
+            if best is None or t < table[best]:
+                best = (W, K)
+        # keep at most the best pool alive between candidates
+        loser = W if best[0] != W else (prev[0] if prev is not None and prev[0] != W else None)
+        if loser is not None and (loser, dev) in _pools:
+            _pools.pop((loser, dev)).close()
+    return best, table
+
+
+def fwi_iterations(instances, iters: int, mode: str = "batched", workers: int = 4, ckpt_every: int = 100,
+                   step: float = 20.0, vmin: float = 1500.0, vmax: float = 4500.0):
+    """Steepest descent with a normalised step (at most ``step`` m/s per cell per
+    iteration) on every instance; returns per-iteration total misfit and time."""
+    hist = []
+    for _ in range(iters):
+        Js, gs, t = sweep(instances, mode, workers, ckpt_every)
+        hist.append((float(sum(float(J[0]) for J in Js)), t))
+        with torch.no_grad():
+            for inst, g in zip(instances, gs):
+                inst.c.sub_(step * g / g.abs().max().clamp_min(1e-30)).clamp_(vmin, vmax)
+    return hist

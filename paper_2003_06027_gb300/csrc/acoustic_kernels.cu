@@ -113,13 +113,14 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* red) {
 }
 
 // Issue the TMA fetches of tile t into one buffer (one elected thread).
-__device__ __forceinline__ void fetch_tile(const CUtensorMap* fmap, const CUtensorMap* mmap, const Grid& g, int S,
-                                           int pair, int t, float* dst_u, float* dst_m, uint64_t* bar) {
+// plane0: the pair plane of this launch's first shot.
+__device__ __forceinline__ void fetch_tile(const CUtensorMap* fmap, const CUtensorMap* mmap, const Grid& g, int plane0,
+                                           int t, float* dst_u, float* dst_m, uint64_t* bar) {
   const TileId id = tile_decode(g, t);
   fence_proxy_async();
   mbar_expect_tx(bar, U_BYTES + M_BYTES);
   // allocation coordinates: padded (i, j) -> (i + APRON, j + APRON)
-  tma_3d(dst_u, fmap, id.x0 - H + APRON, id.z0 - H + APRON, pair * S + id.s, bar);
+  tma_3d(dst_u, fmap, id.x0 - H + APRON, id.z0 - H + APRON, plane0 + id.s, bar);
   tma_2d(dst_m, mmap, id.x0 - 4 + APRON, id.z0 - 4 + APRON, bar);
 }
 
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
   }
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < p.ntiles)
-    fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, blockIdx.x, sh.u, sh.m, &sh.bar);
+    fetch_tile(&tmap_u, &tmap_m, g, p.cur * p.S_pair + p.s0, blockIdx.x, sh.u, sh.m, &sh.bar);
 
   int it = 0;
   for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     const TileId id = tile_decode(g, t);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
-    float* __restrict__ uprev = p.u + (long long)(p.cur ^ 1) * p.S * g.slice + base;
+    float* __restrict__ uprev = p.u + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
     // prefetch u^{n-1} of this thread's 2 x 4 cells
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
     float4 up[2];
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     ucur[0] = ld4(su + (2 * ty + H) * UW + 4 * tx + H);
     ucur[1] = ld4(su + (2 * ty + 1 + H) * UW + 4 * tx + H);
     __syncthreads();
-    if (tid == 0 && tn < p.ntiles) fetch_tile(&tmap_u, &tmap_m, g, p.S, p.cur, tn, sh.u, sh.m, &sh.bar);
+    if (tid == 0 && tn < p.ntiles) fetch_tile(&tmap_u, &tmap_m, g, p.cur * p.S_pair + p.s0, tn, sh.u, sh.m, &sh.bar);
 
     // ---- stage 2: divergence + CPML zeta + leapfrog + source + receivers
     float hzv[2][4];
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
   // tile (its last reader) is done, and overlaps stage 2
   auto fetch = [&](int tt) {
     const TileId f = tile_decode(g, tt);
-    const int plane = p.cur * p.S + f.s;
+    const int plane = p.cur * p.S_pair + p.s0 + f.s;
     const CUtensorMap* xm = tile_pml_x(g, f.x0) ? &tmap_hx : &tmap_lx;
     const CUtensorMap* zm = tile_pml_z(g, f.z0) ? &tmap_hz : &tmap_lz;
     fence_proxy_async();
@@ -649,13 +650,13 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         const int r = 2 * ty + rr;
         if (!pmlx) lc[rr] = ld4(sx + r * UW + H + 4 * tx);
         else if (!pmlz) lc[rr] = ld4(sz + (r + H) * TILE_X + 4 * tx);
-        else lc[rr] = ldg4(p.lam + (long long)p.cur * p.S * g.slice + base + (long long)(z0 + r) * pitch + xb);
+        else lc[rr] = ldg4(p.lam + (long long)(p.cur * p.S_pair + p.s0) * g.slice + base + (long long)(z0 + r) * pitch + xb);
       }
       __syncthreads();
       if (tid == 0 && tn < p.ntiles) fetch(tn);  // the operand buffer is free
 
       // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
-      float* __restrict__ lprev = p.lam + (long long)(p.cur ^ 1) * p.S * g.slice + base;
+      float* __restrict__ lprev = p.lam + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
       float* __restrict__ gp = p.gpart + base;
       float4 lo[2], go[2];
       lo[0] = ldg4(lprev + (long long)zr0 * pitch + xb);

@@ -282,6 +282,8 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
   memset(&p, 0, sizeof p);
   p.g = g;
   p.S = P.S;
+  p.S_pair = P.S;
+  p.s0 = 0;
   p.N = P.N;
   p.nt = P.nt;
   p.nrec = P.nrec;
@@ -337,6 +339,96 @@ void set_fwd_state(const Plan& P, AcuStep& p, int n) {
 }
 
 fwi_status finish_status(fwi_ctx* ctx, const Plan& P, cudaStream_t st) { return finish_status_dev(ctx, P.status, st); }
+
+// ---------------------------------------------------------------------------
+// Shot groups: the shots are split into up to MAX_GROUPS contiguous groups whose
+// step launches run on separate streams. Each step kernel is a persistent walk
+// over its tiles, and its last partial wave leaves SMs idle; concurrent groups
+// fill them. Everything that couples shots (misfit, folds, source gradients)
+// runs on the call's stream after a join.
+constexpr int MAX_GROUPS = 4;
+
+struct Groups {
+  int G = 1;
+  int s0[MAX_GROUPS] = {0, 0, 0, 0};
+  int n[MAX_GROUPS] = {0, 0, 0, 0};
+  cudaStream_t st[MAX_GROUPS] = {};
+};
+
+fwi_status make_groups(fwi_ctx* ctx, int S, cudaStream_t main, Groups& gr) {
+  gr.G = std::max(1, std::min(MAX_GROUPS, S));
+  for (int g = 0, s0 = 0; g < gr.G; g++) {
+    gr.n[g] = S / gr.G + (g < S % gr.G ? 1 : 0);
+    gr.s0[g] = s0;
+    s0 += gr.n[g];
+  }
+  if (gr.G == 1) {
+    gr.st[0] = main;
+    return FWI_OK;
+  }
+  for (int g = 0; g < gr.G; g++) {
+    if (!ctx->gstream[g]) CK(cudaStreamCreateWithFlags(&ctx->gstream[g], cudaStreamNonBlocking));
+    if (!ctx->join_ev[g]) CK(cudaEventCreateWithFlags(&ctx->join_ev[g], cudaEventDisableTiming));
+    gr.st[g] = ctx->gstream[g];
+  }
+  if (!ctx->fork_ev) CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+  return FWI_OK;
+}
+
+fwi_status fork(fwi_ctx* ctx, const Groups& gr, cudaStream_t main) {
+  if (gr.G == 1) return FWI_OK;
+  CK(cudaEventRecord(ctx->fork_ev, main));
+  for (int g = 0; g < gr.G; g++) CK(cudaStreamWaitEvent(gr.st[g], ctx->fork_ev, 0));
+  return FWI_OK;
+}
+
+fwi_status join(fwi_ctx* ctx, const Groups& gr, cudaStream_t main) {
+  if (gr.G == 1) return FWI_OK;
+  for (int g = 0; g < gr.G; g++) {
+    CK(cudaEventRecord(ctx->join_ev[g], gr.st[g]));
+    CK(cudaStreamWaitEvent(main, ctx->join_ev[g], 0));
+  }
+  return FWI_OK;
+}
+
+// The step parameters of one group: shots [s0, s0 + Sg). Per-shot arrays are
+// offset to the group's first shot; the u and lambda pairs keep their base and
+// the kernels index them with (pair * S_pair + s0 + s).
+AcuStep group_view(const AcuStep& p, const Plan& P, int s0, int Sg) {
+  AcuStep q = p;
+  const long long sl = P.g.slice, ns = (long long)p.nrec * p.nt;
+  auto off = [&](auto* ptr, long long per) { return ptr ? ptr + s0 * per : ptr; };
+  q.S = Sg;
+  q.s0 = s0;
+  q.ntiles = Sg * P.g.ntx * P.g.ntz;
+  q.psix_in = off(p.psix_in, sl);
+  q.psix_out = off(p.psix_out, sl);
+  q.psiz_in = off(p.psiz_in, sl);
+  q.psiz_out = off(p.psiz_out, sl);
+  q.zetx = off(p.zetx, sl);
+  q.zetz = off(p.zetz, sl);
+  q.src_box = off(p.src_box, 2);
+  q.src_w = off(p.src_w, SRC_W * SRC_W);
+  q.stf = off(p.stf, p.nt);
+  q.x0 = off(p.x0, 2);
+  q.seis = off(p.seis, ns);
+  q.slot_px = off(p.slot_px, sl);
+  q.slot_pz = off(p.slot_pz, sl);
+  q.zx_in = off(p.zx_in, sl);
+  q.zx_out = off(p.zx_out, sl);
+  q.zz_in = off(p.zz_in, sl);
+  q.zz_out = off(p.zz_out, sl);
+  q.px_in = off(p.px_in, sl);
+  q.px_out = off(p.px_out, sl);
+  q.pz_in = off(p.pz_in, sl);
+  q.pz_out = off(p.pz_out, sl);
+  q.hx_out = off(p.hx_out, sl);
+  q.hz_out = off(p.hz_out, sl);
+  q.res = off(p.res, ns);
+  q.gpart = off(p.gpart, sl);
+  q.src_part = off(p.src_part, (long long)p.nt * SRC_SLOTS * 3);
+  return q;
+}
 
 }  // namespace
 
@@ -433,6 +525,11 @@ fwi_status fwi_destroy(fwi_ctx* ctx) {
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : ctx->seg_ev) cudaEventDestroy(e);
+  for (int g = 0; g < 4; g++) {
+    if (ctx->gstream[g]) cudaStreamDestroy(ctx->gstream[g]);
+    if (ctx->join_ev[g]) cudaEventDestroy(ctx->join_ev[g]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   delete ctx;
   return FWI_OK;
 }
@@ -498,11 +595,15 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   AcuMaps maps;
   CK(acu_make_maps(&maps, P.g, P.S, P.u, P.m));
   ensure_events(ctx, 0);
+  Groups gr;
+  if ((v = make_groups(ctx, P.S, st, gr)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[0], st));
+  if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
   for (int n = 0; n < nt; n++) {
     set_fwd_state(P, p, n);
-    LK(1, launch_acu_fwd(p, maps, true, false, st));
+    for (int g = 0; g < gr.G; g++) LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
   }
+  if ((v = join(ctx, gr, st)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[1], st));
   const long long ns = (long long)P.S * P.nrec * nt;
   if (ns > 0) {
@@ -553,18 +654,27 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   CK(acu_make_adj_maps(&maps, P.g, P.S, P.lam, P.hx, P.hz));
   ensure_events(ctx, P.nseg);
 
+  Groups gr;
+  if ((v = make_groups(ctx, P.S, st, gr)) != FWI_OK) return v;
+  const size_t sl = (size_t)P.g.slice;
+
   // forward sweep with a full-state checkpoint at the start of every segment
   CK(cudaEventRecord(ctx->ev[0], st));
+  if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
   for (int n = 0; n < nt; n++) {
     if (n % K == 0) {
       float* ck = P.ckpt + (size_t)(n / K) * 6 * field;
       const float* src[6] = {P.u + (n & 1) * field, P.u + ((n + 1) & 1) * field, P.psix[n & 1], P.psiz[n & 1],
                              P.zetx, P.zetz};
-      for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(ck + f * field, src[f], field * 4, cudaMemcpyDeviceToDevice, st));
+      for (int g = 0; g < gr.G; g++)
+        for (int f = 0; f < 6; f++)
+          CK(cudaMemcpyAsync(ck + f * field + gr.s0[g] * sl, src[f] + gr.s0[g] * sl, gr.n[g] * sl * 4,
+                             cudaMemcpyDeviceToDevice, gr.st[g]));
     }
     set_fwd_state(P, p, n);
-    LK(1, launch_acu_fwd(p, maps, true, false, st));
+    for (int g = 0; g < gr.G; g++) LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
   }
+  if ((v = join(ctx, gr, st)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[1], st));
   if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
   else CK(cudaMemsetAsync(P.J, 0, 8, st));
@@ -581,15 +691,23 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     const float* ck = P.ckpt + (size_t)seg * 6 * field;
     float* dst[6] = {P.u + (n0 & 1) * field, P.u + ((n0 + 1) & 1) * field, P.psix[n0 & 1], P.psiz[n0 & 1], P.zetx,
                      P.zetz};
-    for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(dst[f], ck + f * field, field * 4, cudaMemcpyDeviceToDevice, st));
+    // recompute (from the checkpoint) on the group streams
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
+    if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
+    for (int g = 0; g < gr.G; g++)
+      for (int f = 0; f < 6; f++)
+        CK(cudaMemcpyAsync(dst[f] + gr.s0[g] * sl, ck + f * field + gr.s0[g] * sl, gr.n[g] * sl * 4,
+                           cudaMemcpyDeviceToDevice, gr.st[g]));
     for (int n = n0; n < n1; n++) {
       set_fwd_state(P, p, n);
       p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
       p.slot_pz = p.slot_px + field;
-      LK(1, launch_acu_fwd(p, maps, false, true, st));
+      for (int g = 0; g < gr.G; g++)
+        LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, gr.st[g]));
     }
+    if ((v = join(ctx, gr, st)) != FWI_OK) return v;
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
+    if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
     for (int n = n1 - 1; n >= n0; n--) {
       pa.n = n;
       pa.cur = (n + 1) & 1;  // lambda_{n+1}; lambda_{n+2} -> lambda_n in the other buffer
@@ -605,8 +723,9 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       pa.pz_out = P.pz[n & 1];
       pa.hx_out = P.hx + (n & 1) * field;
       pa.hz_out = P.hz + (n & 1) * field;
-      LK(1, launch_acu_adj(pa, maps, st));
+      for (int g = 0; g < gr.G; g++) LK(1, launch_acu_adj(group_view(pa, P, gr.s0[g], gr.n[g]), maps, gr.st[g]));
     }
+    if ((v = join(ctx, gr, st)) != FWI_OK) return v;
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
     LK(1, launch_fold(P.gpart, P.S, P.g.slice, P.G, st));
   }

@@ -20,6 +20,10 @@ struct fwi_ctx {
   float phase_ms[3] = {0, 0, 0};
   float kernel_ms[3] = {0, 0, 0};
   int64_t launches = 0;
+  // shot groups run concurrently on these streams, forked from and joined to the call's stream
+  cudaStream_t gstream[4] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[4] = {};
 };
 
 namespace fwi {

@@ -70,7 +70,8 @@ struct AcuMaps {
 // Everything one acoustic step kernel needs (passed by value).
 struct AcuStep {
   Grid g;
-  int S, N, n, nt, nrec;
+  int S, N, n, nt, nrec;   // S: shots of this launch (one shot group)
+  int S_pair, s0;         // shots per half of the u / lambda pairs, and this group's first shot there
   int cur;                // pair index holding u^n (forward) or lambda_{n+1} (adjoint)
   int ntiles;             // S * ntx * ntz
   float c1x[4], c1z[4];   // stage-1 weights (flux):  fwd a_k/dx;  adj -a_k dt^2/dx

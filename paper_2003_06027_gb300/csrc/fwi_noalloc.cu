@@ -191,6 +191,8 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   memset(&p, 0, sizeof p);
   p.g = g;
   p.S = S;
+  p.S_pair = S;
+  p.s0 = 0;
   p.N = M->order / 2;
   p.nt = nt;
   p.nrec = nrec;

@@ -106,6 +106,15 @@ def context(device: int = 0):
     return ctxs[device]
 
 
+def release_context(device: int | None = None):
+    """Destroy the calling thread's library context(s), freeing their device
+    arenas (a thread that ends without this keeps its arena until exit)."""
+    ctxs = getattr(_ctx, "ctxs", None) or {}
+    for dev in list(ctxs):
+        if device is None or dev == device:
+            _check(library().fwi_destroy(ctxs.pop(dev)))
+
+
 @dataclass
 class Timing:
     forward_ms: float      # forward sweep (with checkpoint saves)

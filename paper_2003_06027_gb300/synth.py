@@ -131,6 +131,31 @@ def acoustic_xl(nshots: int = 256, nt: int = 3000) -> dict:
     return d
 
 
+def uneven_instance(seed: int, i: int) -> dict:
+    """Instance i of the batched uneven workload (seed ``seed``): nz ~ U{128..512}
+    and nx ~ U{128..1024} in steps of 32, nt ~ U{1000..4000} in steps of 100,
+    shots ~ U{4..16}; the 201 x 601 discretisation (order 8, 32 CPML cells,
+    dx = 10 m, dt = 0.8 ms, 8 Hz Ricker); a layered model without faults (true)
+    and its sigma = 10 cell smoothing (start); sources and receivers (every 4th
+    cell) at iz = 2."""
+    rng = np.random.default_rng([seed, i])
+    nz = int(rng.integers(4, 17)) * 32
+    nx = int(rng.integers(4, 33)) * 32
+    nt = int(rng.integers(10, 41)) * 100
+    S = int(rng.integers(4, 17))
+    dx, dt, f0 = 10.0, 0.8e-3, 8.0
+    true = layered_model(int(rng.integers(1 << 30)), nz, nx, dx, n_faults=0)
+    start = smooth(true, 10.0)
+    x0 = np.stack([np.linspace(0, nx - 1, S) * dx, np.full(S, 2 * dx)], axis=1).astype(np.float32)
+    rec_ix = np.arange(0, nx, 4, dtype=np.int32)
+    return dict(
+        name=f"uneven-{seed}-{i}-{nz}x{nx}-nt{nt}-{S}shots", nz=nz, nx=nx, dz=dx, dx=dx, dt=dt, nt=nt,
+        order=8, npml=32, pml_R=1e-5, pml_vmax=4500.0, pml_f0=f0, src_kind=0, c=start, c_true=true,
+        stf=np.tile(ricker(f0, dt, nt), (S, 1)), x0=x0, rec_iz=np.full(rec_ix.shape, 2, dtype=np.int32),
+        rec_ix=rec_ix, ckpt_every=100,
+    )
+
+
 def random_acoustic(seed: int, nz: int, nx: int, nt: int, nshots: int, order: int, npml: int,
                     src_kind: int = 0, nrec: int = 7, dx: float = 10.0, dt: float = 1e-3,
                     f0: float = 15.0) -> dict:
