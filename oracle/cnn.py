@@ -94,3 +94,12 @@ def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def bf16_round(x):
+    """FP32 values rounded to the nearest BF16 (8-bit significand, ties to even),
+    returned as float64: the operands the tensor-core GEMMs actually multiply."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (a >> 16) & 1
+    r = ((a + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)

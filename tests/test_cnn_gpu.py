@@ -1,0 +1,116 @@
+"""Parity of the start-model network's layers (libfwi CNN kernels, tensor-core
+GEMMs through the C ABI) with the FP64 reference layers of oracle/cnn.py.
+
+The GEMMs multiply BF16-rounded operands with FP32 accumulation, so the oracle
+is evaluated on the same BF16-rounded operands (oracle.cnn.bf16_round) and the
+remaining difference is FP32 accumulation: relative L2 <= 1e-5. Upsampling is
+exact; MSE and Adam are FP32 element-wise against FP64 (1e-6)."""
+
+import numpy as np
+import pytest
+
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _cuda(a):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+SHAPES = [  # C, B, H, W, O, sh, sw, relu
+    (3, 2, 17, 13, 5, 1, 1, True),
+    (16, 3, 40, 16, 8, 4, 1, True),
+    (8, 2, 25, 12, 16, 2, 2, False),
+    (32, 1, 9, 33, 4, 2, 1, True),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}x{s[3]}-o{s[4]}-s{s[5]}{s[6]}" for s in SHAPES])
+def test_conv_forward_backward(fwi_lib, shape):
+    from paper_2003_06027_gb300 import learned as L
+
+    C, B, H, W, O, sh, sw, relu = shape
+    rng = np.random.default_rng(C * 100 + H)
+    x = rng.standard_normal((C, B, H, W)).astype(np.float32)
+    w = (rng.standard_normal((O, C, 3, 3)) * 0.3).astype(np.float32)
+    b = rng.standard_normal(O).astype(np.float32) * 0.1
+    h = L.Handle(0)
+    wb = L.to_bf16(_cuda(w))
+    y = L.conv_forward(h, _cuda(x), wb, _cuda(b), sh, sw, relu)
+    xr, wr = cnn.bf16_round(x), cnn.bf16_round(w)
+    pre = cnn.conv2d(xr, wr, np.float64(b), sh, sw)
+    want = cnn.relu(pre) if relu else pre
+    assert y.shape == want.shape
+    assert rel(y.cpu().numpy(), want) <= 1e-5
+
+    dy = rng.standard_normal(want.shape).astype(np.float32)
+    dyt = _cuda(dy)
+    dx, dw, db = L.conv_backward(h, _cuda(x), wb, y, dyt, sh, sw, relu, need_dx=True)
+    g = cnn.relu_backward(y.cpu().numpy().astype(np.float64), dy) if relu else np.float64(dy)
+    # dy is overwritten with the pre-activation gradient (FP32, before rounding)
+    np.testing.assert_array_equal(dyt.cpu().numpy(), np.float32(g))
+    dxo, dwo, dbo = cnn.conv2d_backward(xr, wr, cnn.bf16_round(np.float32(g)), sh, sw)
+    assert rel(dx.cpu().numpy(), dxo) <= 1e-5
+    assert rel(dw.cpu().numpy(), dwo) <= 1e-5
+    assert rel(db.cpu().numpy(), g.sum(axis=(1, 2, 3))) <= 1e-6
+    _, dw2, _ = L.conv_backward(h, _cuda(x), wb, y, _cuda(dy), sh, sw, relu, need_dx=False)
+    assert np.array_equal(dw2.cpu().numpy(), dw.cpu().numpy())
+
+
+def test_upsample_and_mse_and_adam(fwi_lib):
+    from paper_2003_06027_gb300 import learned as L
+
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((3, 2, 5, 7)).astype(np.float32)
+    u = L.upsample2(_cuda(x)).cpu().numpy()
+    np.testing.assert_array_equal(u, cnn.upsample2(x))
+    d = rng.standard_normal(u.shape).astype(np.float32)
+    np.testing.assert_allclose(L.upsample2_backward(_cuda(d)).cpu().numpy(), cnn.upsample2_backward(np.float64(d)),
+                               rtol=1e-6, atol=1e-6)
+    p, t = rng.standard_normal(5000).astype(np.float32), rng.standard_normal(5000).astype(np.float32)
+    loss, dp = L.mse(_cuda(p), _cuda(t))
+    lo, go = cnn.mse(np.float64(p), np.float64(t))
+    assert float(loss[0]) == pytest.approx(lo, rel=1e-6)  # FP32 residuals, FP64 sum
+    assert rel(dp.cpu().numpy(), go) <= 1e-6
+    import ctypes
+
+    th, g = rng.standard_normal(777).astype(np.float32), rng.standard_normal(777).astype(np.float32)
+    tt, gg, m, v = _cuda(th), _cuda(g), _cuda(np.zeros(777)), _cuda(np.zeros(777))
+    thb = L.to_bf16(tt)
+    want, mo, vo = np.float64(th), np.zeros(777), np.zeros(777)
+    for step in (1, 2, 3):
+        L._chk(L._lib().fwi_cnn_adam(L._p(tt), L._p(gg), L._p(m), L._p(v), 777, step, 1e-2, 0.9, 0.999, 1e-8,
+                                     L._p(thb), L._st()))
+        want, mo, vo = cnn.adam_step(want, np.float64(g), mo, vo, step, 1e-2)
+    assert rel(tt.cpu().numpy(), want) <= 1e-6
+    assert np.array_equal(thb.cpu().numpy().view(np.uint16),
+                          (cnn.bf16_round(tt.cpu().numpy()).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16))
+
+
+def test_network_learns_layered_models(fwi_lib):
+    """A short training run on solver-generated gathers lowers the loss, and the
+    network beats the best constant model on held-out surveys."""
+    import torch
+
+    from paper_2003_06027_gb300 import learned as L
+
+    X, Y, _ = L.make_dataset(192, seed=101)
+    Xt, Yt, _ = L.make_dataset(16, seed=202)
+    net = L.Net(0, seed=1)
+    log = L.train(net, X, Y, epochs=6, batch=16, lr=1e-3)
+    assert np.isfinite(log.loss).all()
+    assert np.mean(log.loss[-5:]) < 0.5 * np.mean(log.loss[:5])
+    with torch.no_grad():
+        pred = net.forward(Xt)
+        err_net = float(((pred - Yt) ** 2).mean())
+        err_const = float(((Yt.mean() - Yt) ** 2).mean())
+    assert err_net < err_const, (err_net, err_const)

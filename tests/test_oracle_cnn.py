@@ -83,3 +83,13 @@ def test_adam_step_by_hand():
     mh = (0.9 * 0.05 - 0.05) / (1 - 0.81)
     vh = (0.999 * 0.00025 + 0.001 * 0.25) / (1 - 0.998001)
     assert th2[0] == pytest.approx(th[0] - 0.1 * mh / (np.sqrt(vh) + 1e-8), rel=1e-13)
+
+
+def test_bf16_round_matches_torch_conversion():
+    import torch
+
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-20, 20, 10000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38]]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).float().double().numpy()
+    np.testing.assert_array_equal(cnn.bf16_round(x), want)
