@@ -230,6 +230,51 @@ def batched_measure(n_inst=8):
             "timing": "host wall time per sweep, device idle before and after (each call ends synchronised)"}
 
 
+def learned_measure():
+    """Training throughput of the start-model network (its 3x3 convolutions are
+    the project's one dense contraction: BF16 tensor-core GEMMs with FP32
+    accumulation): one Adam step on a batch of 32 surveys (16 x 1000 x 64
+    inputs, 128 x 256 targets), synthetic inputs of those shapes, against the
+    measured sustained BF16 GEMM rate."""
+    import torch
+
+    from paper_2003_06027_gb300 import learned as L
+
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peak = float(json.load(open(p)).get("bf16_tflops_sustained", 0.0)) or None
+    B = 32
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn((L.NSHOT, B, L.NT, L.NREC), device="cuda", generator=g) * 0.1
+    Y = torch.randn((1, B, L.NZ, L.NX), device="cuda", generator=g) * 0.1
+    net = L.Net(0, seed=0)
+
+    def step():
+        out = net.forward(X)
+        _, dout = L.mse(out, Y)
+        net.backward(dout)
+        net.step(1e-4)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 10
+    e0.record()
+    for _ in range(n):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    tfl = 3.0 * L.network_flops_per_sample() * B / (ms / 1e3) / 1e12
+    return {"workload": f"start-model CNN training step, batch {B}, {net.nparams} parameters",
+            "ms_per_step": ms, "samples_per_s": B / (ms / 1e3),
+            "roofline": {"bound": "tensor", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tfl / peak if peak else None, "peak_source": "measured sustained bf16"},
+            "experiment": "profiles/learned_start_experiment.md"}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -442,6 +487,7 @@ def main():
         res["elastic"] = elastic_measure(2)
         res["acoustic_xl"] = acoustic_xl_measure(peak)
         res["batched_uneven"] = batched_measure()
+        res["learned"] = learned_measure()
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
 

@@ -356,12 +356,15 @@ def fwi_run(c0: torch.Tensor, observed: torch.Tensor, d: dict, c_true: torch.Ten
     return hist
 
 
-def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, sigma: float = 10.0, device=0):
+def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, sigma: float = 10.0, device=0,
+                mean_model=None):
     """For held-out random models: FWI from the Gaussian-smoothed true model
-    (sigma cells, the plain start) and from the network's prediction. Returns the
-    per-model histories and a summary (mean final misfit and model error of each
-    start, and the GPU time the learned start needs to reach the plain start's
-    final misfit, or None where it does not)."""
+    (sigma cells, the plain start), from the network's prediction, and (if
+    given) from `mean_model`, a start that knows nothing of the survey (the mean
+    of the training models). Returns the per-model histories and a summary (mean
+    start / final misfit and model error of each start, and the GPU time the
+    learned start needs to reach the plain start's final misfit, or None where
+    it does not)."""
     from . import synth
 
     dev = torch.device("cuda", device)
@@ -377,9 +380,10 @@ def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, s
         learned0 = net.predict(gathers_to_input(obs).unsqueeze(1))[0].contiguous()
         hp = fwi_run(plain0, obs, d, c_true, iters)
         hl = fwi_run(learned0, obs, d, c_true, iters)
+        hm = fwi_run(mean_model.clone(), obs, d, c_true, iters) if mean_model is not None else None
         target = hp[-1][0]
         reach = next((h[2] for h in hl if h[0] <= target), None)
-        runs.append(dict(plain=hp, learned=hl, learned_time_to_plain_final=reach, plain_time=hp[-1][2]))
+        runs.append(dict(plain=hp, learned=hl, mean=hm, learned_time_to_plain_final=reach, plain_time=hp[-1][2]))
     mean = lambda xs: float(np.mean(xs))
     summary = dict(
         models=n_models, iters=iters, smooth_sigma_cells=sigma,
@@ -389,10 +393,17 @@ def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, s
         learned_final_misfit=mean([r["learned"][-1][0] for r in runs]),
         plain_final_model_error=mean([r["plain"][-1][1] for r in runs]),
         learned_final_model_error=mean([r["learned"][-1][1] for r in runs]),
+        plain_start_misfit=mean([r["plain"][0][0] for r in runs]),
+        learned_start_misfit=mean([r["learned"][0][0] for r in runs]),
         plain_fwi_seconds=mean([r["plain_time"] for r in runs]),
         learned_reaches_plain_final=sum(r["learned_time_to_plain_final"] is not None for r in runs),
         learned_seconds_to_plain_final=[r["learned_time_to_plain_final"] for r in runs],
     )
+    if mean_model is not None:
+        summary.update(mean_start_model_error=mean([r["mean"][0][1] for r in runs]),
+                       mean_start_misfit=mean([r["mean"][0][0] for r in runs]),
+                       mean_final_misfit=mean([r["mean"][-1][0] for r in runs]),
+                       mean_final_model_error=mean([r["mean"][-1][1] for r in runs]))
     return runs, summary
 
 
@@ -407,8 +418,10 @@ def experiment(n_train=8000, epochs=12, batch=32, n_test=8, iters=50, device=0, 
     net = Net(device, seed)
     log = train(net, X, Y, epochs=epochs, batch=batch)
     fl = 3.0 * network_flops_per_sample() * log.samples
+    mean_model = (V_MID + V_HALF * Y[0].mean(dim=0)).contiguous()
     del X, Y
-    _, summary = compare_fwi(net, n_models=n_test, seed=seed + 1000, iters=iters, device=device)
+    _, summary = compare_fwi(net, n_models=n_test, seed=seed + 1000, iters=iters, device=device,
+                             mean_model=mean_model)
     return dict(train_samples=n_train, epochs=epochs, params=net.nparams, data_seconds=t_data,
                 train_seconds=log.seconds, train_tflops=fl / log.seconds / 1e12,
                 loss_first=float(np.mean(log.loss[:20])), loss_last=float(np.mean(log.loss[-20:])), **summary)
