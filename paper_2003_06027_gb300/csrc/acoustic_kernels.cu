@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
+  const uint64_t pol = STORE ? l2_evict_first() : 0ull;  // segment slots stream through L2
 
   // one operand buffer: the next tile's fetch is issued once stage 1 of this
   // tile (its last reader) is done, and overlaps stage 2
@@ -240,7 +241,8 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       for (int e = 0; e < 4; e++) q[e] = (rowok && hb + e >= 0 && hb + e < g.Nx - 1) ? (mv[e] + mv[e + 1]) * pp[e] : 0.f;
       st4(sh.qx + r * QXW + 4 * gq, make_float4(q[0], q[1], q[2], q[3]));
       // every own row is written (zero beyond the grid): the adjoint multiplies these by zero there
-      if (STORE && own) st4(p.slot_px + id0, rowok ? make_float4(pp[0], pp[1], pp[2], pp[3]) : make_float4(0.f, 0.f, 0.f, 0.f));
+      if (STORE && own)
+        st4_stream(p.slot_px + id0, rowok ? make_float4(pp[0], pp[1], pp[2], pp[3]) : make_float4(0.f, 0.f, 0.f, 0.f), pol);
     };
     // ---- stage 1b: z fluxes at one half row (the tile's halo rows)
     auto qz_item = [&](int hr, int c) {
@@ -315,8 +317,8 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         q[3] = (hv && xb + 3 < g.Nx) ? (ma.w + mb.w) * pp[rr][3] : 0.f;
         st4(sh.qz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(q[0], q[1], q[2], q[3]));
         if (STORE)
-          st4(p.slot_pz + idz, hz < g.Nz ? make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3])
-                                         : make_float4(0.f, 0.f, 0.f, 0.f));
+          st4_stream(p.slot_pz + idz, hz < g.Nz ? make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3])
+                                                : make_float4(0.f, 0.f, 0.f, 0.f), pol);
       }
     }
     if (tid < 128) {
@@ -449,6 +451,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
+  const uint64_t pol = l2_evict_first();  // the stored fluxes are read once: evict them first
 
   // one operand buffer: the next tile's fetch is issued once stage 1 of this
   // tile (its last reader) is done, and overlaps stage 2
@@ -480,10 +483,10 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
     // stored fluxes p^n of this thread's own half points (x and z), fetched before the wait
     float4 pfx[2], pfz[2];
-    pfx[0] = ldg4(p.slot_px + base + (long long)zr0 * pitch + xb);
-    pfx[1] = ldg4(p.slot_px + base + (long long)(zr0 + 1) * pitch + xb);
-    pfz[0] = ldg4(p.slot_pz + base + (long long)zr0 * pitch + xb);
-    pfz[1] = ldg4(p.slot_pz + base + (long long)(zr0 + 1) * pitch + xb);
+    pfx[0] = ld4_stream(p.slot_px + base + (long long)zr0 * pitch + xb, pol);
+    pfx[1] = ld4_stream(p.slot_px + base + (long long)(zr0 + 1) * pitch + xb, pol);
+    pfz[0] = ld4_stream(p.slot_pz + base + (long long)zr0 * pitch + xb, pol);
+    pfz[1] = ld4_stream(p.slot_pz + base + (long long)(zr0 + 1) * pitch + xb, pol);
 
     const bool ok = mbar_wait(&sh.bar, it & 1);
     if (__syncthreads_or(!ok)) {
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
         float pf[4] = {0.f, 0.f, 0.f, 0.f};
         if (pre) f4a(*pre, pf);
-        else if (image && (!EDGE || hb >= 0)) f4a(ldg4(p.slot_px + id0), pf);  // the apron holds no flux
+        else if (image && (!EDGE || hb >= 0)) f4a(ld4_stream(p.slot_px + id0, pol), pf);  // the apron holds no flux
         const bool rowok = !EDGE || z < g.Nz;
         float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
         if (pmlx) {  // one round trip: tables and P together
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
         const long long idz = base + (long long)hz * pitch + xc;
         float pf[4] = {0.f, 0.f, 0.f, 0.f};
-        if (image && (!EDGE || hz >= 0)) f4a(ldg4(p.slot_pz + idz), pf);
+        if (image && (!EDGE || hz >= 0)) f4a(ld4_stream(p.slot_pz + idz, pol), pf);
         float aa = 0.f;
         float Pv[4] = {0.f, 0.f, 0.f, 0.f};
         if (pmlz) {

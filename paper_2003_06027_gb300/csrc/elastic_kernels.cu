@@ -313,8 +313,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     st4(p.vx + id, a4f(vxn[rr]));
     st4(p.vz + id, a4f(vzn[rr]));
     if (STORE) {
-      st4(p.slot[0] + id, a4f(fx));
-      st4(p.slot[1] + id, a4f(fz));
+      st4_stream(p.slot[0] + id, a4f(fx), l2_evict_first());
+      st4_stream(p.slot[1] + id, a4f(fz), l2_evict_first());
     }
   }
   if (RECORD) {
@@ -440,9 +440,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     st4(p.szz + id, a4f(sz));
     st4(p.sxz + id, a4f(sh));
     if (STORE) {
-      st4(p.slot[2] + id, a4f(d5));
-      st4(p.slot[3] + id, a4f(d6[rr]));
-      st4(p.slot[4] + id, a4f(exz));
+      st4_stream(p.slot[2] + id, a4f(d5), l2_evict_first());
+      st4_stream(p.slot[3] + id, a4f(d6[rr]), l2_evict_first());
+      st4_stream(p.slot[4] + id, a4f(exz), l2_evict_first());
     }
   }
   ELA_WALK_END()
@@ -594,9 +594,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     st4(p.Vz + id, a4f(vzb));
     // gradient correlations of step n
     float ex[4], ez[4], exz[4], gl[4], gm[4], gx[4];
-    f4a(ldg4(p.slot[2] + id), ex);
-    f4a(ldg4(p.slot[3] + id), ez);
-    f4a(ldg4(p.slot[4] + id), exz);
+    f4a(ld4_stream(p.slot[2] + id, l2_evict_first()), ex);
+    f4a(ld4_stream(p.slot[3] + id, l2_evict_first()), ez);
+    f4a(ld4_stream(p.slot[4] + id, l2_evict_first()), exz);
     f4a(ld4(s_Sxx + (r + 4) * W72 + 4 * tx + 4), Sx_own[rr]);
     f4a(ld4(s_Szz + (r + 4) * W72 + 4 * tx + 4), Sz_own[rr]);
     f4a(ld4(s_Sxz + (r + 4) * W72 + 4 * tx + 4), Sh_own[rr]);
@@ -782,8 +782,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     st4(p.Sxz + id, a4f(sh));
     // buoyancy correlations
     float fx[4], fz[4], vx_[4], vz_[4], gbx[4], gbz[4];
-    f4a(ldg4(p.slot[0] + id), fx);
-    f4a(ldg4(p.slot[1] + id), fz);
+    f4a(ld4_stream(p.slot[0] + id, l2_evict_first()), fx);
+    f4a(ld4_stream(p.slot[1] + id, l2_evict_first()), fz);
     f4a(ld4(s_Vx + (r + 4) * W72 + 4 * tx + 4), vx_);
     f4a(ld4(s_Vz + (r + 4) * W72 + 4 * tx + 4), vz_);
     f4a(ld4(p.g_bx + id), gbx);

@@ -36,6 +36,27 @@ struct Grid {
   long long off0;     // offset of padded cell (0,0)
 };
 
+// L2 policy for data that is streamed once per sweep (the segment slots: written
+// by the recompute step, read back once by the adjoint step): such lines are
+// evicted first, so they do not push the step's resident fields (wavefield
+// pairs, gradient partials, CPML memory) out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ld4_stream(const float* ptr, uint64_t pol) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st4_stream(float* ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x),
+               "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol));  // no later reader in the same kernel
+}
+
 // Tile t of a persistent walk over all shots: t = (s * ntz + tz) * ntx + tx.
 struct TileId {
   int s, x0, z0, tx, tz;
