@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfwi.so")
 SOURCES = ["acoustic_kernels.cu", "elastic_kernels.cu", "prep_kernels.cu", "fwi_capi.cu", "fwi_elastic.cu",
-           "fwi_noalloc.cu", "cnn.cu"]
+           "fwi_noalloc.cu", "cnn.cu", "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             if err:
                 sys.stderr.write(err)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcudart", "-lcublas"]
+    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -1,14 +1,22 @@
 // cnn.cu - layers of the learned start-model network (sm_103a).
 //
 // The one dense contraction of the project: 3x3 convolutions written as GEMMs
-// over the whole batch (activations are channel-major [C][B][H][W], so the
-// im2col matrix of a layer is [C*9][B*Ho*Wo] and y = W col is a single
-// [O][C*9] x [C*9][B*Ho*Wo] product). The GEMMs run on the tensor cores through
-// cuBLAS with BF16 operands and FP32 accumulation; the data movement around
-// them (im2col with the FP32 -> BF16 rounding, col2im as a deterministic gather,
-// bias + ReLU epilogue, bias gradient, upsampling, loss, Adam) is in the kernels
-// below. No floating-point atomics: every reduction has a fixed order.
-#include <cublas_v2.h>
+// over the whole batch, run on the tcgen05 tensor cores by tc_gemm.cu (BF16
+// operands, FP32 accumulation in tensor memory). Activations are channel-major
+// [C][B][H][W]; with Npix = B*Ho*Wo output pixels and K9 = 9C taps:
+//   forward   y[o][pix]   = act(sum_k colT[pix][k] W[o][k] + bias[o])
+//             A = colT [Npix][K9] (im2col, pixel-major), B = W [O][K9];
+//             the epilogue adds the bias, applies the ReLU and writes y
+//             channel-major directly from the accumulator;
+//   data grad dcol[k][pix] = sum_o dyT[pix][o] W[o][k]
+//             A = dyT [Npix][O], B = W^T [K9][O]; col2im gathers dx;
+//   weight gr dw[o][k]    = sum_pix col[k][pix] dy[o][pix]
+//             A = col [K9][Npix] (im2col, tap-major), B = dy [O][Npix],
+//             split over pixel runs into FP32 partials summed in a fixed order.
+// The data movement around the GEMMs (im2col in both layouts with the FP32 ->
+// BF16 rounding, col2im as a deterministic gather, ReLU backward, bias
+// gradient, transposes, upsampling, loss, Adam) is in the kernels below. No
+// floating-point atomics: every reduction has a fixed order.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -18,6 +26,8 @@
 
 #include "fwi_cnn.h"
 #include "fwi_host.h"
+#include "fwi_internal.cuh"
+#include "tc_gemm.h"
 
 namespace fwi {
 namespace {
@@ -28,77 +38,127 @@ __device__ __forceinline__ uint16_t to_bf16_bits(float f) {
 }
 
 __host__ __device__ __forceinline__ int conv_out(int n, int s) { return (n - 1) / s + 1; }
+__host__ __device__ __forceinline__ long long round8(long long v) { return (v + 7) / 8 * 8; }
 
-// col[k][n], k = c*9 + p*3 + q, n = (b*Ho + i)*Wo + j  <-  x[c][b][sh i + p - 1][sw j + q - 1] (0 outside)
-__global__ void k_im2col(const float* __restrict__ x, int C, int B, int H, int W, int sh, int sw, int Ho, int Wo,
-                         uint16_t* __restrict__ col) {
-  const long long N = (long long)B * Ho * Wo, total = (long long)C * 9 * N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / N, n = e - k * N;
-    const int c = (int)(k / 9), pq = (int)(k - (long long)c * 9), p = pq / 3, q = pq - 3 * p;
-    const int j = (int)(n % Wo);
-    const long long bi = n / Wo;
-    const int i = (int)(bi % Ho), b = (int)(bi / Ho);
-    const int r = sh * i + p - 1, s = sw * j + q - 1;
-    float v = 0.f;
-    if (r >= 0 && r < H && s >= 0 && s < W) v = x[(((long long)c * B + b) * H + r) * W + s];
-    col[e] = to_bf16_bits(v);
+struct ConvDims {
+  int C, B, H, W, sh, sw, Ho, Wo;
+  int K9, Npix;
+};
+
+// x[c][b][sh i + p - 1][sw j + q - 1] for tap k = c*9 + p*3 + q of pixel (b, i, j); 0 in the padding
+__device__ __forceinline__ float tap(const float* __restrict__ x, const ConvDims& d, int k, int b, int i, int j) {
+  const int c = k / 9, pq = k - 9 * c, p = pq / 3, q = pq - 3 * p;
+  const int r = d.sh * i + p - 1, s = d.sw * j + q - 1;
+  if (r < 0 || r >= d.H || s < 0 || s >= d.W) return 0.f;
+  return __ldg(x + (((long long)c * d.B + b) * d.H + r) * d.W + s);
+}
+
+// colT[pix][k] (row stride ldk, BF16): 64 pixels x 64 taps per block, read
+// along pixels (coalesced in x), transposed through shared memory, written as
+// 16-byte runs of taps. Taps k >= K9 up to ldk are written as zeros.
+__global__ void __launch_bounds__(256) k_im2col_t(const float* __restrict__ x, const ConvDims d, int ldk,
+                                                  uint16_t* __restrict__ colT) {
+  __shared__ uint16_t tile[64][66];
+  const int t = threadIdx.x;
+  const int n0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
+  const int nl = t & 63, n = n0 + nl;
+  int b = 0, i = 0, j = 0;
+  const bool nok = n < d.Npix;
+  if (nok) {
+    j = n % d.Wo;
+    const int bi = n / d.Wo;
+    i = bi % d.Ho;
+    b = bi / d.Ho;
+  }
+  for (int kl = t >> 6; kl < 64; kl += 4) {
+    const int k = k0 + kl;
+    tile[kl][nl] = to_bf16_bits(nok && k < d.K9 ? tap(x, d, k, b, i, j) : 0.f);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int pass = 0; pass < 2; pass++) {
+    const int nl2 = pass * 32 + (t >> 3), kg = t & 7;
+    const int n2 = n0 + nl2, kk = k0 + 8 * kg;
+    if (n2 < d.Npix && kk < ldk) {
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        w[u] = (uint32_t)tile[8 * kg + 2 * u][nl2] | ((uint32_t)tile[8 * kg + 2 * u + 1][nl2] << 16);
+      *reinterpret_cast<uint4*>(colT + (long long)n2 * ldk + kk) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// col[k][pix] (row stride ldn, BF16): one tap row per blockIdx.y, 4 pixels per thread
+__global__ void __launch_bounds__(256) k_im2col_n(const float* __restrict__ x, const ConvDims d, long long ldn,
+                                                  uint16_t* __restrict__ col) {
+  const int k = blockIdx.y;
+  const int nb = (blockIdx.x * 256 + threadIdx.x) * 4;
+  if (nb >= d.Npix) return;
+  uint16_t v[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const int n = nb + u;
+    float f = 0.f;
+    if (n < d.Npix) {
+      const int j = n % d.Wo, bi = n / d.Wo, i = bi % d.Ho, b = bi / d.Ho;
+      f = tap(x, d, k, b, i, j);
+    }
+    v[u] = to_bf16_bits(f);
+  }
+  uint16_t* dst = col + (long long)k * ldn + nb;
+  if (nb + 3 < d.Npix) {
+    *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
+                                                (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+  } else {
+    for (int u = 0; u < 4 && nb + u < d.Npix; u++) dst[u] = v[u];
   }
 }
 
 // dx[c][b][r][s] = sum over the taps (p, q) that read (r, s): dcol[c*9+p*3+q][(b*Ho+i)*Wo+j]
 // with r = sh i + p - 1, s = sw j + q - 1 (a gather: each output written once, fixed order).
-__global__ void k_col2im(const float* __restrict__ dcol, int C, int B, int H, int W, int sh, int sw, int Ho, int Wo,
-                         float* __restrict__ dx) {
-  const long long N = (long long)B * Ho * Wo, total = (long long)C * B * H * W;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e % W);
-    const long long t1 = e / W;
-    const int r = (int)(t1 % H);
-    const long long t2 = t1 / H;
-    const int b = (int)(t2 % B), c = (int)(t2 / B);
+__global__ void __launch_bounds__(256) k_col2im(const float* __restrict__ dcol, const ConvDims d,
+                                                float* __restrict__ dx) {
+  const int total = d.C * d.B * d.H * d.W;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int s = e % d.W, t1 = e / d.W, r = t1 % d.H, t2 = t1 / d.H, b = t2 % d.B, c = t2 / d.B;
     float acc = 0.f;
+#pragma unroll
     for (int p = 0; p < 3; p++) {
       const int ri = r + 1 - p;
-      if (ri < 0 || ri % sh != 0) continue;
-      const int i = ri / sh;
-      if (i >= Ho) continue;
+      if (ri < 0 || ri % d.sh != 0) continue;
+      const int i = ri / d.sh;
+      if (i >= d.Ho) continue;
+#pragma unroll
       for (int q = 0; q < 3; q++) {
         const int sj = s + 1 - q;
-        if (sj < 0 || sj % sw != 0) continue;
-        const int j = sj / sw;
-        if (j >= Wo) continue;
-        acc += dcol[(long long)(c * 9 + p * 3 + q) * N + ((long long)b * Ho + i) * Wo + j];
+        if (sj < 0 || sj % d.sw != 0) continue;
+        const int j = sj / d.sw;
+        if (j >= d.Wo) continue;
+        acc += __ldg(dcol + (long long)(c * 9 + p * 3 + q) * d.Npix + (b * d.Ho + i) * d.Wo + j);
       }
     }
     dx[e] = acc;
   }
 }
 
-// y[o][n] += bias[o]; optional ReLU
-__global__ void k_bias_act(float* __restrict__ y, const float* __restrict__ bias, long long N, int O, int relu) {
-  const long long total = (long long)O * N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    float v = y[e] + bias[e / N];
-    y[e] = relu ? fmaxf(v, 0.f) : v;
-  }
-}
-
-// dy *= (y > 0) if relu; dy_bf16 = bf16(dy); db[o] = sum_n dy[o][n] (one block per channel, fixed tree)
-__global__ void k_act_back(float* __restrict__ dy, const float* __restrict__ y, long long N, int relu,
-                           uint16_t* __restrict__ dyb, float* __restrict__ db) {
-  __shared__ float red[32];
-  const int o = blockIdx.x;
+// ReLU backward and the BF16 copy of the pre-activation gradient:
+// dy *= (y > 0) if relu (in place, [O][Npix]); dyb[o][pix] = bf16(dy) (row stride ldn);
+// part[o][chunk] = sum of the chunk's dy (fixed tree), summed by k_db.
+constexpr int ACT_CHUNK = 4096;
+__global__ void __launch_bounds__(256) k_act_back(float* __restrict__ dy, const float* __restrict__ y, int Npix,
+                                                  long long ldn, int relu, uint16_t* __restrict__ dyb,
+                                                  float* __restrict__ part) {
+  __shared__ float red[8];
+  const int o = blockIdx.y, chunk = blockIdx.x;
+  const long long row = (long long)o * Npix;
   float acc = 0.f;
-  for (long long n = threadIdx.x; n < N; n += blockDim.x) {
-    const long long e = (long long)o * N + n;
-    float g = dy[e];
-    if (relu && !(y[e] > 0.f)) g = 0.f;
-    dy[e] = g;
-    dyb[e] = to_bf16_bits(g);
+  const int e0 = chunk * ACT_CHUNK, e1 = min(Npix, e0 + ACT_CHUNK);
+  for (int n = e0 + threadIdx.x; n < e1; n += 256) {
+    float g = dy[row + n];
+    if (relu && !(y[row + n] > 0.f)) g = 0.f;
+    dy[row + n] = g;
+    dyb[(long long)o * ldn + n] = to_bf16_bits(g);
     acc += g;
   }
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -106,32 +166,73 @@ __global__ void k_act_back(float* __restrict__ dy, const float* __restrict__ y, 
   __syncthreads();
   if (threadIdx.x == 0) {
     float s = 0.f;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
-    db[o] = s;
+    for (int w = 0; w < 8; w++) s += red[w];
+    part[(long long)o * gridDim.x + chunk] = s;
+  }
+}
+// db[o] = sum of the chunk partials in chunk order (one thread per channel)
+__global__ void k_db(const float* __restrict__ part, int O, int nchunk, float* __restrict__ db) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= O) return;
+  float s = 0.f;
+  for (int c = 0; c < nchunk; c++) s += part[(long long)o * nchunk + c];
+  db[o] = s;
+}
+
+// dyT[pix][o] (row stride ldo) = dyb[o][pix] (row stride ldn): 32 x 32 tiles through shared memory
+__global__ void k_dy_transpose(const uint16_t* __restrict__ dyb, int O, int Npix, long long ldn, int ldo,
+                               uint16_t* __restrict__ dyT) {
+  __shared__ uint16_t tile[32][34];
+  const int n0 = blockIdx.x * 32, o0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int o = o0 + r, n = n0 + threadIdx.x;
+    tile[r][threadIdx.x] = (o < O && n < Npix) ? dyb[(long long)o * ldn + n] : (uint16_t)0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int n = n0 + r, o = o0 + threadIdx.x;
+    if (n < Npix && o < ldo) dyT[(long long)n * ldo + o] = tile[threadIdx.x][r];
   }
 }
 
-__global__ void k_upsample2(const float* __restrict__ x, long long CB, int H, int W, float* __restrict__ y) {
-  const long long total = CB * 4 * H * W;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e % (2 * W));
-    const long long t = e / (2 * W);
-    const int r = (int)(t % (2 * H));
-    const long long cb = t / (2 * H);
-    y[e] = x[(cb * H + r / 2) * W + s / 2];
+// Weights as GEMM operands: Wp[o][k] (row stride ldk, 16-byte aligned rows) and Wt[k][o] (row stride ldo)
+__global__ void k_wprep(const uint16_t* __restrict__ w, int O, int K9, int ldk, int ldo, uint16_t* __restrict__ Wp,
+                        uint16_t* __restrict__ Wt) {
+  const int total = O * K9;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int o = e / K9, k = e - o * K9;
+    const uint16_t v = w[e];
+    if (Wp) Wp[(long long)o * ldk + k] = v;
+    if (Wt) Wt[(long long)k * ldo + o] = v;
   }
 }
 
-__global__ void k_upsample2_back(const float* __restrict__ dy, long long CB, int H, int W, float* __restrict__ dx) {
-  const long long total = CB * H * W;
+// out[e] = sum over splits s (in order) of part[s * n + e]
+__global__ void k_split_sum(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < splits; k++) s += part[(long long)k * n + e];
+    out[e] = s;
+  }
+}
+
+__global__ void k_upsample2(const float* __restrict__ x, int CB, int H, int W, float* __restrict__ y) {
+  const int W2 = 2 * W, H2 = 2 * H;
+  const long long total = (long long)CB * H2 * W2;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int s = (int)(e % W);
-    const long long t = e / W;
-    const int r = (int)(t % H);
-    const long long cb = t / H;
-    const float* d = dy + (cb * 2 * H + 2 * r) * (2 * W) + 2 * s;
+    const int row = (int)(e / W2), s = (int)(e - (long long)row * W2);  // row = cb * 2H + r
+    const int cb = row / H2, r = row - cb * H2;
+    y[e] = x[((long long)cb * H + (r >> 1)) * W + (s >> 1)];
+  }
+}
+
+__global__ void k_upsample2_back(const float* __restrict__ dy, int CB, int H, int W, float* __restrict__ dx) {
+  const long long total = (long long)CB * H * W;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(e / W), s = (int)(e - (long long)row * W);  // row = cb * H + r
+    const float* d = dy + (long long)row * 4 * W + 2 * s;           // (cb * 2H + 2r) * 2W + 2s
     dx[e] = (d[0] + d[1]) + (d[2 * W] + d[2 * W + 1]);
   }
 }
@@ -186,7 +287,9 @@ int blocks_for(long long n) { return (int)std::max<long long>(1, std::min<long l
 // C ABI
 struct fwi_cnn {
   int device = 0;
-  cublasHandle_t blas = nullptr;
+  void* ws = nullptr;     // workspace of the layer calls (grows to the largest layer)
+  size_t ws_bytes = 0;
+  int* status = nullptr;  // device status word of the GEMMs (timeout bit)
 };
 
 namespace {
@@ -196,36 +299,54 @@ using fwi::blocks_for;
 fwi_status cuda_fail(cudaError_t e, const char* what) {
   return fwi::host_fail(FWI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
-fwi_status blas_fail(cublasStatus_t s, const char* what) {
-  return fwi::host_fail(FWI_ECUDA, std::string(what) + ": cuBLAS status " + std::to_string((int)s));
-}
 
 #define CNN_CK(call, what)                              \
   do {                                                  \
     cudaError_t e_ = (call);                            \
     if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
   } while (0)
-#define CNN_BLAS(call, what)                                        \
-  do {                                                              \
-    cublasStatus_t s_ = (call);                                     \
-    if (s_ != CUBLAS_STATUS_SUCCESS) return blas_fail(s_, what);    \
-  } while (0)
 
-// Row-major C[M][N] = A[M][K] . B[K][N] with BF16 A, B and FP32 C, as the
-// column-major product C^T = B^T A^T (cuBLAS is column-major). ta / tb say
-// whether the row-major operand is stored transposed ([K][M] / [N][K]).
-fwi_status gemm_rm(cublasHandle_t h, bool ta, bool tb, int M, int N, int K, const uint16_t* A, const uint16_t* B,
-                   float* C, const char* what) {
-  const float one = 1.f, zero = 0.f;
-  const int lda = ta ? M : K, ldb = tb ? K : N;
-  CNN_BLAS(cublasGemmEx(h, tb ? CUBLAS_OP_T : CUBLAS_OP_N, ta ? CUBLAS_OP_T : CUBLAS_OP_N, N, M, K, &one, B,
-                        CUDA_R_16BF, ldb, A, CUDA_R_16BF, lda, &zero, C, CUDA_R_32F, N, CUBLAS_COMPUTE_32F,
-                        CUBLAS_GEMM_DEFAULT),
-           what);
+bool bad_dims(int C, int B, int H, int W) { return C < 1 || B < 1 || H < 1 || W < 1; }
+
+// Carves 256-byte aligned pieces out of the handle's workspace.
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  }
+};
+
+// Grow the workspace to `bytes` (cudaFree synchronises the device, so no call
+// still in flight uses the old buffer).
+fwi_status ws_reserve(fwi_cnn* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return FWI_OK;
+  if (h->ws) CNN_CK(cudaFree(h->ws), "cudaFree");
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  const size_t want = bytes + bytes / 4;
+  CNN_CK(cudaMalloc(&h->ws, want), "cudaMalloc (cnn workspace)");
+  h->ws_bytes = want;
   return FWI_OK;
 }
 
-bool bad_dims(int C, int B, int H, int W) { return C < 1 || B < 1 || H < 1 || W < 1; }
+fwi_status dims_of(int C, int B, int H, int W, int sh, int sw, fwi::ConvDims* d) {
+  d->C = C; d->B = B; d->H = H; d->W = W; d->sh = sh; d->sw = sw;
+  d->Ho = fwi::conv_out(H, sh);
+  d->Wo = fwi::conv_out(W, sw);
+  const long long npix = (long long)B * d->Ho * d->Wo, k9 = 9LL * C;
+  if (npix > 0x7fffff00LL || k9 > 65535 || (long long)C * B * H * W > 0x7fffff00LL)
+    return fwi::host_fail(FWI_EINVAL, "layer too large");
+  d->K9 = (int)k9;
+  d->Npix = (int)npix;
+  return FWI_OK;
+}
+
+int gemm_blocks(long long tiles_per_split) {
+  // splits so that about two waves of CTAs cover the GPU's 152 SMs
+  return (int)std::max<long long>(1, (2 * 152 + tiles_per_split - 1) / tiles_per_split);
+}
 
 }  // namespace
 
@@ -236,10 +357,12 @@ fwi_status fwi_cnn_create(fwi_cnn** h, int device) {
   CNN_CK(cudaSetDevice(device), "cudaSetDevice");
   fwi_cnn* c = new fwi_cnn;
   c->device = device;
-  cublasStatus_t s = cublasCreate(&c->blas);
-  if (s != CUBLAS_STATUS_SUCCESS) {
+  cudaError_t e = cudaMalloc(&c->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    if (c->status) cudaFree(c->status);
     delete c;
-    return blas_fail(s, "cublasCreate");
+    return cuda_fail(e, "cudaMalloc (status)");
   }
   *h = c;
   return FWI_OK;
@@ -248,57 +371,134 @@ fwi_status fwi_cnn_create(fwi_cnn** h, int device) {
 fwi_status fwi_cnn_destroy(fwi_cnn* h) {
   if (!h) return FWI_OK;
   cudaSetDevice(h->device);
-  if (h->blas) cublasDestroy(h->blas);
+  if (h->ws) cudaFree(h->ws);
+  if (h->status) cudaFree(h->status);
   delete h;
+  return FWI_OK;
+}
+
+fwi_status fwi_cnn_check(fwi_cnn* h, void* stream) {
+  if (!h) return fwi::host_fail(FWI_EINVAL, "h must not be NULL");
+  CNN_CK(cudaSetDevice(h->device), "cudaSetDevice");
+  int st = 0;
+  CNN_CK(cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream), "status read");
+  CNN_CK(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+  if (st) {
+    CNN_CK(cudaMemset(h->status, 0, sizeof(int)), "status clear");
+    return fwi::host_fail(FWI_ETIMEOUT, "a tensor-core GEMM wait timed out; its output holds NaN");
+  }
+  return FWI_OK;
+}
+
+fwi_status fwi_cnn_gemm_bt(fwi_cnn* h, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, int64_t M,
+                           int32_t N, int64_t K, float* out, int64_t ldo, const float* bias, int32_t relu,
+                           int32_t splits, void* stream) {
+  if (!h || !A || !B || !out) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
+  if (M < 1 || N < 1 || K < 1 || splits < 1 || ldo < M || lda < K || ldb < K || lda % 8 || ldb % 8)
+    return fwi::host_fail(FWI_EINVAL, "bad sizes or leading dimensions (lda, ldb: multiples of 8, >= K; ldo >= M)");
+  if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return fwi::host_fail(FWI_EINVAL, "A and B must be 16-byte aligned");
+  CNN_CK(cudaSetDevice(h->device), "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = fwi::tc_split_count(K, splits);
+  float* dst = out;
+  if (S > 1) {
+    const fwi_status v = ws_reserve(h, (size_t)S * N * ldo * sizeof(float));
+    if (v != FWI_OK) return v;
+    dst = (float*)h->ws;
+  }
+  fwi::TcGemm g{A, lda, B, ldb, M, N, K, dst, ldo, (long long)N * ldo, S > 1 ? nullptr : bias, S > 1 ? 0 : relu, S,
+                h->status};
+  CNN_CK(fwi::tc_gemm(g, st), "tcgen05 GEMM");
+  if (S > 1) {
+    if (bias || relu) return fwi::host_fail(FWI_EINVAL, "bias / relu need splits == 1");
+    fwi::k_split_sum<<<blocks_for((long long)N * ldo), 256, 0, st>>>(dst, S, (long long)N * ldo, out);
+    CNN_CK(cudaGetLastError(), "split sum");
+  }
   return FWI_OK;
 }
 
 fwi_status fwi_cnn_conv_forward(fwi_cnn* h, const float* x, int32_t C, int32_t B, int32_t H, int32_t W,
                                 const uint16_t* w_bf16, const float* bias, int32_t O, int32_t sh, int32_t sw,
-                                int32_t relu, uint16_t* col, float* y, void* stream) {
-  if (!h || !x || !w_bf16 || !bias || !col || !y) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
+                                int32_t relu, float* y, void* stream) {
+  if (!h || !x || !w_bf16 || !bias || !y) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (bad_dims(C, B, H, W) || O < 1 || sh < 1 || sw < 1) return fwi::host_fail(FWI_EINVAL, "bad sizes");
+  fwi::ConvDims d;
+  fwi_status v = dims_of(C, B, H, W, sh, sw, &d);
+  if (v != FWI_OK) return v;
   CNN_CK(cudaSetDevice(h->device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  const int Ho = fwi::conv_out(H, sh), Wo = fwi::conv_out(W, sw);
-  const long long N = (long long)B * Ho * Wo, K = 9LL * C;
-  if (N > 0x7fffffffLL || K * N > (1LL << 40)) return fwi::host_fail(FWI_EINVAL, "layer too large for one GEMM");
-  fwi::k_im2col<<<blocks_for(K * N), 256, 0, st>>>(x, C, B, H, W, sh, sw, Ho, Wo, col);
+  const int ldk = (int)fwi::round8(d.K9);
+  Carve cv;
+  const size_t o_col = cv.take((size_t)d.Npix * ldk * 2), o_wp = cv.take((size_t)O * ldk * 2);
+  if ((v = ws_reserve(h, cv.off)) != FWI_OK) return v;
+  char* ws = (char*)h->ws;
+  uint16_t* colT = (uint16_t*)(ws + o_col);
+  uint16_t* Wp = (uint16_t*)(ws + o_wp);
+  fwi::k_wprep<<<blocks_for((long long)O * d.K9), 256, 0, st>>>(w_bf16, O, d.K9, ldk, 0, Wp, nullptr);
+  CNN_CK(cudaGetLastError(), "weight layout");
+  fwi::k_im2col_t<<<dim3((d.Npix + 63) / 64, (ldk + 63) / 64), 256, 0, st>>>(x, d, ldk, colT);
   CNN_CK(cudaGetLastError(), "im2col");
-  CNN_BLAS(cublasSetStream(h->blas, st), "cublasSetStream");
-  fwi_status v = gemm_rm(h->blas, false, false, O, (int)N, (int)K, w_bf16, col, y, "conv forward GEMM");
-  if (v != FWI_OK) return v;
-  fwi::k_bias_act<<<blocks_for((long long)O * N), 256, 0, st>>>(y, bias, N, O, relu);
-  CNN_CK(cudaGetLastError(), "bias/activation");
+  fwi::TcGemm g{colT, ldk, Wp, ldk, d.Npix, O, d.K9, y, d.Npix, 0, bias, relu, 1, h->status};
+  CNN_CK(fwi::tc_gemm(g, st), "conv forward GEMM");
   return FWI_OK;
 }
 
 fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t B, int32_t H, int32_t W,
                                  const uint16_t* w_bf16, int32_t O, int32_t sh, int32_t sw, int32_t relu,
-                                 const float* y, float* dy, uint16_t* col, uint16_t* dy_bf16, float* dcol, float* dx,
-                                 float* dw, float* db, void* stream) {
-  if (!h || !x || !w_bf16 || !y || !dy || !col || !dy_bf16 || !dw || !db || (dx && !dcol))
-    return fwi::host_fail(FWI_EINVAL, "NULL pointer");
+                                 const float* y, float* dy, float* dx, float* dw, float* db, void* stream) {
+  if (!h || !x || !w_bf16 || !y || !dy || !dw || !db) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (bad_dims(C, B, H, W) || O < 1 || sh < 1 || sw < 1) return fwi::host_fail(FWI_EINVAL, "bad sizes");
+  fwi::ConvDims d;
+  fwi_status v = dims_of(C, B, H, W, sh, sw, &d);
+  if (v != FWI_OK) return v;
   CNN_CK(cudaSetDevice(h->device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  const int Ho = fwi::conv_out(H, sh), Wo = fwi::conv_out(W, sw);
-  const long long N = (long long)B * Ho * Wo, K = 9LL * C;
-  if (N > 0x7fffffffLL) return fwi::host_fail(FWI_EINVAL, "layer too large for one GEMM");
-  fwi::k_act_back<<<O, 256, 0, st>>>(dy, y, N, relu, dy_bf16, db);
+  const long long ldn = fwi::round8(d.Npix);
+  const int ldo = (int)fwi::round8(O);
+  const int nchunk = (d.Npix + fwi::ACT_CHUNK - 1) / fwi::ACT_CHUNK;
+  // weight gradient split over pixel runs: about two waves of CTAs
+  const long long mt = (d.K9 + 127) / 128, nt = (O + 255) / 256;
+  const int S = fwi::tc_split_count(d.Npix, gemm_blocks(mt * nt));
+  Carve cv;
+  const size_t o_dyb = cv.take((size_t)O * ldn * 2), o_bp = cv.take((size_t)O * nchunk * 4);
+  const size_t o_col = cv.take(std::max<size_t>((size_t)d.K9 * ldn, dx ? (size_t)d.Npix * ldo : 0) * 2);
+  const size_t o_wt = cv.take(dx ? (size_t)d.K9 * ldo * 2 : 0);
+  const size_t o_dcol = cv.take(dx ? (size_t)d.K9 * d.Npix * 4 : 0);
+  const size_t o_part = cv.take(S > 1 ? (size_t)S * O * d.K9 * 4 : 0);
+  if ((v = ws_reserve(h, cv.off)) != FWI_OK) return v;
+  char* ws = (char*)h->ws;
+  uint16_t* dyb = (uint16_t*)(ws + o_dyb);
+  float* bpart = (float*)(ws + o_bp);
+  uint16_t* colb = (uint16_t*)(ws + o_col);
+  uint16_t* Wt = (uint16_t*)(ws + o_wt);
+  float* dcol = (float*)(ws + o_dcol);
+  float* part = (float*)(ws + o_part);
+
+  fwi::k_act_back<<<dim3(nchunk, O), 256, 0, st>>>(dy, y, d.Npix, ldn, relu, dyb, bpart);
   CNN_CK(cudaGetLastError(), "activation backward");
-  fwi::k_im2col<<<blocks_for(K * N), 256, 0, st>>>(x, C, B, H, W, sh, sw, Ho, Wo, col);
-  CNN_CK(cudaGetLastError(), "im2col");
-  CNN_BLAS(cublasSetStream(h->blas, st), "cublasSetStream");
-  // dw[O][K] = dy[O][N] . col^T  (col stored [K][N])
-  fwi_status v = gemm_rm(h->blas, false, true, O, (int)K, (int)N, dy_bf16, col, dw, "conv weight-gradient GEMM");
-  if (v != FWI_OK) return v;
+  fwi::k_db<<<(O + 127) / 128, 128, 0, st>>>(bpart, O, nchunk, db);
+  CNN_CK(cudaGetLastError(), "bias gradient");
   if (dx) {
-    // dcol[K][N] = w^T . dy  (w stored [O][K])
-    v = gemm_rm(h->blas, true, false, (int)K, (int)N, O, w_bf16, dy_bf16, dcol, "conv data-gradient GEMM");
-    if (v != FWI_OK) return v;
-    fwi::k_col2im<<<blocks_for((long long)C * B * H * W), 256, 0, st>>>(dcol, C, B, H, W, sh, sw, Ho, Wo, dx);
+    // dcol[k][pix] = sum_o dyT[pix][o] W[o][k], then the col2im gather
+    fwi::k_dy_transpose<<<dim3((d.Npix + 31) / 32, (ldo + 31) / 32), dim3(32, 8), 0, st>>>(dyb, O, d.Npix, ldn, ldo,
+                                                                                          colb);
+    CNN_CK(cudaGetLastError(), "dy transpose");
+    fwi::k_wprep<<<blocks_for((long long)O * d.K9), 256, 0, st>>>(w_bf16, O, d.K9, 0, ldo, nullptr, Wt);
+    CNN_CK(cudaGetLastError(), "weight layout");
+    fwi::TcGemm g{colb, ldo, Wt, ldo, d.Npix, d.K9, O, dcol, d.Npix, 0, nullptr, 0, 1, h->status};
+    CNN_CK(fwi::tc_gemm(g, st), "conv data-gradient GEMM");
+    fwi::k_col2im<<<blocks_for((long long)C * B * H * W), 256, 0, st>>>(dcol, d, dx);
     CNN_CK(cudaGetLastError(), "col2im");
+  }
+  // dw[o][k] = sum_pix col[k][pix] dy[o][pix]
+  fwi::k_im2col_n<<<dim3((d.Npix + 1023) / 1024, d.K9), 256, 0, st>>>(x, d, ldn, colb);
+  CNN_CK(cudaGetLastError(), "im2col");
+  fwi::TcGemm g{colb, ldn, dyb, ldn, d.K9, O, d.Npix, S > 1 ? part : dw, d.K9, (long long)O * d.K9, nullptr, 0, S,
+                h->status};
+  CNN_CK(fwi::tc_gemm(g, st), "conv weight-gradient GEMM");
+  if (S > 1) {
+    fwi::k_split_sum<<<blocks_for((long long)O * d.K9), 256, 0, st>>>(part, S, (long long)O * d.K9, dw);
+    CNN_CK(cudaGetLastError(), "split sum");
   }
   return FWI_OK;
 }
@@ -306,8 +506,9 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
 fwi_status fwi_cnn_upsample2(const float* x, int32_t C, int32_t B, int32_t H, int32_t W, float* y, void* stream) {
   if (!x || !y) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (bad_dims(C, B, H, W)) return fwi::host_fail(FWI_EINVAL, "bad sizes");
-  const long long CB = (long long)C * B;
-  fwi::k_upsample2<<<blocks_for(CB * 4 * H * W), 256, 0, (cudaStream_t)stream>>>(x, CB, H, W, y);
+  if ((long long)C * B * 4 * H * W > 0x7fffff00LL) return fwi::host_fail(FWI_EINVAL, "tensor too large");
+  const int CB = C * B;
+  fwi::k_upsample2<<<blocks_for(4LL * CB * H * W), 256, 0, (cudaStream_t)stream>>>(x, CB, H, W, y);
   CNN_CK(cudaGetLastError(), "upsample");
   return FWI_OK;
 }
@@ -316,8 +517,9 @@ fwi_status fwi_cnn_upsample2_backward(const float* dy, int32_t C, int32_t B, int
                                       void* stream) {
   if (!dy || !dx) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (bad_dims(C, B, H, W)) return fwi::host_fail(FWI_EINVAL, "bad sizes");
-  const long long CB = (long long)C * B;
-  fwi::k_upsample2_back<<<blocks_for(CB * H * W), 256, 0, (cudaStream_t)stream>>>(dy, CB, H, W, dx);
+  if ((long long)C * B * 4 * H * W > 0x7fffff00LL) return fwi::host_fail(FWI_EINVAL, "tensor too large");
+  const int CB = C * B;
+  fwi::k_upsample2_back<<<blocks_for((long long)CB * H * W), 256, 0, (cudaStream_t)stream>>>(dy, CB, H, W, dx);
   CNN_CK(cudaGetLastError(), "upsample backward");
   return FWI_OK;
 }

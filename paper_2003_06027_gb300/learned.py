@@ -48,15 +48,17 @@ def _lib():
         P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
         L.fwi_cnn_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
         L.fwi_cnn_destroy.argtypes = [P]
-        L.fwi_cnn_conv_forward.argtypes = [P, P, i32, i32, i32, i32, P, P, i32, i32, i32, i32, P, P, P]
-        L.fwi_cnn_conv_backward.argtypes = [P, P, i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P, P,
-                                            P, P]
+        L.fwi_cnn_check.argtypes = [P, P]
+        L.fwi_cnn_gemm_bt.argtypes = [P, P, i64, P, i64, i64, i32, i64, P, i64, P, i32, i32, P]
+        L.fwi_cnn_conv_forward.argtypes = [P, P, i32, i32, i32, i32, P, P, i32, i32, i32, i32, P, P]
+        L.fwi_cnn_conv_backward.argtypes = [P, P, i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P]
         L.fwi_cnn_upsample2.argtypes = [P, i32, i32, i32, i32, P, P]
         L.fwi_cnn_upsample2_backward.argtypes = [P, i32, i32, i32, i32, P, P]
         L.fwi_cnn_mse.argtypes = [P, P, i64, P, P, P]
         L.fwi_cnn_adam.argtypes = [P, P, P, P, i64, i32, f32, f32, f32, f32, P, P]
         L.fwi_cnn_to_bf16.argtypes = [P, P, i64, P]
-        for f in ("fwi_cnn_create", "fwi_cnn_destroy", "fwi_cnn_conv_forward", "fwi_cnn_conv_backward",
+        for f in ("fwi_cnn_create", "fwi_cnn_destroy", "fwi_cnn_check", "fwi_cnn_gemm_bt", "fwi_cnn_conv_forward",
+                  "fwi_cnn_conv_backward",
                   "fwi_cnn_upsample2", "fwi_cnn_upsample2_backward", "fwi_cnn_mse", "fwi_cnn_adam",
                   "fwi_cnn_to_bf16"):
             getattr(L, f).restype = ctypes.c_int
@@ -77,11 +79,16 @@ def _chk(st):
 
 
 class Handle:
-    """A cuBLAS-owning handle of the CNN layers on one device."""
+    """The CNN layers' handle on one device (workspace and GEMM status word).
+    Its calls must be issued in order on one stream."""
 
     def __init__(self, device=0):
         self.h = ctypes.c_void_p()
         _chk(_lib().fwi_cnn_create(ctypes.byref(self.h), int(device)))
+
+    def check(self):
+        """Wait for the current stream; raise if a GEMM wait timed out."""
+        _chk(_lib().fwi_cnn_check(self.h, _st()))
 
     def __del__(self):
         try:
@@ -100,35 +107,40 @@ def to_bf16(x: torch.Tensor) -> torch.Tensor:
     return y
 
 
-def conv_forward(h: Handle, x, w_bf16, bias, sh, sw, relu, col=None):
+def gemm_bt(h: Handle, A, B, out=None, bias=None, relu=False, splits=1):
+    """out[n][m] = act(sum_k A[m][k] B[n][k] + bias[n]) for BF16 (int16-viewed)
+    A [M][lda], B [N][ldb] with the contraction over their first K columns,
+    K = A.shape[1] = B.shape[1] (fwi_cnn_gemm_bt)."""
+    M, K = A.shape
+    N = B.shape[0]
+    if out is None:
+        out = torch.empty((N, M), dtype=torch.float32, device=A.device)
+    _chk(_lib().fwi_cnn_gemm_bt(h.h, _p(A), A.stride(0), _p(B), B.stride(0), M, N, K, _p(out), out.stride(0),
+                                _p(bias), int(relu), int(splits), _st()))
+    return out
+
+
+def conv_forward(h: Handle, x, w_bf16, bias, sh, sw, relu):
     """x [C][B][H][W] -> y [O][B][Ho][Wo] (fwi_cnn_conv_forward)."""
     C, B, H, W = x.shape
     O = bias.shape[0]
     Ho, Wo = conv_out(H, sh), conv_out(W, sw)
-    if col is None:
-        col = torch.empty(C * 9 * B * Ho * Wo, dtype=torch.int16, device=x.device)
     y = torch.empty((O, B, Ho, Wo), dtype=torch.float32, device=x.device)
-    _chk(_lib().fwi_cnn_conv_forward(h.h, _p(x), C, B, H, W, _p(w_bf16), _p(bias), O, sh, sw, int(relu), _p(col),
-                                     _p(y), _st()))
+    _chk(_lib().fwi_cnn_conv_forward(h.h, _p(x), C, B, H, W, _p(w_bf16), _p(bias), O, sh, sw, int(relu), _p(y),
+                                     _st()))
     return y
 
 
-def conv_backward(h: Handle, x, w_bf16, y, dy, sh, sw, relu, need_dx=True, ws=None):
+def conv_backward(h: Handle, x, w_bf16, y, dy, sh, sw, relu, need_dx=True):
     """(dx or None, dw, db); dy is overwritten with the pre-activation gradient."""
     C, B, H, W = x.shape
-    O, _, Ho, Wo = dy.shape
+    O = dy.shape[0]
     dev = x.device
-    ws = ws or {}
-    col = ws.get("col")
-    if col is None or col.numel() < C * 9 * B * Ho * Wo:
-        col = torch.empty(C * 9 * B * Ho * Wo, dtype=torch.int16, device=dev)
-    dyb = torch.empty(dy.numel(), dtype=torch.int16, device=dev)
-    dcol = torch.empty(C * 9 * B * Ho * Wo, dtype=torch.float32, device=dev) if need_dx else None
     dx = torch.empty_like(x) if need_dx else None
     dw = torch.empty((O, C, 3, 3), dtype=torch.float32, device=dev)
     db = torch.empty(O, dtype=torch.float32, device=dev)
     _chk(_lib().fwi_cnn_conv_backward(h.h, _p(x), C, B, H, W, _p(w_bf16), O, sh, sw, int(relu), _p(y), _p(dy),
-                                      _p(col), _p(dyb), _p(dcol), _p(dx), _p(dw), _p(db), _st()))
+                                      _p(dx), _p(dw), _p(db), _st()))
     return dx, dw, db
 
 

@@ -1,5 +1,7 @@
-"""Parity of the start-model network's layers (libfwi CNN kernels, tensor-core
-GEMMs through the C ABI) with the FP64 reference layers of oracle/cnn.py.
+"""Parity of the start-model network's layers (libfwi CNN kernels, tcgen05
+tensor-core GEMMs through the C ABI) with the FP64 reference layers of
+oracle/cnn.py, and of the GEMM itself with an FP64 product of the same
+BF16-rounded operands.
 
 The GEMMs multiply BF16-rounded operands with FP32 accumulation, so the oracle
 is evaluated on the same BF16-rounded operands (oracle.cnn.bf16_round) and the
@@ -24,6 +26,49 @@ def _cuda(a):
     import torch
 
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+GEMMS = [  # M, N, K, splits, bias+relu, row padding of A and B
+    (128, 16, 64, 1, False, 0),
+    (300, 40, 200, 1, True, 8),
+    (1000, 256, 1152, 1, True, 0),
+    (77, 300, 16, 1, False, 16),
+    (144, 32, 5000, 8, False, 0),
+    (27, 5, 442, 3, False, 24),
+]
+
+
+@pytest.mark.parametrize("case", GEMMS, ids=[f"{c[0]}x{c[1]}x{c[2]}-s{c[3]}" for c in GEMMS])
+def test_tcgen05_gemm(fwi_lib, case):
+    """out[n][m] = act(sum_k A[m][k] B[n][k] + bias[n]) on BF16 operands with
+    FP32 accumulation: ragged M, N, K (zero fill at the tile edges), N over
+    several tiles, split K, strided operands."""
+    import torch
+
+    from paper_2003_06027_gb300 import learned as L
+
+    M, N, K, splits, act, pad = case
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    a = rng.standard_normal((M, K)).astype(np.float32)
+    b = rng.standard_normal((N, K)).astype(np.float32)
+    bias = rng.standard_normal(N).astype(np.float32)
+    lda = (K + 7) // 8 * 8 + pad
+    h = L.Handle(0)
+    Ab = torch.zeros((M, lda), dtype=torch.int16, device="cuda")
+    Bb = torch.zeros((N, lda), dtype=torch.int16, device="cuda")
+    Ab[:, :K] = L.to_bf16(_cuda(a))
+    Bb[:, :K] = L.to_bf16(_cuda(b))
+    out = L.gemm_bt(h, Ab[:, :K], Bb[:, :K], bias=_cuda(bias) if act else None, relu=act, splits=splits)
+    h.check()
+    want = np.float64(cnn.bf16_round(b)) @ np.float64(cnn.bf16_round(a)).T
+    if act:
+        want = np.maximum(want + np.float64(bias)[:, None], 0.0)
+    got = out.cpu().numpy()
+    assert got.shape == (N, M)
+    assert np.isfinite(got).all()
+    assert rel(got, want) <= 1e-5
+    again = L.gemm_bt(h, Ab[:, :K], Bb[:, :K], bias=_cuda(bias) if act else None, relu=act, splits=splits)
+    assert torch.equal(again, out)  # deterministic: fixed-order split sums, no atomics
 
 
 SHAPES = [  # C, B, H, W, O, sh, sw, relu
@@ -63,6 +108,7 @@ def test_conv_forward_backward(fwi_lib, shape):
     assert rel(dw.cpu().numpy(), dwo) <= 1e-5
     assert rel(db.cpu().numpy(), g.sum(axis=(1, 2, 3))) <= 1e-6
     _, dw2, _ = L.conv_backward(h, _cuda(x), wb, y, _cuda(dy), sh, sw, relu, need_dx=False)
+    h.check()
     assert np.array_equal(dw2.cpu().numpy(), dw.cpu().numpy())
 
 
