@@ -252,7 +252,7 @@ def learned_measure():
 
     def step():
         out = net.forward(X)
-        _, dout = L.mse(out, Y)
+        _, dout = L.mse(net.h, out, Y)
         net.backward(dout)
         net.step(1e-4)
 

@@ -72,7 +72,9 @@ fwi_status fwi_cnn_conv_forward(fwi_cnn *h, const float *x, int32_t C, int32_t B
  * y: the layer's output from fwi_cnn_conv_forward (used for the ReLU mask when relu != 0).
  * dy: dL/dy [O][B][Ho][Wo]; overwritten with dL/d(pre-activation).
  * dx: dL/dx [C][B][H][W], or NULL (first layer); dw [O][C][3][3]; db [O].
- * The GEMM operands are the BF16-rounded pre-activation gradient, x and w. */
+ * The GEMM operands are the BF16-rounded pre-activation gradient, x and w. A
+ * stride-1 layer's dx is one GEMM (the gradient convolved with the flipped
+ * weights); a strided layer's goes through a tap matrix and a col2im gather. */
 fwi_status fwi_cnn_conv_backward(fwi_cnn *h, const float *x, int32_t C, int32_t B, int32_t H, int32_t W,
                                  const uint16_t *w_bf16, int32_t O, int32_t sh, int32_t sw, int32_t relu,
                                  const float *y, float *dy, float *dx, float *dw, float *db, void *cuda_stream);
@@ -84,8 +86,10 @@ fwi_status fwi_cnn_upsample2(const float *x, int32_t C, int32_t B, int32_t H, in
 fwi_status fwi_cnn_upsample2_backward(const float *dy, int32_t C, int32_t B, int32_t H, int32_t W, float *dx,
                                       void *cuda_stream);
 
-/* loss = 1/(2n) sum (p - t)^2 (FP64, one device double) and dp = (p - t) / n. */
-fwi_status fwi_cnn_mse(const float *p, const float *t, int64_t n, double *loss, float *dp, void *cuda_stream);
+/* loss = 1/(2n) sum (p - t)^2 (FP64, one device double) and dp = (p - t) / n.
+ * The FP64 sum runs over a fixed number of block partials held by the handle. */
+fwi_status fwi_cnn_mse(fwi_cnn *h, const float *p, const float *t, int64_t n, double *loss, float *dp,
+                       void *cuda_stream);
 
 /* One bias-corrected Adam step (Kingma & Ba) on n parameters at step >= 1;
  * theta_bf16, if not NULL, receives the BF16 copy of the updated theta. */

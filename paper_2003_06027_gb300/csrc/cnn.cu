@@ -40,18 +40,31 @@ __device__ __forceinline__ uint16_t to_bf16_bits(float f) {
 __host__ __device__ __forceinline__ int conv_out(int n, int s) { return (n - 1) / s + 1; }
 __host__ __device__ __forceinline__ long long round8(long long v) { return (v + 7) / 8 * 8; }
 
+// Division by a loop-invariant divisor d >= 1 for dividends n < 2^31, as a
+// multiply and a shift (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", 1994): with l = ceil(log2 d) and m = ceil(2^(32+l) / d),
+// floor(n / d) = floor(n m / 2^(32+l)) exactly, since the error of m adds less
+// than 2^(-1-l) <= 1/(2d) to n/d, whose fractional part is at most (d-1)/d.
+struct FastDiv {
+  uint32_t d = 1, s = 32;
+  unsigned long long m = 1ull;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t dv) : d(dv) {
+    uint32_t l = 0;
+    while ((1ull << l) < dv) l++;
+    s = 32 + l;
+    m = ((1ull << s) + dv - 1) / dv;
+  }
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return (uint32_t)(((unsigned long long)n * m) >> s); }
+  __device__ __forceinline__ uint32_t mod(uint32_t n, uint32_t q) const { return n - q * d; }
+};
+
 struct ConvDims {
   int C, B, H, W, sh, sw, Ho, Wo;
   int K9, Npix;
+  FastDiv fWo, fHo;  // pixel n = (b * Ho + i) * Wo + j
+  FastDiv fW, fH, fB;  // input element e = ((c * B + b) * H + r) * W + s
 };
-
-// x[c][b][sh i + p - 1][sw j + q - 1] for tap k = c*9 + p*3 + q of pixel (b, i, j); 0 in the padding
-__device__ __forceinline__ float tap(const float* __restrict__ x, const ConvDims& d, int k, int b, int i, int j) {
-  const int c = k / 9, pq = k - 9 * c, p = pq / 3, q = pq - 3 * p;
-  const int r = d.sh * i + p - 1, s = d.sw * j + q - 1;
-  if (r < 0 || r >= d.H || s < 0 || s >= d.W) return 0.f;
-  return __ldg(x + (((long long)c * d.B + b) * d.H + r) * d.W + s);
-}
 
 // colT[pix][k] (row stride ldk, BF16): 64 pixels x 64 taps per block, read
 // along pixels (coalesced in x), transposed through shared memory, written as
@@ -65,15 +78,25 @@ __global__ void __launch_bounds__(256) k_im2col_t(const float* __restrict__ x, c
   int b = 0, i = 0, j = 0;
   const bool nok = n < d.Npix;
   if (nok) {
-    j = n % d.Wo;
-    const int bi = n / d.Wo;
-    i = bi % d.Ho;
-    b = bi / d.Ho;
+    const uint32_t bi = d.fWo.div((uint32_t)n);
+    j = (int)d.fWo.mod((uint32_t)n, bi);
+    b = (int)d.fHo.div(bi);
+    i = (int)d.fHo.mod(bi, (uint32_t)b);
   }
-  for (int kl = t >> 6; kl < 64; kl += 4) {
-    const int k = k0 + kl;
-    tile[kl][nl] = to_bf16_bits(nok && k < d.K9 ? tap(x, d, k, b, i, j) : 0.f);
+  const long long plane = (long long)d.B * d.H * d.W;
+  const float* xb = x + (long long)b * d.H * d.W;
+  const int r0 = d.sh * i - 1, s0 = d.sw * j - 1;
+  float v[16];
+#pragma unroll
+  for (int u = 0; u < 16; u++) {  // all 16 loads in flight before the first use
+    const int k = k0 + (t >> 6) + 4 * u;
+    const int c = k / 9, pq = k - 9 * c, p = pq / 3, q = pq - 3 * p;
+    const int r = r0 + p, s = s0 + q;
+    v[u] = (nok && k < d.K9 && r >= 0 && r < d.H && s >= 0 && s < d.W) ? __ldg(xb + c * plane + (long long)r * d.W + s)
+                                                                       : 0.f;
   }
+#pragma unroll
+  for (int u = 0; u < 16; u++) tile[(t >> 6) + 4 * u][nl] = to_bf16_bits(v[u]);
   __syncthreads();
 #pragma unroll
   for (int pass = 0; pass < 2; pass++) {
@@ -89,23 +112,39 @@ __global__ void __launch_bounds__(256) k_im2col_t(const float* __restrict__ x, c
   }
 }
 
-// col[k][pix] (row stride ldn, BF16): one tap row per blockIdx.y, 4 pixels per thread
+// col[k][pix] (row stride ldn, BF16): one tap row per blockIdx.y, 4 pixels per
+// thread; the first pixel's (b, i, j) is decoded once and the next ones step
+// along the row.
 __global__ void __launch_bounds__(256) k_im2col_n(const float* __restrict__ x, const ConvDims d, long long ldn,
                                                   uint16_t* __restrict__ col) {
   const int k = blockIdx.y;
   const int nb = (blockIdx.x * 256 + threadIdx.x) * 4;
   if (nb >= d.Npix) return;
-  uint16_t v[4];
+  const int c = k / 9, pq = k - 9 * c, p = pq / 3, q = pq - 3 * p;
+  const float* xc = x + (long long)c * d.B * d.H * d.W;
+  uint32_t bi = d.fWo.div((uint32_t)nb);
+  int j = (int)d.fWo.mod((uint32_t)nb, bi);
+  uint32_t b = d.fHo.div(bi);
+  int i = (int)d.fHo.mod(bi, b);
+  float f[4];
 #pragma unroll
   for (int u = 0; u < 4; u++) {
-    const int n = nb + u;
-    float f = 0.f;
-    if (n < d.Npix) {
-      const int j = n % d.Wo, bi = n / d.Wo, i = bi % d.Ho, b = bi / d.Ho;
-      f = tap(x, d, k, b, i, j);
+    if (j == d.Wo) {  // next pixel row (next image after its last row)
+      j = 0;
+      if (++i == d.Ho) {
+        i = 0;
+        b++;
+      }
     }
-    v[u] = to_bf16_bits(f);
+    const int r = d.sh * i + p - 1, s = d.sw * j + q - 1;
+    f[u] = (nb + u < d.Npix && r >= 0 && r < d.H && s >= 0 && s < d.W)
+               ? __ldg(xc + ((long long)b * d.H + r) * d.W + s)
+               : 0.f;
+    j++;
   }
+  uint16_t v[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) v[u] = to_bf16_bits(f[u]);
   uint16_t* dst = col + (long long)k * ldn + nb;
   if (nb + 3 < d.Npix) {
     *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
@@ -121,7 +160,8 @@ __global__ void __launch_bounds__(256) k_col2im(const float* __restrict__ dcol, 
                                                 float* __restrict__ dx) {
   const int total = d.C * d.B * d.H * d.W;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int s = e % d.W, t1 = e / d.W, r = t1 % d.H, t2 = t1 / d.H, b = t2 % d.B, c = t2 / d.B;
+    const uint32_t t1 = d.fW.div((uint32_t)e), t2 = d.fH.div(t1), c = d.fB.div(t2);
+    const int s = (int)d.fW.mod((uint32_t)e, t1), r = (int)d.fH.mod(t1, t2), b = (int)d.fB.mod(t2, c);
     float acc = 0.f;
 #pragma unroll
     for (int p = 0; p < 3; p++) {
@@ -207,6 +247,16 @@ __global__ void k_wprep(const uint16_t* __restrict__ w, int O, int K9, int ldk, 
   }
 }
 
+// Flipped, transposed weights of a stride-1 layer's data gradient:
+// Wf[c][o*9 + p*3 + q] = w[o][c][2-p][2-q] (row stride ldf).
+__global__ void k_wflip(const uint16_t* __restrict__ w, int O, int C, int ldf, uint16_t* __restrict__ Wf) {
+  const int total = O * C * 9;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int o = e / (C * 9), r = e - o * C * 9, c = r / 9, pq = r - 9 * c;  // e = (o, c, p, q)
+    Wf[(long long)c * ldf + o * 9 + (8 - pq)] = w[e];
+  }
+}
+
 // out[e] = sum over splits s (in order) of part[s * n + e]
 __global__ void k_split_sum(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -237,13 +287,16 @@ __global__ void k_upsample2_back(const float* __restrict__ dy, int CB, int H, in
   }
 }
 
-// loss = 1/(2n) sum (p - t)^2 in FP64 (one block, fixed order), dp = (p - t)/n
-__global__ void k_mse(const float* __restrict__ p, const float* __restrict__ t, long long n, double* loss,
-                      float* __restrict__ dp) {
-  __shared__ double red[32];
+// loss = 1/(2n) sum (p - t)^2 in FP64, dp = (p - t)/n: each block sums a fixed
+// slice of the elements (fixed tree) into part[block]; k_mse_final adds the
+// block partials in block order. MSE_BLOCKS is fixed, so the order is too.
+constexpr int MSE_BLOCKS = 304;
+__global__ void __launch_bounds__(256) k_mse(const float* __restrict__ p, const float* __restrict__ t, long long n,
+                                             double* __restrict__ part, float* __restrict__ dp) {
+  __shared__ double red[8];
   double acc = 0.0;
   const float inv = (float)(1.0 / (double)n);
-  for (long long e = threadIdx.x; e < n; e += blockDim.x) {
+  for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)MSE_BLOCKS * 256) {
     const float r = p[e] - t[e];
     dp[e] = r * inv;
     acc += (double)r * (double)r;
@@ -253,7 +306,14 @@ __global__ void k_mse(const float* __restrict__ p, const float* __restrict__ t, 
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+    for (int w = 0; w < 8; w++) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+__global__ void k_mse_final(const double* __restrict__ part, long long n, double* loss) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < MSE_BLOCKS; k++) s += part[k];
     *loss = 0.5 * s / (double)n;
   }
 }
@@ -290,6 +350,7 @@ struct fwi_cnn {
   void* ws = nullptr;     // workspace of the layer calls (grows to the largest layer)
   size_t ws_bytes = 0;
   int* status = nullptr;  // device status word of the GEMMs (timeout bit)
+  double* red = nullptr;  // block partials of the loss reduction
 };
 
 namespace {
@@ -340,6 +401,11 @@ fwi_status dims_of(int C, int B, int H, int W, int sh, int sw, fwi::ConvDims* d)
     return fwi::host_fail(FWI_EINVAL, "layer too large");
   d->K9 = (int)k9;
   d->Npix = (int)npix;
+  d->fWo = fwi::FastDiv((uint32_t)d->Wo);
+  d->fHo = fwi::FastDiv((uint32_t)d->Ho);
+  d->fW = fwi::FastDiv((uint32_t)W);
+  d->fH = fwi::FastDiv((uint32_t)H);
+  d->fB = fwi::FastDiv((uint32_t)B);
   return FWI_OK;
 }
 
@@ -359,8 +425,10 @@ fwi_status fwi_cnn_create(fwi_cnn** h, int device) {
   c->device = device;
   cudaError_t e = cudaMalloc(&c->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->red, fwi::MSE_BLOCKS * sizeof(double));
   if (e != cudaSuccess) {
     if (c->status) cudaFree(c->status);
+    if (c->red) cudaFree(c->red);
     delete c;
     return cuda_fail(e, "cudaMalloc (status)");
   }
@@ -373,6 +441,7 @@ fwi_status fwi_cnn_destroy(fwi_cnn* h) {
   cudaSetDevice(h->device);
   if (h->ws) cudaFree(h->ws);
   if (h->status) cudaFree(h->status);
+  if (h->red) cudaFree(h->red);
   delete h;
   return FWI_OK;
 }
@@ -459,11 +528,20 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
   // weight gradient split over pixel runs: about two waves of CTAs
   const long long mt = (d.K9 + 127) / 128, nt = (O + 255) / 256;
   const int S = fwi::tc_split_count(d.Npix, gemm_blocks(mt * nt));
+  // stride-1 data gradient: dy seen as a [O][B][H][W] activation, convolved with the flipped weights
+  fwi::ConvDims dd = d;
+  dd.C = O;
+  dd.K9 = 9 * O;
+  dd.Npix = B * H * W;  // = d.Npix at stride 1
+  const int ldf = (int)fwi::round8(dd.K9);
+  const bool s1 = sh == 1 && sw == 1;
   Carve cv;
   const size_t o_dyb = cv.take((size_t)O * ldn * 2), o_bp = cv.take((size_t)O * nchunk * 4);
-  const size_t o_col = cv.take(std::max<size_t>((size_t)d.K9 * ldn, dx ? (size_t)d.Npix * ldo : 0) * 2);
-  const size_t o_wt = cv.take(dx ? (size_t)d.K9 * ldo * 2 : 0);
-  const size_t o_dcol = cv.take(dx ? (size_t)d.K9 * d.Npix * 4 : 0);
+  size_t colb_elems = (size_t)d.K9 * ldn;
+  if (dx) colb_elems = std::max(colb_elems, s1 ? (size_t)dd.Npix * ldf : (size_t)d.Npix * ldo);
+  const size_t o_col = cv.take(colb_elems * 2);
+  const size_t o_wt = cv.take(dx ? (size_t)(s1 ? C * ldf : d.K9 * ldo) * 2 : 0);
+  const size_t o_dcol = cv.take(dx && !s1 ? (size_t)d.K9 * d.Npix * 4 : 0);
   const size_t o_part = cv.take(S > 1 ? (size_t)S * O * d.K9 * 4 : 0);
   if ((v = ws_reserve(h, cv.off)) != FWI_OK) return v;
   char* ws = (char*)h->ws;
@@ -471,6 +549,7 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
   float* bpart = (float*)(ws + o_bp);
   uint16_t* colb = (uint16_t*)(ws + o_col);
   uint16_t* Wt = (uint16_t*)(ws + o_wt);
+  uint16_t* Wf = Wt;  // stride 1: the flipped weights in the same slot
   float* dcol = (float*)(ws + o_dcol);
   float* part = (float*)(ws + o_part);
 
@@ -478,7 +557,17 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
   CNN_CK(cudaGetLastError(), "activation backward");
   fwi::k_db<<<(O + 127) / 128, 128, 0, st>>>(bpart, O, nchunk, db);
   CNN_CK(cudaGetLastError(), "bias gradient");
-  if (dx) {
+  if (dx && s1) {
+    // stride 1: dx is the convolution of the pre-activation gradient with the
+    // flipped, transposed weights, dx[c][pix] = sum_{o,p,q} dy[o][pix shifted by (1-p, 1-q)] w[o][c][p][q]:
+    // im2col of dy (BF16, the same rounding as dyb) and one GEMM, no dcol / col2im
+    fwi::k_wflip<<<blocks_for(9LL * O * C), 256, 0, st>>>(w_bf16, O, C, ldf, Wf);
+    CNN_CK(cudaGetLastError(), "weight flip");
+    fwi::k_im2col_t<<<dim3((dd.Npix + 63) / 64, (ldf + 63) / 64), 256, 0, st>>>(dy, dd, ldf, colb);
+    CNN_CK(cudaGetLastError(), "im2col of dy");
+    fwi::TcGemm g{colb, ldf, Wf, ldf, dd.Npix, C, dd.K9, dx, dd.Npix, 0, nullptr, 0, 1, h->status};
+    CNN_CK(fwi::tc_gemm(g, st), "conv data-gradient GEMM");
+  } else if (dx) {
     // dcol[k][pix] = sum_o dyT[pix][o] W[o][k], then the col2im gather
     fwi::k_dy_transpose<<<dim3((d.Npix + 31) / 32, (ldo + 31) / 32), dim3(32, 8), 0, st>>>(dyb, O, d.Npix, ldn, ldo,
                                                                                           colb);
@@ -524,10 +613,14 @@ fwi_status fwi_cnn_upsample2_backward(const float* dy, int32_t C, int32_t B, int
   return FWI_OK;
 }
 
-fwi_status fwi_cnn_mse(const float* p, const float* t, int64_t n, double* loss, float* dp, void* stream) {
-  if (!p || !t || !loss || !dp) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
+fwi_status fwi_cnn_mse(fwi_cnn* h, const float* p, const float* t, int64_t n, double* loss, float* dp,
+                       void* stream) {
+  if (!h || !p || !t || !loss || !dp) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (n < 1) return fwi::host_fail(FWI_EINVAL, "n must be >= 1");
-  fwi::k_mse<<<1, 1024, 0, (cudaStream_t)stream>>>(p, t, n, loss, dp);
+  CNN_CK(cudaSetDevice(h->device), "cudaSetDevice");
+  fwi::k_mse<<<fwi::MSE_BLOCKS, 256, 0, (cudaStream_t)stream>>>(p, t, n, h->red, dp);
+  CNN_CK(cudaGetLastError(), "mse");
+  fwi::k_mse_final<<<1, 32, 0, (cudaStream_t)stream>>>(h->red, n, loss);
   CNN_CK(cudaGetLastError(), "mse");
   return FWI_OK;
 }

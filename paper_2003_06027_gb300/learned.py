@@ -54,7 +54,7 @@ def _lib():
         L.fwi_cnn_conv_backward.argtypes = [P, P, i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P]
         L.fwi_cnn_upsample2.argtypes = [P, i32, i32, i32, i32, P, P]
         L.fwi_cnn_upsample2_backward.argtypes = [P, i32, i32, i32, i32, P, P]
-        L.fwi_cnn_mse.argtypes = [P, P, i64, P, P, P]
+        L.fwi_cnn_mse.argtypes = [P, P, P, i64, P, P, P]
         L.fwi_cnn_adam.argtypes = [P, P, P, P, i64, i32, f32, f32, f32, f32, P, P]
         L.fwi_cnn_to_bf16.argtypes = [P, P, i64, P]
         for f in ("fwi_cnn_create", "fwi_cnn_destroy", "fwi_cnn_check", "fwi_cnn_gemm_bt", "fwi_cnn_conv_forward",
@@ -158,11 +158,11 @@ def upsample2_backward(dy):
     return dx
 
 
-def mse(p, t):
+def mse(h: Handle, p, t):
     """(loss as a 1-element FP64 tensor, dL/dp)."""
     loss = torch.empty(1, dtype=torch.float64, device=p.device)
     dp = torch.empty_like(p)
-    _chk(_lib().fwi_cnn_mse(_p(p), _p(t), p.numel(), _p(loss), _p(dp), _st()))
+    _chk(_lib().fwi_cnn_mse(h.h, _p(p), _p(t), p.numel(), _p(loss), _p(dp), _st()))
     return loss, dp
 
 
@@ -317,7 +317,7 @@ def train(net: Net, X, Y, epochs=10, batch=32, lr=1e-3, seed=0, log_every=0):
             xb = X.index_select(1, idx)
             yb = Y.index_select(1, idx)
             out = net.forward(xb)
-            loss, dout = mse(out, yb)
+            loss, dout = mse(net.h, out, yb)
             net.backward(dout)
             net.step(lr * (0.5 ** (ep / max(1, epochs // 3))))
             log.loss.append(loss)

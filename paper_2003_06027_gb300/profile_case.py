@@ -20,6 +20,8 @@ CASES = {
     "fwi16-nt20": (16, 20, 10),
     # elastic 300 x 800 discretisation (4th order, 32 CPML cells), 8 shots
     "ela8-nt20": (8, 20, 10),
+    # start-model network: training steps on a batch of 32 surveys (shots = batch, steps = Adam steps)
+    "cnn32-step4": (32, 4, 0),
 }
 
 
@@ -33,6 +35,21 @@ def main():
     ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
     S, nt, K = CASES[args.case]
+    if args.case.startswith("cnn"):
+        from paper_2003_06027_gb300 import learned as L
+
+        g = torch.Generator(device="cuda").manual_seed(0)
+        X = torch.randn((L.NSHOT, S, L.NT, L.NREC), device="cuda", generator=g) * 0.1
+        Y = torch.randn((1, S, L.NZ, L.NX), device="cuda", generator=g) * 0.1
+        net = L.Net(0, seed=0)
+        for _ in range(nt):
+            out = net.forward(X)
+            loss, dout = L.mse(net.h, out, Y)
+            net.backward(dout)
+            net.step(1e-4)
+        net.h.check()
+        print(f"case {args.case}: loss {float(loss[0]):.6e}")
+        return
     if args.case.startswith("ela"):
         d = synth.elastic_layered(nshots=S, nt=nt)
         kw = fwi.problem_kwargs(d)

@@ -76,6 +76,8 @@ SHAPES = [  # C, B, H, W, O, sh, sw, relu
     (16, 3, 40, 16, 8, 4, 1, True),
     (8, 2, 25, 12, 16, 2, 2, False),
     (32, 1, 9, 33, 4, 2, 1, True),
+    (64, 2, 16, 32, 32, 1, 1, True),
+    (20, 3, 7, 40, 24, 1, 1, False),
 ]
 
 
@@ -122,11 +124,13 @@ def test_upsample_and_mse_and_adam(fwi_lib):
     d = rng.standard_normal(u.shape).astype(np.float32)
     np.testing.assert_allclose(L.upsample2_backward(_cuda(d)).cpu().numpy(), cnn.upsample2_backward(np.float64(d)),
                                rtol=1e-6, atol=1e-6)
-    p, t = rng.standard_normal(5000).astype(np.float32), rng.standard_normal(5000).astype(np.float32)
-    loss, dp = L.mse(_cuda(p), _cuda(t))
-    lo, go = cnn.mse(np.float64(p), np.float64(t))
-    assert float(loss[0]) == pytest.approx(lo, rel=1e-6)  # FP32 residuals, FP64 sum
-    assert rel(dp.cpu().numpy(), go) <= 1e-6
+    h = L.Handle(0)
+    for n in (5000, 1_000_003):  # one block's worth, and many blocks with a ragged tail
+        p, t = rng.standard_normal(n).astype(np.float32), rng.standard_normal(n).astype(np.float32)
+        loss, dp = L.mse(h, _cuda(p), _cuda(t))
+        lo, go = cnn.mse(np.float64(p), np.float64(t))
+        assert float(loss[0]) == pytest.approx(lo, rel=1e-6)  # FP32 residuals, FP64 sum
+        assert rel(dp.cpu().numpy(), go) <= 1e-6
     import ctypes
 
     th, g = rng.standard_normal(777).astype(np.float32), rng.standard_normal(777).astype(np.float32)
