@@ -16,9 +16,11 @@
 //   * stage 1 evaluates each half-point flux once (x: q at the half columns
 //     of the tile and its halo; z: a register window over two rows per thread),
 //     stage 2 the divergence, update, sources and receivers;
-//   * per-cell operands that do not need a halo (u^{n-1}, lambda_{n+2}, the
-//     gradient partial) are read with float4 loads issued before the wait, so
-//     their latency overlaps the tile fetch.
+//   * per-cell operands that do not need a halo: u^{n-1} is copied into shared
+//     memory by cp.async issued before the wait (its latency overlaps the tile
+//     fetch and stage 1 without holding registers); the adjoint's stored fluxes
+//     are float4 loads issued there too, its lambda_{n+2} and gradient partial
+//     are loaded at the start of stage 2.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -67,12 +69,28 @@ __device__ __forceinline__ void acc4(float4& acc, float c, const float4 p, const
   acc.x += c * (p.x - m.x); acc.y += c * (p.y - m.y); acc.z += c * (p.z - m.z); acc.w += c * (p.w - m.w);
 }
 
+// 16-byte asynchronous global -> shared copies (L2 only): per-cell operands of
+// stage 2 land in shared memory while stage 1 runs, holding no registers.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ bool tile_pml_x(const Grid& g, int x0) {
   return g.npml > 0 && (x0 - H < g.npml || x0 + TILE_X + H > g.npml + g.nx - 1);
 }
 __device__ __forceinline__ bool tile_pml_z(const Grid& g, int z0) {
   return g.npml > 0 && (z0 - H < g.npml || z0 + TILE_Z + H > g.npml + g.nz - 1);
 }
+
+// Points of one axis where the CPML coefficients can be nonzero (the tables are
+// built with a layer distance l > 0 only there): half points h < npml or
+// h >= npml + n - 1, integer points x < npml or x >= npml + n (n physical
+// cells). A tile that touches a layer runs its CPML updates only on the items
+// [h0, h1] that meet one; elsewhere a = 0 and the memory variables stay zero.
+__device__ __forceinline__ bool layer_h(int h0, int h1, int npml, int n) { return h0 < npml || h1 >= npml + n - 1; }
+__device__ __forceinline__ bool layer_c(int x0, int x1, int npml, int n) { return x0 < npml || x1 >= npml + n; }
 
 // Tiles that leave hhat behind for the next adjoint step: those whose own
 // columns (rows) lie in the stencil reach of a CPML tile (itself or a neighbour).
@@ -130,6 +148,7 @@ struct FwdSmem {
   float m[M_SLOT / 4];
   float qx[TILE_Z * QXW];
   float qz[QZH * TILE_X];
+  float4 up4[2 * NTHREADS];  // u^{n-1} of the own cells, [row][thread] (cp.async)
   float red[32];
   uint64_t bar;
 };
@@ -180,11 +199,12 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
     float* __restrict__ uprev = p.u + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
-    // prefetch u^{n-1} of this thread's 2 x 4 cells
+    // u^{n-1} of this thread's 2 x 4 cells: copied into shared memory while the
+    // tile is fetched and stage 1 runs
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
-    float4 up[2];
-    up[0] = ldg4(uprev + (long long)zr0 * pitch + xb);
-    up[1] = ldg4(uprev + (long long)(zr0 + 1) * pitch + xb);
+#pragma unroll
+    for (int rr = 0; rr < 2; rr++) cp_async16(&sh.up4[rr * NTHREADS + tid], uprev + (long long)(zr0 + rr) * pitch + xb);
+    cp_async_commit();
     // small per-tile operands, fetched before the wait as well
     const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
     const float stf_n = __ldg(p.stf + (long long)s * p.nt + p.n);
@@ -197,6 +217,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
 
     const bool ok = mbar_wait(&sh.bar, it & 1);
     if (__syncthreads_or(!ok)) {
+      cp_async_wait_all();  // no copy may land after the CTA has exited
       if (tid == 0) {
         atomicOr(p.status, ST_TIMEOUT);
         mbar_wait(&sh.bar, it & 1);  // let a late copy land before the CTA exits
@@ -223,7 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         pp[e] = gx;
       }
       const long long id0 = base + (long long)z * pitch + hb;
-      if (pmlx) {
+      if (pmlx && layer_h(hb, hb + 3, g.npml, g.nx)) {
         const float4 a4 = ldg4(p.axh + hb + TAB_OFF);
         if (a4.x != 0.f || a4.y != 0.f || a4.z != 0.f || a4.w != 0.f) {
           // psi <- b psi + a g; zero where a = 0 (psi stays zero outside the layer)
@@ -253,7 +274,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         acc4(acc, p.c1z[k - 1], ld4(su + (hr + 4 + k) * UW + 8 + 4 * c), ld4(su + (hr + 5 - k) * UW + 8 + 4 * c));
       float pp[4];
       f4a(acc, pp);
-      if (pmlz) {
+      if (pmlz && layer_h(hz, hz, g.npml, g.nz)) {
         const float aa = __ldg(p.azh + hz + TAB_OFF);
         if (aa != 0.f) {
           const float bb = __ldg(p.bzh + hz + TAB_OFF);
@@ -291,7 +312,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       for (int rr = 0; rr < 2; rr++) {
         const int hz = zr0 + rr;
         const long long idz = base + (long long)hz * pitch + xb;
-        if (pmlz) {
+        if (pmlz && layer_h(hz, hz, g.npml, g.nz)) {
           const float aa = __ldg(p.azh + hz + TAB_OFF);
           if (aa != 0.f) {
             const float bb = __ldg(p.bzh + hz + TAB_OFF);
@@ -336,6 +357,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     if (tid == 0 && tn < p.ntiles) fetch_tile(&tmap_u, &tmap_m, g, p.cur * p.S_pair + p.s0, tn, sh.u, sh.m, &sh.bar);
 
     // ---- stage 2: divergence + CPML zeta + leapfrog + source + receivers
+    cp_async_wait_all();  // this thread's own u^{n-1} copies
     float hzv[2][4];
     {
       float4 w[2 * N + 1];
@@ -353,7 +375,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     const int i0 = box.x, j0 = box.y, nb = p.src_n;
     const bool srcbox = i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0;
     float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
-    if (pmlx) ax4 = ldg4(p.ax + xb + TAB_OFF);
+    if (pmlx && layer_c(xb, xb + 3, g.npml, g.nx)) ax4 = ldg4(p.ax + xb + TAB_OFF);
     const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
     if (zx_on) bx4 = ldg4(p.bx + xb + TAB_OFF);
     float un[2][4];
@@ -382,7 +404,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         st4(p.zetx + idc0, zn);
         rv[0] += zn.x; rv[1] += zn.y; rv[2] += zn.z; rv[3] += zn.w;
       }
-      if (pmlz) {
+      if (pmlz && layer_c(z, z, g.npml, g.nz)) {
         const float aa = __ldg(p.az + z + TAB_OFF);
         if (aa != 0.f) {
           const float bb = __ldg(p.bz + z + TAB_OFF);
@@ -395,10 +417,11 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         }
       }
       const float4 uc = ucur[rr];
-      un[rr][0] = 2.f * uc.x - up[rr].x + rv[0];
-      un[rr][1] = 2.f * uc.y - up[rr].y + rv[1];
-      un[rr][2] = 2.f * uc.z - up[rr].z + rv[2];
-      un[rr][3] = 2.f * uc.w - up[rr].w + rv[3];
+      const float4 upv = sh.up4[rr * NTHREADS + tid];
+      un[rr][0] = 2.f * uc.x - upv.x + rv[0];
+      un[rr][1] = 2.f * uc.y - upv.y + rv[1];
+      un[rr][2] = 2.f * uc.z - upv.z + rv[2];
+      un[rr][3] = 2.f * uc.w - upv.w + rv[3];
       if (srcbox) {
         const int di = z - i0;
         if (di >= 0 && di < nb) {
@@ -518,7 +541,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         else if (image && (!EDGE || hb >= 0)) f4a(ld4_stream(p.slot_px + id0, pol), pf);  // the apron holds no flux
         const bool rowok = !EDGE || z < g.Nz;
         float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
-        if (pmlx) {  // one round trip: tables and P together
+        if (pmlx && layer_h(hb, hb + 3, g.npml, g.nx)) {  // one round trip: tables and P together
           a4 = ldg4(p.axh + hb + TAB_OFF);
           b4 = ldg4(p.bxh + hb + TAB_OFF);
           P4 = ld4(p.px_in + id0);
@@ -553,7 +576,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         if (image && (!EDGE || hz >= 0)) f4a(ld4_stream(p.slot_pz + idz, pol), pf);
         float aa = 0.f;
         float Pv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (pmlz) {
+        if (pmlz && layer_h(hz, hz, g.npml, g.nz)) {
           aa = __ldg(p.azh + hz + TAB_OFF);
           f4a(*reinterpret_cast<const float4*>(p.pz_in + idz), Pv);
         }
@@ -587,7 +610,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         // own z half rows 2ty, 2ty+1 from a (2N+1)-row window of hhat
         float aa[2] = {0.f, 0.f}, bb[2] = {1.f, 1.f};
         float4 Pz[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-        if (pmlz) {
+        if (pmlz && layer_h(zr0, zr0 + 1, g.npml, g.nz)) {
   #pragma unroll
           for (int rr = 0; rr < 2; rr++) {
             aa[rr] = __ldg(p.azh + zr0 + rr + TAB_OFF);
@@ -731,7 +754,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
       }
       const bool wx = tile_writes_hx(g, id.tx), wz = tile_writes_hz(g, id.tz);
       float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
-      if (pmlx) {
+      if (pmlx && layer_c(xb, xb + 3, g.npml, g.nx)) {
         ax4 = ldg4(p.ax + xb + TAB_OFF);
         bx4 = ldg4(p.bx + xb + TAB_OFF);
       }
@@ -753,7 +776,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           st4(p.zx_out + idc0, Zx);
         }
         float az = 0.f;
-        if (pmlz) {
+        if (pmlz && layer_c(z, z, g.npml, g.nz)) {
           az = __ldg(p.az + z + TAB_OFF);
           if (az != 0.f) {
             const float bz = __ldg(p.bz + z + TAB_OFF);
