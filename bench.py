@@ -211,23 +211,28 @@ def acoustic_xl_measure(peak):
 def batched_measure(n_inst=8):
     """Batched vs plain per-shot gradient sweeps over the first ``n_inst``
     instances of the seeded uneven workload (seed 4; grids 128..512 x
-    128..1024, nt 1000..4000, 4..16 shots). The batched sweep's (streams,
-    checkpoint interval) comes from the autotuner run on the same instances."""
+    128..1024, nt 1000..4000, 4..16 shots). The batched sweep's (mode: host
+    threads or recorded CUDA graphs, streams, checkpoint interval) comes from the
+    autotuner run on the same instances."""
     from paper_2003_06027_gb300 import batch, synth
 
     inst = batch.prepare([synth.uneven_instance(4, i) for i in range(n_inst)])
     cells = sum(i.cell_steps for i in inst)
-    best, table = batch.autotune(inst, workers=(1, 2, 4, 8), ckpt=(100,))
-    _, _, tb = batch.sweep(inst, "batched", *best)
+    best, table = batch.autotune(inst, workers=(2, 4, 8), ckpt=(100,), modes=("batched", "graph"))
+    _, _, tb = batch.sweep(inst, best[0], best[1], best[2])
     batch.sweep(inst, "plain", ckpt_every=100)
     _, _, tp = batch.sweep(inst, "plain", ckpt_every=100)
+    best_of = {m: min(t for (mm, _, _), t in table.items() if mm == m) for m in ("batched", "graph")}
+    batch.close_graphs()
     return {"workload": f"uneven-seed4-{n_inst}-instances", "cell_steps_per_sweep": cells,
-            "batched": {"value": cells / tb / 1e9, "unit": UNIT, "s_per_sweep": tb, "streams": best[0],
-                        "ckpt_every": best[1]},
+            "batched": {"value": cells / tb / 1e9, "unit": UNIT, "s_per_sweep": tb, "mode": best[0],
+                        "streams": best[1], "ckpt_every": best[2]},
+            "threads_best": {"value": cells / best_of["batched"] / 1e9, "s_per_sweep": best_of["batched"]},
+            "graphs_best": {"value": cells / best_of["graph"] / 1e9, "s_per_sweep": best_of["graph"]},
             "plain_per_shot": {"value": cells / tp / 1e9, "unit": UNIT, "s_per_sweep": tp},
             "speedup": tp / tb,
-            "autotune_s": {f"{w}x{k}": t for (w, k), t in table.items()},
-            "timing": "host wall time per sweep, device idle before and after (each call ends synchronised)"}
+            "autotune_s": {f"{m}-{w}x{k}": t for (m, w, k), t in table.items()},
+            "timing": "host wall time per sweep, device idle before and after (each sweep ends synchronised)"}
 
 
 def learned_measure():

@@ -140,6 +140,38 @@ fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
                            float *grad, float *grad_stf, float *grad_x0, float *seis_out,
                            void *cuda_stream);
 
+/* A recorded gradient: one acoustic fwi_misfit_grad call captured as a CUDA
+ * graph, for loops that evaluate the same problem many times (an FWI iteration
+ * per launch) or many small problems side by side, where launching the tens of
+ * thousands of step kernels of a call one by one costs host time. The paper's
+ * method is unchanged: each launch computes exactly what fwi_misfit_grad
+ * computes (Eqs. adjoint-backward, adjoint-gradient) from the CURRENT contents
+ * of the buffers named at recording time, so an inversion updates the model in
+ * place and launches again.
+ *
+ * fwi_misfit_grad_graph: arguments as fwi_misfit_grad (no seis_out, no stream);
+ *   every buffer must be device memory (FWI_EINVAL otherwise) and stays owned
+ *   by the caller, who keeps it alive and at the same address while the graph
+ *   exists. Runs the call once on the context's own stream (its results are
+ *   left in the outputs), then records it. FWI_ENOTIMPL for elastic models.
+ *   The graph uses ctx's workspace: it is valid until a call on ctx needs a
+ *   larger workspace or a different problem layout, after which
+ *   fwi_graph_launch returns FWI_EINVAL. Use one context per recorded problem.
+ * fwi_graph_launch: enqueue one evaluation on cuda_stream (asynchronous). Two
+ *   launches of graphs of the SAME context must not overlap (they share the
+ *   workspace); graphs of different contexts may run concurrently.
+ * fwi_graph_status: wait for cuda_stream and decode the device status word of
+ *   the last evaluation (the codes of fwi_misfit_grad).
+ * fwi_graph_destroy: free the graph (not the context). */
+typedef struct fwi_graph fwi_graph;
+fwi_status fwi_misfit_grad_graph(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
+                                 const fwi_receivers *rec, int32_t nt, float dt, const float *observed,
+                                 int32_t ckpt_every, double *misfit, float *grad, float *grad_stf,
+                                 float *grad_x0, fwi_graph **graph);
+fwi_status fwi_graph_launch(fwi_graph *graph, void *cuda_stream);
+fwi_status fwi_graph_status(fwi_graph *graph, void *cuda_stream);
+fwi_status fwi_graph_destroy(fwi_graph *graph);
+
 /* Forward modelling that allocates no device memory, for callers that cannot
  * let a library call cudaMalloc: applications that hand all device memory to
  * their own allocator and account for every byte, and latency-sensitive loops

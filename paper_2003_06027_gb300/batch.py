@@ -11,9 +11,14 @@ Two ways to run the same gradient sweep (J_i and dJ_i/dc_i of every instance i):
   its own CUDA stream and library context (a pool of W persistent host threads,
   one per stream; the library call releases the GIL). Instances are handed out
   largest first.
+* ``graph``: every instance's gradient call is recorded once as a CUDA graph
+  (fwi.GradGraph, one library context per instance); a sweep is then one graph
+  launch per instance, spread over W streams from a single host thread, so the
+  host issues one launch per instance instead of tens of thousands of step
+  kernels.
 
 ``autotune`` measures a sweep on the instances themselves for each candidate
-(W, checkpoint interval K) and keeps the fastest. Both modes compute the same
+(mode, W, checkpoint interval K) and keeps the fastest. Both modes compute the same
 gradients (up to the order of the shot sum), so an FWI loop reaches the same
 misfit in the same number of iterations; what differs is GPU time per iteration.
 All wave propagation and all gradients run in the library's kernels; the model
@@ -80,6 +85,32 @@ def _grad_per_shot(inst: Instance, K: int):
         J = Js if J is None else J + Js
         g = gs if g is None else g + gs
     return J, g
+
+
+_graphs = {}
+_graph_streams = {}
+
+
+def _graph_of(inst: Instance, K: int) -> fwi.GradGraph:
+    key = (id(inst), K)
+    g = _graphs.get(key)
+    if g is None or g._a.c.data_ptr() != inst.c.data_ptr():
+        g = fwi.GradGraph(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed, ckpt_every=K, **inst.kw)
+        _graphs[key] = g
+    return g
+
+
+def close_graphs():
+    """Free the recorded graphs and their contexts."""
+    for k in list(_graphs):
+        _graphs.pop(k).close()
+
+
+def _streams(W: int, device: int):
+    key = (W, device)
+    if key not in _graph_streams:
+        _graph_streams[key] = [torch.cuda.Stream(device) for _ in range(W)]
+    return _graph_streams[key]
 
 
 class _Pool:
@@ -163,32 +194,50 @@ def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 
 
         order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
         pool(max(1, min(workers, n)), torch.cuda.current_device()).run([job(i) for i in order])
+    elif mode == "graph":
+        order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
+        graphs = {i: _graph_of(instances[i], min(ckpt_every, int(instances[i].stf.shape[1]))) for i in order}
+        streams = _streams(max(1, min(workers, n)), torch.cuda.current_device())
+        main = torch.cuda.current_stream()
+        for s in streams:
+            s.wait_stream(main)
+        for k, i in enumerate(order):
+            graphs[i].launch(streams[k % len(streams)])
+        for k, i in enumerate(order):
+            graphs[i].check(streams[k % len(streams)])
+            Js[i], gs[i] = graphs[i].misfit.clone(), graphs[i].grad.clone()
     else:
         raise ValueError(f"unknown mode {mode!r}")
     torch.cuda.synchronize()
     return Js, gs, time.perf_counter() - t0
 
 
-def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200)):
-    """Pick (workers, ckpt_every) by timing one batched sweep per candidate on
-    the given instances (the first call of each candidate also sizes the
-    per-thread arenas, so each candidate is run twice and the second run counts).
-    The pools of the losing worker counts are closed, freeing their arenas."""
+def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batched",)):
+    """Pick (mode, workers, ckpt_every) by timing one sweep per candidate on the
+    given instances (the first sweep of each candidate also sizes the arenas or
+    records the graphs, so each candidate is run twice and the second run
+    counts). The pools of the losing worker counts are closed, and the graphs
+    the winner does not use are freed."""
     best = None
     table = {}
     dev = torch.cuda.current_device()
-    for W in workers:
-        prev = best
-        for K in ckpt:
-            sweep(instances, "batched", W, K)
-            _, _, t = sweep(instances, "batched", W, K)
-            table[(W, K)] = t
-            if best is None or t < table[best]:
-                best = (W, K)
-        # keep at most the best pool alive between candidates
-        loser = W if best[0] != W else (prev[0] if prev is not None and prev[0] != W else None)
-        if loser is not None and (loser, dev) in _pools:
-            _pools.pop((loser, dev)).close()
+    for mode in modes:
+        for W in workers:
+            prev = best
+            for K in ckpt:
+                sweep(instances, mode, W, K)
+                _, _, t = sweep(instances, mode, W, K)
+                table[(mode, W, K)] = t
+                if best is None or t < table[best]:
+                    best = (mode, W, K)
+            if mode == "batched":  # keep at most the best pool alive between candidates
+                bw = best[1] if best[0] == "batched" else None
+                loser = W if bw != W else (prev[1] if prev is not None and prev[0] == "batched" and prev[1] != W
+                                           else None)
+                if loser is not None and (loser, dev) in _pools:
+                    _pools.pop((loser, dev)).close()
+    for key in [k for k in _graphs if not (best[0] == "graph" and k[1] == best[2])]:
+        _graphs.pop(key).close()  # graphs the winner does not use
     return best, table
 
 

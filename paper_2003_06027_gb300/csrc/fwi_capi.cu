@@ -459,10 +459,12 @@ fwi_status fwi::arena_acquire(fwi_ctx* ctx, size_t bytes, const std::string& key
     ctx->arena = (char*)p;
     ctx->arena_bytes = bytes;
     ctx->layout_key.clear();
+    ctx->arena_epoch++;
   }
   if (ctx->layout_key != key) {
     CK(cudaMemsetAsync(ctx->arena, 0, bytes, st));
     ctx->layout_key = key;
+    ctx->arena_epoch++;
   } else {
     CK(cudaMemsetAsync(ctx->arena + zero_lo, 0, zero_hi - zero_lo, st));
     CK(cudaMemsetAsync(ctx->arena, 0, 64, st));
@@ -530,6 +532,7 @@ fwi_status fwi_destroy(fwi_ctx* ctx) {
     if (ctx->join_ev[g]) cudaEventDestroy(ctx->join_ev[g]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return FWI_OK;
 }
@@ -625,19 +628,24 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   return v;
 }
 
-fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+}  // extern "C"
+
+namespace {
+
+// The acoustic misfit/gradient call. With `capture` the device work is being
+// recorded into a graph: the arena is already sized and laid out by an earlier
+// call with the same problem, and the ending synchronisation (status read,
+// phase timings) is left out.
+fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
                            int32_t nt, float dt, const float* observed, int32_t K, double* misfit, float* grad,
-                           float* grad_stf, float* grad_x0, float* seis_out, void* stream) {
-  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
-  if (M && M->physics == FWI_ELASTIC)
-    return ela_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, seis_out, stream);
+                           float* grad_stf, float* grad_x0, float* seis_out, cudaStream_t st, bool capture,
+                           int** status_out) {
   fwi_status v = validate(M, Sv, R, nt, dt);
   if (v != FWI_OK) return v;
   if (!observed && R->nrec > 0) return fail(FWI_EINVAL, "observed must not be NULL");
   if (!misfit) return fail(FWI_EINVAL, "misfit must not be NULL");
   if (K < 1 || K > nt) return fail(FWI_EINVAL, "ckpt_every must be in [1, nt]");
   CK(cudaSetDevice(ctx->device));
-  cudaStream_t st = (cudaStream_t)stream;
   Plan P;
   make_plan(P, M, Sv, R, nt, K, true);
   v = ensure_arena(ctx, P, st);
@@ -743,6 +751,8 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   if (seis_out && ns > 0) CK(cudaMemcpyAsync(seis_out, P.seis, (size_t)ns * 4, cudaMemcpyDefault, st));
   CK(cudaMemcpyAsync(misfit, P.J, 8, cudaMemcpyDefault, st));
   CK(cudaEventRecord(ctx->ev[3], st));
+  if (status_out) *status_out = P.status;
+  if (capture) return FWI_OK;
   v = finish_status(ctx, P, st);
   float t = 0.f;
   cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
@@ -764,6 +774,110 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   ctx->kernel_ms[2] = adj / nt;
   if (v == FWI_OK) g_err.clear();
   return v;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct fwi_graph {
+  fwi_ctx* ctx = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int* status = nullptr;  // device status word inside ctx's arena
+  unsigned long long epoch = 0;
+};
+
+extern "C" {
+
+fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                           int32_t nt, float dt, const float* observed, int32_t K, double* misfit, float* grad,
+                           float* grad_stf, float* grad_x0, float* seis_out, void* stream) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (M && M->physics == FWI_ELASTIC)
+    return ela_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, seis_out, stream);
+  return acu_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, seis_out,
+                         (cudaStream_t)stream, false, nullptr);
+}
+
+fwi_status fwi_misfit_grad_graph(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                                 int32_t nt, float dt, const float* observed, int32_t K, double* misfit,
+                                 float* grad, float* grad_stf, float* grad_x0, fwi_graph** out) {
+  if (!ctx || !out) return fail(FWI_EINVAL, "ctx and graph must not be NULL");
+  *out = nullptr;
+  if (!M || M->physics != FWI_ACOUSTIC) return fail(FWI_ENOTIMPL, "graphs are recorded for the acoustic gradient only");
+  fwi_status v = validate(M, Sv, R, nt, dt);
+  if (v != FWI_OK) return v;
+  const void* ptrs[] = {M->vp, Sv->x0, Sv->stf, R->iz, R->ix, observed, misfit, grad, grad_stf, grad_x0};
+  for (const void* p : ptrs)
+    if (!is_device_ptr(p)) return fail(FWI_EINVAL, "every buffer of a recorded call must be device memory");
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = ctx->cap_stream;
+  // one ordinary call first: it validates the inputs on the device, sizes and
+  // lays out the arena, and creates the group streams and events
+  v = acu_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, nullptr, cs, false,
+                      nullptr);
+  if (v != FWI_OK) return v;
+  const unsigned long long epoch = ctx->arena_epoch;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  int* dstatus = nullptr;
+  v = acu_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, nullptr, cs, true,
+                      &dstatus);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (v == FWI_OK && (e != cudaSuccess || ctx->arena_epoch != epoch))
+    v = fail(FWI_ECUDA, std::string("graph capture: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "arena changed"));
+  cudaGraphExec_t exec = nullptr;
+  if (v == FWI_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (ei != cudaSuccess) v = fail(FWI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (v != FWI_OK) {
+    cudaGetLastError();
+    return v;
+  }
+  fwi_graph* g = new fwi_graph;
+  g->ctx = ctx;
+  g->exec = exec;
+  g->status = dstatus;
+  g->epoch = epoch;
+  *out = g;
+  g_err.clear();
+  return FWI_OK;
+}
+
+fwi_status fwi_graph_launch(fwi_graph* g, void* stream) {
+  if (!g) return fail(FWI_EINVAL, "graph must not be NULL");
+  if (g->ctx->arena_epoch != g->epoch)
+    return fail(FWI_EINVAL, "the context's workspace was reallocated or relaid out since the graph was recorded");
+  CK(cudaSetDevice(g->ctx->device));
+  CK(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  return FWI_OK;
+}
+
+fwi_status fwi_graph_status(fwi_graph* g, void* stream) {
+  if (!g) return fail(FWI_EINVAL, "graph must not be NULL");
+  CK(cudaSetDevice(g->ctx->device));
+  fwi_status v = finish_status_dev(g->ctx, g->status, (cudaStream_t)stream);
+  if (v == FWI_OK) g_err.clear();
+  return v;
+}
+
+fwi_status fwi_graph_destroy(fwi_graph* g) {
+  if (!g) return FWI_OK;
+  cudaSetDevice(g->ctx->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+  return FWI_OK;
 }
 
 }  // extern "C"

@@ -24,6 +24,10 @@ struct fwi_ctx {
   cudaStream_t gstream[4] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[4] = {};
+  // bumped whenever the arena is reallocated or takes a new layout: a recorded
+  // graph (fwi_misfit_grad_graph) is valid only for the epoch it was captured in
+  unsigned long long arena_epoch = 0;
+  cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
 };
 
 namespace fwi {

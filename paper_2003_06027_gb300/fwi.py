@@ -52,7 +52,8 @@ _lib_lock = threading.Lock()
 _ctx = threading.local()
 
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
-           "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout", "fwi_last_error"]
+           "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout",
+           "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -82,6 +83,12 @@ def library(build_if_missing: bool = True):
                                               P]
             L.fwi_elastic_velocity_grad.argtypes = [P, P, P, P, P, ctypes.c_int64, P]
             L.fwi_selftest_wait_timeout.argtypes = [P, P]
+            L.fwi_misfit_grad_graph.argtypes = [P, ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                                ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
+                                                ctypes.c_int32, P, P, P, P, ctypes.POINTER(P)]
+            L.fwi_graph_launch.argtypes = [P, P]
+            L.fwi_graph_status.argtypes = [P, P]
+            L.fwi_graph_destroy.argtypes = [P]
             L.fwi_last_error.restype = ctypes.c_char_p
             for f in EXPORTS[:-1]:
                 getattr(L, f).restype = ctypes.c_int
@@ -260,6 +267,65 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
         _ptr(out.get("grad_stf")), _ptr(out.get("grad_x0")), _ptr(out.get("seis")),
         _stream(ref, stream)))
     return out["misfit"], out.get("grad"), out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
+class GradGraph:
+    """One acoustic misfit/gradient evaluation recorded as a CUDA graph
+    (fwi_misfit_grad_graph) on a library context of its own.
+
+    All arguments must be device tensors; they are kept referenced and are read
+    again at every launch, so an inversion updates ``c`` in place and launches
+    again. Outputs live in ``self.misfit``, ``self.grad`` (and ``grad_stf``,
+    ``grad_x0`` when ``want_src``). Recording runs the evaluation once."""
+
+    def __init__(self, c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
+                 pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, ckpt_every=100, want_src=False):
+        for t in (c, stf, x0, rec_iz, rec_ix, observed):
+            if not (_is_torch(t) and t.is_cuda):
+                raise ValueError("GradGraph takes CUDA tensors only")
+        self._a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+        a = self._a
+        self._obs = _arr(observed, np.float32)
+        self.device = a.c.device.index
+        self.misfit = _empty_like_place(a.c, (1,), np.float64)
+        self.grad = _empty_like_place(a.c, tuple(a.c.shape))
+        self.grad_stf = _empty_like_place(a.c, (a.S, a.nt)) if want_src else None
+        self.grad_x0 = _empty_like_place(a.c, (a.S, 2)) if want_src else None
+        L = library()
+        self._L = L
+        self.ctx = ctypes.c_void_p()
+        _check(L.fwi_create(ctypes.byref(self.ctx), int(self.device)))
+        self.graph = ctypes.c_void_p()
+        K = max(1, min(int(ckpt_every), a.nt))
+        st = L.fwi_misfit_grad_graph(self.ctx, ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
+                                     float(dt), _ptr(self._obs), K, _ptr(self.misfit), _ptr(self.grad),
+                                     _ptr(self.grad_stf), _ptr(self.grad_x0), ctypes.byref(self.graph))
+        if st != 0:
+            L.fwi_destroy(self.ctx)
+            self.ctx = None
+            _check(st)
+
+    def launch(self, stream=None):
+        """Enqueue one evaluation on ``stream`` (default: the current stream)."""
+        _check(self._L.fwi_graph_launch(self.graph, _stream(self._a.c, stream)))
+
+    def check(self, stream=None):
+        """Wait for ``stream`` and raise if the last evaluation reported an error."""
+        _check(self._L.fwi_graph_status(self.graph, _stream(self._a.c, stream)))
+
+    def close(self):
+        if getattr(self, "graph", None):
+            self._L.fwi_graph_destroy(self.graph)
+            self.graph = None
+        if getattr(self, "ctx", None):
+            self._L.fwi_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class _ECall:

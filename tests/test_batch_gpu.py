@@ -59,6 +59,53 @@ def test_autotune_picks_a_candidate(fwi_lib):
     from paper_2003_06027_gb300 import batch
 
     inst = batch.prepare(_small_instances(2))
-    best, table = batch.autotune(inst, workers=(1, 2), ckpt=(50, 100))
-    assert best in table and len(table) == 4
+    best, table = batch.autotune(inst, workers=(1, 2), ckpt=(50, 100), modes=("batched", "graph"))
+    assert best in table and len(table) == 8
     assert table[best] == min(table.values())
+    batch.close_graphs()
+
+
+def test_graph_sweep_equals_batched(fwi_lib):
+    """Recorded CUDA graphs run the same kernels in the same order: the same
+    misfits and gradients bit for bit, sweep after sweep, and an in-place model
+    update is picked up by the next launch."""
+    import torch
+
+    from paper_2003_06027_gb300 import batch, fwi
+
+    inst = batch.prepare(_small_instances(3))
+    Jb, gb, _ = batch.sweep(inst, "batched", workers=2)
+    for _ in range(2):
+        Jg, gg, _ = batch.sweep(inst, "graph", workers=2)
+        for i in range(len(inst)):
+            assert float(Jg[i][0]) == float(Jb[i][0])
+            assert torch.equal(gg[i], gb[i])
+    with torch.no_grad():
+        inst[0].c.mul_(1.01)
+    Jg, gg, _ = batch.sweep(inst, "graph", workers=2)
+    J1, g1, _, _, _ = fwi.misfit_grad(inst[0].c, inst[0].stf, inst[0].x0, inst[0].rec_iz, inst[0].rec_ix,
+                                      inst[0].observed, ckpt_every=100, want_src=False, **inst[0].kw)
+    assert float(Jg[0][0]) == float(J1[0]) and torch.equal(gg[0], g1)
+    batch.close_graphs()
+
+
+def test_graph_refuses_a_relaid_workspace(fwi_lib):
+    """A graph is tied to its context's workspace: after a call with another
+    problem layout on the same context, launching it fails with FWI_EINVAL."""
+    import ctypes
+
+    from paper_2003_06027_gb300 import batch, fwi
+
+    a, b = batch.prepare(_small_instances(2))
+    g = fwi.GradGraph(a.c, a.stf, a.x0, a.rec_iz, a.rec_ix, a.observed, ckpt_every=100, **a.kw)
+    g.launch()
+    g.check()
+    other = fwi._Call(b.c, b.stf, b.x0, b.rec_iz, b.rec_ix, b.kw["dx"], b.kw["dz"], b.kw["order"], b.kw["npml"],
+                      b.kw["pml_R"], b.kw["pml_vmax"], b.kw["pml_f0"], b.kw["src_kind"])
+    out = fwi._empty_like_place(b.c, (b.shots, other.nrec, other.nt))
+    L = fwi.library()
+    fwi._check(L.fwi_forward(g.ctx, ctypes.byref(other.model), ctypes.byref(other.src), ctypes.byref(other.rec),
+                             other.nt, float(b.kw["dt"]), fwi._ptr(out), fwi._stream(b.c, None)))
+    with pytest.raises(fwi.FwiError):
+        g.launch()
+    g.close()
