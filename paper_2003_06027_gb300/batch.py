@@ -34,7 +34,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import fwi
+from . import fwi, optim
 
 
 @dataclass
@@ -253,3 +253,25 @@ def fwi_iterations(instances, iters: int, mode: str = "batched", workers: int = 
             for inst, g in zip(instances, gs):
                 inst.c.sub_(step * g / g.abs().max().clamp_min(1e-30)).clamp_(vmin, vmax)
     return hist
+
+
+def fwi_lbfgs(inst: Instance, iters: int, ckpt_every: int = 100, step0: float = 40.0, m: int = 5,
+              vmin: float = 1500.0, vmax: float = 4500.0):
+    """FWI of one instance with the paper's outer loop, L-BFGS (optim.lbfgs,
+    velocity bounds [vmin, vmax], first step at most ``step0`` m/s per cell),
+    each misfit/gradient evaluation one launch of the instance's recorded
+    graph. Updates ``inst.c``; returns the optimiser's log."""
+    K = min(ckpt_every, int(inst.stf.shape[1]))
+    g = _graph_of(inst, K)
+
+    def fun_grad(c):
+        with torch.no_grad():
+            inst.c.copy_(c)
+        g.launch()
+        g.check()
+        return float(g.misfit[0]), g.grad.clone()
+
+    c, log = optim.lbfgs(fun_grad, inst.c, iters, m=m, step0=step0, lower=vmin, upper=vmax)
+    with torch.no_grad():
+        inst.c.copy_(c)
+    return log

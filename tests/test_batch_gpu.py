@@ -109,3 +109,21 @@ def test_graph_refuses_a_relaid_workspace(fwi_lib):
     with pytest.raises(fwi.FwiError):
         g.launch()
     g.close()
+
+
+def test_lbfgs_fwi_descends_faster_than_normalised_steepest_descent(fwi_lib):
+    """The paper's outer loop (L-BFGS) on recorded-graph gradients: every
+    accepted step lowers the misfit, and after the same number of iterations it
+    is below plain normalised steepest descent's."""
+    from paper_2003_06027_gb300 import batch
+
+    problems = _small_instances(1)
+    a = batch.prepare(problems)
+    b = batch.prepare(problems)
+    log = batch.fwi_lbfgs(a[0], 6, step0=20.0)
+    assert all(f1 < f0 for f0, f1 in zip(log.f, log.f[1:]))
+    assert len(log.f) == 7
+    hist = batch.fwi_iterations(b, 7, "batched", workers=1, step=20.0)
+    J_sd = hist[-1][0]  # misfit at the start of the 7th steepest-descent iteration, i.e. after 6 steps
+    assert log.f[-1] < J_sd, (log.f, [h[0] for h in hist])
+    batch.close_graphs()
