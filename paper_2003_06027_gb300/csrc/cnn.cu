@@ -112,6 +112,95 @@ __global__ void __launch_bounds__(256) k_im2col_t(const float* __restrict__ x, c
   }
 }
 
+// colT[pix][k] (row stride ldk, BF16), row-staged: a block takes one output
+// row (b, i), a run of 64 output columns and 8 input channels. It stages the 3
+// input rows each channel's taps read (64 sw + 2 columns, zero outside the
+// image) in shared memory, reading every input value once, then writes each
+// pixel's 72 taps of the chunk as 9 runs of 16 bytes. Taps in [K9, ldk) are
+// written as zeros. Dynamic shared memory: IM_CC * 3 * (64 sw + 2) floats.
+constexpr int IM_CC = 8;    // channels per block
+constexpr int IM_PIX = 64;  // output columns per block
+__global__ void __launch_bounds__(256) k_im2col_rows_t(const float* __restrict__ x, const ConvDims d, int ldk,
+                                                       uint16_t* __restrict__ colT) {
+  extern __shared__ float xs[];  // [IM_CC][3][JW]
+  const int row = blockIdx.x;    // b * Ho + i
+  const int j0 = blockIdx.y * IM_PIX, c0 = blockIdx.z * IM_CC;
+  const uint32_t b = d.fHo.div((uint32_t)row);
+  const int i = row - (int)b * d.Ho;
+  const int JW = IM_PIX * d.sw + 2, s0 = d.sw * j0 - 1;
+  const long long plane = (long long)d.B * d.H * d.W;
+  for (int e = threadIdx.x; e < IM_CC * 3 * JW; e += 256) {  // all staging loads independent
+    const int cp = e / JW, col = e - cp * JW;
+    const int cc = cp / 3, p = cp - 3 * cc, c = c0 + cc, r = d.sh * i + p - 1, s = s0 + col;
+    xs[e] = (c < d.C && r >= 0 && r < d.H && s >= 0 && s < d.W)
+                ? __ldg(x + c * plane + ((long long)b * d.H + r) * d.W + s)
+                : 0.f;
+  }
+  __syncthreads();
+  const long long pix0 = (long long)row * d.Wo;
+  for (int v = threadIdx.x; v < IM_PIX * 9; v += 256) {
+    const int jl = v / 9, vv = v - 9 * jl, j = j0 + jl;
+    const int k0 = c0 * 9 + 8 * vv;
+    if (j >= d.Wo || k0 >= ldk) continue;
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      uint32_t h2[2];
+#pragma unroll
+      for (int e = 0; e < 2; e++) {
+        const int t = 8 * vv + 2 * u + e;  // tap within the chunk: (cc, p, q)
+        const int cc = t / 9, pq = t - 9 * cc, p = pq / 3, q = pq - 3 * p;
+        h2[e] = to_bf16_bits(xs[(3 * cc + p) * JW + d.sw * jl + q]);
+      }
+      w[u] = h2[0] | (h2[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(colT + (pix0 + j) * ldk + k0) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// col[k][pix] (row stride ldn, BF16), row-staged: a block takes one input
+// channel c and R consecutive output rows; it stages the 3 input rows of each
+// output row (sw Wo + 2 columns) in shared memory and writes the 9 tap rows
+// k = 9c .. 9c+8 over those pixels, 4 pixels (8 bytes) per store where the
+// pixel index allows. Dynamic shared memory: R * 3 * (sw Wo + 2) floats.
+__global__ void __launch_bounds__(256) k_im2col_rows_n(const float* __restrict__ x, const ConvDims d, int R,
+                                                       long long ldn, uint16_t* __restrict__ col) {
+  extern __shared__ float xs[];  // [R][3][JW]
+  const int c = blockIdx.y, row0 = blockIdx.x * R;
+  const int nrows = min(R, d.B * d.Ho - row0);
+  const int JW = d.sw * d.Wo + 2;
+  const float* xc = x + (long long)c * d.B * d.H * d.W;
+  for (int e = threadIdx.x; e < nrows * 3 * JW; e += 256) {  // all staging loads independent
+    const int rp = e / JW, colx = e - rp * JW;
+    const int rl = rp / 3, p = rp - 3 * rl, row = row0 + rl;
+    const uint32_t b = d.fHo.div((uint32_t)row);
+    const int i = row - (int)b * d.Ho, r = d.sh * i + p - 1, s = colx - 1;
+    xs[e] = (r >= 0 && r < d.H && s >= 0 && s < d.W) ? __ldg(xc + ((long long)b * d.H + r) * d.W + s) : 0.f;
+  }
+  __syncthreads();
+  const int q4 = (d.Wo + 3) / 4;  // 4-pixel groups per output row
+  const bool vec = (d.Wo & 3) == 0;
+  for (int e = threadIdx.x; e < nrows * 9 * q4; e += 256) {
+    const int jq = e % q4, t = e / q4, kk = t % 9, rl = t / 9;
+    const int p = kk / 3, q = kk - 3 * p;
+    const float* xr = xs + (3 * rl + p) * JW;
+    const long long n0 = (long long)(row0 + rl) * d.Wo + 4 * jq;
+    uint16_t* dst = col + (long long)(9 * c + kk) * ldn + n0;
+    uint16_t v[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int j = 4 * jq + u;
+      v[u] = to_bf16_bits(j < d.Wo ? xr[d.sw * j + q] : 0.f);
+    }
+    if (vec) {
+      *reinterpret_cast<uint2*>(dst) = make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
+                                                  (uint32_t)v[2] | ((uint32_t)v[3] << 16));
+    } else {
+      for (int u = 0; u < 4 && 4 * jq + u < d.Wo; u++) dst[u] = v[u];
+    }
+  }
+}
+
 // col[k][pix] (row stride ldn, BF16): one tap row per blockIdx.y, 4 pixels per
 // thread; the first pixel's (b, i, j) is decoded once and the next ones step
 // along the row.
@@ -409,6 +498,32 @@ fwi_status dims_of(int C, int B, int H, int W, int sh, int sw, fwi::ConvDims* d)
   return FWI_OK;
 }
 
+// The row-staged im2col kernels where their staging fits in shared memory
+// (every layer of the network does), else the per-element ones.
+cudaError_t im2col_t(const float* x, const fwi::ConvDims& d, int ldk, uint16_t* colT, cudaStream_t st) {
+  const size_t smem = (size_t)fwi::IM_CC * 3 * (fwi::IM_PIX * d.sw + 2) * sizeof(float);
+  const int rows = d.B * d.Ho;
+  if (smem <= 48 * 1024 && d.C <= 65535 * fwi::IM_CC) {
+    const dim3 grid((unsigned)rows, (unsigned)((d.Wo + fwi::IM_PIX - 1) / fwi::IM_PIX),
+                    (unsigned)((d.C + fwi::IM_CC - 1) / fwi::IM_CC));
+    fwi::k_im2col_rows_t<<<grid, 256, smem, st>>>(x, d, ldk, colT);
+  } else {
+    fwi::k_im2col_t<<<dim3((d.Npix + 63) / 64, (ldk + 63) / 64), 256, 0, st>>>(x, d, ldk, colT);
+  }
+  return cudaGetLastError();
+}
+cudaError_t im2col_n(const float* x, const fwi::ConvDims& d, long long ldn, uint16_t* col, cudaStream_t st) {
+  const int R = std::max(1, std::min(16, 1024 / std::max(1, d.Wo)));
+  const size_t smem = (size_t)R * 3 * (d.sw * d.Wo + 2) * sizeof(float);
+  const int rows = d.B * d.Ho;
+  if (smem <= 48 * 1024 && d.C <= 65535) {
+    fwi::k_im2col_rows_n<<<dim3((unsigned)((rows + R - 1) / R), (unsigned)d.C), 256, smem, st>>>(x, d, R, ldn, col);
+  } else {
+    fwi::k_im2col_n<<<dim3((d.Npix + 1023) / 1024, d.K9), 256, 0, st>>>(x, d, ldn, col);
+  }
+  return cudaGetLastError();
+}
+
 int gemm_blocks(long long tiles_per_split) {
   // splits so that about two waves of CTAs cover the GPU's 152 SMs
   return (int)std::max<long long>(1, (2 * 152 + tiles_per_split - 1) / tiles_per_split);
@@ -505,8 +620,7 @@ fwi_status fwi_cnn_conv_forward(fwi_cnn* h, const float* x, int32_t C, int32_t B
   uint16_t* Wp = (uint16_t*)(ws + o_wp);
   fwi::k_wprep<<<blocks_for((long long)O * d.K9), 256, 0, st>>>(w_bf16, O, d.K9, ldk, 0, Wp, nullptr);
   CNN_CK(cudaGetLastError(), "weight layout");
-  fwi::k_im2col_t<<<dim3((d.Npix + 63) / 64, (ldk + 63) / 64), 256, 0, st>>>(x, d, ldk, colT);
-  CNN_CK(cudaGetLastError(), "im2col");
+  CNN_CK(im2col_t(x, d, ldk, colT, st), "im2col");
   fwi::TcGemm g{colT, ldk, Wp, ldk, d.Npix, O, d.K9, y, d.Npix, 0, bias, relu, 1, h->status};
   CNN_CK(fwi::tc_gemm(g, st), "conv forward GEMM");
   return FWI_OK;
@@ -563,8 +677,7 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
     // im2col of dy (BF16, the same rounding as dyb) and one GEMM, no dcol / col2im
     fwi::k_wflip<<<blocks_for(9LL * O * C), 256, 0, st>>>(w_bf16, O, C, ldf, Wf);
     CNN_CK(cudaGetLastError(), "weight flip");
-    fwi::k_im2col_t<<<dim3((dd.Npix + 63) / 64, (ldf + 63) / 64), 256, 0, st>>>(dy, dd, ldf, colb);
-    CNN_CK(cudaGetLastError(), "im2col of dy");
+    CNN_CK(im2col_t(dy, dd, ldf, colb, st), "im2col of dy");
     fwi::TcGemm g{colb, ldf, Wf, ldf, dd.Npix, C, dd.K9, dx, dd.Npix, 0, nullptr, 0, 1, h->status};
     CNN_CK(fwi::tc_gemm(g, st), "conv data-gradient GEMM");
   } else if (dx) {
@@ -580,8 +693,7 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
     CNN_CK(cudaGetLastError(), "col2im");
   }
   // dw[o][k] = sum_pix col[k][pix] dy[o][pix]
-  fwi::k_im2col_n<<<dim3((d.Npix + 1023) / 1024, d.K9), 256, 0, st>>>(x, d, ldn, colb);
-  CNN_CK(cudaGetLastError(), "im2col");
+  CNN_CK(im2col_n(x, d, ldn, colb, st), "im2col");
   fwi::TcGemm g{colb, ldn, dyb, ldn, d.K9, O, d.Npix, S > 1 ? part : dw, d.K9, (long long)O * d.K9, nullptr, 0, S,
                 h->status};
   CNN_CK(fwi::tc_gemm(g, st), "conv weight-gradient GEMM");
