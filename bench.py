@@ -43,6 +43,15 @@ UNIT = "Gcell-steps/s"
 # plus, per cell inside an x- or z-CPML strip and per active axis, 16 B:
 #   forward psi and zeta read+write; adjoint Z and P read+write.
 BYTES = {"fwd": (16, 16), "store": (24, 16), "adj": (32, 16)}
+# Whole-path algorithmic bytes per cell-step (one sweep of every field per step,
+# halos cached, CPML memory not counted): acoustic forward 16 B; acoustic
+# gradient 48 B (forward 16, stored wavefield 4 + reload 4, adjoint 16, FP32
+# gradient partial r/w 8); elastic forward 52 B (5 fields r/w, 3 parameters);
+# elastic gradient 168 B (forward 52, stored 20 + reload 20, adjoint 52, 3
+# partials r/w 24). The kernels move more (two kernels per elastic step, stored
+# fluxes instead of wavefields, recomputation), so these fractions are lower
+# than the per-kernel ones.
+PATH_BYTES = {"acoustic_forward": 16, "acoustic_gradient": 48, "elastic_forward": 52, "elastic_gradient": 168}
 
 
 def padded(d):
@@ -176,7 +185,12 @@ def elastic_measure(steps):
     e1.record()
     torch.cuda.synchronize()
     fms = e0.elapsed_time(e1) / steps
+    peak, kind = load_peaks()
+    path = {k: {"bytes_per_cell_step": b, "GBps": b * cs / (t / 1e3) / 1e9, "frac": b * cs / (t / 1e3) / 1e9 / peak,
+                "peak_source": kind} for k, b, t in (("forward", PATH_BYTES["elastic_forward"], fms),
+                                                    ("gradient", PATH_BYTES["elastic_gradient"], ms))}
     return {"workload": d["name"] + "-ckpt100", "value": cs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "path_roofline": path,
             "forward": {"value": cs / (fms / 1e3) / 1e9, "ms_per_step": fms},
             "cell_steps_per_step": cs, "step_launch_ms": {"fwd_vel+str": t.fwd_step_ms,
                                                           "recompute_vel+str": t.store_step_ms,
@@ -280,7 +294,10 @@ def learned_measure():
             "experiment": "profiles/learned_start_experiment.md"}
 
 
-def dist_setup():
+def dist_setup(backend: str = "nccl"):
+    """(world size, rank, local rank) from the torchrun environment; joins the
+    process group when there is more than one rank (NCCL on GPUs; the host-side
+    logic below also runs under gloo, which the CPU tests use)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -288,8 +305,9 @@ def dist_setup():
         import torch
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -301,14 +319,23 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x, local):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
+    dev = f"cuda:{local}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(ws, units_per_rank, ms):
+    """Whole-job throughput (weak scaling: every rank processes its own
+    units_per_rank, no data-path collective): all ranks' units / the max-over-
+    ranks time, in G units per second."""
+    return ws * units_per_rank / (ms / 1e3) / 1e9
 
 
 def cpu_oracle_sample(d, shots, nt):
@@ -432,7 +459,7 @@ def main():
     barrier(ws)
     clocks = sampler.stop() if sampler else None
     ms = max_over_ranks(ws, e0.elapsed_time(e1) / args.steps, local)
-    value = ws * cell_steps / (ms / 1e3) / 1e9
+    value = job_value(ws, cell_steps, ms)
 
     # forward only (same workload), for reference beside the gradient
     for _ in range(2):
@@ -484,6 +511,10 @@ def main():
            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(d),
            "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+           "path_roofline": {k: {"bytes_per_cell_step": PATH_BYTES[b], "GBps": PATH_BYTES[b] * v,
+                                 "frac": PATH_BYTES[b] * v / peak, "peak_source": peak_kind}
+                             for k, b, v in (("gradient", "acoustic_gradient", value / ws),
+                                             ("forward", "acoustic_forward", cell_steps / (fwd_ms / 1e3) / 1e9))},
            "forward": {"value": ws * cell_steps / (fwd_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": fwd_ms},
            "e2e": {"value": ws * cell_steps / (e2e_ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
