@@ -113,12 +113,16 @@ __global__ void __launch_bounds__(256) k_im2col_t(const float* __restrict__ x, c
 }
 
 // colT[pix][k] (row stride ldk, BF16), row-staged: a block takes one output
-// row (b, i), a run of 64 output columns and 8 input channels. It stages the 3
+// row (b, i), a run of 64 output columns and 16 input channels. It stages the 3
 // input rows each channel's taps read (64 sw + 2 columns, zero outside the
 // image) in shared memory, reading every input value once, then writes each
-// pixel's 72 taps of the chunk as 9 runs of 16 bytes. Taps in [K9, ldk) are
-// written as zeros. Dynamic shared memory: IM_CC * 3 * (64 sw + 2) floats.
-constexpr int IM_CC = 8;    // channels per block
+// pixel's 144 taps of the chunk as 18 runs of 16 bytes (288 bytes, whole
+// 32-byte sectors when the row stride is a multiple of 288 bytes, as for 16
+// channels or a multiple: no sector is shared between two blocks' writes).
+// Taps in [K9, ldk) are written as zeros. Dynamic shared memory:
+// IM_CC * 3 * (64 sw + 2) floats.
+constexpr int IM_CC = 16;   // channels per block
+constexpr int IM_VPP = IM_CC * 9 / 8;  // 16-byte runs per pixel
 constexpr int IM_PIX = 64;  // output columns per block
 __global__ void __launch_bounds__(256) k_im2col_rows_t(const float* __restrict__ x, const ConvDims d, int ldk,
                                                        uint16_t* __restrict__ colT) {
@@ -138,8 +142,8 @@ __global__ void __launch_bounds__(256) k_im2col_rows_t(const float* __restrict__
   }
   __syncthreads();
   const long long pix0 = (long long)row * d.Wo;
-  for (int v = threadIdx.x; v < IM_PIX * 9; v += 256) {
-    const int jl = v / 9, vv = v - 9 * jl, j = j0 + jl;
+  for (int v = threadIdx.x; v < IM_PIX * IM_VPP; v += 256) {
+    const int jl = v / IM_VPP, vv = v - IM_VPP * jl, j = j0 + jl;
     const int k0 = c0 * 9 + 8 * vv;
     if (j >= d.Wo || k0 >= ldk) continue;
     uint32_t w[4];
