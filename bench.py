@@ -36,7 +36,7 @@ METRIC = "FWI Gcell-steps/s (fwd+adjoint), % HBM roofline, batched/learned vs pl
 UNIT = "Gcell-steps/s"
 
 # Algorithmic HBM bytes per cell-step of each step kernel (FP32): every field
-# streamed once per step, halos assumed cached (kernel table).
+# streamed once per step, halos assumed cached.
 #   forward (recording):  read u^n, u^{n-1}, m; write u^{n+1}                         16 B
 #   forward (storing):    + write the fluxes p_x, p_z to the segment slot             24 B
 #   adjoint:              read lam_{n+1}, lam_{n+2}, m, p_x, p_z, g; write lam_n, g   32 B

@@ -4,7 +4,7 @@
  * point (cycle skipping). This part of libfwi trains a small encoder-decoder
  * CNN, on shot gathers that the library's own forward modelling generates, to
  * predict a starting velocity model; plain smooth-start FWI stays the fallback
- * and the judge of its error. The network is not from the paper.
+ * and the yardstick of its error. The network is not from the paper.
  *
  * Conventions of every call:
  *   - activations are FP32, channel-major [C][B][H][W] (channel, batch, rows,

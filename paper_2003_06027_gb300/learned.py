@@ -6,7 +6,7 @@ encoder-decoder CNN maps the 16 shot gathers of a survey (64 receivers x 1000
 samples) to a 128 x 256 velocity model. It is trained on gathers that the
 library's own forward modelling computes from random layered models, and its
 prediction is then used as the start of ordinary FWI. Plain smooth-start FWI
-stays the fallback and the judge: `compare_fwi` runs both from the same data.
+stays the fallback and the yardstick: `compare_fwi` runs both from the same data.
 
 Network (activations channel-major [C][B][H][W]; H = time or depth, W = receivers
 or x; every conv 3x3, pad 1, ReLU except the last):
