@@ -50,7 +50,7 @@ typedef enum {
   FWI_ECUDA = 4,      /* a CUDA runtime call failed (message in fwi_last_error) */
   FWI_EUNSTABLE = 5,  /* non-finite value in the seismograms or the misfit */
   FWI_ETIMEOUT = 6,   /* a bounded device wait gave up (results invalid; context usable) */
-  FWI_ENOTIMPL = 7    /* combination not supported by this build */
+  FWI_ENOTIMPL = 7    /* combination the library does not implement */
 } fwi_status;
 
 enum { FWI_ACOUSTIC = 0, FWI_ELASTIC = 1 };
