@@ -498,7 +498,7 @@ def main():
     avg_ms = statistics.mean(kms[dom])
     achieved = launch_bytes(d, dom) / (avg_ms / 1e3) / 1e9
     kernel_names = {"fwd": "acu_fwd_step<4,record>", "store": "acu_fwd_step<4,store>", "adj": "acu_adj_step<4>"}
-    groups = min(4, S)
+    groups = min(2 if dom == "adj" else 4, S)  # shot groups per step of the kernel (the library's choice)
     roof = {"bound": "hbm", "kernel": kernel_names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_kind, "launches_per_step": groups,
             "note": f"one step of the kernel is {groups} concurrent launches (one per shot group, own stream); "
