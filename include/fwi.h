@@ -140,6 +140,16 @@ fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
                            float *grad, float *grad_stf, float *grad_x0, float *seis_out,
                            void *cuda_stream);
 
+/* Launch shape of the acoustic calls on ctx: the shots of a call are split
+ * into forward_groups (forward and recompute steps) and adjoint_groups
+ * (adjoint steps) contiguous groups, each step launched once per group on its
+ * own stream, so that the groups' launches fill each other's idle SMs. 0 keeps
+ * the library's default (4 and 2); at most 4; never more groups than shots.
+ * Results do not depend on it (the per-shot arithmetic and the fixed-order
+ * cross-shot sums are the same). Takes effect for later calls and recordings;
+ * FWI_EINVAL outside [0, 4]. */
+fwi_status fwi_set_shot_groups(fwi_ctx *ctx, int32_t forward_groups, int32_t adjoint_groups);
+
 /* A recorded gradient: one acoustic fwi_misfit_grad call captured as a CUDA
  * graph, for loops that evaluate the same problem many times (an FWI iteration
  * per launch) or many small problems side by side, where launching the tens of

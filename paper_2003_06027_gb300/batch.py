@@ -70,7 +70,8 @@ def prepare(problems, device=0) -> list:
     return out
 
 
-def _grad_batched(inst: Instance, K: int):
+def _grad_batched(inst: Instance, K: int, groups=(0, 0)):
+    fwi.set_shot_groups(*groups, device=inst.c.device.index)
     J, g, _, _, _ = fwi.misfit_grad(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed,
                                     ckpt_every=K, want_src=False, **inst.kw)
     return J, g
@@ -91,11 +92,12 @@ _graphs = {}
 _graph_streams = {}
 
 
-def _graph_of(inst: Instance, K: int) -> fwi.GradGraph:
-    key = (id(inst), K)
+def _graph_of(inst: Instance, K: int, groups=(0, 0)) -> fwi.GradGraph:
+    key = (id(inst), K, tuple(groups))
     g = _graphs.get(key)
     if g is None or g._a.c.data_ptr() != inst.c.data_ptr():
-        g = fwi.GradGraph(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed, ckpt_every=K, **inst.kw)
+        g = fwi.GradGraph(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed, ckpt_every=K,
+                          groups=groups, **inst.kw)
         _graphs[key] = g
     return g
 
@@ -174,7 +176,7 @@ def close_pools():
         _pools.pop(k).close()
 
 
-def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 100):
+def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 100, groups=(0, 0)):
     """One gradient sweep over all instances; returns ([J_i], [g_i], seconds).
     The time is host wall time with the device idle on both sides (every
     library call ends with a stream synchronisation)."""
@@ -189,14 +191,14 @@ def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 
         def job(i):
             def fn():
                 inst = instances[i]
-                Js[i], gs[i] = _grad_batched(inst, min(ckpt_every, int(inst.stf.shape[1])))
+                Js[i], gs[i] = _grad_batched(inst, min(ckpt_every, int(inst.stf.shape[1])), groups)
             return fn
 
         order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
         pool(max(1, min(workers, n)), torch.cuda.current_device()).run([job(i) for i in order])
     elif mode == "graph":
         order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
-        graphs = {i: _graph_of(instances[i], min(ckpt_every, int(instances[i].stf.shape[1]))) for i in order}
+        graphs = {i: _graph_of(instances[i], min(ckpt_every, int(instances[i].stf.shape[1])), groups) for i in order}
         streams = _streams(max(1, min(workers, n)), torch.cuda.current_device())
         main = torch.cuda.current_stream()
         for s in streams:
@@ -212,12 +214,14 @@ def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 
     return Js, gs, time.perf_counter() - t0
 
 
-def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batched",)):
-    """Pick (mode, workers, ckpt_every) by timing one sweep per candidate on the
-    given instances (the first sweep of each candidate also sizes the arenas or
-    records the graphs, so each candidate is run twice and the second run
-    counts). The pools of the losing worker counts are closed, and the graphs
-    the winner does not use are freed."""
+def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batched",), groups=((0, 0),)):
+    """Pick (mode, workers, ckpt_every, shot groups) by timing one sweep per
+    candidate on the given instances (the first sweep of each candidate also
+    sizes the arenas or records the graphs, so each candidate is run twice and
+    the second run counts). ``groups`` lists (forward, adjoint) shot-group
+    counts, the step kernels' launch shape (fwi_set_shot_groups). The pools of
+    the losing worker counts are closed, and the graphs the winner does not use
+    are freed."""
     best = None
     table = {}
     dev = torch.cuda.current_device()
@@ -225,18 +229,22 @@ def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batch
         for W in workers:
             prev = best
             for K in ckpt:
-                sweep(instances, mode, W, K)
-                _, _, t = sweep(instances, mode, W, K)
-                table[(mode, W, K)] = t
-                if best is None or t < table[best]:
-                    best = (mode, W, K)
+                for grp in groups:
+                    grp = tuple(grp)
+                    sweep(instances, mode, W, K, grp)
+                    _, _, t = sweep(instances, mode, W, K, grp)
+                    key = (mode, W, K) if len(groups) == 1 else (mode, W, K, grp)
+                    table[key] = t
+                    if best is None or t < table[best]:
+                        best = key
             if mode == "batched":  # keep at most the best pool alive between candidates
                 bw = best[1] if best[0] == "batched" else None
                 loser = W if bw != W else (prev[1] if prev is not None and prev[0] == "batched" and prev[1] != W
                                            else None)
                 if loser is not None and (loser, dev) in _pools:
                     _pools.pop((loser, dev)).close()
-    for key in [k for k in _graphs if not (best[0] == "graph" and k[1] == best[2])]:
+    bgrp = tuple(best[3]) if len(best) > 3 else (0, 0)
+    for key in [k for k in _graphs if not (best[0] == "graph" and k[1] == best[2] and k[2] == bgrp)]:
         _graphs.pop(key).close()  # graphs the winner does not use
     return best, table
 

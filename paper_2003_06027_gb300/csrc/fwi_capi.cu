@@ -572,6 +572,15 @@ fwi_status fwi_selftest_wait_timeout(fwi_ctx* ctx, int64_t* waited_ns) {
   return fail(FWI_ECUDA, "self-test: a wait that cannot complete reported completion");
 }
 
+fwi_status fwi_set_shot_groups(fwi_ctx* ctx, int32_t forward_groups, int32_t adjoint_groups) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (forward_groups < 0 || forward_groups > MAX_GROUPS || adjoint_groups < 0 || adjoint_groups > MAX_GROUPS)
+    return fail(FWI_EINVAL, "shot groups must be in [0, " + std::to_string(MAX_GROUPS) + "] (0: default)");
+  ctx->fwd_groups = forward_groups;
+  ctx->adj_groups = adjoint_groups;
+  return FWI_OK;
+}
+
 fwi_status fwi_last_timing(const fwi_ctx* ctx, float* phase_ms3, float* kernel_ms3, int64_t* launches) {
   if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
   for (int k = 0; k < 3; k++) {
@@ -603,7 +612,7 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   CK(acu_make_maps(&maps, P.g, P.S, P.u, P.m));
   ensure_events(ctx, 0);
   Groups gr;
-  if ((v = make_groups(ctx, P.S, st, gr)) != FWI_OK) return v;
+  if ((v = make_groups(ctx, P.S, st, gr, ctx->fwd_groups ? ctx->fwd_groups : MAX_GROUPS)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[0], st));
   if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
   for (int n = 0; n < nt; n++) {
@@ -667,8 +676,8 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   ensure_events(ctx, P.nseg);
 
   Groups gr, gra;
-  if ((v = make_groups(ctx, P.S, st, gr)) != FWI_OK) return v;
-  if ((v = make_groups(ctx, P.S, st, gra, ADJ_GROUPS)) != FWI_OK) return v;
+  if ((v = make_groups(ctx, P.S, st, gr, ctx->fwd_groups ? ctx->fwd_groups : MAX_GROUPS)) != FWI_OK) return v;
+  if ((v = make_groups(ctx, P.S, st, gra, ctx->adj_groups ? ctx->adj_groups : ADJ_GROUPS)) != FWI_OK) return v;
   const size_t sl = (size_t)P.g.slice;
 
   // forward sweep with a full-state checkpoint at the start of every segment

@@ -27,6 +27,7 @@ struct fwi_ctx {
   // bumped whenever the arena is reallocated or takes a new layout: a recorded
   // graph (fwi_misfit_grad_graph) is valid only for the epoch it was captured in
   unsigned long long arena_epoch = 0;
+  int fwd_groups = 0, adj_groups = 0;  // shot groups of the acoustic step launches (0: the library's default)
   cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
 };
 

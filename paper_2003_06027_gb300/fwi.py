@@ -53,7 +53,8 @@ _ctx = threading.local()
 
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
            "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout",
-           "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy", "fwi_last_error"]
+           "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy",
+           "fwi_set_shot_groups", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -89,6 +90,7 @@ def library(build_if_missing: bool = True):
             L.fwi_graph_launch.argtypes = [P, P]
             L.fwi_graph_status.argtypes = [P, P]
             L.fwi_graph_destroy.argtypes = [P]
+            L.fwi_set_shot_groups.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
             L.fwi_last_error.restype = ctypes.c_char_p
             for f in EXPORTS[:-1]:
                 getattr(L, f).restype = ctypes.c_int
@@ -131,6 +133,13 @@ class Timing:
     store_step_ms: float   # average launch of the storing forward step (recompute)
     adj_step_ms: float     # average launch of the adjoint step
     launches: int          # kernels launched by the call
+
+
+def set_shot_groups(forward_groups: int = 0, adjoint_groups: int = 0, device: int = 0):
+    """Launch shape of this thread's context for acoustic calls: shot groups of
+    the forward/recompute steps and of the adjoint steps (0: the library's
+    default; fwi_set_shot_groups)."""
+    _check(library().fwi_set_shot_groups(context(device), int(forward_groups), int(adjoint_groups)))
 
 
 def last_timing(device: int = 0) -> Timing:
@@ -276,10 +285,12 @@ class GradGraph:
     All arguments must be device tensors; they are kept referenced and are read
     again at every launch, so an inversion updates ``c`` in place and launches
     again. Outputs live in ``self.misfit``, ``self.grad`` (and ``grad_stf``,
-    ``grad_x0`` when ``want_src``). Recording runs the evaluation once."""
+    ``grad_x0`` when ``want_src``). ``groups`` = (forward, adjoint) shot groups
+    of the recorded launches (0: default). Recording runs the evaluation once."""
 
     def __init__(self, c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
-                 pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, ckpt_every=100, want_src=False):
+                 pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, ckpt_every=100, want_src=False,
+                 groups=(0, 0)):
         for t in (c, stf, x0, rec_iz, rec_ix, observed):
             if not (_is_torch(t) and t.is_cuda):
                 raise ValueError("GradGraph takes CUDA tensors only")
@@ -295,6 +306,12 @@ class GradGraph:
         self._L = L
         self.ctx = ctypes.c_void_p()
         _check(L.fwi_create(ctypes.byref(self.ctx), int(self.device)))
+        self.groups = tuple(groups)
+        st = L.fwi_set_shot_groups(self.ctx, int(groups[0]), int(groups[1]))
+        if st != 0:
+            L.fwi_destroy(self.ctx)
+            self.ctx = None
+            _check(st)
         self.graph = ctypes.c_void_p()
         K = max(1, min(int(ckpt_every), a.nt))
         st = L.fwi_misfit_grad_graph(self.ctx, ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,

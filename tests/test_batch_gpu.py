@@ -127,3 +127,39 @@ def test_lbfgs_fwi_descends_faster_than_normalised_steepest_descent(fwi_lib):
     J_sd = hist[-1][0]  # misfit at the start of the 7th steepest-descent iteration, i.e. after 6 steps
     assert log.f[-1] < J_sd, (log.f, [h[0] for h in hist])
     batch.close_graphs()
+
+
+def test_shot_groups_do_not_change_results(fwi_lib):
+    """The launch shape (shot groups of the forward and adjoint steps) changes
+    only how the step kernels are launched: the misfit and every gradient are
+    bit-identical for any split; values outside [0, 4] are refused."""
+    import torch
+
+    from paper_2003_06027_gb300 import batch, fwi
+
+    inst = batch.prepare(_small_instances(1))[0]
+    outs = []
+    for grp in ((1, 1), (4, 2), (3, 3), (0, 0)):
+        fwi.set_shot_groups(*grp)
+        outs.append(fwi.misfit_grad(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed,
+                                    ckpt_every=100, **inst.kw))
+    for o in outs[1:]:
+        assert float(o[0][0]) == float(outs[0][0][0])
+        for a, b in zip(o[1:4], outs[0][1:4]):
+            assert torch.equal(a, b)
+    with pytest.raises(fwi.FwiError):
+        fwi.set_shot_groups(5, 0)
+    fwi.set_shot_groups(0, 0)
+
+
+def test_autotune_over_launch_shapes(fwi_lib):
+    from paper_2003_06027_gb300 import batch
+
+    inst = batch.prepare(_small_instances(2))
+    best, table = batch.autotune(inst, workers=(2,), ckpt=(100,), modes=("graph",), groups=((1, 1), (4, 2)))
+    assert len(table) == 2 and best in table and table[best] == min(table.values())
+    Jg, gg, _ = batch.sweep(inst, "graph", 2, 100, best[3])
+    Jb, gb, _ = batch.sweep(inst, "batched", 2, 100)
+    for i in range(len(inst)):
+        assert float(Jg[i][0]) == float(Jb[i][0])
+    batch.close_graphs()
