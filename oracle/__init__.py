@@ -60,6 +60,7 @@ class AcousticCfg(ctypes.Structure):
         ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
         ("pml_R", ctypes.c_double), ("pml_vmax", ctypes.c_double), ("pml_f0", ctypes.c_double),
         ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
+        ("line_len", ctypes.c_int),
     ]
 
 
@@ -125,20 +126,33 @@ class _Geom:
             pml_vmax=g.get("pml_vmax", 4500.0), pml_f0=g.get("pml_f0", 10.0),
             rec_iz=self.iz.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
             rec_ix=self.ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+            line_len=g.get("line_len", 0),
         )
+
+
+def _stf_array(g, stf, dt_):
+    """[S][nt] time functions, or [S][nt][line_len] per-cell ones of a line source."""
+    if g.get("src_kind", 0) == 3:
+        stf = np.ascontiguousarray(stf, dtype=dt_)
+        if stf.ndim == 2:
+            stf = stf[None]
+        assert stf.ndim == 3 and stf.shape[2] == g["line_len"]
+        return stf
+    return np.ascontiguousarray(np.atleast_2d(stf), dtype=dt_)
 
 
 def acoustic_forward(g: dict, c, stf, x0, complex_step: bool = False) -> np.ndarray:
     """Seismograms [nshots][nrec][nt] of the acoustic recursion.
 
     ``g`` holds the geometry (nz, nx, npml, order, nt, dz, dx, dt, src_kind,
-    pml_R, pml_vmax, pml_f0, rec_iz, rec_ix); c is [nz][nx], stf [S][nt],
-    x0 [S][2] = (x, z) in metres. With ``complex_step`` every input may be
+    pml_R, pml_vmax, pml_f0, rec_iz, rec_ix, and line_len for a line source);
+    c is [nz][nx], stf [S][nt] ([S][nt][line_len] for a line source, src_kind
+    3), x0 [S][2] = (x, z) in metres. With ``complex_step`` every input may be
     complex and the map is evaluated in complex arithmetic.
     """
     dt_ = np.complex128 if complex_step else np.float64
     c = np.ascontiguousarray(c, dtype=dt_)
-    stf = np.ascontiguousarray(np.atleast_2d(stf), dtype=dt_)
+    stf = _stf_array(g, stf, dt_)
     x0 = np.ascontiguousarray(np.reshape(x0, (-1, 2)), dtype=dt_)
     S = stf.shape[0]
     assert x0.shape[0] == S and c.shape == (g["nz"], g["nx"]) and stf.shape[1] == g["nt"]
@@ -151,17 +165,18 @@ def acoustic_forward(g: dict, c, stf, x0, complex_step: bool = False) -> np.ndar
 
 
 def acoustic_adjoint(g: dict, c, stf, x0, res):
-    """Gradients (dJ/dc [nz][nx], dJ/dstf [S][nt], dJ/dx0 [S][2]) of any
-    misfit whose derivative with respect to the seismograms is ``res``."""
+    """Gradients (dJ/dc [nz][nx], dJ/dstf [S][nt] (line source: [S][nt][line_len]),
+    dJ/dx0 [S][2]) of any misfit whose derivative with respect to the
+    seismograms is ``res``."""
     c = np.ascontiguousarray(c, dtype=np.float64)
-    stf = np.ascontiguousarray(np.atleast_2d(stf), dtype=np.float64)
+    stf = _stf_array(g, stf, np.float64)
     x0 = np.ascontiguousarray(np.reshape(x0, (-1, 2)), dtype=np.float64)
     res = np.ascontiguousarray(res, dtype=np.float64)
     S = stf.shape[0]
     geo = _Geom(AcousticCfg, g, S)
     assert res.shape == (S, geo.cfg.nrec, g["nt"])
     gc = np.zeros((g["nz"], g["nx"]), dtype=np.float64)
-    gs = np.zeros((S, g["nt"]), dtype=np.float64)
+    gs = np.zeros(stf.shape, dtype=np.float64)
     gx = np.zeros((S, 2), dtype=np.float64)
     if lib().or_acoustic_adjoint(ctypes.byref(geo.cfg), _ptr(c), _ptr(stf), _ptr(x0), _ptr(res),
                                  _ptr(gc), _ptr(gs), _ptr(gx)) != 0:

@@ -118,6 +118,8 @@ void or_cpml_profile(int n_phys, int npml, double h, double dt, double R,
 static int check_cfg(const or_acoustic_cfg *cfg) {
   if (cfg->nz < 1 || cfg->nx < 1 || cfg->nt < 1 || cfg->nshots < 0 || cfg->npml < 0) return -1;
   if (cfg->order != 4 && cfg->order != 8 && cfg->order != 2 && cfg->order != 6) return -1;
+  if (cfg->src_kind != 0 && cfg->src_kind != 1 && cfg->src_kind != 3) return -1;
+  if (cfg->src_kind == 3 && cfg->line_len < 1) return -1;
   for (int r = 0; r < cfg->nrec; r++)
     if (cfg->rec_iz[r] < 0 || cfg->rec_iz[r] >= cfg->nz || cfg->rec_ix[r] < 0 || cfg->rec_ix[r] >= cfg->nx)
       return -1;
@@ -130,7 +132,7 @@ int or_acoustic_forward(const or_acoustic_cfg *cfg, const double *c,
   int err = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
   for (int s = 0; s < cfg->nshots; s++)
-    err |= acoustic_shot_r(cfg, c, stf + (size_t)s * cfg->nt, x0 + 2 * s,
+    err |= acoustic_shot_r(cfg, c, stf + (size_t)s * OR_STF_STRIDE(cfg), x0 + 2 * s,
                            seis + (size_t)s * cfg->nrec * cfg->nt, NULL, NULL) != 0;
   return err ? -1 : 0;
 }
@@ -143,7 +145,7 @@ int or_acoustic_forward_cplx(const or_acoustic_cfg *cfg, const void *c_,
   int err = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
   for (int s = 0; s < cfg->nshots; s++)
-    err |= acoustic_shot_c(cfg, c, stf + (size_t)s * cfg->nt, x0 + 2 * s,
+    err |= acoustic_shot_c(cfg, c, stf + (size_t)s * OR_STF_STRIDE(cfg), x0 + 2 * s,
                            seis + (size_t)s * cfg->nrec * cfg->nt, NULL, NULL) != 0;
   return err ? -1 : 0;
 }
@@ -213,9 +215,11 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
   double *gbx = calloc(NN, sizeof(double)), *gbz = calloc(NN, sizeof(double));
   double *gmx = calloc(NN, sizeof(double)), *gmz = calloc(NN, sizeof(double));
 
-  int ci[49], cj[49], nsup = 0;
-  double w[49];
+  const int cap = OR_MAX_SUPPORT(cfg);
+  int *ci = malloc(sizeof(int) * cap), *cj = malloc(sizeof(int) * cap), nsup = 0;
+  double *w = malloc(sizeof(double) * cap);
   source_support_r(cfg, x0s, ci, cj, &nsup, w);
+  const int line = cfg->src_kind == 3;
   double sg = 0.5 * dx;
 
 #define AT(arr, iZ, jX) (((iZ) >= 0 && (iZ) < Nz && (jX) >= 0 && (jX) < Nx) ? (arr)[(size_t)(iZ) * Nx + (jX)] : 0.0)
@@ -231,7 +235,7 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
     /* lam1 is now complete: source terms F_n = dt^2 w g(t_n) */
     for (int q = 0; q < nsup; q++) {
       double l = lam1[(size_t)ci[q] * Nx + cj[q]];
-      if (gstf) gstf[n] += dt * dt * w[q] * l;
+      if (gstf) gstf[line ? (size_t)n * nsup + q : (size_t)n] += dt * dt * w[q] * l;
       if (gx0 && cfg->src_kind == 1) {
         double xi = (cj[q] - np) * dx - x0s[0], zi = (ci[q] - np) * dz - x0s[1];
         gx0[0] += stf[n] * dt * dt * l * w[q] * xi / (sg * sg);
@@ -312,6 +316,7 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
   free(ax); free(bx); free(axh); free(bxh); free(az); free(bz); free(azh); free(bzh);
   free(m); free(mhx); free(mhz); free(lam1); free(lam0); free(zx); free(zz);
   free(px_); free(pz_); free(hbx); free(hbz); free(gbx); free(gbz); free(gmx); free(gmz);
+  free(ci); free(cj); free(w);
   return 0;
 }
 
@@ -323,7 +328,7 @@ int or_acoustic_adjoint(const or_acoustic_cfg *cfg, const double *c,
   const int Nz = nz + 2 * np, Nx = nx + 2 * np;
   const size_t NN = (size_t)Nz * Nx;
   double *gm_all = calloc(NN * (size_t)cfg->nshots, sizeof(double));
-  double *gstf = calloc((size_t)cfg->nshots * cfg->nt, sizeof(double));
+  double *gstf = calloc((size_t)cfg->nshots * OR_STF_STRIDE(cfg), sizeof(double));
   double *gx0 = calloc((size_t)cfg->nshots * 2, sizeof(double));
   if (!gm_all || !gstf || !gx0) {
     free(gm_all); free(gstf); free(gx0);
@@ -332,9 +337,9 @@ int or_acoustic_adjoint(const or_acoustic_cfg *cfg, const double *c,
   int err = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
   for (int s = 0; s < cfg->nshots; s++)
-    err |= acoustic_shot_adjoint(cfg, c, stf + (size_t)s * cfg->nt, x0 + 2 * s,
+    err |= acoustic_shot_adjoint(cfg, c, stf + (size_t)s * OR_STF_STRIDE(cfg), x0 + 2 * s,
                                  res + (size_t)s * cfg->nrec * cfg->nt, gm_all + NN * s,
-                                 gstf + (size_t)s * cfg->nt, gx0 + 2 * s) != 0;
+                                 gstf + (size_t)s * OR_STF_STRIDE(cfg), gx0 + 2 * s) != 0;
   if (!err) {
     if (grad_c) {
       /* sum over shots, transpose of the edge replication into the CPML,
@@ -352,7 +357,7 @@ int or_acoustic_adjoint(const or_acoustic_cfg *cfg, const double *c,
           }
       for (size_t k = 0; k < (size_t)nz * nx; k++) grad_c[k] *= 2.0 * c[k];
     }
-    if (grad_stf) memcpy(grad_stf, gstf, sizeof(double) * (size_t)cfg->nshots * cfg->nt);
+    if (grad_stf) memcpy(grad_stf, gstf, sizeof(double) * (size_t)cfg->nshots * OR_STF_STRIDE(cfg));
     if (grad_x0) memcpy(grad_x0, gx0, sizeof(double) * 2 * (size_t)cfg->nshots);
   }
   free(gm_all); free(gstf); free(gx0);

@@ -16,7 +16,11 @@
 /* Source weights of one shot on the padded grid: a point source puts
  * 1/(dx dz) on the nearest cell; the Gaussian source spreads
  * g(t)/(2 pi s^2) exp(-|x-x0|^2/(2 s^2)) with s = dx/2 over +-3 cells
- * (Earthquake Location section, Gaussian re-parameterisation). */
+ * (Earthquake Location section, Gaussian re-parameterisation); a line source
+ * (the paper's plane-wave sources, FWI section: a line of sources fired with
+ * delays) puts 1/(dx dz) on each of line_len cells of one row, from the cell
+ * nearest x0, each cell with its own time function. The arrays hold at least
+ * OR_MAX_SUPPORT(cfg) entries. */
 static int FN(source_support)(const or_acoustic_cfg *cfg, const REAL *x0s,
                               int *ci, int *cj, int *nsup, REAL *w) {
   double xr = RE(x0s[0]), zr = RE(x0s[1]);
@@ -28,6 +32,14 @@ static int FN(source_support)(const or_acoustic_cfg *cfg, const REAL *x0s,
     if (ic < 0 || ic >= Nz || jc < 0 || jc >= Nx) return -1;
     ci[0] = ic; cj[0] = jc; w[0] = 1.0 / (cfg->dx * cfg->dz);
     *nsup = 1;
+    return 0;
+  }
+  if (cfg->src_kind == 3) {
+    if (cfg->line_len < 1 || ic < 0 || ic >= Nz || jc < 0 || jc + cfg->line_len > Nx) return -1;
+    for (int q = 0; q < cfg->line_len; q++) {
+      ci[q] = ic; cj[q] = jc + q; w[q] = 1.0 / (cfg->dx * cfg->dz);
+    }
+    *nsup = cfg->line_len;
     return 0;
   }
   double sg = 0.5 * cfg->dx;
@@ -95,8 +107,10 @@ static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
     for (int jX = 0; jX < Nx; jX++)
       mhz[(size_t)h * Nx + jX] = 0.5 * (m[(size_t)h * Nx + jX] + m[(size_t)(h + 1) * Nx + jX]);
 
-  int ci[49], cj[49], nsup = 0;
-  REAL w[49];
+  const int cap = OR_MAX_SUPPORT(cfg);
+  int *ci = malloc(sizeof(int) * cap), *cj = malloc(sizeof(int) * cap), nsup = 0;
+  REAL *w = malloc(sizeof(REAL) * cap);
+  const int line = cfg->src_kind == 3;
   int rc = FN(source_support)(cfg, x0s, ci, cj, &nsup, w);
 
 #define U_AT(arr, iZ, jX) (((iZ) >= 0 && (iZ) < Nz && (jX) >= 0 && (jX) < Nx) ? (arr)[(size_t)(iZ) * Nx + (jX)] : (REAL)0)
@@ -144,9 +158,9 @@ static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
         REAL r = hx + zetx[id] + hz + zetz[id];
         un[id] = 2.0 * u[id] - up[id] + dt * dt * r;
       }
-    /* source term F_n = dt^2 f(t_n) */
+    /* source term F_n = dt^2 f(t_n) (a line source: each cell its own f) */
     for (int q = 0; q < nsup; q++)
-      un[(size_t)ci[q] * Nx + cj[q]] += dt * dt * w[q] * stf[n];
+      un[(size_t)ci[q] * Nx + cj[q]] += dt * dt * w[q] * (line ? stf[(size_t)n * nsup + q] : stf[n]);
     /* receivers sample u^{n+1} */
     for (int r = 0; r < cfg->nrec; r++) {
       int iZ = cfg->rec_iz[r] + np, jX = cfg->rec_ix[r] + np;
@@ -163,5 +177,6 @@ static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
   free(ax); free(bx); free(axh); free(bxh); free(az); free(bz); free(azh); free(bzh);
   free(m); free(mhx); free(mhz); free(u); free(up); free(un);
   free(psix); free(psiz); free(zetx); free(zetz); free(qx); free(qz);
+  free(ci); free(cj); free(w);
   return rc;
 }

@@ -39,6 +39,7 @@
 static int el_check(const or_acoustic_cfg *cfg) {
   if (cfg->nz < 1 || cfg->nx < 1 || cfg->nt < 1 || cfg->nshots < 0 || cfg->npml < 0) return -1;
   if (cfg->order != 4 && cfg->order != 8) return -1;
+  if (cfg->src_kind != 0 && cfg->src_kind != 1) return -1;  /* point or Gaussian moment tensors only */
   for (int r = 0; r < cfg->nrec; r++)
     if (cfg->rec_iz[r] < 0 || cfg->rec_iz[r] >= cfg->nz || cfg->rec_ix[r] < 0 || cfg->rec_ix[r] >= cfg->nx)
       return -1;

@@ -29,12 +29,19 @@ typedef struct {
   int order;          /* spatial order: 4 or 8 (staggered first derivatives) */
   int nt;             /* number of time steps */
   int nshots;
-  int src_kind;       /* 0 = point source on the nearest cell, 1 = Gaussian */
+  int src_kind;       /* 0 = point source on the nearest cell, 1 = Gaussian,
+                         3 = line of line_len cells along one row (acoustic) */
   int nrec;
   double dz, dx, dt;
   double pml_R, pml_vmax, pml_f0;  /* CPML constants (not differentiated) */
   const int *rec_iz, *rec_ix;      /* [nrec] physical cell indices */
+  int line_len;       /* src_kind 3: cells of the line; stf is then [nshots][nt][line_len] */
 } or_acoustic_cfg;
+
+/* Largest source support: the 7 x 7 Gaussian or a line of line_len cells. */
+#define OR_MAX_SUPPORT(cfg) ((cfg)->src_kind == 3 ? ((cfg)->line_len > 49 ? (cfg)->line_len : 49) : 49)
+/* Values of stf per shot: nt, or nt * line_len for a line source. */
+#define OR_STF_STRIDE(cfg) ((size_t)(cfg)->nt * ((cfg)->src_kind == 3 ? (size_t)(cfg)->line_len : 1))
 
 /* Staggered first-derivative coefficients a_1..a_N (N = order/2). */
 int or_fd_coeffs(int order, double *a);
@@ -46,7 +53,9 @@ void or_cpml_profile(int n_phys, int npml, double h, double dt, double R,
                      double *b);
 
 /* Forward modelling: seis[s][r][n] = u^{n+1}(receiver r) for shot s.
- * c [nz][nx], stf [nshots][nt], x0 [nshots][2] = (x, z) metres. */
+ * c [nz][nx], stf [nshots][nt] (line source: [nshots][nt][line_len], one
+ * time function per cell), x0 [nshots][2] = (x, z) metres (line source: the
+ * first cell of the line and its row). */
 int or_acoustic_forward(const or_acoustic_cfg *cfg, const double *c,
                         const double *stf, const double *x0, double *seis);
 

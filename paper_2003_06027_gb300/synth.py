@@ -179,6 +179,48 @@ def random_acoustic(seed: int, nz: int, nx: int, nt: int, nshots: int, order: in
     )
 
 
+def plane_wave(wavelet: np.ndarray, dt: float, theta_deg: float, c_ref: float, line_len: int,
+               dx: float) -> np.ndarray:
+    """Per-cell time functions [nt][line_len] of a plane wave launched from a
+    line of cells (the paper's plane-wave sources: a line of sources fired
+    with delays): cell q fires the sampled ``wavelet`` delayed by
+    tau_q = q dx sin(theta) / c_ref, shifted so that the earliest cell fires
+    at delay 0, by linear interpolation between samples (zero before t = 0)."""
+    nt = wavelet.shape[0]
+    tau = np.arange(line_len) * dx * np.sin(np.radians(theta_deg)) / c_ref
+    tau -= tau.min()
+    t = np.arange(nt)[:, None] * dt - tau[None, :]
+    k = np.floor(t / dt).astype(np.int64)
+    f = t / dt - k
+    w = np.concatenate([wavelet.astype(np.float64), [0.0]])
+    k0 = np.clip(k, -1, nt - 1)
+    k1 = np.clip(k + 1, -1, nt - 1)
+    v0 = np.where(k0 >= 0, w[np.maximum(k0, 0)], 0.0)
+    v1 = np.where((k1 >= 0) & (k + 1 < nt), w[np.maximum(k1, 0)], 0.0)
+    return ((1.0 - f) * v0 + f * v1).astype(np.float32)
+
+
+def line_source_problem(seed: int, nz: int, nx: int, nt: int, nshots: int, order: int, npml: int,
+                        line_len: int, nrec: int = 7, dx: float = 10.0, dt: float = 1e-3,
+                        f0: float = 15.0, rec_on_line: bool = True) -> dict:
+    """Small seeded heterogeneous problem with plane-wave (line) sources: shot s
+    fires a line of ``line_len`` cells along one row with a Ricker plane wave
+    at angle -30 + 20 s degrees (as the paper's bottom plane waves); some
+    receivers lie on the source row when ``rec_on_line``."""
+    d = random_acoustic(seed, nz, nx, nt, nshots, order, npml, src_kind=0, nrec=nrec, dx=dx, dt=dt, f0=f0)
+    rng = np.random.default_rng(seed + 1)
+    rows = rng.integers(0, nz, nshots)
+    cols = rng.integers(0, nx - line_len + 1, nshots)
+    wav = ricker(f0, dt, nt)
+    stf = np.stack([plane_wave(wav, dt, -30.0 + 20.0 * s, 2200.0, line_len, dx) for s in range(nshots)])
+    x0 = np.stack([cols * dx, rows * dx], axis=1).astype(np.float32)
+    if rec_on_line and nrec >= 2:
+        d["rec_iz"][:2] = rows[0]
+        d["rec_ix"][:2] = [cols[0], cols[0] + line_len - 1]
+    d.update(name=f"acoustic-line-{nz}x{nx}-o{order}-nt{nt}", src_kind=3, line_len=line_len, stf=stf, x0=x0)
+    return d
+
+
 def double_couple(phi: np.ndarray) -> np.ndarray:
     """2D double-couple moment tensors (Mxx, Mzz, Mxz) = (-sin 2phi, sin 2phi, cos 2phi)."""
     return np.stack([-np.sin(2 * phi), np.sin(2 * phi), np.cos(2 * phi)], axis=1)
