@@ -54,7 +54,7 @@ typedef enum {
 } fwi_status;
 
 enum { FWI_ACOUSTIC = 0, FWI_ELASTIC = 1 };
-enum { FWI_SRC_POINT = 0, FWI_SRC_GAUSSIAN = 1, FWI_SRC_MOMENT = 2 };
+enum { FWI_SRC_POINT = 0, FWI_SRC_GAUSSIAN = 1, FWI_SRC_MOMENT = 2, FWI_SRC_LINE = 3 };
 
 typedef struct fwi_ctx fwi_ctx; /* opaque; owns only its device workspace */
 
@@ -89,13 +89,21 @@ typedef struct {
  *       ignored for FWI_ACOUSTIC. Elastic sources inject sigma <- sigma -
  *       dt M g(t_n) w into the stresses at step n (g is the moment rate), with
  *       point or Gaussian weights w on the normal-stress grid and on the shear
- *       grid (offset by half a cell); FWI_SRC_MOMENT means Gaussian weights. */
+ *       grid (offset by half a cell); FWI_SRC_MOMENT means Gaussian weights.
+ *       FWI_SRC_LINE (acoustic): the paper's plane-wave sources, as a row of
+ *       line_len physical cells starting at the cell nearest x0 (x of the
+ *       first cell, z of the row), each cell with weight 1/(dx dz) and its own
+ *       time function: stf is then [nshots][nt][line_len] and grad_stf of
+ *       fwi_misfit_grad has that shape too (grad_x0 must be NULL). A plane
+ *       wave is the same wavelet delayed linearly along the row.
+ * line_len  cells of a FWI_SRC_LINE source (ignored otherwise). */
 typedef struct {
   int32_t nshots;
   int32_t kind;
   const float *x0;
   const float *stf;
   const float *mt;
+  int32_t line_len;
 } fwi_sources;
 
 /* Receivers, shared by all shots: physical cell indices iz[r], ix[r]. An

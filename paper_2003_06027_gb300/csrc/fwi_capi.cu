@@ -42,6 +42,12 @@ cudaError_t launch_selftest_wait(int* status, unsigned long long* waited_ns, cud
 cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
                                      float* gout, long long n, cudaStream_t st);
 cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st);
+cudaError_t launch_line_prep(int S, int L, const float* x0, const Grid& g, float dx, float dz, int* line_cell,
+                             int* box, int* status, cudaStream_t st);
+cudaError_t launch_line_inject(int S, int L, int n, int nt, float scale, const float* amp, const int* line_cell,
+                               float* u, const Grid& g, const int* rec_cell, int nrec, float* seis, cudaStream_t st);
+cudaError_t launch_line_grad(int S, int L, int n, int nt, float scale, const int* line_cell, const float* lam,
+                             const Grid& g, float* gamp, cudaStream_t st);
 cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st);
 cudaError_t launch_grad_c(const double* G, const Grid& g, const float* c, float* grad, cudaStream_t st);
 cudaError_t launch_src_grad(const float* part, int S, int nt, int nslots, double scale, const float* stf,
@@ -89,12 +95,14 @@ bool fd_coeffs(int order, float a[4]) {
 struct Plan {
   Grid g{};
   int S = 0, nt = 0, nrec = 0, K = 0, nseg = 0, N = 0, kind = 0;
+  int L = 0;  // cells of a line source (FWI_SRC_LINE), else 0
   bool grad = false;
   int tablen = 0;
   // base
   float *m = nullptr, *tab = nullptr, *c = nullptr, *stf = nullptr, *x0 = nullptr, *src_w = nullptr;
   int *src_box = nullptr, *rec_in = nullptr, *rec_cell = nullptr, *rec_key = nullptr, *tstart = nullptr;
   int *tcursor = nullptr, *tlist = nullptr;
+  int* line_cell = nullptr;  // [S][2] padded (row, first column) of a line source
   float *u = nullptr;  // [2][S][slice]: pair of wavefield buffers
   float *psix[2] = {}, *psiz[2] = {}, *zetx = nullptr, *zetz = nullptr, *seis = nullptr;
   int* status = nullptr;
@@ -123,7 +131,9 @@ void layout(Plan& P, char* base) {
   P.m = (float*)take((size_t)P.g.slice * 4);
   P.tab = (float*)take((size_t)8 * P.tablen * 4);
   P.c = (float*)take((size_t)P.g.nz * P.g.nx * 4);
-  P.stf = (float*)take((size_t)P.S * P.nt * 4);
+  const size_t stf_len = (size_t)P.S * P.nt * (size_t)std::max(1, P.L);  // [S][nt] or [S][nt][L]
+  P.stf = (float*)take(stf_len * 4);
+  P.line_cell = (int*)take((size_t)P.S * 2 * 4);
   P.x0 = (float*)take((size_t)P.S * 2 * 4);
   P.src_w = (float*)take((size_t)P.S * SRC_W * SRC_W * 4);
   P.src_box = (int*)take((size_t)P.S * 2 * 4);
@@ -161,7 +171,7 @@ void layout(Plan& P, char* base) {
     P.Jpart = (double*)take((size_t)MISFIT_BLOCKS * 8);
     P.J = (double*)take(8);
     P.grad_c = (float*)take((size_t)P.g.nz * P.g.nx * 4);
-    P.gstf = (float*)take((size_t)P.S * P.nt * 4);
+    P.gstf = (float*)take(stf_len * 4);
     P.gx0 = (float*)take((size_t)P.S * 2 * 4);
     P.ckpt = (float*)take(field * 6 * (size_t)P.nseg);
     P.slot = (float*)take(field * 2 * (size_t)P.K);  // per step: p_x, p_z
@@ -198,8 +208,10 @@ fwi_status validate(const fwi_model* M, const fwi_sources* Sv, const fwi_receive
     return fail(FWI_EINVAL, "CPML needs 0 < pml_R < 1, pml_vmax > 0, pml_f0 >= 0");
   if (!M->vp) return fail(FWI_EINVAL, "vp must not be NULL");
   if (Sv->nshots < 1) return fail(FWI_EINVAL, "nshots must be >= 1");
-  if (Sv->kind != FWI_SRC_POINT && Sv->kind != FWI_SRC_GAUSSIAN)
-    return fail(FWI_EINVAL, "acoustic sources are FWI_SRC_POINT or FWI_SRC_GAUSSIAN");
+  if (Sv->kind != FWI_SRC_POINT && Sv->kind != FWI_SRC_GAUSSIAN && Sv->kind != FWI_SRC_LINE)
+    return fail(FWI_EINVAL, "acoustic sources are FWI_SRC_POINT, FWI_SRC_GAUSSIAN or FWI_SRC_LINE");
+  if (Sv->kind == FWI_SRC_LINE && (Sv->line_len < 1 || Sv->line_len > M->nx))
+    return fail(FWI_EINVAL, "a line source needs 1 <= line_len <= nx");
   if (!Sv->x0 || !Sv->stf) return fail(FWI_EINVAL, "x0 and stf must not be NULL");
   if (R->nrec < 0 || (R->nrec > 0 && (!R->iz || !R->ix))) return fail(FWI_EINVAL, "bad receiver arrays");
   if (nt < 1) return fail(FWI_EINVAL, "nt must be >= 1");
@@ -228,6 +240,7 @@ void make_plan(Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_rec
   P.nrec = R->nrec;
   P.N = M->order / 2;
   P.kind = Sv->kind;
+  P.L = Sv->kind == FWI_SRC_LINE ? Sv->line_len : 0;
   P.grad = grad;
   P.K = grad ? K : 0;
   P.nseg = grad ? (nt + K - 1) / K : 0;
@@ -236,8 +249,8 @@ void make_plan(Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_rec
 
 std::string plan_key(const Plan& P) {
   char b[256];
-  snprintf(b, sizeof b, "%d %d %d %d %lld %d %d %d %d %d %d", P.g.Nz, P.g.Nx, P.g.pitch, P.g.rows, P.g.slice,
-           P.S, P.nt, P.nrec, P.K, (int)P.grad, P.tablen);
+  snprintf(b, sizeof b, "%d %d %d %d %lld %d %d %d %d %d %d %d", P.g.Nz, P.g.Nx, P.g.pitch, P.g.rows, P.g.slice,
+           P.S, P.nt, P.nrec, P.K, (int)P.grad, P.tablen, P.L);
   return b;
 }
 
@@ -256,7 +269,7 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
                    float dt, cudaStream_t st, AcuStep& p) {
   const Grid& g = P.g;
   CK(cudaMemcpyAsync(P.c, M->vp, (size_t)g.nz * g.nx * 4, cudaMemcpyDefault, st));
-  CK(cudaMemcpyAsync(P.stf, Sv->stf, (size_t)P.S * P.nt * 4, cudaMemcpyDefault, st));
+  CK(cudaMemcpyAsync(P.stf, Sv->stf, (size_t)P.S * P.nt * std::max(1, P.L) * 4, cudaMemcpyDefault, st));
   CK(cudaMemcpyAsync(P.x0, Sv->x0, (size_t)P.S * 2 * 4, cudaMemcpyDefault, st));
   if (P.nrec > 0) {
     CK(cudaMemcpyAsync(P.rec_in, R->iz, (size_t)P.nrec * 4, cudaMemcpyDefault, st));
@@ -275,7 +288,10 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
                         T + 3 * L, st));
   LK(1, launch_cpml_tables(g.nz, g.npml, g.Nz, L, M->dz, dt, M->pml_R, M->pml_vmax, M->pml_f0, T + 4 * L, T + 5 * L,
                         T + 6 * L, T + 7 * L, st));
-  LK(1, launch_src_prep(P.S, P.kind, P.x0, g, M->dx, M->dz, P.src_box, P.src_w, P.status, st));
+  if (P.L > 0)
+    LK(1, launch_line_prep(P.S, P.L, P.x0, g, M->dx, M->dz, P.line_cell, P.src_box, P.status, st));
+  else
+    LK(1, launch_src_prep(P.S, P.kind, P.x0, g, M->dx, M->dz, P.src_box, P.src_w, P.status, st));
   LK(1, launch_rec_csr(P.nrec, P.rec_in, P.rec_in + P.nrec, g, P.rec_cell, P.rec_key, P.tstart, P.tcursor, P.tlist,
                        P.status, st));
 
@@ -615,9 +631,17 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   if ((v = make_groups(ctx, P.S, st, gr, ctx->fwd_groups ? ctx->fwd_groups : MAX_GROUPS)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[0], st));
   if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
+  const size_t fieldf = (size_t)P.S * P.g.slice;
+  const float lscale = (float)((double)dt * dt / ((double)M->dx * M->dz));
   for (int n = 0; n < nt; n++) {
     set_fwd_state(P, p, n);
-    for (int g = 0; g < gr.G; g++) LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
+    for (int g = 0; g < gr.G; g++) {
+      LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
+      if (P.L > 0)
+        LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
+                                 P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * fieldf + gr.s0[g] * P.g.slice,
+                                 P.g, P.rec_cell, P.nrec, P.seis + (size_t)gr.s0[g] * P.nrec * nt, gr.st[g]));
+    }
   }
   if ((v = join(ctx, gr, st)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[1], st));
@@ -658,7 +682,9 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   if (!observed && R->nrec > 0) return fail(FWI_EINVAL, "observed must not be NULL");
   if (!misfit) return fail(FWI_EINVAL, "misfit must not be NULL");
   if (K < 1 || K > nt) return fail(FWI_EINVAL, "ckpt_every must be in [1, nt]");
+  if (Sv->kind == FWI_SRC_LINE && grad_x0) return fail(FWI_EINVAL, "a line source has no position gradient");
   CK(cudaSetDevice(ctx->device));
+  const float lscale = (float)((double)dt * dt / ((double)M->dx * M->dz));
   Plan P;
   make_plan(P, M, Sv, R, nt, K, true);
   v = ensure_arena(ctx, P, st);
@@ -694,7 +720,13 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
                              cudaMemcpyDeviceToDevice, gr.st[g]));
     }
     set_fwd_state(P, p, n);
-    for (int g = 0; g < gr.G; g++) LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
+    for (int g = 0; g < gr.G; g++) {
+      LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
+      if (P.L > 0)
+        LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
+                                 P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
+                                 P.rec_cell, P.nrec, P.seis + (size_t)gr.s0[g] * P.nrec * nt, gr.st[g]));
+    }
   }
   if ((v = join(ctx, gr, st)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[1], st));
@@ -708,6 +740,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   AcuStep pa = p;
   set_adjoint_weights(pa, p);
   LK(1, launch_adj_init(pa, P.lam + (nt & 1) * field, P.hx + (nt & 1) * field, P.hz + (nt & 1) * field, st));
+  if (P.L > 0) LK(1, launch_line_grad(P.S, P.L, nt - 1, nt, lscale, P.line_cell, P.lam + (nt & 1) * field, P.g, P.gstf, st));
   for (int seg = P.nseg - 1; seg >= 0; seg--) {
     const int n0 = seg * K, n1 = std::min(nt, n0 + K);
     const float* ck = P.ckpt + (size_t)seg * 6 * field;
@@ -724,8 +757,13 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       set_fwd_state(P, p, n);
       p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
       p.slot_pz = p.slot_px + field;
-      for (int g = 0; g < gr.G; g++)
+      for (int g = 0; g < gr.G; g++) {
         LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, gr.st[g]));
+        if (P.L > 0)
+          LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
+                                   P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
+                                   P.rec_cell, P.nrec, nullptr, gr.st[g]));
+      }
     }
     if ((v = join(ctx, gr, st)) != FWI_OK) return v;
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
@@ -745,8 +783,13 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       pa.pz_out = P.pz[n & 1];
       pa.hx_out = P.hx + (n & 1) * field;
       pa.hz_out = P.hz + (n & 1) * field;
-      for (int g = 0; g < gra.G; g++)
+      for (int g = 0; g < gra.G; g++) {
         LK(1, launch_acu_adj(group_view(pa, P, gra.s0[g], gra.n[g]), maps, gra.st[g]));
+        if (P.L > 0 && n >= 1)  // lambda_n is complete: the derivative for amp[n - 1]
+          LK(1, launch_line_grad(gra.n[g], P.L, n - 1, nt, lscale, P.line_cell + 2 * gra.s0[g],
+                                 P.lam + (n & 1) * field + gra.s0[g] * sl, P.g, P.gstf + (size_t)gra.s0[g] * nt * P.L,
+                                 gra.st[g]));
+      }
     }
     if ((v = join(ctx, gra, st)) != FWI_OK) return v;
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
@@ -757,7 +800,9 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     LK(1, launch_grad_c(P.G, P.g, P.c, P.grad_c, st));
     CK(cudaMemcpyAsync(grad, P.grad_c, (size_t)P.g.nz * P.g.nx * 4, cudaMemcpyDefault, st));
   }
-  if (grad_stf || grad_x0) {
+  if (P.L > 0) {
+    if (grad_stf) CK(cudaMemcpyAsync(grad_stf, P.gstf, (size_t)P.S * nt * P.L * 4, cudaMemcpyDefault, st));
+  } else if (grad_stf || grad_x0) {
     LK(1, launch_src_grad(P.src_part, P.S, nt, SRC_SLOTS, (double)dt * dt, P.stf, 1.0 / (0.25 * (double)M->dx * M->dx), P.kind,
                        P.gstf, P.gx0, st));
     if (grad_stf) CK(cudaMemcpyAsync(grad_stf, P.gstf, (size_t)P.S * nt * 4, cudaMemcpyDefault, st));

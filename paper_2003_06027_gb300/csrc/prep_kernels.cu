@@ -364,6 +364,61 @@ __global__ void k_src_grad(const float* __restrict__ part, int S, int nt, int ns
 
 // ---------------------------------------------------------------------------
 // launchers
+// Line sources (the paper's plane-wave sources: a row of L cells, each firing
+// its own time function amp[s][n][q] with weight 1/(dx dz)). The step kernels
+// see no source box for them (box = -1); the line is injected by its own small
+// kernel after each step and read back by another after each adjoint step.
+//
+// k_line_prep: padded (row, first column) of each shot's line from x0 = (x of
+// the first cell, z of the row) in metres; every cell must be physical.
+__global__ void k_line_prep(int S, int L, const float* __restrict__ x0, Grid g, float dx, float dz, int* line_cell,
+                            int* box, int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  const double xr = x0[2 * s], zr = x0[2 * s + 1];
+  const int j0 = (int)llround(xr / (double)dx) + g.npml;
+  const int i0 = (int)llround(zr / (double)dz) + g.npml;
+  const bool ok = isfinite(xr) && isfinite(zr) && i0 >= g.npml && i0 < g.npml + g.nz && j0 >= g.npml &&
+                  j0 + L <= g.npml + g.nx;
+  line_cell[2 * s] = ok ? i0 : -1;
+  line_cell[2 * s + 1] = ok ? j0 : -1;
+  box[2 * s] = -1;  // no box source for the step kernels
+  box[2 * s + 1] = -1;
+  if (!ok) atomicOr(status, ST_BADSRC);
+}
+
+// u^{n+1}(row, j0 + q) += scale * amp[s][n][q] for the S shots of a group
+// (shot s of the group at u + s * slice); with `seis`, the samples already
+// recorded from those cells at step n get the same increment (a receiver on
+// the line records u^{n+1} with its source term, as the recursion defines it).
+__global__ void k_line_inject(int S, int L, int n, int nt, float scale, const float* __restrict__ amp,
+                              const int* __restrict__ line_cell, float* u, long long slice, long long off0, int pitch,
+                              const int* __restrict__ rec_cell, int nrec, float* seis) {
+  const int s = blockIdx.y;
+  const int i0 = line_cell[2 * s], j0 = line_cell[2 * s + 1];
+  if (i0 < 0) return;
+  const float* a = amp + ((long long)s * nt + n) * L;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L + (seis ? nrec : 0); k += gridDim.x * blockDim.x) {
+    if (k < L) {
+      u[(long long)s * slice + off0 + (long long)i0 * pitch + j0 + k] += scale * a[k];
+    } else {
+      const int r = k - L, ri = rec_cell[2 * r], rj = rec_cell[2 * r + 1];
+      if (ri == i0 && rj >= j0 && rj < j0 + L) seis[((long long)s * nrec + r) * nt + n] += scale * a[rj - j0];
+    }
+  }
+}
+
+// gamp[s][n][q] = scale * lambda(row, j0 + q): the derivative of the misfit with
+// respect to amp[s][n][q] (lambda the adjoint of u^{n+1}, complete).
+__global__ void k_line_grad(int S, int L, int n, int nt, float scale, const int* __restrict__ line_cell,
+                            const float* __restrict__ lam, long long slice, long long off0, int pitch, float* gamp) {
+  const int s = blockIdx.y;
+  const int i0 = line_cell[2 * s], j0 = line_cell[2 * s + 1];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < L; k += gridDim.x * blockDim.x)
+    gamp[((long long)s * nt + n) * L + k] =
+        i0 < 0 ? 0.f : scale * lam[(long long)s * slice + off0 + (long long)i0 * pitch + j0 + k];
+}
+
 cudaError_t launch_pad_model(const float* c, const Grid& g, float* m, cudaStream_t st) {
   k_pad_model_sq<<<304, 256, 0, st>>>(c, g, m);
   return cudaGetLastError();
@@ -372,6 +427,24 @@ cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h
                                double vmax, double f0, float* a, float* b, float* ah, float* bh,
                                cudaStream_t st) {
   k_cpml_tables<<<(len + 255) / 256, 256, 0, st>>>(n_phys, npml, Npad, len, h, dt, R, vmax, f0, a, b, ah, bh);
+  return cudaGetLastError();
+}
+cudaError_t launch_line_prep(int S, int L, const float* x0, const Grid& g, float dx, float dz, int* line_cell,
+                             int* box, int* status, cudaStream_t st) {
+  k_line_prep<<<(S + 127) / 128, 128, 0, st>>>(S, L, x0, g, dx, dz, line_cell, box, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_line_inject(int S, int L, int n, int nt, float scale, const float* amp, const int* line_cell,
+                               float* u, const Grid& g, const int* rec_cell, int nrec, float* seis, cudaStream_t st) {
+  const int work = L + (seis ? nrec : 0);
+  k_line_inject<<<dim3((work + 255) / 256, S), 256, 0, st>>>(S, L, n, nt, scale, amp, line_cell, u, g.slice, g.off0,
+                                                           g.pitch, rec_cell, nrec, seis);
+  return cudaGetLastError();
+}
+cudaError_t launch_line_grad(int S, int L, int n, int nt, float scale, const int* line_cell, const float* lam,
+                             const Grid& g, float* gamp, cudaStream_t st) {
+  k_line_grad<<<dim3((L + 255) / 256, S), 256, 0, st>>>(S, L, n, nt, scale, line_cell, lam, g.slice, g.off0, g.pitch,
+                                                       gamp);
   return cudaGetLastError();
 }
 cudaError_t launch_src_prep(int S, int kind, const float* x0, const Grid& g, float dx, float dz, int* box,

@@ -19,7 +19,7 @@ import numpy as np
 from . import build as _build
 
 FWI_ACOUSTIC, FWI_ELASTIC = 0, 1
-FWI_SRC_POINT, FWI_SRC_GAUSSIAN, FWI_SRC_MOMENT = 0, 1, 2
+FWI_SRC_POINT, FWI_SRC_GAUSSIAN, FWI_SRC_MOMENT, FWI_SRC_LINE = 0, 1, 2, 3
 STATUS = {0: "FWI_OK", 1: "FWI_EINVAL", 2: "FWI_ECFL", 3: "FWI_ENOMEM", 4: "FWI_ECUDA",
           5: "FWI_EUNSTABLE", 6: "FWI_ETIMEOUT", 7: "FWI_ENOTIMPL"}
 
@@ -40,7 +40,7 @@ class _Model(ctypes.Structure):
 
 class _Sources(ctypes.Structure):
     _fields_ = [("nshots", ctypes.c_int32), ("kind", ctypes.c_int32), ("x0", ctypes.c_void_p),
-                ("stf", ctypes.c_void_p), ("mt", ctypes.c_void_p)]
+                ("stf", ctypes.c_void_p), ("mt", ctypes.c_void_p), ("line_len", ctypes.c_int32)]
 
 
 class _Receivers(ctypes.Structure):
@@ -206,17 +206,23 @@ class _Call:
                  src_kind):
         self.c = _arr(c, np.float32)
         self.stf = _arr(stf, np.float32)
-        if self.stf.ndim == 1:
+        # a line source (plane wave) has one time function per cell: stf [S][nt][line_len]
+        self.line_len = 0
+        if src_kind == FWI_SRC_LINE:
+            if self.stf.ndim == 2:
+                self.stf = self.stf.reshape(1, *self.stf.shape)
+            self.line_len = int(self.stf.shape[2])
+        elif self.stf.ndim == 1:
             self.stf = self.stf.reshape(1, -1)
         self.x0 = _arr(x0, np.float32).reshape(-1, 2)
         self.iz = _arr(rec_iz, np.int32).reshape(-1)
         self.ix = _arr(rec_ix, np.int32).reshape(-1)
         nz, nx = self.c.shape
-        self.S, self.nt = self.stf.shape
+        self.S, self.nt = self.stf.shape[:2]
         self.nrec = self.iz.shape[0]
         self.model = _Model(FWI_ACOUSTIC, nz, nx, dz, dx, order, npml, pml_R, pml_vmax, pml_f0,
                             _ptr(self.c), None, None)
-        self.src = _Sources(self.S, src_kind, _ptr(self.x0), _ptr(self.stf), None)
+        self.src = _Sources(self.S, src_kind, _ptr(self.x0), _ptr(self.stf), None, self.line_len)
         self.rec = _Receivers(self.nrec, _ptr(self.iz), _ptr(self.ix))
 
 
@@ -253,6 +259,8 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
     """(J, dJ/dc, dJ/dstf, dJ/dx0, seis) of J = 1/2 sum (d - d_obs)^2 (fwi_misfit_grad).
 
     ``out`` may hold preallocated outputs {"misfit", "grad", "grad_stf", "grad_x0", "seis"}.
+    With ``src_kind=FWI_SRC_LINE`` (plane-wave sources) stf and dJ/dstf are
+    [S][nt][line_len] and dJ/dx0 is None.
     """
     a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
     obs = _arr(observed, np.float32)
@@ -262,9 +270,10 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
         out["misfit"] = _empty_like_place(ref, (1,), np.float64)
     if want_grad and "grad" not in out:
         out["grad"] = _empty_like_place(ref, tuple(a.c.shape))
+    line = src_kind == FWI_SRC_LINE
     if want_src and "grad_stf" not in out:
-        out["grad_stf"] = _empty_like_place(ref, (a.S, a.nt))
-    if want_src and "grad_x0" not in out:
+        out["grad_stf"] = _empty_like_place(ref, (a.S, a.nt, a.line_len) if line else (a.S, a.nt))
+    if want_src and not line and "grad_x0" not in out:  # a line source has no position gradient
         out["grad_x0"] = _empty_like_place(ref, (a.S, 2))
     if want_seis and "seis" not in out:
         out["seis"] = _empty_like_place(ref, (a.S, a.nrec, a.nt))

@@ -276,3 +276,49 @@ def test_bounded_wait_gives_up_and_context_survives(fwi_lib):
     d = synth.random_acoustic(23, 20, 24, 60, 1, 4, 4, nrec=4)
     do = oracle.acoustic_forward(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
     assert rel(gpu_forward(d), do) <= SEIS_TOL
+
+
+# ------------------------------------------------------------- line (plane-wave) sources
+LINE_CASES = [  # seed, nz, nx, nt, shots, order, npml, line_len, K
+    (21, 30, 70, 160, 3, 8, 8, 40, 40),
+    (22, 40, 33, 130, 5, 4, 6, 33, 50),
+]
+
+
+@pytest.mark.parametrize("case", LINE_CASES, ids=[f"{c[1]}x{c[2]}-o{c[5]}-L{c[7]}-S{c[4]}" for c in LINE_CASES])
+def test_line_source_parity(fwi_lib, case):
+    """Plane-wave (line) sources against the oracle: seismograms (receivers on
+    the source row included), misfit, dJ/dc and the per-cell dJ/damp, with
+    several shot groups and checkpoint segments."""
+    from paper_2003_06027_gb300 import fwi
+
+    seed, nz, nx, nt, S, order, npml, L, K = case
+    d = synth.line_source_problem(seed, nz, nx, nt, S, order, npml, line_len=L, nrec=9)
+    g = dict(_geom(d), line_len=L)
+    kw = fwi.problem_kwargs(d)
+    args = [_cuda(d["c"]), _cuda(d["stf"]), _cuda(d["x0"]), _cuda(d["rec_iz"]), _cuda(d["rec_ix"])]
+    seis = fwi.forward(*args, **kw).cpu().numpy()
+    so = oracle.acoustic_forward(g, np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(seis, so) <= SEIS_TOL, rel(seis, so)
+    obs = oracle.acoustic_forward(g, np.float64(d["c"]) * 1.03, np.float64(d["stf"]), np.float64(d["x0"]))
+    J, gc, gs, gx, _ = fwi.misfit_grad(*args, _cuda(obs), ckpt_every=K, **kw)
+    Jo, gco, gso, _ = oracle.acoustic_misfit_grad(g, np.float64(d["c"]), np.float64(d["stf"]),
+                                                  np.float64(d["x0"]), obs)
+    assert gx is None and gs.shape == d["stf"].shape
+    assert abs(float(J[0]) - Jo) <= GRAD_TOL * Jo
+    assert rel(gc.cpu().numpy(), gco) <= GRAD_TOL, rel(gc.cpu().numpy(), gco)
+    assert rel(gs.cpu().numpy(), gso) <= GRAD_TOL, rel(gs.cpu().numpy(), gso)
+
+
+def test_line_source_errors(fwi_lib):
+    from paper_2003_06027_gb300 import fwi
+
+    d = synth.line_source_problem(23, 20, 30, 40, 2, 4, 5, line_len=10)
+    kw = fwi.problem_kwargs(d)
+    x0 = d["x0"].copy()
+    x0[1, 0] = (d["nx"] - 5) * d["dx"]  # the line would leave the physical grid
+    with pytest.raises(fwi.FwiError):
+        fwi.forward(_cuda(d["c"]), _cuda(d["stf"]), _cuda(x0), _cuda(d["rec_iz"]), _cuda(d["rec_ix"]), **kw)
+    # the context stays usable
+    seis = fwi.forward(_cuda(d["c"]), _cuda(d["stf"]), _cuda(d["x0"]), _cuda(d["rec_iz"]), _cuda(d["rec_ix"]), **kw)
+    assert np.isfinite(seis.cpu().numpy()).all()
