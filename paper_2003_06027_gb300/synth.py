@@ -221,6 +221,31 @@ def line_source_problem(seed: int, nz: int, nx: int, nt: int, nshots: int, order
     return d
 
 
+def plane_wave_survey(nz: int = 60, nx: int = 100, nt: int = 700, dx: float = 10.0, dt: float = 1e-3,
+                      f0: float = 12.0, angles=(-30.0, -10.0, 10.0, 30.0), order: int = 8, npml: int = 20,
+                      seed: int = 31) -> dict:
+    """A small instance of the paper's plane-wave FWI setting (a layered crust
+    with an elliptical anomaly, plane waves from the bottom at -30, -10, 10, 30
+    degrees, receivers along the surface; the paper gives no sizes, so these
+    are this generator's): true model with a slow ellipse in two layers, start
+    model = the layers without the ellipse; one shot per angle, each a line
+    source along the deepest physical row firing a Ricker plane wave."""
+    rng = np.random.default_rng(seed)
+    z = np.arange(nz)[:, None] * dx
+    x = np.arange(nx)[None, :] * dx
+    layers = np.where(z < nz * dx * 0.5, 2200.0, 2800.0) + 0.0 * x
+    ex, ez = nx * dx * (0.45 + 0.1 * rng.random()), nz * dx * 0.45
+    ell = ((x - ex) / (0.18 * nx * dx)) ** 2 + ((z - ez) / (0.12 * nz * dx)) ** 2 < 1.0
+    true = np.where(ell, layers - 300.0, layers).astype(np.float32)
+    wav = ricker(f0, dt, nt)
+    stf = np.stack([plane_wave(wav, dt, a, 2800.0, nx, dx) for a in angles])
+    x0 = np.stack([np.zeros(len(angles)), np.full(len(angles), (nz - 1) * dx)], axis=1).astype(np.float32)
+    return dict(name=f"acoustic-planewave-{nz}x{nx}-nt{nt}", nz=nz, nx=nx, dz=dx, dx=dx, dt=dt, nt=nt, order=order,
+                npml=npml, pml_R=1e-3, pml_vmax=4500.0, pml_f0=f0, src_kind=3, line_len=nx, c=layers.astype(np.float32),
+                c_true=true, stf=stf, x0=x0, rec_iz=np.full(nx // 2, 1, np.int32),
+                rec_ix=np.arange(0, nx, 2, dtype=np.int32), ckpt_every=100)
+
+
 def double_couple(phi: np.ndarray) -> np.ndarray:
     """2D double-couple moment tensors (Mxx, Mzz, Mxz) = (-sin 2phi, sin 2phi, cos 2phi)."""
     return np.stack([-np.sin(2 * phi), np.sin(2 * phi), np.cos(2 * phi)], axis=1)
