@@ -35,6 +35,9 @@ GEMMS = [  # M, N, K, splits, bias+relu, row padding of A and B
     (77, 300, 16, 1, False, 16),
     (144, 32, 5000, 8, False, 0),
     (27, 5, 442, 3, False, 24),
+    (1, 1, 1, 1, True, 0),       # degenerate: one row, one column, one term (all zero-filled to the tile)
+    (129, 17, 8, 1, False, 0),   # one row past a tile; N one past a multiple of 16
+    (5, 256, 70, 2, False, 0),   # N at the single-tile maximum; split K with a ragged last block
 ]
 
 
