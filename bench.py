@@ -52,6 +52,15 @@ BYTES = {"fwd": (16, 16), "store": (24, 16), "adj": (32, 16)}
 # fluxes instead of wavefields, recomputation), so these fractions are lower
 # than the per-kernel ones.
 PATH_BYTES = {"acoustic_forward": 16, "acoustic_gradient": 48, "elastic_forward": 52, "elastic_gradient": 168}
+# Elastic step kernels, per cell-step of one step (velocity and stress kernels together):
+#   forward:   vel 36 B (read sxx, szz, sxz, vx, vz, bx, bz; write vx, vz) + str 44 B (read vx, vz, sxx, szz,
+#              sxz, lambda, lambda+2mu, mu_xz; write sxx, szz, sxz)                                        80 B
+#   recompute: + the stored forces fx, fz and strains ex, ez, exz                                          100 B
+#   adjoint:   str 76 B (adjoint stresses read through TMA, adjoint velocities r/w, lambda, lambda+2mu,
+#              mu_xz, stored strains, 3 partials r/w) + vel 64 B (adjoint velocities read, adjoint
+#              stresses r/w, bx, bz, stored forces, 2 partials r/w)                                        140 B
+# plus 32 B per cell and CPML axis (two memory variables r/w in each of the two kernels).
+ELA_BYTES = {"fwd": (80, 32), "store": (100, 32), "adj": (140, 32)}
 
 
 def padded(d):
@@ -186,11 +195,18 @@ def elastic_measure(steps):
     torch.cuda.synchronize()
     fms = e0.elapsed_time(e1) / steps
     peak, kind = load_peaks()
-    path = {k: {"bytes_per_cell_step": b, "GBps": b * cs / (t / 1e3) / 1e9, "frac": b * cs / (t / 1e3) / 1e9 / peak,
-                "peak_source": kind} for k, b, t in (("forward", PATH_BYTES["elastic_forward"], fms),
-                                                    ("gradient", PATH_BYTES["elastic_gradient"], ms))}
+    path = {k: {"bytes_per_cell_step": b, "GBps": b * cs / (tm / 1e3) / 1e9, "frac": b * cs / (tm / 1e3) / 1e9 / peak,
+                "peak_source": kind} for k, b, tm in (("forward", PATH_BYTES["elastic_forward"], fms),
+                                                     ("gradient", PATH_BYTES["elastic_gradient"], ms))}
+    cells = S * Nz * Nx
+    pml_pairs = S * (Nz * 2 * d["npml"] + Nx * 2 * d["npml"])
+    kern = {}
+    for k, tms in (("fwd", t.fwd_step_ms), ("store", t.store_step_ms), ("adj", t.adj_step_ms)):
+        base, per_pml = ELA_BYTES[k]
+        gbs = (base * cells + per_pml * pml_pairs) / (tms / 1e3) / 1e9
+        kern[k] = {"step_ms": tms, "algorithmic_GBps": gbs, "frac": gbs / peak, "peak_source": kind}
     return {"workload": d["name"] + "-ckpt100", "value": cs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
-            "path_roofline": path,
+            "path_roofline": path, "kernels": kern,
             "forward": {"value": cs / (fms / 1e3) / 1e9, "ms_per_step": fms},
             "cell_steps_per_step": cs, "step_launch_ms": {"fwd_vel+str": t.fwd_step_ms,
                                                           "recompute_vel+str": t.store_step_ms,
