@@ -60,7 +60,7 @@ class AcousticCfg(ctypes.Structure):
         ("dz", ctypes.c_double), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
         ("pml_R", ctypes.c_double), ("pml_vmax", ctypes.c_double), ("pml_f0", ctypes.c_double),
         ("rec_iz", ctypes.POINTER(ctypes.c_int)), ("rec_ix", ctypes.POINTER(ctypes.c_int)),
-        ("line_len", ctypes.c_int),
+        ("line_len", ctypes.c_int), ("op", ctypes.c_int),
     ]
 
 
@@ -126,7 +126,7 @@ class _Geom:
             pml_vmax=g.get("pml_vmax", 4500.0), pml_f0=g.get("pml_f0", 10.0),
             rec_iz=self.iz.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
             rec_ix=self.ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-            line_len=g.get("line_len", 0),
+            line_len=g.get("line_len", 0), op=g.get("op", 0),
         )
 
 
@@ -145,7 +145,8 @@ def acoustic_forward(g: dict, c, stf, x0, complex_step: bool = False) -> np.ndar
     """Seismograms [nshots][nrec][nt] of the acoustic recursion.
 
     ``g`` holds the geometry (nz, nx, npml, order, nt, dz, dx, dt, src_kind,
-    pml_R, pml_vmax, pml_f0, rec_iz, rec_ix, and line_len for a line source);
+    pml_R, pml_vmax, pml_f0, rec_iz, rec_ix, line_len for a line source, op: 0
+    the divergence form div(c^2 grad u), 1 the c^2 Laplacian form);
     c is [nz][nx], stf [S][nt] ([S][nt][line_len] for a line source, src_kind
     3), x0 [S][2] = (x, z) in metres. With ``complex_step`` every input may be
     complex and the map is evaluated in complex arithmetic.

@@ -120,6 +120,7 @@ static int check_cfg(const or_acoustic_cfg *cfg) {
   if (cfg->order != 4 && cfg->order != 8 && cfg->order != 2 && cfg->order != 6) return -1;
   if (cfg->src_kind != 0 && cfg->src_kind != 1 && cfg->src_kind != 3) return -1;
   if (cfg->src_kind == 3 && cfg->line_len < 1) return -1;
+  if (cfg->op != 0 && cfg->op != 1) return -1;
   for (int r = 0; r < cfg->nrec; r++)
     if (cfg->rec_iz[r] < 0 || cfg->rec_iz[r] >= cfg->nz || cfg->rec_ix[r] < 0 || cfg->rec_ix[r] >= cfg->nx)
       return -1;
@@ -214,6 +215,8 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
   double *hbx = calloc(NN, sizeof(double)), *hbz = calloc(NN, sizeof(double));
   double *gbx = calloc(NN, sizeof(double)), *gbz = calloc(NN, sizeof(double));
   double *gmx = calloc(NN, sizeof(double)), *gmz = calloc(NN, sizeof(double));
+  double *gmc = calloc(NN, sizeof(double));  /* op 1: dJ/dm at the cells */
+  const int op = cfg->op;
 
   const int cap = OR_MAX_SUPPORT(cfg);
   int *ci = malloc(sizeof(int) * cap), *cj = malloc(sizeof(int) * cap), nsup = 0;
@@ -246,7 +249,9 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
     for (int iZ = 0; iZ < Nz; iZ++)
       for (int jX = 0; jX < Nx; jX++) {
         size_t id = (size_t)iZ * Nx + jX;
-        double rb = dt * dt * lam1[id];
+        /* op 1: u^{n+1} += dt^2 m r, so dJ/dm += dt^2 lam r and rbar = dt^2 m lam */
+        if (op) gmc[id] += dt * dt * lam1[id] * pxs[(size_t)n * NN + id];
+        double rb = dt * dt * (op ? m[id] : 1.0) * lam1[id];
         double t = zx[id] + rb;
         hbx[id] = rb + ax[jX] * t;
         zx[id] = bx[jX] * t;
@@ -261,8 +266,8 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
         double qb = 0;
         for (int k = 1; k <= N; k++) qb += a[k - 1] * (AT(hbx, iZ, h - k + 1) - AT(hbx, iZ, h + k));
         qb /= dx;
-        gmx[id] += qb * pxs[(size_t)n * NN + id];
-        double pb = mhx[id] * qb;
+        if (!op) gmx[id] += qb * pxs[(size_t)n * NN + id];
+        double pb = op ? qb : mhx[id] * qb;
         double t = px_[id] + pb;
         gbx[id] = pb + axh[h] * t;
         px_[id] = bxh[h] * t;
@@ -273,8 +278,8 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
         double qb = 0;
         for (int k = 1; k <= N; k++) qb += a[k - 1] * (AT(hbz, h - k + 1, jX) - AT(hbz, h + k, jX));
         qb /= dz;
-        gmz[id] += qb * pzs[(size_t)n * NN + id];
-        double pb = mhz[id] * qb;
+        if (!op) gmz[id] += qb * pzs[(size_t)n * NN + id];
+        double pb = op ? qb : mhz[id] * qb;
         double t = pz_[id] + pb;
         gbz[id] = pb + azh[h] * t;
         pz_[id] = bzh[h] * t;
@@ -309,13 +314,13 @@ static int acoustic_shot_adjoint(const or_acoustic_cfg *cfg, const double *c,
       if (jX < Nx - 1) g += 0.5 * gmx[(size_t)iZ * Nx + jX];
       if (iZ - 1 >= 0) g += 0.5 * gmz[(size_t)(iZ - 1) * Nx + jX];
       if (iZ < Nz - 1) g += 0.5 * gmz[(size_t)iZ * Nx + jX];
-      gm_pad[(size_t)iZ * Nx + jX] = g;
+      gm_pad[(size_t)iZ * Nx + jX] = op ? gmc[(size_t)iZ * Nx + jX] : g;
     }
 
   free(pxs); free(pzs);
   free(ax); free(bx); free(axh); free(bxh); free(az); free(bz); free(azh); free(bzh);
   free(m); free(mhx); free(mhz); free(lam1); free(lam0); free(zx); free(zz);
-  free(px_); free(pz_); free(hbx); free(hbz); free(gbx); free(gbz); free(gmx); free(gmz);
+  free(px_); free(pz_); free(hbx); free(hbz); free(gbx); free(gbz); free(gmx); free(gmz); free(gmc);
   free(ci); free(cj); free(w);
   return 0;
 }

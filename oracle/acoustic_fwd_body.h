@@ -59,7 +59,9 @@ static int FN(source_support)(const or_acoustic_cfg *cfg, const REAL *x0s,
 
 /* One shot of forward modelling. If px_store / pz_store are given, the
  * quantities p_x = D+x u + psi_x and p_z (the factors that multiply the
- * half-point coefficient m = c^2) of every step n are saved, nt x size. */
+ * half-point coefficient m = c^2) of every step n are saved, nt x size; with
+ * op = 1 (c^2 Laplacian form) px_store receives instead r = D-x p_x + zeta_x +
+ * D-z p_z + zeta_z at the cells, the factor that multiplies m there. */
 static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
                              const REAL *stf, const REAL *x0s, REAL *seis,
                              REAL *px_store, REAL *pz_store) {
@@ -127,8 +129,8 @@ static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
         size_t id = (size_t)iZ * Nx + h;
         psix[id] = bxh[h] * psix[id] + axh[h] * g;
         REAL p = g + psix[id];
-        if (px_store) px_store[(size_t)n * NN + id] = p;
-        qx[id] = mhx[id] * p;
+        if (px_store && !cfg->op) px_store[(size_t)n * NN + id] = p;
+        qx[id] = cfg->op ? p : mhx[id] * p;
       }
     /* z: the same along the depth axis */
     for (int h = 0; h < Nz - 1; h++)
@@ -139,8 +141,8 @@ static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
         size_t id = (size_t)h * Nx + jX;
         psiz[id] = bzh[h] * psiz[id] + azh[h] * g;
         REAL p = g + psiz[id];
-        if (pz_store) pz_store[(size_t)n * NN + id] = p;
-        qz[id] = mhz[id] * p;
+        if (pz_store && !cfg->op) pz_store[(size_t)n * NN + id] = p;
+        qz[id] = cfg->op ? p : mhz[id] * p;
       }
     /* divergence with its own memory variables, then the leapfrog update */
     for (int iZ = 0; iZ < Nz; iZ++)
@@ -156,7 +158,10 @@ static int FN(acoustic_shot)(const or_acoustic_cfg *cfg, const REAL *c,
         zetx[id] = bx[jX] * zetx[id] + ax[jX] * hx;
         zetz[id] = bz[iZ] * zetz[id] + az[iZ] * hz;
         REAL r = hx + zetx[id] + hz + zetz[id];
-        un[id] = 2.0 * u[id] - up[id] + dt * dt * r;
+        /* c^2 Laplacian form: the coefficient multiplies the whole operator at the
+         * cell, and r (the Laplacian with its CPML terms) is what the gradient needs */
+        if (cfg->op && px_store) px_store[(size_t)n * NN + id] = r;
+        un[id] = 2.0 * u[id] - up[id] + dt * dt * (cfg->op ? m[id] * r : r);
       }
     /* source term F_n = dt^2 f(t_n) (a line source: each cell its own f) */
     for (int q = 0; q < nsup; q++)

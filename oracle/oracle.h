@@ -36,6 +36,8 @@ typedef struct {
   double pml_R, pml_vmax, pml_f0;  /* CPML constants (not differentiated) */
   const int *rec_iz, *rec_ix;      /* [nrec] physical cell indices */
   int line_len;       /* src_kind 3: cells of the line; stf is then [nshots][nt][line_len] */
+  int op;             /* acoustic operator: 0 = div(c^2 grad u) (the paper's Eq. acoustic, staggered
+                         divergence form, c^2 at half points), 1 = c^2 (Laplacian u), c^2 at cells */
 } or_acoustic_cfg;
 
 /* Largest source support: the 7 x 7 Gaussian or a line of line_len cells. */
