@@ -54,6 +54,14 @@ typedef enum {
 } fwi_status;
 
 enum { FWI_ACOUSTIC = 0, FWI_ELASTIC = 1 };
+/* Acoustic operator: the paper's divergence form div(c^2 grad u) (Eq.
+ * acoustic; staggered, c^2 averaged to the half points), or the c^2 Laplacian
+ * form c^2 (D-x D+x u + D-z D+z u) with c^2 at the cells (same derivatives and
+ * CPML). They coincide in homogeneous media and differ at interfaces (normal
+ * reflection (c1 - c2)/(c1 + c2) against (c2 - c1)/(c2 + c1)). The Laplacian
+ * form runs on plain per-point kernels, not on the tiled kernels of the
+ * divergence form. */
+enum { FWI_OP_DIVERGENCE = 0, FWI_OP_LAPLACIAN = 1 };
 enum { FWI_SRC_POINT = 0, FWI_SRC_GAUSSIAN = 1, FWI_SRC_MOMENT = 2, FWI_SRC_LINE = 3 };
 
 typedef struct fwi_ctx fwi_ctx; /* opaque; owns only its device workspace */
@@ -75,6 +83,7 @@ typedef struct {
   int32_t npml;
   float pml_R, pml_vmax, pml_f0;
   const float *vp, *vs, *rho;
+  int32_t op;  /* acoustic operator: FWI_OP_DIVERGENCE (0) or FWI_OP_LAPLACIAN (1) */
 } fwi_model;
 
 /* Sources, one per shot.

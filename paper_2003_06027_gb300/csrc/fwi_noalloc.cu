@@ -111,6 +111,7 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
     return err(FWI_EINVAL, "CPML needs 0 < pml_R < 1, pml_vmax > 0, pml_f0 >= 0");
   if (Sv->nshots < 1 || (Sv->kind != FWI_SRC_POINT && Sv->kind != FWI_SRC_GAUSSIAN))
     return err(FWI_EINVAL, "bad sources");
+  if (M->op != FWI_OP_DIVERGENCE) return err(FWI_ENOTIMPL, "only the divergence-form operator runs without allocation");
   if (nt < 1 || !(dt > 0.f)) return err(FWI_EINVAL, "nt must be >= 1 and dt > 0");
   if (R->nrec < 0) return err(FWI_EINVAL, "nrec must be >= 0");
   if (!on_device(M->vp) || !on_device(Sv->stf) || !on_device(Sv->x0) ||

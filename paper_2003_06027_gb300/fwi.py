@@ -20,6 +20,7 @@ from . import build as _build
 
 FWI_ACOUSTIC, FWI_ELASTIC = 0, 1
 FWI_SRC_POINT, FWI_SRC_GAUSSIAN, FWI_SRC_MOMENT, FWI_SRC_LINE = 0, 1, 2, 3
+FWI_OP_DIVERGENCE, FWI_OP_LAPLACIAN = 0, 1
 STATUS = {0: "FWI_OK", 1: "FWI_EINVAL", 2: "FWI_ECFL", 3: "FWI_ENOMEM", 4: "FWI_ECUDA",
           5: "FWI_EUNSTABLE", 6: "FWI_ETIMEOUT", 7: "FWI_ENOTIMPL"}
 
@@ -35,7 +36,7 @@ class _Model(ctypes.Structure):
                 ("dz", ctypes.c_float), ("dx", ctypes.c_float), ("order", ctypes.c_int32),
                 ("npml", ctypes.c_int32), ("pml_R", ctypes.c_float), ("pml_vmax", ctypes.c_float),
                 ("pml_f0", ctypes.c_float), ("vp", ctypes.c_void_p), ("vs", ctypes.c_void_p),
-                ("rho", ctypes.c_void_p)]
+                ("rho", ctypes.c_void_p), ("op", ctypes.c_int32)]
 
 
 class _Sources(ctypes.Structure):
@@ -203,7 +204,7 @@ class _Call:
     """Holds the marshalled arguments (and keeps their buffers alive)."""
 
     def __init__(self, c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0,
-                 src_kind):
+                 src_kind, op=FWI_OP_DIVERGENCE):
         self.c = _arr(c, np.float32)
         self.stf = _arr(stf, np.float32)
         # a line source (plane wave) has one time function per cell: stf [S][nt][line_len]
@@ -221,16 +222,16 @@ class _Call:
         self.S, self.nt = self.stf.shape[:2]
         self.nrec = self.iz.shape[0]
         self.model = _Model(FWI_ACOUSTIC, nz, nx, dz, dx, order, npml, pml_R, pml_vmax, pml_f0,
-                            _ptr(self.c), None, None)
+                            _ptr(self.c), None, None, int(op))
         self.src = _Sources(self.S, src_kind, _ptr(self.x0), _ptr(self.stf), None, self.line_len)
         self.rec = _Receivers(self.nrec, _ptr(self.iz), _ptr(self.ix))
 
 
 def forward(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
-            pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, out=None, stream=None,
+            pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, out=None, stream=None,
             device=None):
     """Seismograms [nshots][nrec][nt] (fwi_forward). nt = stf.shape[-1]."""
-    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
     if out is None:
         out = _empty_like_place(a.c, (a.S, a.nrec, a.nt))
     dev = _device(a.c, device)
@@ -240,12 +241,12 @@ def forward(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1
 
 
 def forward_noalloc(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
-                    pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, out=None, stream=None):
+                    pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, out=None, stream=None):
     """fwi_forward_noalloc: the forward map without any device allocation by
     the library (for callers whose device memory is fully managed by their own
     allocator). All arrays must be CUDA tensors on the current device; ``out``
     (the seismograms) is allocated here by torch when not given."""
-    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
     if out is None:
         out = _empty_like_place(a.c, (a.S, a.nrec, a.nt))
     _check(library().fwi_forward_noalloc(ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec),
@@ -254,7 +255,7 @@ def forward_noalloc(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20,
 
 
 def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20,
-                pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, ckpt_every=100,
+                pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, ckpt_every=100,
                 want_grad=True, want_src=True, want_seis=False, out=None, stream=None, device=None):
     """(J, dJ/dc, dJ/dstf, dJ/dx0, seis) of J = 1/2 sum (d - d_obs)^2 (fwi_misfit_grad).
 
@@ -262,7 +263,7 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
     With ``src_kind=FWI_SRC_LINE`` (plane-wave sources) stf and dJ/dstf are
     [S][nt][line_len] and dJ/dx0 is None.
     """
-    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
     obs = _arr(observed, np.float32)
     out = dict(out or {})
     ref = a.c
@@ -298,12 +299,13 @@ class GradGraph:
     of the recorded launches (0: default). Recording runs the evaluation once."""
 
     def __init__(self, c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
-                 pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, ckpt_every=100, want_src=False,
+                 pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, ckpt_every=100,
+                 want_src=False,
                  groups=(0, 0)):
         for t in (c, stf, x0, rec_iz, rec_ix, observed):
             if not (_is_torch(t) and t.is_cuda):
                 raise ValueError("GradGraph takes CUDA tensors only")
-        self._a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+        self._a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
         a = self._a
         self._obs = _arr(observed, np.float32)
         self.device = a.c.device.index
@@ -445,5 +447,8 @@ def selftest_wait_timeout(device: int = 0):
 
 def problem_kwargs(d: dict) -> dict:
     """Keyword arguments of forward()/misfit_grad() from a synth problem dict."""
-    return dict(dx=d["dx"], dz=d["dz"], dt=d["dt"], order=d["order"], npml=d["npml"],
-                pml_R=d["pml_R"], pml_vmax=d["pml_vmax"], pml_f0=d["pml_f0"], src_kind=d["src_kind"])
+    kw = dict(dx=d["dx"], dz=d["dz"], dt=d["dt"], order=d["order"], npml=d["npml"],
+              pml_R=d["pml_R"], pml_vmax=d["pml_vmax"], pml_f0=d["pml_f0"], src_kind=d["src_kind"])
+    if d.get("op", 0):
+        kw["op"] = d["op"]
+    return kw

@@ -322,3 +322,54 @@ def test_line_source_errors(fwi_lib):
     # the context stays usable
     seis = fwi.forward(_cuda(d["c"]), _cuda(d["stf"]), _cuda(d["x0"]), _cuda(d["rec_iz"]), _cuda(d["rec_ix"]), **kw)
     assert np.isfinite(seis.cpu().numpy()).all()
+
+
+# ------------------------------------------------------------- c^2 Laplacian operator
+LAP_CASES = [  # nz, nx, nt, shots, order, npml, kind, seed, K
+    (37, 71, 150, 2, 4, 10, 0, 41, 50),
+    (30, 44, 140, 3, 8, 9, 1, 42, 47),
+]
+
+
+@pytest.mark.parametrize("case", LAP_CASES, ids=[f"{c[0]}x{c[1]}-o{c[4]}-k{c[6]}" for c in LAP_CASES])
+def test_laplacian_operator_parity(fwi_lib, case):
+    """FWI_OP_LAPLACIAN (u_tt = c^2 Laplacian u) against the oracle's op 1:
+    seismograms, misfit, dJ/dc, dJ/dstf and (Gaussian sources) dJ/dx0 over
+    several checkpoint segments; and it differs from the divergence form."""
+    nz, nx, nt, S, order, npml, kind, seed, K = case
+    d = dict(synth.random_acoustic(seed, nz, nx, nt, S, order, npml, src_kind=kind, nrec=9), op=1)
+    d["rec_iz"][:2] = [0, nz - 1]
+    dg = gpu_forward(d)
+    g = dict(_geom(d), op=1)
+    do = oracle.acoustic_forward(g, np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(dg, do) <= SEIS_TOL, rel(dg, do)
+    d0 = oracle.acoustic_forward(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(d0, do) > 100 * SEIS_TOL  # the two operators are different maps in this medium
+    rng = np.random.default_rng(seed)
+    obs = (rng.standard_normal(dg.shape) * np.abs(do).max() * 0.3).astype(np.float32)
+    Jg, gg, gsg, gxg, _ = gpu_misfit_grad(d, obs, K=K)
+    Jo, go, gso, gxo = oracle.acoustic_misfit_grad(g, np.float64(d["c"]), np.float64(d["stf"]),
+                                                   np.float64(d["x0"]), np.float64(obs))
+    assert abs(Jg - Jo) <= SEIS_TOL * Jo
+    assert rel(gg, go) <= GRAD_TOL, rel(gg, go)
+    assert rel(gsg, gso) <= GRAD_TOL, rel(gsg, gso)
+    if kind == 1:
+        assert rel(gxg, gxo) <= GRAD_TOL, (gxg, gxo)
+
+
+def test_laplacian_operator_line_source(fwi_lib):
+    from paper_2003_06027_gb300 import fwi
+
+    d = dict(synth.line_source_problem(43, 26, 40, 120, 2, 8, 6, line_len=20, nrec=7), op=1)
+    g = dict(_geom(d), line_len=20, op=1)
+    kw = fwi.problem_kwargs(d)
+    args = [_cuda(d["c"]), _cuda(d["stf"]), _cuda(d["x0"]), _cuda(d["rec_iz"]), _cuda(d["rec_ix"])]
+    so = oracle.acoustic_forward(g, np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(fwi.forward(*args, **kw).cpu().numpy(), so) <= SEIS_TOL
+    obs = oracle.acoustic_forward(g, np.float64(d["c"]) * 1.03, np.float64(d["stf"]), np.float64(d["x0"]))
+    J, gc, gs, _, _ = fwi.misfit_grad(*args, _cuda(obs), ckpt_every=40, **kw)
+    Jo, gco, gso, _ = oracle.acoustic_misfit_grad(g, np.float64(d["c"]), np.float64(d["stf"]),
+                                                  np.float64(d["x0"]), obs)
+    assert abs(float(J[0]) - Jo) <= GRAD_TOL * Jo
+    assert rel(gc.cpu().numpy(), gco) <= GRAD_TOL
+    assert rel(gs.cpu().numpy(), gso) <= GRAD_TOL
