@@ -670,9 +670,9 @@ fwi_status lap_step(fwi_ctx* ctx, const Plan& P, const LapStep& q, int n, float 
   const int nb = P.kind == FWI_SRC_GAUSSIAN ? SRC_W : 1;
   LK(2, launch_lap_forward_step(q, P.S, u, un, P.psix[0], P.psiz[0], P.psix[1], P.psiz[1], P.zetx, P.zetz,
                                 P.src_box, P.src_w, nb, P.stf, P.nt, n, rstore, st));
+  // the receivers are sampled after the line injection, so no seismogram fix-up is needed here
   if (P.L > 0)
-    LK(1, launch_line_inject(P.S, P.L, n, P.nt, lscale, P.stf, P.line_cell, un, P.g, P.rec_cell, P.nrec,
-                             record ? P.seis : nullptr, st));
+    LK(1, launch_line_inject(P.S, P.L, n, P.nt, lscale, P.stf, P.line_cell, un, P.g, P.rec_cell, P.nrec, nullptr, st));
   if (record) LK(1, launch_lap_record(un, P.g, P.S, P.nrec, P.nt, n, P.rec_cell, P.seis, st));
   return FWI_OK;
 }
