@@ -238,6 +238,43 @@ def acoustic_xl_measure(peak):
     return out
 
 
+def laplacian_op_measure(peak, steps=2):
+    """The c^2 Laplacian operator variant (FWI_OP_LAPLACIAN, plain per-point
+    kernels) on the headline workload: gradient and forward throughput, with
+    whole-path fractions by the same per-cell-step byte model as the
+    divergence form (48 and 16 B)."""
+    import torch
+
+    from paper_2003_06027_gb300 import fwi, synth
+
+    d = dict(synth.acoustic_fwi(), op=1)
+    kw = fwi.problem_kwargs(d)
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    c, stf, x0, iz, ix = cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
+    obs = fwi.forward(cu(d["c_true"]), stf, x0, iz, ix, **kw)
+    Nz, Nx = padded(d)
+    S, nt = d["stf"].shape
+    cs = S * Nz * Nx * nt
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, call, b in (("gradient", lambda: fwi.misfit_grad(c, stf, x0, iz, ix, obs, ckpt_every=d["ckpt_every"],
+                                                                **kw), PATH_BYTES["acoustic_gradient"]),
+                          ("forward", lambda: fwi.forward(c, stf, x0, iz, ix, out=obs, **kw),
+                           PATH_BYTES["acoustic_forward"])):
+        call()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        v = cs / (ms / 1e3) / 1e9
+        res[name] = {"value": v, "unit": UNIT, "ms_per_step": ms, "bytes_per_cell_step": b,
+                     "path_frac": b * v / peak}
+    return {"workload": d["name"] + "-c2laplacian-ckpt100", "kernels": "plain per-point (acoustic_lap.cu)", **res}
+
+
 def batched_measure(n_inst=8):
     """Batched vs plain per-shot gradient sweeps over the first ``n_inst``
     instances of the seeded uneven workload (seed 4; grids 128..512 x
@@ -538,6 +575,7 @@ def main():
     if not args.no_extra:
         res["elastic"] = elastic_measure(2)
         res["acoustic_xl"] = acoustic_xl_measure(peak)
+        res["laplacian_op"] = laplacian_op_measure(peak)
         res["batched_uneven"] = batched_measure()
         res["learned"] = learned_measure()
     if ws == 1 and not args.no_cpu_baseline:

@@ -37,6 +37,7 @@ __device__ __forceinline__ long long cell_index(const Grid& g, int s, int i, int
 
 // p = D+u + psi at the half points (i, j+1/2) and (i+1/2, j), psi updated in
 // place; zero at the half points outside [0, N-1).
+template <int N>
 __global__ void k_lap_flux(const LapStep p, const float* __restrict__ u, float* psix, float* psiz, float* qx,
                            float* qz) {
   const Grid& g = p.g;
@@ -46,14 +47,16 @@ __global__ void k_lap_flux(const LapStep p, const float* __restrict__ u, float* 
   float vx = 0.f, vz = 0.f;
   if (j < g.Nx - 1) {
     float d = 0.f;
-    for (int k = 1; k <= p.N; k++) d += p.c1x[k - 1] * (u[id + k] - u[id - k + 1]);
+#pragma unroll
+    for (int k = 1; k <= N; k++) d += p.c1x[k - 1] * (u[id + k] - u[id - k + 1]);
     const float ps = p.bxh[j + TAB_OFF] * psix[id] + p.axh[j + TAB_OFF] * d;
     psix[id] = ps;
     vx = d + ps;
   }
   if (i < g.Nz - 1) {
     float d = 0.f;
-    for (int k = 1; k <= p.N; k++) d += p.c1z[k - 1] * (u[id + (long long)k * g.pitch] - u[id - (long long)(k - 1) * g.pitch]);
+#pragma unroll
+    for (int k = 1; k <= N; k++) d += p.c1z[k - 1] * (u[id + (long long)k * g.pitch] - u[id - (long long)(k - 1) * g.pitch]);
     const float ps = p.bzh[i + TAB_OFF] * psiz[id] + p.azh[i + TAB_OFF] * d;
     psiz[id] = ps;
     vz = d + ps;
@@ -65,6 +68,7 @@ __global__ void k_lap_flux(const LapStep p, const float* __restrict__ u, float* 
 // r = D-x qx + zeta_x + D-z qz + zeta_z (zeta updated in place);
 // u^{n+1} = 2 u^n - u^{n-1} + dt^2 m r + dt^2 w g(t_n), written over u^{n-1};
 // rstore (if not null) keeps r for the gradient.
+template <int N>
 __global__ void k_lap_update(const LapStep p, const float* __restrict__ u, float* uprev, const float* __restrict__ qx,
                              const float* __restrict__ qz, float* zetx, float* zetz, const int* __restrict__ box,
                              const float* __restrict__ w, int nb, const float* __restrict__ stf, int nt, int n,
@@ -74,7 +78,8 @@ __global__ void k_lap_update(const LapStep p, const float* __restrict__ u, float
   if (j >= g.Nx) return;
   const long long id = cell_index(g, s, i, j);
   float hx = 0.f, hz = 0.f;
-  for (int k = 1; k <= p.N; k++) {
+#pragma unroll
+  for (int k = 1; k <= N; k++) {
     hx += p.c1x[k - 1] * (qx[id + k - 1] - qx[id - k]);
     hz += p.c1z[k - 1] * (qz[id + (long long)(k - 1) * g.pitch] - qz[id - (long long)k * g.pitch]);
   }
@@ -97,15 +102,42 @@ __global__ void k_lap_record(const float* __restrict__ u, const Grid g, int S, i
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= S * nrec) return;
   const int s = k / nrec, r = k - s * nrec;
-  seis[((long long)s * nrec + r) * nt + n] = u[cell_index(g, s, rec_cell[2 * r], rec_cell[2 * r + 1])];
+  const int i = rec_cell[2 * r], j = rec_cell[2 * r + 1];
+  seis[((long long)s * nrec + r) * nt + n] = i < 0 ? 0.f : u[cell_index(g, s, i, j)];  // -1: outside the grid
 }
-// lam(receiver cell r) += res[s][r][n]; receivers sharing a cell add in receiver order (one thread per shot)
-__global__ void k_lap_inject_res(float* lam, const Grid g, int S, int nrec, int nt, int n,
-                                 const int* __restrict__ rec_cell, const float* __restrict__ res) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  for (int r = 0; r < nrec; r++)
-    lam[cell_index(g, s, rec_cell[2 * r], rec_cell[2 * r + 1])] += res[((long long)s * nrec + r) * nt + n];
+// lam(receiver cell r) += res[s][r][n], one thread per (receiver, shot).
+// Receivers that share a cell are added by the first of them, in receiver
+// order, so the sum is the sequential one and the kernel deterministic. The
+// block scans the receiver cells in ascending chunks staged in shared memory:
+// every earlier receiver is seen before any later one. Receivers outside the
+// grid (cell -1, reported through the status word) are skipped.
+constexpr int INJ_THREADS = 128;
+__global__ void __launch_bounds__(INJ_THREADS) k_lap_inject_res(float* lam, const Grid g, int S, int nrec, int nt,
+                                                                int n, const int* __restrict__ rec_cell,
+                                                                const float* __restrict__ res) {
+  __shared__ int2 cells[INJ_THREADS];
+  const int s = blockIdx.y, r = blockIdx.x * INJ_THREADS + threadIdx.x;
+  const int2* rc = reinterpret_cast<const int2*>(rec_cell);
+  const int2 c = r < nrec ? rc[r] : make_int2(-1, -1);
+  bool first = c.x >= 0;
+  const float* rs = res + (long long)s * nrec * nt + n;
+  const long long id = first ? cell_index(g, s, c.x, c.y) : 0;
+  float v = first ? lam[id] + rs[(long long)r * nt] : 0.f;
+  for (int q0 = 0; q0 < nrec; q0 += INJ_THREADS) {
+    __syncthreads();  // the previous chunk is no longer read
+    if (q0 + (int)threadIdx.x < nrec) cells[threadIdx.x] = rc[q0 + threadIdx.x];
+    __syncthreads();
+    const int m = min(INJ_THREADS, nrec - q0);
+    for (int t = 0; t < m; t++) {
+      const int2 o = cells[t];
+      if (o.x == c.x && o.y == c.y) {
+        const int q = q0 + t;
+        if (q < r) first = false;                      // an earlier receiver adds this cell's samples
+        else if (q > r && first) v += rs[(long long)q * nt];
+      }
+    }
+  }
+  if (first) lam[id] = v;
 }
 
 // Adjoint of the update at the cells, given lambda_{n+1} (complete):
@@ -130,6 +162,7 @@ __global__ void k_lap_adj_update(const LapStep p, const float* __restrict__ lam1
 
 // Adjoint of the divergence and of the fluxes at the half points:
 //   qbar = -D+ hbar, gbar = qbar + a_h (P + qbar), P <- b_h (P + qbar); zero outside [0, N-1).
+template <int N>
 __global__ void k_lap_adj_flux(const LapStep p, const float* __restrict__ hbx, const float* __restrict__ hbz,
                                float* Px, float* Pz, float* gbx, float* gbz) {
   const Grid& g = p.g;
@@ -139,14 +172,16 @@ __global__ void k_lap_adj_flux(const LapStep p, const float* __restrict__ hbx, c
   float vx = 0.f, vz = 0.f;
   if (j < g.Nx - 1) {
     float q = 0.f;
-    for (int k = 1; k <= p.N; k++) q += p.c1x[k - 1] * (hbx[id - k + 1] - hbx[id + k]);
+#pragma unroll
+    for (int k = 1; k <= N; k++) q += p.c1x[k - 1] * (hbx[id - k + 1] - hbx[id + k]);
     const float t = Px[id] + q;
     vx = q + p.axh[j + TAB_OFF] * t;
     Px[id] = p.bxh[j + TAB_OFF] * t;
   }
   if (i < g.Nz - 1) {
     float q = 0.f;
-    for (int k = 1; k <= p.N; k++) q += p.c1z[k - 1] * (hbz[id - (long long)(k - 1) * g.pitch] - hbz[id + (long long)k * g.pitch]);
+#pragma unroll
+    for (int k = 1; k <= N; k++) q += p.c1z[k - 1] * (hbz[id - (long long)(k - 1) * g.pitch] - hbz[id + (long long)k * g.pitch]);
     const float t = Pz[id] + q;
     vz = q + p.azh[i + TAB_OFF] * t;
     Pz[id] = p.bzh[i + TAB_OFF] * t;
@@ -156,6 +191,7 @@ __global__ void k_lap_adj_flux(const LapStep p, const float* __restrict__ hbx, c
 }
 
 // lambda_n = 2 lambda_{n+1} - lambda_{n+2} + D+^T gbar, written over lambda_{n+2}
+template <int N>
 __global__ void k_lap_adj_lambda(const LapStep p, const float* __restrict__ lam1, float* lam2,
                                  const float* __restrict__ gbx, const float* __restrict__ gbz) {
   const Grid& g = p.g;
@@ -163,7 +199,8 @@ __global__ void k_lap_adj_lambda(const LapStep p, const float* __restrict__ lam1
   if (j >= g.Nx) return;
   const long long id = cell_index(g, s, i, j);
   float acc = 0.f;
-  for (int k = 1; k <= p.N; k++) {
+#pragma unroll
+  for (int k = 1; k <= N; k++) {
     acc += p.c1x[k - 1] * (gbx[id - k] - gbx[id + k - 1]);
     acc += p.c1z[k - 1] * (gbz[id - (long long)k * g.pitch] - gbz[id + (long long)(k - 1) * g.pitch]);
   }
@@ -200,8 +237,13 @@ dim3 grid_of(const Grid& g, int S) { return dim3((unsigned)((g.Nx + 127) / 128),
 cudaError_t launch_lap_forward_step(const LapStep& p, int S, const float* u, float* uprev, float* psix, float* psiz,
                                     float* qx, float* qz, float* zetx, float* zetz, const int* box, const float* w,
                                     int nb, const float* stf, int nt, int n, float* rstore, cudaStream_t st) {
-  k_lap_flux<<<grid_of(p.g, S), 128, 0, st>>>(p, u, psix, psiz, qx, qz);
-  k_lap_update<<<grid_of(p.g, S), 128, 0, st>>>(p, u, uprev, qx, qz, zetx, zetz, box, w, nb, stf, nt, n, rstore);
+  if (p.N == 2) {
+    k_lap_flux<2><<<grid_of(p.g, S), 128, 0, st>>>(p, u, psix, psiz, qx, qz);
+    k_lap_update<2><<<grid_of(p.g, S), 128, 0, st>>>(p, u, uprev, qx, qz, zetx, zetz, box, w, nb, stf, nt, n, rstore);
+  } else {
+    k_lap_flux<4><<<grid_of(p.g, S), 128, 0, st>>>(p, u, psix, psiz, qx, qz);
+    k_lap_update<4><<<grid_of(p.g, S), 128, 0, st>>>(p, u, uprev, qx, qz, zetx, zetz, box, w, nb, stf, nt, n, rstore);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_lap_record(const float* u, const Grid& g, int S, int nrec, int nt, int n, const int* rec_cell,
@@ -213,15 +255,21 @@ cudaError_t launch_lap_record(const float* u, const Grid& g, int S, int nrec, in
 cudaError_t launch_lap_inject_res(float* lam, const Grid& g, int S, int nrec, int nt, int n, const int* rec_cell,
                                   const float* res, cudaStream_t st) {
   if (S * nrec == 0) return cudaSuccess;
-  k_lap_inject_res<<<(S + 127) / 128, 128, 0, st>>>(lam, g, S, nrec, nt, n, rec_cell, res);
+  k_lap_inject_res<<<dim3((unsigned)((nrec + INJ_THREADS - 1) / INJ_THREADS), (unsigned)S), INJ_THREADS, 0, st>>>(
+      lam, g, S, nrec, nt, n, rec_cell, res);
   return cudaGetLastError();
 }
 cudaError_t launch_lap_adjoint_step(const LapStep& p, int S, const float* lam1, float* lam2, const float* rst,
                                     float* gpart, float* Zx, float* Zz, float* Px, float* Pz, float* hbx, float* hbz,
                                     float* gbx, float* gbz, cudaStream_t st) {
   k_lap_adj_update<<<grid_of(p.g, S), 128, 0, st>>>(p, lam1, rst, gpart, Zx, Zz, hbx, hbz);
-  k_lap_adj_flux<<<grid_of(p.g, S), 128, 0, st>>>(p, hbx, hbz, Px, Pz, gbx, gbz);
-  k_lap_adj_lambda<<<grid_of(p.g, S), 128, 0, st>>>(p, lam1, lam2, gbx, gbz);
+  if (p.N == 2) {
+    k_lap_adj_flux<2><<<grid_of(p.g, S), 128, 0, st>>>(p, hbx, hbz, Px, Pz, gbx, gbz);
+    k_lap_adj_lambda<2><<<grid_of(p.g, S), 128, 0, st>>>(p, lam1, lam2, gbx, gbz);
+  } else {
+    k_lap_adj_flux<4><<<grid_of(p.g, S), 128, 0, st>>>(p, hbx, hbz, Px, Pz, gbx, gbz);
+    k_lap_adj_lambda<4><<<grid_of(p.g, S), 128, 0, st>>>(p, lam1, lam2, gbx, gbz);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_lap_src_part(const float* lam1, const Grid& g, int S, int nt, int n, const int* box,

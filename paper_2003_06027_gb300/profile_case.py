@@ -18,6 +18,8 @@ CASES = {
     # shots, time steps, checkpoint interval
     "fwi48-nt20": (48, 20, 10),
     "fwi16-nt20": (16, 20, 10),
+    # the same with the c^2 Laplacian operator (plain per-point kernels)
+    "lap16-nt20": (16, 20, 10),
     # elastic 300 x 800 discretisation (4th order, 32 CPML cells), 8 shots
     "ela8-nt20": (8, 20, 10),
     # start-model network: training steps on a batch of 32 surveys (shots = batch, steps = Adam steps)
@@ -64,6 +66,8 @@ def main():
               f"store {t.store_step_ms * 1e3:.1f} us, adj {t.adj_step_ms * 1e3:.1f} us per step")
         return
     d = synth.acoustic_fwi(nshots=S, nt=nt)
+    if args.case.startswith("lap"):
+        d["op"] = fwi.FWI_OP_LAPLACIAN
     cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
     kw = fwi.problem_kwargs(d)
     c, stf, x0, iz, ix = cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])

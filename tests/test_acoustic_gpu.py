@@ -373,3 +373,45 @@ def test_laplacian_operator_line_source(fwi_lib):
     assert abs(float(J[0]) - Jo) <= GRAD_TOL * Jo
     assert rel(gc.cpu().numpy(), gco) <= GRAD_TOL
     assert rel(gs.cpu().numpy(), gso) <= GRAD_TOL
+
+
+def test_laplacian_operator_graph_replay_and_noalloc(fwi_lib):
+    """The c^2 Laplacian operator with receivers that share cells (their
+    residuals enter the adjoint in receiver order) against the oracle; through
+    a recorded CUDA graph it gives the direct call's misfit and gradients bit
+    for bit (same kernels, same order, one stream), on every replay; the
+    allocation-free forward refuses it with FWI_ENOTIMPL."""
+    import torch
+
+    from paper_2003_06027_gb300 import fwi
+
+    d = dict(synth.random_acoustic(44, 30, 52, 130, 2, 8, 8, src_kind=1, nrec=6), op=1)
+    for r in (3, 5):  # receivers 1, 3 and 5 record the same cell
+        d["rec_iz"][r], d["rec_ix"][r] = d["rec_iz"][1], d["rec_ix"][1]
+    kw = fwi.problem_kwargs(d)
+    g64 = dict(_geom(d), op=1)
+    args = [_cuda(d["c"]), _cuda(d["stf"]), _cuda(d["x0"]), _cuda(d["rec_iz"]), _cuda(d["rec_ix"])]
+    obs64 = oracle.acoustic_forward(g64, np.float64(d["c"]) * 1.02, np.float64(d["stf"]), np.float64(d["x0"]))
+    obs64[:, 3] *= 0.5  # different data at the shared cell: the three residuals differ
+    obs64[:, 5] *= -1.0
+    obs = _cuda(obs64.astype(np.float32))
+    J, gc, gs, gx, _ = fwi.misfit_grad(*args, obs, ckpt_every=40, **kw)
+    Jo, gco, gso, gxo = oracle.acoustic_misfit_grad(g64, np.float64(d["c"]), np.float64(d["stf"]),
+                                                    np.float64(d["x0"]), np.float64(obs64.astype(np.float32)))
+    assert abs(float(J[0]) - Jo) <= SEIS_TOL * Jo
+    assert rel(gc.cpu().numpy(), gco) <= GRAD_TOL, rel(gc.cpu().numpy(), gco)
+    assert rel(gs.cpu().numpy(), gso) <= GRAD_TOL, rel(gs.cpu().numpy(), gso)
+    assert rel(gx.cpu().numpy(), gxo) <= GRAD_TOL, (gx, gxo)
+    g = fwi.GradGraph(*args, obs, ckpt_every=40, want_src=True, **kw)
+    try:
+        for _ in range(2):
+            g.launch()
+            g.check()
+            torch.cuda.synchronize()
+            assert float(g.misfit[0]) == float(J[0])
+            assert torch.equal(g.grad, gc) and torch.equal(g.grad_stf, gs) and torch.equal(g.grad_x0, gx)
+    finally:
+        g.close()
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.forward_noalloc(*args, **kw)
+    assert e.value.status == 7
