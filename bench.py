@@ -412,6 +412,22 @@ def cpu_oracle_sample(d, shots, nt):
     return shots * Nz * Nx * nt / sec / 1e9, sec, min(oracle.num_threads(), shots)
 
 
+def cpu_uneven_sample(n_inst=4, shots=2, nt=100):
+    """The FP64 oracle on a bounded subset of the uneven batched workload: the
+    first ``n_inst`` instances (seed 4), ``shots`` shots and ``nt`` steps of
+    each. Returns (Gcell-steps/s over the subset, seconds, threads)."""
+    from paper_2003_06027_gb300 import synth
+
+    cells, sec, cores = 0, 0.0, 1
+    for i in range(n_inst):
+        d = synth.uneven_instance(4, i)
+        v, t, c = cpu_oracle_sample(d, shots, nt)
+        cells += v * 1e9 * t
+        sec += t
+        cores = max(cores, c)
+    return cells / sec / 1e9, sec, cores
+
+
 def run_reference(args, ws, rank):
     """The oracle, timed on the host cores, on bounded samples of the workload."""
     if rank != 0:
@@ -586,6 +602,16 @@ def main():
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{shots} shots x 150 steps of the same 265x665 8th-order grid, "
                                          f"FP64 oracle fwd+adjoint, {sec:.1f} s"}
+        # the oracle parallelises over shots only: a one-shot sample runs on one thread
+        v1, sec1, _ = cpu_oracle_sample(d, 1, 150)
+        res["cpu_baseline"]["single_thread"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                                "sample": f"1 shot x 150 steps of the same grid, {sec1:.1f} s"}
+        if not args.no_extra:
+            vu, secu, cu_ = cpu_uneven_sample()
+            res["cpu_baseline"]["uneven_subset"] = {
+                "value": vu, "unit": UNIT, "cores": cu_,
+                "sample": f"instances 0-3 of the uneven workload (seed 4), 2 shots x 100 steps each, {secu:.1f} s",
+                "gpu_batched_value": res["batched_uneven"]["batched"]["value"]}
     print(json.dumps(res), flush=True)
 
 
