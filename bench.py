@@ -85,10 +85,27 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_traffic(kernel_file):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source (its file and the two headers it includes) is unchanged since the
-    counters were taken."""
+def adj_source_hash():
+    """sha256 of the source the acoustic adjoint kernel is compiled from: the
+    part of csrc/acoustic_kernels.cu before the forward-step section (shared
+    definitions), its adjoint-step section (up to the bounded-wait self-test),
+    and the two headers it includes. Edits elsewhere in the file (the forward
+    kernels, the launch code) leave it unchanged."""
+    csrc = os.path.join(ROOT, "paper_2003_06027_gb300", "csrc")
+    src = open(os.path.join(csrc, "acoustic_kernels.cu")).read()
+    a = src.index("// Forward step n:")
+    b = src.index("// Adjoint step n (")
+    c = src.index("// Self-test of the bounded wait")
+    h = hashlib.sha256()
+    for part in (src[:a], src[b:c], open(os.path.join(csrc, "tma.cuh")).read(),
+                 open(os.path.join(csrc, "fwi_internal.cuh")).read()):
+        h.update(part.encode())
+    return h.hexdigest()
+
+
+def load_traffic():
+    """DRAM bytes per adjoint step from the committed ncu summary, if the
+    adjoint kernel's source is unchanged since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -97,14 +114,11 @@ def load_traffic(kernel_file):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for f in (kernel_file, "tma.cuh", "fwi_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2003_06027_gb300", "csrc", f), "rb").read())
-    if kv.get("source_sha256") != h.hexdigest():
-        return None
     try:
+        if kv.get("adj_source_sha256") != adj_source_hash():
+            return None
         return float(kv["adj_dram_bytes_per_launch_full"])
-    except (KeyError, ValueError):
+    except (KeyError, ValueError, OSError):
         return None
 
 
@@ -236,6 +250,34 @@ def acoustic_xl_measure(peak):
         gbs = launch_bytes(d, k) / (ms / 1e3) / 1e9
         out[k] = {"avg_launch_ms": ms, "algorithmic_GBps": gbs, "frac": gbs / peak}
     return out
+
+
+def store_all_measure(d, args_dev, obs, kw, value_k, steps=3):
+    """The headline gradient with ckpt_every = nt: the forward sweep stores the
+    fluxes of every step (2 nt fields in HBM) and no step is recomputed, the
+    memory-for-time trade the GPU's HBM allows on this workload."""
+    import torch
+
+    from paper_2003_06027_gb300 import fwi
+
+    Nz, Nx = padded(d)
+    S, nt = d["stf"].shape
+    cs = S * Nz * Nx * nt
+    call = lambda: fwi.misfit_grad(*args_dev, obs, ckpt_every=nt, **kw)
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pitch = -(-Nx // 64) * 64 + 16
+    rows = -(-Nz // 32) * 32 + 16
+    return {"workload": d["name"] + f"-ckpt{nt}", "value": cs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+            "stored_flux_GB": 2 * nt * S * pitch * rows * 4 / 1e9, "vs_ckpt": value_k and cs / (ms / 1e3) / 1e9 / value_k,
+            "path_frac": PATH_BYTES["acoustic_gradient"] * cs / (ms / 1e3) / 1e9 / load_peaks()[0]}
 
 
 def laplacian_op_measure(peak, steps=2):
@@ -561,7 +603,9 @@ def main():
     if rank != 0:
         return
     # roofline of the dominant kernel (largest device time per step)
-    tot = {k: statistics.mean(v) * nt for k, v in kms.items()}
+    # steps of each kernel per call: the last checkpoint segment is stored by the forward sweep, not recomputed
+    nrec_steps = ((nt + K - 1) // K - 1) * K
+    tot = {k: statistics.mean(v) * (nrec_steps if k == "store" else nt) for k, v in kms.items()}
     dom = max(tot, key=tot.get)
     peak, peak_kind = load_peaks()
     avg_ms = statistics.mean(kms[dom])
@@ -572,7 +616,7 @@ def main():
             "frac": achieved / peak, "peak_source": peak_kind, "launches_per_step": groups,
             "note": f"one step of the kernel is {groups} concurrent launches (one per shot group, own stream); "
                     "achieved = the step's algorithmic bytes / the step's duration, traffic likewise per step",
-            "traffic": load_traffic("acoustic_kernels.cu") if dom == "adj" else None,
+            "traffic": load_traffic() if dom == "adj" else None,
             "algorithmic_bytes_per_launch": launch_bytes(d, dom), "avg_launch_ms": avg_ms}
     kernels = {k: {"avg_launch_ms": statistics.mean(v), "algorithmic_GBps": launch_bytes(d, k) / (statistics.mean(v) / 1e3) / 1e9,
                    "share_of_step": tot[k] / ms} for k, v in kms.items()}
@@ -592,6 +636,7 @@ def main():
         res["elastic"] = elastic_measure(2)
         res["acoustic_xl"] = acoustic_xl_measure(peak)
         res["laplacian_op"] = laplacian_op_measure(peak)
+        res["store_all"] = store_all_measure(d, (c, stf, x0, iz, ix), obs, kw, value)
         res["batched_uneven"] = batched_measure()
         res["learned"] = learned_measure()
     if ws == 1 and not args.no_cpu_baseline:

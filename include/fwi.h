@@ -143,7 +143,11 @@ fwi_status fwi_forward(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *
 /* Misfit and exact gradient (Eqs. adjoint-backward and adjoint-gradient).
  * observed   FP32 observed seismograms, shaped like seis of fwi_forward.
  * ckpt_every wavefield checkpoint interval K (1..nt); the reverse sweep
- *            recomputes each K-step segment from its checkpoint.
+ *            recomputes each K-step segment from its checkpoint. Acoustic
+ *            calls keep the last segment's stored fields from the forward
+ *            sweep itself, so only the first ceil(nt/K) - 1 segments are
+ *            recomputed: K = nt recomputes nothing, at the cost of 2 nt
+ *            stored fields (each nshots x the tile-aligned padded grid, FP32).
  * misfit     J = 1/2 sum_{s,r,n} (seis - observed)^2, one double (host or device).
  * grad       acoustic: [nz][nx] dJ/dc; elastic: [3][nz][nx] the partial
  *            derivatives dJ/dlambda, dJ/dmu, dJ/drho (lambda = rho (vp^2 - 2 vs^2),
@@ -221,8 +225,8 @@ fwi_status fwi_forward_noalloc(const fwi_model *model, const fwi_sources *src,
  * stream. phase_ms3: [0] forward sweep (with checkpoint saves), [1] reverse
  * sweep (recompute + adjoint + folds), [2] whole call. kernel_ms3: average
  * duration of one time step of [0] the recording forward step, [1] the storing
- * forward step of the recompute (with the checkpoint restores), [2] the
- * adjoint step; 0 if none ran. Acoustic calls split the shots into up to 4
+ * forward step of the recompute (with the checkpoint restores; per recomputed
+ * step), [2] the adjoint step; 0 if none ran. Acoustic calls split the shots into up to 4
  * groups whose launches run concurrently on internal streams (forked from and
  * joined to the call's stream), so one step is one launch per group, and the
  * step time includes launch gaps. launches: number of kernels the call

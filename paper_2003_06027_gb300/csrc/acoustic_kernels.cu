@@ -859,7 +859,7 @@ namespace {
 
 std::mutex g_init_mu;
 unsigned long long g_inited = 0;  // bit per device
-int g_grid_fwd[64][2][3], g_grid_adj[64][2];
+int g_grid_fwd[64][2][4], g_grid_adj[64][2];
 
 template <typename K>
 cudaError_t setup_kernel(K k, int smem, int* grid) {
@@ -885,9 +885,11 @@ cudaError_t ensure_init(int* dev_out) {
   if ((e = setup_kernel(acu_fwd_step<2, false, false>, fs, &g_grid_fwd[dev][0][0])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_fwd_step<2, true, false>, fs, &g_grid_fwd[dev][0][1])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_fwd_step<2, false, true>, fs, &g_grid_fwd[dev][0][2])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<2, true, true>, fs, &g_grid_fwd[dev][0][3])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_fwd_step<4, false, false>, fs, &g_grid_fwd[dev][1][0])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_fwd_step<4, true, false>, fs, &g_grid_fwd[dev][1][1])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_fwd_step<4, false, true>, fs, &g_grid_fwd[dev][1][2])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<4, true, true>, fs, &g_grid_fwd[dev][1][3])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_adj_step<2>, as, &g_grid_adj[dev][0])) != cudaSuccess) return e;
   if ((e = setup_kernel(acu_adj_step<4>, as, &g_grid_adj[dev][1])) != cudaSuccess) return e;
   g_inited |= 1ull << dev;
@@ -924,16 +926,18 @@ cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, b
   int dev;
   cudaError_t e = ensure_init(&dev);
   if (e != cudaSuccess) return e;
-  const int v = record ? 1 : (store ? 2 : 0);
+  const int v = (record ? 1 : 0) + (store ? 2 : 0);
   const int o = p.N == 2 ? 0 : 1;
   const int grid = std::min(p.ntiles, g_grid_fwd[dev][o][v]);
   const size_t smem = sizeof(FwdSmem);
   if (p.N == 2) {
-    if (record) acu_fwd_step<2, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    if (record && store) acu_fwd_step<2, true, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    else if (record) acu_fwd_step<2, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
     else if (store) acu_fwd_step<2, false, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
     else acu_fwd_step<2, false, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
   } else {
-    if (record) acu_fwd_step<4, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    if (record && store) acu_fwd_step<4, true, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    else if (record) acu_fwd_step<4, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
     else if (store) acu_fwd_step<4, false, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
     else acu_fwd_step<4, false, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
   }

@@ -741,10 +741,14 @@ fwi_status lap_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   const float lscale = (float)((double)dt * dt / ((double)M->dx * M->dz));
   const size_t field = (size_t)P.S * P.g.slice;
   ensure_events(ctx, P.nseg);
+  // the forward sweep keeps r^n of the last segment itself, so that segment is never recomputed
+  const int nlast = (P.nseg - 1) * K;
   CK(cudaEventRecord(ctx->ev[0], st));
   for (int n = 0; n < nt; n++) {
-    if (n % K == 0 && (v = lap_save(P, n, P.ckpt + (size_t)(n / K) * 6 * field, st)) != FWI_OK) return v;
-    if ((v = lap_step(ctx, P, q, n, lscale, true, nullptr, st)) != FWI_OK) return v;
+    if (n % K == 0 && n < nlast && (v = lap_save(P, n, P.ckpt + (size_t)(n / K) * 6 * field, st)) != FWI_OK)
+      return v;
+    float* keep = n >= nlast ? P.slot + (size_t)(n - nlast) * 2 * field : nullptr;
+    if ((v = lap_step(ctx, P, q, n, lscale, true, keep, st)) != FWI_OK) return v;
   }
   CK(cudaEventRecord(ctx->ev[1], st));
   if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
@@ -755,9 +759,12 @@ fwi_status lap_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   for (int seg = P.nseg - 1; seg >= 0; seg--) {
     const int n0 = seg * K, n1 = std::min(nt, n0 + K);
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
-    if ((v = lap_restore(P, n0, P.ckpt + (size_t)seg * 6 * field, st)) != FWI_OK) return v;
-    for (int n = n0; n < n1; n++)
-      if ((v = lap_step(ctx, P, q, n, lscale, false, P.slot + (size_t)(n - n0) * 2 * field, st)) != FWI_OK) return v;
+    if (seg < P.nseg - 1) {
+      if ((v = lap_restore(P, n0, P.ckpt + (size_t)seg * 6 * field, st)) != FWI_OK) return v;
+      for (int n = n0; n < n1; n++)
+        if ((v = lap_step(ctx, P, q, n, lscale, false, P.slot + (size_t)(n - n0) * 2 * field, st)) != FWI_OK)
+          return v;
+    }
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
     for (int n = n1 - 1; n >= n0; n--) {
       const float* lam1 = P.lam + ((n + 1) & 1) * field;  // lambda_{n+1}, complete
@@ -911,10 +918,13 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   const size_t sl = (size_t)P.g.slice;
 
   // forward sweep with a full-state checkpoint at the start of every segment
+  // but the last: the sweep itself keeps the last segment's fluxes (recording
+  // and storing in one launch), so that segment is never recomputed
+  const int nlast = (P.nseg - 1) * K;
   CK(cudaEventRecord(ctx->ev[0], st));
   if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
   for (int n = 0; n < nt; n++) {
-    if (n % K == 0) {
+    if (n % K == 0 && n < nlast) {
       float* ck = P.ckpt + (size_t)(n / K) * 6 * field;
       const float* src[6] = {P.u + (n & 1) * field, P.u + ((n + 1) & 1) * field, P.psix[n & 1], P.psiz[n & 1],
                              P.zetx, P.zetz};
@@ -924,8 +934,13 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
                              cudaMemcpyDeviceToDevice, gr.st[g]));
     }
     set_fwd_state(P, p, n);
+    const bool keep = n >= nlast;
+    if (keep) {
+      p.slot_px = P.slot + (size_t)(n - nlast) * 2 * field;
+      p.slot_pz = p.slot_px + field;
+    }
     for (int g = 0; g < gr.G; g++) {
-      LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
+      LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, keep, gr.st[g]));
       if (P.L > 0)
         LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                  P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
@@ -950,26 +965,29 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     const float* ck = P.ckpt + (size_t)seg * 6 * field;
     float* dst[6] = {P.u + (n0 & 1) * field, P.u + ((n0 + 1) & 1) * field, P.psix[n0 & 1], P.psiz[n0 & 1], P.zetx,
                      P.zetz};
-    // recompute (from the checkpoint) on the group streams
+    // recompute (from the checkpoint) on the group streams; the last segment's
+    // fluxes are already stored by the forward sweep
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
-    if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
-    for (int g = 0; g < gr.G; g++)
-      for (int f = 0; f < 6; f++)
-        CK(cudaMemcpyAsync(dst[f] + gr.s0[g] * sl, ck + f * field + gr.s0[g] * sl, gr.n[g] * sl * 4,
-                           cudaMemcpyDeviceToDevice, gr.st[g]));
-    for (int n = n0; n < n1; n++) {
-      set_fwd_state(P, p, n);
-      p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
-      p.slot_pz = p.slot_px + field;
-      for (int g = 0; g < gr.G; g++) {
-        LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, gr.st[g]));
-        if (P.L > 0)
-          LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
-                                   P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
-                                   P.rec_cell, P.nrec, nullptr, gr.st[g]));
+    if (seg < P.nseg - 1) {
+      if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
+      for (int g = 0; g < gr.G; g++)
+        for (int f = 0; f < 6; f++)
+          CK(cudaMemcpyAsync(dst[f] + gr.s0[g] * sl, ck + f * field + gr.s0[g] * sl, gr.n[g] * sl * 4,
+                             cudaMemcpyDeviceToDevice, gr.st[g]));
+      for (int n = n0; n < n1; n++) {
+        set_fwd_state(P, p, n);
+        p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
+        p.slot_pz = p.slot_px + field;
+        for (int g = 0; g < gr.G; g++) {
+          LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, gr.st[g]));
+          if (P.L > 0)
+            LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
+                                     P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
+                                     P.rec_cell, P.nrec, nullptr, gr.st[g]));
+        }
       }
+      if ((v = join(ctx, gr, st)) != FWI_OK) return v;
     }
-    if ((v = join(ctx, gr, st)) != FWI_OK) return v;
     CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
     if ((v = fork(ctx, gra, st)) != FWI_OK) return v;
     for (int n = n1 - 1; n >= n0; n--) {
@@ -1034,7 +1052,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 1], ctx->seg_ev[4 * seg + 2]);
     adj += ta;
   }
-  ctx->kernel_ms[1] = rec / nt;
+  ctx->kernel_ms[1] = nlast > 0 ? rec / nlast : 0.f;  // per recomputed step
   ctx->kernel_ms[2] = adj / nt;
   if (v == FWI_OK) g_err.clear();
   return v;
