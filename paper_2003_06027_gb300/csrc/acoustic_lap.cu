@@ -96,7 +96,7 @@ __global__ void k_lap_update(const LapStep p, const float* __restrict__ u, float
   uprev[id] = v;
 }
 
-// seis[s][r][n] = u(receiver cell r) (or += add[s][r][n] into lam for the adjoint seed)
+// seis[s][r][n] = u^{n+1}(receiver cell r), one thread per (shot, receiver)
 __global__ void k_lap_record(const float* __restrict__ u, const Grid g, int S, int nrec, int nt, int n,
                              const int* __restrict__ rec_cell, float* seis) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -105,8 +105,10 @@ __global__ void k_lap_record(const float* __restrict__ u, const Grid g, int S, i
   const int i = rec_cell[2 * r], j = rec_cell[2 * r + 1];
   seis[((long long)s * nrec + r) * nt + n] = i < 0 ? 0.f : u[cell_index(g, s, i, j)];  // -1: outside the grid
 }
-// lam(receiver cell r) += res[s][r][n], one thread per (receiver, shot).
-// Receivers that share a cell are added by the first of them, in receiver
+
+// lam(receiver cell r) += res[s][r][n], one thread per (receiver, shot): the
+// residual of sample n enters lambda_{n+1} (the adjoint seed, and the adjoint
+// sweep's source). Receivers that share a cell are added by the first of them, in receiver
 // order, so the sum is the sequential one and the kernel deterministic. The
 // block scans the receiver cells in ascending chunks staged in shared memory:
 // every earlier receiver is seen before any later one. Receivers outside the
