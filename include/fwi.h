@@ -161,6 +161,34 @@ fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
                            float *grad, float *grad_stf, float *grad_x0, float *seis_out,
                            void *cuda_stream);
 
+/* Device workspace (bytes) that a call allocates in its context: the forward
+ * call (ckpt_every = 0) or fwi_misfit_grad with checkpoint interval
+ * ckpt_every (1..nt), for the given model, sources, receivers and nt; sized
+ * by the layout the call itself uses, so a context whose arena is at least
+ * this large allocates nothing for that call. The dominant terms are fields
+ * of nshots x R x P floats, R = ceil(Nz/32)*32 + 16 rows and
+ * P = ceil(Nx/64)*64 + 16 columns (the padded grid Nz x Nx, tile-aligned,
+ * with an 8-cell apron): per gradient call 6 per checkpoint (ceil(nt/K) of
+ * them, acoustic; 13 elastic) and 2 per step of a segment (K of them,
+ * acoustic; 5 elastic). Host arithmetic only: no device is touched; inputs are
+ * validated as by the call (FWI_EINVAL, FWI_ENOTIMPL). */
+fwi_status fwi_workspace_bytes(const fwi_model *model, const fwi_sources *src,
+                               const fwi_receivers *rec, int32_t nt, int32_t ckpt_every,
+                               uint64_t *bytes);
+
+/* Checkpoint interval for fwi_misfit_grad that fits a memory budget: among
+ * the K in [1, nt] whose workspace (fwi_workspace_bytes) is at most
+ * budget_bytes, the one that recomputes the fewest forward steps (acoustic:
+ * (ceil(nt/K) - 1) K, since the forward sweep keeps the last segment; elastic:
+ * nt for every K), then the fewest segments, then the least memory. K = nt
+ * (no recomputation) whenever it fits. budget_bytes = 0 means the device's
+ * free memory plus ctx's current arena, less max(1 GiB, 2% of the device):
+ * that needs ctx; an explicit budget needs no device (ctx may be NULL).
+ * FWI_ENOMEM (with the smallest workspace in fwi_last_error) if no K fits. */
+fwi_status fwi_choose_ckpt(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
+                           const fwi_receivers *rec, int32_t nt, uint64_t budget_bytes,
+                           int32_t *ckpt_every);
+
 /* Launch shape of the acoustic calls on ctx: the shots of a call are split
  * into forward_groups (forward and recompute steps) and adjoint_groups
  * (adjoint steps) contiguous groups, each step launched once per group on its

@@ -1163,3 +1163,88 @@ fwi_status fwi_graph_destroy(fwi_graph* g) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// Workspace of one call, sized by the layout the call itself uses; the model
+// and geometry must already be valid.
+uint64_t workspace_of(const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int nt, int K) {
+  if (M->physics == FWI_ELASTIC) {
+    uint64_t b = 0;
+    return ela_workspace_bytes(M, Sv, R, nt, K, &b) == FWI_OK ? b : UINT64_MAX;
+  }
+  Plan P;
+  make_plan(P, M, Sv, R, nt, K, K > 0);
+  layout(P, nullptr);
+  return (uint64_t)P.bytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_workspace_bytes(const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int32_t nt,
+                               int32_t ckpt_every, uint64_t* bytes) {
+  if (!bytes) return fail(FWI_EINVAL, "bytes must not be NULL");
+  if (M && M->physics == FWI_ELASTIC) {
+    const fwi_status v = ela_workspace_bytes(M, Sv, R, nt, ckpt_every, bytes);
+    if (v == FWI_OK) g_err.clear();
+    return v;
+  }
+  const fwi_status v = validate(M, Sv, R, nt, 1.f);
+  if (v != FWI_OK) return v;
+  if (ckpt_every < 0 || ckpt_every > nt) return fail(FWI_EINVAL, "ckpt_every must be in [0, nt] (0: the forward call)");
+  *bytes = workspace_of(M, Sv, R, nt, ckpt_every);
+  g_err.clear();
+  return FWI_OK;
+}
+
+fwi_status fwi_choose_ckpt(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                           int32_t nt, uint64_t budget_bytes, int32_t* ckpt_every) {
+  if (!ckpt_every) return fail(FWI_EINVAL, "ckpt_every must not be NULL");
+  uint64_t w = 0;
+  fwi_status v = fwi_workspace_bytes(M, Sv, R, nt, 0, &w);  // validates the call
+  if (v != FWI_OK) return v;
+  uint64_t budget = budget_bytes;
+  if (budget == 0) {
+    if (!ctx) return fail(FWI_EINVAL, "a zero budget (the device's free memory) needs a context");
+    CK(cudaSetDevice(ctx->device));
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    // the context's own arena is freed before a larger one is allocated
+    const uint64_t avail = (uint64_t)fr + (uint64_t)ctx->arena_bytes;
+    const uint64_t margin = std::max<uint64_t>(1ull << 30, (uint64_t)tot / 50);
+    budget = avail > margin ? avail - margin : 0;
+  }
+  const bool elastic = M->physics == FWI_ELASTIC;
+  int best = 0, best_seg = 0;
+  long long best_rec = 0;
+  uint64_t best_w = 0, min_w = UINT64_MAX;
+  int min_k = 1;
+  for (int K = nt; K >= 1; K--) {
+    w = workspace_of(M, Sv, R, nt, K);
+    if (w < min_w) {
+      min_w = w;
+      min_k = K;
+    }
+    if (w > budget) continue;
+    const int nseg = (nt + K - 1) / K;
+    // recomputed forward steps: acoustic calls store the last segment in the forward sweep
+    const long long rec = elastic ? (long long)nt : (long long)(nseg - 1) * K;
+    if (!best || rec < best_rec || (rec == best_rec && (nseg < best_seg || (nseg == best_seg && w < best_w)))) {
+      best = K;
+      best_rec = rec;
+      best_seg = nseg;
+      best_w = w;
+    }
+  }
+  if (!best)
+    return fail(FWI_ENOMEM, "the smallest gradient workspace (" + std::to_string(min_w) + " bytes, ckpt_every = " +
+                                std::to_string(min_k) + ") exceeds the budget of " + std::to_string(budget) +
+                                " bytes");
+  *ckpt_every = best;
+  g_err.clear();
+  return FWI_OK;
+}
+
+}  // extern "C"

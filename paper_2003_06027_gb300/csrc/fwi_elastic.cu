@@ -195,6 +195,24 @@ void ela_make_plan(EPlan& P, const fwi_model* M, const fwi_sources* Sv, const fw
   P.tablen = std::max(g.ntx * TILE_X, g.ntz * TILE_Z) + 2 * APRON + 2 * TAB_OFF;
 }
 
+}  // namespace
+
+// Device workspace of an elastic call: the forward call (K = 0) or the
+// gradient with checkpoint interval K; the plan's own layout, sized only.
+fwi_status ela_workspace_bytes(const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int32_t nt,
+                               int32_t K, uint64_t* bytes) {
+  const fwi_status v = ela_validate(M, Sv, R, nt, 1.f);
+  if (v != FWI_OK) return v;
+  if (K < 0 || K > nt) return host_fail(FWI_EINVAL, "ckpt_every must be in [0, nt] (0: the forward call)");
+  EPlan P;
+  ela_make_plan(P, M, Sv, R, nt, K, K > 0);
+  ela_layout(P, nullptr);
+  *bytes = (uint64_t)P.bytes;
+  return FWI_OK;
+}
+
+namespace {
+
 fwi_status ela_acquire(fwi_ctx* ctx, EPlan& P, cudaStream_t st) {
   ela_layout(P, nullptr);
   char key[256];

@@ -42,6 +42,8 @@ void ensure_events(fwi_ctx* ctx, size_t nseg);
 // elastic paths of fwi_forward / fwi_misfit_grad (fwi_elastic.cu)
 fwi_status ela_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int32_t nt,
                        float dt, float* seis, void* stream);
+fwi_status ela_workspace_bytes(const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int32_t nt,
+                               int32_t K, uint64_t* bytes);
 fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
                            int32_t nt, float dt, const float* observed, int32_t K, double* misfit, float* grad,
                            float* grad_stf, float* grad_x0, float* seis_out, void* stream);

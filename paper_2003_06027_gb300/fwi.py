@@ -55,7 +55,7 @@ _ctx = threading.local()
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
            "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout",
            "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy",
-           "fwi_set_shot_groups", "fwi_last_error"]
+           "fwi_set_shot_groups", "fwi_workspace_bytes", "fwi_choose_ckpt", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -92,6 +92,12 @@ def library(build_if_missing: bool = True):
             L.fwi_graph_status.argtypes = [P, P]
             L.fwi_graph_destroy.argtypes = [P]
             L.fwi_set_shot_groups.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+            L.fwi_workspace_bytes.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                              ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_uint64)]
+            L.fwi_choose_ckpt.argtypes = [P, ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                          ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_uint64,
+                                          ctypes.POINTER(ctypes.c_int32)]
             L.fwi_last_error.restype = ctypes.c_char_p
             for f in EXPORTS[:-1]:
                 getattr(L, f).restype = ctypes.c_int
@@ -376,6 +382,53 @@ class _ECall:
                             _ptr(self.vp), _ptr(self.vs), _ptr(self.rho))
         self.src = _Sources(self.S, src_kind, _ptr(self.x0), _ptr(self.stf), _ptr(self.mt))
         self.rec = _Receivers(self.nrec, _ptr(self.iz), _ptr(self.ix))
+
+
+def _workspace(a, ckpt_every):
+    b = ctypes.c_uint64()
+    _check(library().fwi_workspace_bytes(ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
+                                         int(ckpt_every), ctypes.byref(b)))
+    return int(b.value)
+
+
+def _choose(a, budget_bytes, device):
+    k = ctypes.c_int32()
+    ctx = context(device) if not budget_bytes else None  # 0: the device's free memory
+    _check(library().fwi_choose_ckpt(ctx, ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
+                                     int(budget_bytes), ctypes.byref(k)))
+    return int(k.value)
+
+
+def workspace_bytes(c, stf, x0, rec_iz, rec_ix, *, ckpt_every=0, dx, dz, dt=None, order=4, npml=20, pml_R=1e-3,
+                    pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE):
+    """Device workspace in bytes of the acoustic forward call (ckpt_every=0)
+    or of misfit_grad with that checkpoint interval (fwi_workspace_bytes).
+    Host arithmetic only; the arrays may live anywhere."""
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
+    return _workspace(a, ckpt_every)
+
+
+def choose_ckpt(c, stf, x0, rec_iz, rec_ix, *, budget_bytes=0, device=0, dx, dz, dt=None, order=4, npml=20,
+                pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE):
+    """Checkpoint interval of an acoustic misfit_grad that fits budget_bytes of
+    device memory with the fewest recomputed steps (fwi_choose_ckpt);
+    budget_bytes=0: the free memory of ``device``."""
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
+    return _choose(a, budget_bytes, device)
+
+
+def workspace_bytes_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, *, ckpt_every=0, dx, dz, dt=None, order=4,
+                            npml=20, pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_GAUSSIAN):
+    """workspace_bytes for the elastic calls."""
+    a = _ECall(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    return _workspace(a, ckpt_every)
+
+
+def choose_ckpt_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, *, budget_bytes=0, device=0, dx, dz, dt=None,
+                        order=4, npml=20, pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_GAUSSIAN):
+    """choose_ckpt for the elastic gradient."""
+    a = _ECall(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind)
+    return _choose(a, budget_bytes, device)
 
 
 def forward_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20,
