@@ -24,7 +24,6 @@ optimisation loops are ordinary torch code.
 
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass, field
 
 import torch

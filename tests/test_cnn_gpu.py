@@ -138,8 +138,6 @@ def test_upsample_and_mse_and_adam(fwi_lib):
         lo, go = cnn.mse(np.float64(p), np.float64(t))
         assert float(loss[0]) == pytest.approx(lo, rel=1e-6)  # FP32 residuals, FP64 sum
         assert rel(dp.cpu().numpy(), go) <= 1e-6
-    import ctypes
-
     th, g = rng.standard_normal(777).astype(np.float32), rng.standard_normal(777).astype(np.float32)
     tt, gg, m, v = _cuda(th), _cuda(g), _cuda(np.zeros(777)), _cuda(np.zeros(777))
     thb = L.to_bf16(tt)
