@@ -506,8 +506,8 @@ def workload_config(d):
             "grid_padded": [Nz, Nx], "order": d["order"], "npml": d["npml"], "shots": S, "nt": nt,
             "receivers": int(len(d["rec_iz"])), "ckpt_every": d["ckpt_every"],
             "cell_steps_per_step": S * Nz * Nx * nt,
-            "l2": "no explicit flush: each step streams >6 GB (checkpoints + segment slots) through HBM, "
-                  "far more than the 129 MB L2",
+            "l2": "no explicit flush: each step writes and reads back ~80 GB of stored fluxes (28 MB per time "
+                  "step) and 2.5 GB of checkpoints through HBM, far more than the 129 MB L2",
             "parallelism": "shots batched on one GPU; N GPUs = N independent replicas"}
 
 
