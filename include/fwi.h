@@ -161,6 +161,28 @@ fwi_status fwi_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
                            float *grad, float *grad_stf, float *grad_x0, float *seis_out,
                            void *cuda_stream);
 
+/* Vector-Jacobian product of the forward map d = F(theta): for a cotangent
+ * v = dL/dd of any scalar L of the seismograms, the adjoint sweep seeded with
+ * v at the receivers gives (dF/dtheta)^T v. This is the reverse-mode rule of
+ * the paper's AD section applied step by step (dU_k/dU_{k-1} = A^T, Eq.
+ * ad-backward), with the misfit derivative d - d_obs of Eq. adjoint-backward
+ * replaced by v; fwi_misfit_grad is the special case v = d - d_obs.
+ * Arguments as fwi_misfit_grad, except:
+ * cotangent  v, shaped like the seismograms ([S][nrec][nt] acoustic,
+ *            [S][2][nrec][nt] elastic), host or device; NULL only if nrec = 0.
+ * value      <d, v> = sum of seis * cotangent in FP64 (the linear functional
+ *            whose gradient is returned), one double (host or device), or NULL.
+ * grad, grad_stf, grad_x0  (dF/dtheta)^T v for the model (acoustic c;
+ *            elastic lambda, mu, rho), the source time functions and the
+ *            source positions, laid out as in fwi_misfit_grad; each may be NULL.
+ * Same checkpointing, status codes (FWI_EUNSTABLE on a non-finite <d, v>) and
+ * synchronisation as fwi_misfit_grad. */
+fwi_status fwi_forward_vjp(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
+                           const fwi_receivers *rec, int32_t nt, float dt,
+                           const float *cotangent, int32_t ckpt_every, double *value,
+                           float *grad, float *grad_stf, float *grad_x0, float *seis_out,
+                           void *cuda_stream);
+
 /* Device workspace (bytes) that a call allocates in its context: the forward
  * call (ckpt_every = 0) or fwi_misfit_grad with checkpoint interval
  * ckpt_every (1..nt), for the given model, sources, receivers and nt; sized
@@ -178,9 +200,9 @@ fwi_status fwi_workspace_bytes(const fwi_model *model, const fwi_sources *src,
 
 /* Checkpoint interval for fwi_misfit_grad that fits a memory budget: among
  * the K in [1, nt] whose workspace (fwi_workspace_bytes) is at most
- * budget_bytes, the one that recomputes the fewest forward steps (acoustic:
- * (ceil(nt/K) - 1) K, since the forward sweep keeps the last segment; elastic:
- * nt for every K), then the fewest segments, then the least memory. K = nt
+ * budget_bytes, the one that recomputes the fewest forward steps
+ * ((ceil(nt/K) - 1) K, acoustic and elastic, since the forward sweep keeps the
+ * last segment), then the fewest segments, then the least memory. K = nt
  * (no recomputation) whenever it fits. budget_bytes = 0 means the device's
  * free memory plus ctx's current arena, less max(1 GiB, 2% of the device):
  * that needs ctx; an explicit budget needs no device (ctx may be NULL).
@@ -244,7 +266,13 @@ fwi_status fwi_graph_destroy(fwi_graph *graph);
  * FWI_EINVAL (the message gives the bytes needed). Every call shares that
  * array and clears the part it uses; calls that overlap on the GPU race and
  * must be serialised by the caller. The first call on a device resolves the
- * array's address: make it before any stream capture begins on that device. */
+ * array's address: make it before any stream capture begins on that device
+ * (a call made while capturing, with no earlier call on the device, gets
+ * FWI_EINVAL). Calls outside capture resolve the address again, so a context
+ * that was destroyed and created again is followed. Checked on the host before
+ * any device work: the padded grid (each side <= 2^20 cells, at most 2^31
+ * cells, else FWI_EINVAL "grid too large"), and that every pointer is device
+ * memory of the current device or managed memory (else FWI_EINVAL). */
 fwi_status fwi_forward_noalloc(const fwi_model *model, const fwi_sources *src,
                                const fwi_receivers *rec, int32_t nt, float dt, float *seis,
                                void *cuda_stream);

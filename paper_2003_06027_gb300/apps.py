@@ -7,14 +7,15 @@ imaging).
   Gaussian in space (sigma = half a cell) so that J is differentiable in x0; it
   starts, as in the paper's test, from a given (e.g. random) location and a zero
   source time function.
-* ``SuperposedMisfit``: J = 1/2 || sum_k d_k - d_obs ||^2 for several sources
+* ``superposed_misfit``: J = 1/2 || sum_k d_k - d_obs ||^2 for several sources
   active in ONE wavefield (a rupture: sub-sources switched on along a fault).
   The scheme is linear in its source term, so the wavefield of the sum is the
-  sum of the per-source wavefields; the gradient with respect to every
-  sub-source's time function and position is the adjoint of its own forward
-  map applied to the common residual r = sum_k d_k - d_obs. One batched
-  forward call gives the d_k; one fwi_misfit_grad call with observed_k =
-  d_k - r (so that each shot's residual is exactly r) gives the gradients.
+  sum of the per-source wavefields d_k, which one batched call of the
+  differentiable seismogram operator gives (the sub-sources as shots). The
+  loss is ordinary torch code on those seismograms; its backward seeds every
+  sub-source's adjoint sweep with the common residual dJ/dd_k =
+  sum_k d_k - d_obs (fwi_forward_vjp), which gives the gradient with respect to
+  each sub-source's time function and position.
 * ``gaussian_slip``: the rupture time / amplitude parametrisation
   g_k(t) = A_k exp(-(t - t_k)^2 / (2 s^2)), differentiable in (A_k, t_k).
 
@@ -29,43 +30,18 @@ from dataclasses import dataclass, field
 import torch
 
 from . import fwi
-from .autograd import acoustic_misfit
-
-
-class SuperposedMisfit(torch.autograd.Function):
-    """J(stf, x0) of k sources superposed in one acoustic wavefield."""
-
-    @staticmethod
-    def forward(ctx, stf, x0, c, observed, rec_iz, rec_ix, opts):
-        fwd_opts = {k: v for k, v in opts.items() if k != "ckpt_every"}
-        d = fwi.forward(c, stf, x0, rec_iz, rec_ix, **fwd_opts)           # [k][nrec][nt]
-        r = d.sum(dim=0) - observed                                        # common residual
-        J = 0.5 * torch.sum(r.double() * r.double())
-        want_src = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
-        gs = gx = None
-        if want_src:
-            _, _, gs, gx, _ = fwi.misfit_grad(c, stf, x0, rec_iz, rec_ix, d - r.unsqueeze(0), want_grad=False,
-                                              **opts)
-        ctx.save_for_backward(*(t if t is not None else torch.empty(0) for t in (gs, gx)))
-        ctx.has = want_src
-        return J
-
-    @staticmethod
-    def backward(ctx, gJ):
-        gs, gx = ctx.saved_tensors
-        if not ctx.has:
-            return None, None, None, None, None, None, None
-        s = gJ.to(gs.dtype)
-        return (gs * s if ctx.needs_input_grad[0] else None, gx * s if ctx.needs_input_grad[1] else None,
-                None, None, None, None, None)
+from .autograd import acoustic_misfit, acoustic_seismograms
 
 
 def superposed_misfit(stf, x0, c, observed, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
                       pml_vmax=4500.0, pml_f0=10.0, src_kind=fwi.FWI_SRC_GAUSSIAN, ckpt_every=100):
-    """Differentiable misfit of the sources stf [k][nt] at x0 [k][2] acting together."""
-    opts = dict(dx=dx, dz=dz, dt=dt, order=order, npml=npml, pml_R=pml_R, pml_vmax=pml_vmax, pml_f0=pml_f0,
-                src_kind=src_kind, ckpt_every=ckpt_every)
-    return SuperposedMisfit.apply(stf, x0, c, observed, rec_iz, rec_ix, opts)
+    """Differentiable misfit of the sources stf [k][nt] at x0 [k][2] acting
+    together (a 0-d float64 tensor): the seismogram operator over the k
+    sub-sources, summed, against observed [nrec][nt]."""
+    d = acoustic_seismograms(c, stf, x0, rec_iz, rec_ix, dx=dx, dz=dz, dt=dt, order=order, npml=npml, pml_R=pml_R,
+                             pml_vmax=pml_vmax, pml_f0=pml_f0, src_kind=src_kind, ckpt_every=ckpt_every)
+    r = d.sum(dim=0) - observed
+    return 0.5 * torch.sum(r.double() * r.double())
 
 
 def gaussian_slip(A, t0, sigma, nt, dt):

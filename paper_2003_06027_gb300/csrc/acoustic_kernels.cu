@@ -10,9 +10,11 @@
 //   * persistent CTAs (grid = resident CTAs of the GPU) walk the tiles of all
 //     shots; a tile is 64 x 32 cells of one shot;
 //   * the stencil operand tiles with their 8-cell halo and the coefficient tile are
-//     fetched by TMA (cp.async.bulk.tensor) into one of two shared-memory
-//     buffers, so the next tile's fetch overlaps the current tile's work;
-//     the completion wait on the mbarrier is bounded and reports a timeout;
+//     fetched by TMA (cp.async.bulk.tensor) into the CTA's one operand buffer
+//     as soon as stage 1 (their last reader) has passed its barrier, so the
+//     next tile's fetch overlaps the current tile's stage 2 and the other
+//     resident CTAs cover the rest; the completion wait on the mbarrier is
+//     bounded and reports a timeout;
 //   * stage 1 evaluates each half-point flux once (x: q at the half columns
 //     of the tile and its halo; z: a register window over two rows per thread),
 //     stage 2 the divergence, update, sources and receivers;

@@ -1018,8 +1018,9 @@ constexpr size_t ADJ_B_SMEM = sizeof(float) * (2 * ADJB_BUF + ADJB_SCR) + 2 * si
 
 std::mutex g_ela_mu;
 unsigned long long g_ela_inited = 0;  // bit per device
-// [device][order 4/8][variant]: vel (plain, record, store), str (plain, store), adjA, adjB
-int g_ela_grid[64][2][7];
+// [device][order 4/8][variant]: vel (plain, record, store), str (plain, store), adjA, adjB,
+// vel (record and store: the forward sweep over the last checkpoint segment)
+int g_ela_grid[64][2][8];
 
 template <typename K>
 cudaError_t ela_setup(K k, size_t smem, int* grid) {
@@ -1042,6 +1043,7 @@ cudaError_t ela_setup_order(int* gr) {
   if ((e = ela_setup(ela_str_step<N, false>, STR_SMEM, &gr[3])) != cudaSuccess) return e;
   if ((e = ela_setup(ela_str_step<N, true>, STR_SMEM, &gr[4])) != cudaSuccess) return e;
   if ((e = ela_setup(ela_str_adj<N>, ADJ_A_SMEM, &gr[5])) != cudaSuccess) return e;
+  if ((e = ela_setup(ela_vel_step<N, true, true>, VEL_SMEM, &gr[7])) != cudaSuccess) return e;
   return ela_setup(ela_vel_adj<N>, ADJ_B_SMEM, &gr[6]);
 }
 
@@ -1092,13 +1094,15 @@ cudaError_t launch_ela_vel(const EleStep& p, const EleMaps& m, bool record, bool
   int dev;
   cudaError_t e = ela_ensure_init(&dev);
   if (e != cudaSuccess) return e;
-  const int grid = ela_grid(p, dev, record ? 1 : (store ? 2 : 0));
+  const int grid = ela_grid(p, dev, record ? (store ? 7 : 1) : (store ? 2 : 0));
   if (p.N == 2) {
-    if (record) ela_vel_step<2, true, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    if (record && store) ela_vel_step<2, true, true><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    else if (record) ela_vel_step<2, true, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
     else if (store) ela_vel_step<2, false, true><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
     else ela_vel_step<2, false, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
   } else {
-    if (record) ela_vel_step<4, true, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    if (record && store) ela_vel_step<4, true, true><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
+    else if (record) ela_vel_step<4, true, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
     else if (store) ela_vel_step<4, false, true><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
     else ela_vel_step<4, false, false><<<grid, NTHREADS, VEL_SMEM, st>>>(m.sxx, m.szz, m.sxz, p);
   }

@@ -36,7 +36,7 @@ cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g
                            int* start, int* cursor, int* list, int* status, cudaStream_t st);
 cudaError_t launch_model_check(const float* c, long long n, float coef, int* status, cudaStream_t st);
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
-                          int* status, cudaStream_t st);
+                          int* status, bool vjp, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
 cudaError_t launch_selftest_wait(int* status, unsigned long long* waited_ns, cudaStream_t st);
 cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
@@ -751,7 +751,7 @@ fwi_status lap_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     if ((v = lap_step(ctx, P, q, n, lscale, true, keep, st)) != FWI_OK) return v;
   }
   CK(cudaEventRecord(ctx->ev[1], st));
-  if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
+  if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, ctx->vjp, st));
   else CK(cudaMemsetAsync(P.J, 0, 8, st));
   // adjoint seed: lambda_nt = residual of the last sample; lambda_{nt+1} = 0 (zeroed)
   if (ns > 0) LK(1, launch_lap_inject_res(P.lam + (nt & 1) * field, P.g, P.S, P.nrec, nt, nt - 1, P.rec_cell, P.res, st));
@@ -949,7 +949,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   }
   if ((v = join(ctx, gr, st)) != FWI_OK) return v;
   CK(cudaEventRecord(ctx->ev[1], st));
-  if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
+  if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, ctx->vjp, st));
   else CK(cudaMemsetAsync(P.J, 0, 8, st));
 
   // reverse sweep, segment by segment
@@ -1089,6 +1089,23 @@ fwi_status fwi_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
                          (cudaStream_t)stream, false, nullptr);
 }
 
+fwi_status fwi_forward_vjp(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
+                           int32_t nt, float dt, const float* cotangent, int32_t K, double* value, float* grad,
+                           float* grad_stf, float* grad_x0, float* seis_out, void* stream) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (R && R->nrec > 0 && !cotangent) return fail(FWI_EINVAL, "cotangent must not be NULL");
+  // the misfit call with its residual replaced by the cotangent: the adjoint
+  // sweep is the same, seeded with v instead of d - d_obs
+  double local = 0.0;  // <d, v> when the caller does not want it (the call synchronises before returning)
+  struct Flag {
+    fwi_ctx* c;
+    ~Flag() { c->vjp = false; }
+  } flag{ctx};
+  ctx->vjp = true;
+  return fwi_misfit_grad(ctx, M, Sv, R, nt, dt, cotangent, K, value ? value : &local, grad, grad_stf, grad_x0,
+                         seis_out, stream);
+}
+
 fwi_status fwi_misfit_grad_graph(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
                                  int32_t nt, float dt, const float* observed, int32_t K, double* misfit,
                                  float* grad, float* grad_stf, float* grad_x0, fwi_graph** out) {
@@ -1216,7 +1233,6 @@ fwi_status fwi_choose_ckpt(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     const uint64_t margin = std::max<uint64_t>(1ull << 30, (uint64_t)tot / 50);
     budget = avail > margin ? avail - margin : 0;
   }
-  const bool elastic = M->physics == FWI_ELASTIC;
   int best = 0, best_seg = 0;
   long long best_rec = 0;
   uint64_t best_w = 0, min_w = UINT64_MAX;
@@ -1229,8 +1245,8 @@ fwi_status fwi_choose_ckpt(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     }
     if (w > budget) continue;
     const int nseg = (nt + K - 1) / K;
-    // recomputed forward steps: acoustic calls store the last segment in the forward sweep
-    const long long rec = elastic ? (long long)nt : (long long)(nseg - 1) * K;
+    // recomputed forward steps: the forward sweep stores the last segment itself
+    const long long rec = (long long)(nseg - 1) * K;
     if (!best || rec < best_rec || (rec == best_rec && (nseg < best_seg || (nseg == best_seg && w < best_w)))) {
       best = K;
       best_rec = rec;

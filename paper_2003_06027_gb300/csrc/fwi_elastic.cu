@@ -41,7 +41,7 @@ cudaError_t launch_cpml_tables(int n_phys, int npml, int Npad, int len, double h
 cudaError_t launch_rec_csr(int nrec, const int* iz, const int* ix, const Grid& g, int* rec_cell, int* rec_key,
                            int* start, int* cursor, int* list, int* status, cudaStream_t st);
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
-                          int* status, cudaStream_t st);
+                          int* status, bool vjp, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
 cudaError_t launch_src_grad(const float* part, int S, int nt, int nslots, double scale, const float* stf,
                             double inv_sig2, int kind, float* gstf, float* gx0, cudaStream_t st);
@@ -376,19 +376,26 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   ensure_events(ctx, P.nseg);
 
   // forward sweep with a full-state checkpoint at the start of every segment
+  // but the last: over the last segment the sweep stores the forces and
+  // strains itself (recording and storing in one launch), so that segment is
+  // never recomputed
+  const int nlast = (P.nseg - 1) * K;
   ECK(cudaEventRecord(ctx->ev[0], st));
   for (int n = 0; n < nt; n++) {
-    if (n % K == 0) {
+    if (n % K == 0 && n < nlast) {
       float* ck = P.ckpt + (size_t)(n / K) * NSTATE * field;
       for (int f = 0; f < NSTATE; f++)
         ECK(cudaMemcpyAsync(ck + f * field, P.f[f], field * 4, cudaMemcpyDeviceToDevice, st));
     }
     p.n = n;
-    ELK(1, launch_ela_vel(p, maps, true, false, st));
-    ELK(1, launch_ela_str(p, maps, false, st));
+    const bool keep = n >= nlast;
+    if (keep)
+      for (int k = 0; k < 5; k++) p.slot[k] = P.slot + ((size_t)(n - nlast) * 5 + k) * field;
+    ELK(1, launch_ela_vel(p, maps, true, keep, st));
+    ELK(1, launch_ela_str(p, maps, keep, st));
   }
   ECK(cudaEventRecord(ctx->ev[1], st));
-  if (ns > 0) ELK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, st));
+  if (ns > 0) ELK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, ctx->vjp, st));
   else ECK(cudaMemsetAsync(P.J, 0, 8, st));
 
   // reverse sweep
@@ -406,15 +413,17 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   p.src_part = P.src_part;
   for (int seg = P.nseg - 1; seg >= 0; seg--) {
     const int n0 = seg * K, n1 = std::min(nt, n0 + K);
-    const float* ck = P.ckpt + (size_t)seg * NSTATE * field;
-    for (int f = 0; f < NSTATE; f++)
-      ECK(cudaMemcpyAsync(P.f[f], ck + f * field, field * 4, cudaMemcpyDeviceToDevice, st));
     ECK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
-    for (int n = n0; n < n1; n++) {
-      p.n = n;
-      for (int k = 0; k < 5; k++) p.slot[k] = P.slot + ((size_t)(n - n0) * 5 + k) * field;
-      ELK(1, launch_ela_vel(p, maps, false, true, st));
-      ELK(1, launch_ela_str(p, maps, true, st));
+    if (seg < P.nseg - 1) {  // the last segment's slots are already filled by the forward sweep
+      const float* ck = P.ckpt + (size_t)seg * NSTATE * field;
+      for (int f = 0; f < NSTATE; f++)
+        ECK(cudaMemcpyAsync(P.f[f], ck + f * field, field * 4, cudaMemcpyDeviceToDevice, st));
+      for (int n = n0; n < n1; n++) {
+        p.n = n;
+        for (int k = 0; k < 5; k++) p.slot[k] = P.slot + ((size_t)(n - n0) * 5 + k) * field;
+        ELK(1, launch_ela_vel(p, maps, false, true, st));
+        ELK(1, launch_ela_str(p, maps, true, st));
+      }
     }
     ECK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
     for (int n = n1 - 1; n >= n0; n--) {
@@ -461,7 +470,7 @@ fwi_status ela_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 1], ctx->seg_ev[4 * seg + 2]);
     adj += ta;
   }
-  ctx->kernel_ms[1] = rec / nt;
+  ctx->kernel_ms[1] = nlast > 0 ? rec / nlast : 0.f;  // per recomputed step (checkpoint restores included)
   ctx->kernel_ms[2] = adj / nt;
   if (v == FWI_OK) host_fail(FWI_OK, "");
   return v;

@@ -29,6 +29,9 @@ struct fwi_ctx {
   unsigned long long arena_epoch = 0;
   int fwd_groups = 0, adj_groups = 0;  // shot groups of the acoustic step launches (0: the library's default)
   cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
+  // set for the duration of an fwi_forward_vjp call: the "observed" buffer holds
+  // the cotangent, which seeds the adjoint sweep as it stands
+  bool vjp = false;
 };
 
 namespace fwi {

@@ -20,7 +20,10 @@
 //     race on it and must be serialised by the caller;
 //   - the first call on a device resolves the array's device address
 //     (cudaGetSymbolAddress, with that device current); make that first call
-//     before any stream capture is started on the device.
+//     before any stream capture is started on the device. Later calls resolve
+//     it again (cheap), so a context torn down and created again (for example
+//     after cudaDeviceReset) never gets a stale address; only a call made
+//     while its stream is capturing reuses the address resolved earlier.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -73,28 +76,42 @@ fwi_status err(fwi_status st, const std::string& msg) {
     if (e_ != cudaSuccess) return err(FWI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Device address of the scratch array on the current device (set up once).
-fwi_status scratch_address(void** out) {
+// Device address of the scratch array on the current device. Resolved on every
+// call outside stream capture, so that a module reloaded at another address
+// (after the primary context was destroyed and created again) is followed;
+// during capture (where resolving could load the module, which capture
+// forbids) the address resolved by an earlier call on this device is used.
+fwi_status scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
   NA_CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return err(FWI_EINVAL, "device index out of range");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  NA_CK(cudaStreamIsCapturing(st, &cap));
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[dev]) {
-    void* p = nullptr;
-    NA_CK(cudaGetSymbolAddress(&p, g_scratch));
-    g_scratch_dev[dev] = p;
+  if (cap != cudaStreamCaptureStatusNone) {
+    if (!g_scratch_dev[dev])
+      return err(FWI_EINVAL, "the first fwi_forward_noalloc call on a device must come before any stream capture");
+    *out = g_scratch_dev[dev];
+    return FWI_OK;
   }
-  *out = g_scratch_dev[dev];
+  void* p = nullptr;
+  NA_CK(cudaGetSymbolAddress(&p, g_scratch));
+  g_scratch_dev[dev] = p;
+  *out = p;
   return FWI_OK;
 }
 
-bool on_device(const void* p) {
+// True for device memory on the current device, and for managed memory.
+// Memory of another GPU is refused: the step kernels would read it directly,
+// which faults without peer access.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -114,9 +131,16 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   if (M->op != FWI_OP_DIVERGENCE) return err(FWI_ENOTIMPL, "only the divergence-form operator runs without allocation");
   if (nt < 1 || !(dt > 0.f)) return err(FWI_EINVAL, "nt must be >= 1 and dt > 0");
   if (R->nrec < 0) return err(FWI_EINVAL, "nrec must be >= 0");
-  if (!on_device(M->vp) || !on_device(Sv->stf) || !on_device(Sv->x0) ||
-      (R->nrec > 0 && (!on_device(R->iz) || !on_device(R->ix) || !on_device(seis))))
-    return err(FWI_EINVAL, "fwi_forward_noalloc takes device pointers only (vp, stf, x0, iz, ix, seis)");
+  // the padded grid in 64-bit arithmetic, before any int field is formed from it
+  // (the same bound as the context calls: each side <= 2^20, cells <= 2^31)
+  const long long Nz_ll = (long long)M->nz + 2LL * M->npml, Nx_ll = (long long)M->nx + 2LL * M->npml;
+  if (Nz_ll > (1 << 20) || Nx_ll > (1 << 20) || Nz_ll * Nx_ll > (1LL << 31)) return err(FWI_EINVAL, "grid too large");
+  int dev = 0;
+  NA_CK(cudaGetDevice(&dev));
+  if (!on_device(M->vp, dev) || !on_device(Sv->stf, dev) || !on_device(Sv->x0, dev) ||
+      (R->nrec > 0 && (!on_device(R->iz, dev) || !on_device(R->ix, dev) || !on_device(seis, dev))))
+    return err(FWI_EINVAL,
+               "fwi_forward_noalloc takes device pointers on the current device only (vp, stf, x0, iz, ix, seis)");
   cudaStream_t st = (cudaStream_t)stream;
 
   // grid and the layout of the scratch
@@ -144,9 +168,9 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   const size_t field = (size_t)S * (size_t)g.slice * 4;
   const size_t o_status = take(64), o_m = take((size_t)g.slice * 4), o_tab = take((size_t)8 * tablen * 4);
   const size_t o_box = take((size_t)S * 2 * 4), o_w = take((size_t)S * SRC_W * SRC_W * 4);
-  const size_t o_rc = take((size_t)(nrec + 1) * 2 * 4), o_rk = take((size_t)(nrec + 1) * 4);
-  const size_t o_ts = take((size_t)(ntiles * NTHREADS + 1) * 4), o_tc = take((size_t)(ntiles * NTHREADS + 1) * 4);
-  const size_t o_tl = take((size_t)(nrec + 1) * 4);
+  const size_t o_rc = take(((size_t)nrec + 1) * 2 * 4), o_rk = take(((size_t)nrec + 1) * 4);
+  const size_t o_ts = take(((size_t)ntiles * NTHREADS + 1) * 4), o_tc = take(((size_t)ntiles * NTHREADS + 1) * 4);
+  const size_t o_tl = take(((size_t)nrec + 1) * 4);
   const size_t o_u = take(2 * field);  // wavefield pair, contiguous for its tensor map
   size_t o_f[6];
   for (int k = 0; k < 6; k++) o_f[k] = take(field);
@@ -157,7 +181,7 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
                                " bytes (use fwi_forward)");
 
   void* base_v = nullptr;
-  fwi_status s0 = scratch_address(&base_v);
+  fwi_status s0 = scratch_address(st, &base_v);
   if (s0 != FWI_OK) return s0;
   char* base = (char*)base_v;
   // everything this call relies on being zero: aprons, initial state, status
@@ -241,12 +265,13 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   int h_status = 0;
   NA_CK(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   NA_CK(cudaStreamSynchronize(st));
-  if (h_status & 16) return err(FWI_EINVAL, "velocity model must be finite and > 0");
-  if (h_status & 2) return err(FWI_EINVAL, "a receiver lies outside the physical grid");
-  if (h_status & 4) return err(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
-  if (h_status & 1) return err(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
-  if (h_status & 8) return err(FWI_EUNSTABLE, "non-finite value in the seismograms");
+  // a timeout first: every later result of the call is invalid
   if (h_status & ST_TIMEOUT) return err(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");
+  if (h_status & ST_BADMODEL) return err(FWI_EINVAL, "velocity model must be finite and > 0");
+  if (h_status & ST_BADREC) return err(FWI_EINVAL, "a receiver lies outside the physical grid");
+  if (h_status & ST_BADSRC) return err(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
+  if (h_status & ST_CFL) return err(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
+  if (h_status & ST_NONFINITE) return err(FWI_EUNSTABLE, "non-finite value in the seismograms");
   set_last_error("");
   return FWI_OK;
 }

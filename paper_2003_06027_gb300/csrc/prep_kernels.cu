@@ -212,14 +212,23 @@ __global__ void k_model_check(const float* __restrict__ c, long long n, float co
 
 // Residual r = d - d_obs (in place over the observed copy) and per-block
 // FP64 partial sums of r^2 (fixed reduction tree: deterministic).
+// VJP: the buffer already holds the cotangent v = dL/dd, which is the adjoint
+// source as it stands (it is left unchanged); the partial sums are of d * v,
+// so the scalar returned is <d, v>, the functional whose gradient the adjoint
+// sweep then computes.
+template <bool VJP>
 __global__ void k_misfit(const float* __restrict__ seis, float* res, long long n, double* part) {
   __shared__ double sred[256 / 32];
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const float r = seis[i] - res[i];
-    res[i] = r;
-    acc += (double)r * (double)r;
+    if (VJP) {
+      acc += (double)seis[i] * (double)res[i];
+    } else {
+      const float r = seis[i] - res[i];
+      res[i] = r;
+      acc += (double)r * (double)r;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
@@ -231,11 +240,11 @@ __global__ void k_misfit(const float* __restrict__ seis, float* res, long long n
   }
 }
 
-__global__ void k_misfit_final(const double* part, int nb, double* J, int* status) {
+__global__ void k_misfit_final(const double* part, int nb, double scale, double* J, int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
   for (int b = 0; b < nb; b++) s += part[b];
-  s *= 0.5;
+  s *= scale;
   *J = s;
   if (!isfinite(s)) atomicOr(status, ST_NONFINITE);
 }
@@ -462,9 +471,10 @@ cudaError_t launch_model_check(const float* c, long long n, float coef, int* sta
   return cudaGetLastError();
 }
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
-                          int* status, cudaStream_t st) {
-  k_misfit<<<nb, 256, 0, st>>>(seis, res, n, part);
-  k_misfit_final<<<1, 32, 0, st>>>(part, nb, J, status);
+                          int* status, bool vjp, cudaStream_t st) {
+  if (vjp) k_misfit<true><<<nb, 256, 0, st>>>(seis, res, n, part);
+  else k_misfit<false><<<nb, 256, 0, st>>>(seis, res, n, part);
+  k_misfit_final<<<1, 32, 0, st>>>(part, nb, vjp ? 1.0 : 0.5, J, status);
   return cudaGetLastError();
 }
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st) {

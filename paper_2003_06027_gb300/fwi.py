@@ -55,7 +55,7 @@ _ctx = threading.local()
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
            "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout",
            "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy",
-           "fwi_set_shot_groups", "fwi_workspace_bytes", "fwi_choose_ckpt", "fwi_last_error"]
+           "fwi_set_shot_groups", "fwi_workspace_bytes", "fwi_choose_ckpt", "fwi_forward_vjp", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -79,6 +79,7 @@ def library(build_if_missing: bool = True):
             L.fwi_misfit_grad.argtypes = [P, ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
                                           ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
                                           ctypes.c_int32, P, P, P, P, P, P]
+            L.fwi_forward_vjp.argtypes = L.fwi_misfit_grad.argtypes
             L.fwi_last_timing.argtypes = [P, P, P, P]
             L.fwi_forward_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
                                               ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
@@ -262,7 +263,7 @@ def forward_noalloc(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20,
 
 def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20,
                 pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, ckpt_every=100,
-                want_grad=True, want_src=True, want_seis=False, out=None, stream=None, device=None):
+                want_grad=True, want_src=True, want_seis=False, out=None, stream=None, device=None, _vjp=False):
     """(J, dJ/dc, dJ/dstf, dJ/dx0, seis) of J = 1/2 sum (d - d_obs)^2 (fwi_misfit_grad).
 
     ``out`` may hold preallocated outputs {"misfit", "grad", "grad_stf", "grad_x0", "seis"}.
@@ -286,12 +287,20 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
         out["seis"] = _empty_like_place(ref, (a.S, a.nrec, a.nt))
     dev = _device(ref, device)
     K = max(1, min(int(ckpt_every), a.nt))
-    _check(library().fwi_misfit_grad(
+    fn = library().fwi_forward_vjp if _vjp else library().fwi_misfit_grad
+    _check(fn(
         context(dev), ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
         float(dt), _ptr(obs), K, _ptr(out["misfit"]), _ptr(out.get("grad")),
         _ptr(out.get("grad_stf")), _ptr(out.get("grad_x0")), _ptr(out.get("seis")),
         _stream(ref, stream)))
     return out["misfit"], out.get("grad"), out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
+def forward_vjp(c, stf, x0, rec_iz, rec_ix, cotangent, **kw):
+    """(<d, v>, (dd/dc)^T v, (dd/dstf)^T v, (dd/dx0)^T v, seis) for the
+    seismograms d = forward(c, stf, x0, ...) and a cotangent v shaped like d
+    (fwi_forward_vjp: the adjoint sweep seeded with v). Keywords as misfit_grad."""
+    return misfit_grad(c, stf, x0, rec_iz, rec_ix, cotangent, _vjp=True, **kw)
 
 
 class GradGraph:
@@ -447,9 +456,10 @@ def forward_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, *, dx, dz, dt, ord
 
 def misfit_grad_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4,
                         npml=20, pml_R=1e-3, pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_GAUSSIAN,
-                        ckpt_every=100, want_src=True, want_seis=False, out=None, stream=None,
-                        device=None):
-    """(J, [dJ/dlambda, dJ/dmu, dJ/drho] [3][nz][nx], dJ/dstf, dJ/dx0, seis) (fwi_misfit_grad, FWI_ELASTIC)."""
+                        ckpt_every=100, want_grad=True, want_src=True, want_seis=False, out=None, stream=None,
+                        device=None, _vjp=False):
+    """(J, [dJ/dlambda, dJ/dmu, dJ/drho] [3][nz][nx], dJ/dstf, dJ/dx0, seis) (fwi_misfit_grad, FWI_ELASTIC).
+    With want_grad=False no model gradient is formed (its entry is None)."""
     a = _ECall(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0,
                src_kind)
     obs = _arr(observed, np.float32)
@@ -457,7 +467,8 @@ def misfit_grad_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, observed, *, d
     ref = a.vp
     nz, nx = a.vp.shape
     out.setdefault("misfit", _empty_like_place(ref, (1,), np.float64))
-    out.setdefault("grad", _empty_like_place(ref, (3, nz, nx)))
+    if want_grad:
+        out.setdefault("grad", _empty_like_place(ref, (3, nz, nx)))
     if want_src:
         out.setdefault("grad_stf", _empty_like_place(ref, (a.S, a.nt)))
         out.setdefault("grad_x0", _empty_like_place(ref, (a.S, 2)))
@@ -465,11 +476,19 @@ def misfit_grad_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, observed, *, d
         out.setdefault("seis", _empty_like_place(ref, (a.S, 2, a.nrec, a.nt)))
     dev = _device(ref, device)
     K = max(1, min(int(ckpt_every), a.nt))
-    _check(library().fwi_misfit_grad(
+    fn = library().fwi_forward_vjp if _vjp else library().fwi_misfit_grad
+    _check(fn(
         context(dev), ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
         float(dt), _ptr(obs), K, _ptr(out["misfit"]), _ptr(out.get("grad")), _ptr(out.get("grad_stf")),
         _ptr(out.get("grad_x0")), _ptr(out.get("seis")), _stream(ref, stream)))
-    return out["misfit"], out["grad"], out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+    return out["misfit"], out.get("grad"), out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
+def forward_vjp_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, cotangent, **kw):
+    """(<d, v>, (dd/d(lambda, mu, rho))^T v [3][nz][nx], (dd/dstf)^T v, (dd/dx0)^T v, seis)
+    for the elastic seismograms d [S][2][nrec][nt] and a cotangent v shaped
+    like d (fwi_forward_vjp). Keywords as misfit_grad_elastic."""
+    return misfit_grad_elastic(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, cotangent, _vjp=True, **kw)
 
 
 def elastic_velocity_grad(vp, vs, rho, grad_lame, out=None, stream=None):

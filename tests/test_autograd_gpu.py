@@ -143,3 +143,94 @@ def test_elastic_velocity_grad_elementwise(fwi_lib):
     for k in range(3):
         np.testing.assert_allclose(out[k], want[k], rtol=2e-6, atol=2e-6 * np.abs(want[k]).max())
     assert np.array_equal(g.cpu().numpy(), out)
+
+
+# ------------------------------------------------------ seismogram operators (VJP)
+def test_acoustic_seismogram_vjp_matches_oracle(fwi_lib):
+    """d = F(c, stf, x0) as a differentiable op: backward with a random
+    upstream gradient v is the adjoint sweep seeded with v, (dF/dtheta)^T v,
+    which the oracle computes with the same v as its residual."""
+    import torch
+
+    from paper_2003_06027_gb300.autograd import acoustic_seismograms
+
+    d = synth.random_acoustic(43, 31, 53, 140, 3, 8, 7, src_kind=1, nrec=9)
+    c, stf, x0 = _cuda(d["c"], True), _cuda(d["stf"], True), _cuda(d["x0"], True)
+    seis = acoustic_seismograms(c, stf, x0, _cuda(d["rec_iz"]), _cuda(d["rec_ix"]), **_kw(d, 35))
+    do = oracle.acoustic_forward(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(seis.detach().cpu().numpy(), do) <= SEIS_TOL
+    v = np.random.default_rng(43).standard_normal(do.shape).astype(np.float32)
+    seis.backward(_cuda(v))
+    go, gso, gxo = oracle.acoustic_adjoint(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]),
+                                           np.float64(v))
+    assert rel(c.grad.cpu().numpy(), go) <= GRAD_TOL, rel(c.grad.cpu().numpy(), go)
+    assert rel(stf.grad.cpu().numpy(), gso) <= GRAD_TOL, rel(stf.grad.cpu().numpy(), gso)
+    assert rel(x0.grad.cpu().numpy(), gxo) <= GRAD_TOL, rel(x0.grad.cpu().numpy(), gxo)
+    # a torch loss composed with the operator: L = sum(w * d^2) has dL/dd = 2 w d
+    c.grad = None
+    w = _cuda(np.random.default_rng(44).random(do.shape).astype(np.float32))
+    seis = acoustic_seismograms(c, stf.detach(), x0.detach(), _cuda(d["rec_iz"]), _cuda(d["rec_ix"]), **_kw(d, 35))
+    torch.sum(w * seis * seis).backward()
+    go2, _, _ = oracle.acoustic_adjoint(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]),
+                                        2.0 * np.float64(w.cpu().numpy()) * do)
+    assert rel(c.grad.cpu().numpy(), go2) <= GRAD_TOL, rel(c.grad.cpu().numpy(), go2)
+
+
+def test_forward_vjp_value_is_the_inner_product(fwi_lib):
+    """fwi_forward_vjp's scalar is <d, v> in FP64, and v = d - d_obs reproduces
+    fwi_misfit_grad's gradient bit for bit (the same sweep, the same seed)."""
+    from paper_2003_06027_gb300 import fwi
+
+    d = synth.random_acoustic(45, 29, 41, 120, 2, 4, 6, src_kind=0, nrec=6)
+    args = [_cuda(d[k]) for k in ("c", "stf", "x0", "rec_iz", "rec_ix")]
+    kw = _kw(d, 30)
+    seis = fwi.forward(*args, **fwi.problem_kwargs(d))
+    v = np.random.default_rng(45).standard_normal(tuple(seis.shape)).astype(np.float32)
+    val, _, _, _, _ = fwi.forward_vjp(*args, _cuda(v), **kw)
+    want = float(np.sum(np.float64(seis.cpu().numpy()) * np.float64(v)))
+    assert abs(float(val.cpu()[0]) - want) <= 1e-12 * max(1.0, abs(want)) + 1e-9 * np.abs(v).sum() * float(
+        seis.abs().max())
+    obs = np.float32(seis.cpu().numpy() * 0.5)
+    _, g1, s1, _, _ = fwi.misfit_grad(*args, _cuda(obs), **kw)
+    res = seis.cpu().numpy() - obs  # the residual k_misfit forms, in FP32
+    _, g2, s2, _, _ = fwi.forward_vjp(*args, _cuda(res), **kw)
+    assert np.array_equal(g1.cpu().numpy(), g2.cpu().numpy())
+    assert np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+
+
+def test_elastic_seismogram_vjp_matches_oracle(fwi_lib):
+    from paper_2003_06027_gb300.autograd import elastic_seismograms
+
+    d = synth.random_elastic(53, 27, 36, 100, 2, 4, 6, src_kind=1, nrec=6)
+    ins = [np.float64(d[k]) for k in ("vp", "vs", "rho", "stf", "x0", "mt")]
+    vp, vs, rho = (_cuda(d[k], True) for k in ("vp", "vs", "rho"))
+    stf, x0 = _cuda(d["stf"], True), _cuda(d["x0"], True)
+    seis = elastic_seismograms(vp, vs, rho, stf, x0, _cuda(d["mt"]), _cuda(d["rec_iz"]), _cuda(d["rec_ix"]),
+                               **_kw(d, 30))
+    do = oracle.elastic_forward(_geom(d), *ins)
+    assert rel(seis.detach().cpu().numpy(), do) <= SEIS_TOL
+    v = np.random.default_rng(53).standard_normal(do.shape).astype(np.float32)
+    seis.backward(_cuda(v))
+    gl, gm, gr, gso, gxo = oracle.elastic_adjoint(_geom(d), *ins, np.float64(v))
+    gvp, gvs, grho = oracle.elastic_velocity_grad(ins[0], ins[1], ins[2], gl, gm, gr)
+    for got, want in ((vp, gvp), (vs, gvs), (rho, grho), (stf, gso), (x0, gxo)):
+        assert rel(got.grad.cpu().numpy(), want) <= GRAD_TOL, rel(got.grad.cpu().numpy(), want)
+
+
+def test_elastic_misfit_skips_the_model_gradient_when_not_needed(fwi_lib):
+    """ElasticMisfit with only the sources requiring grad: the library call gets
+    no model-gradient output, and the source gradients still match the oracle."""
+    from paper_2003_06027_gb300.autograd import elastic_misfit
+
+    d = synth.random_elastic(55, 25, 34, 90, 2, 4, 6, src_kind=1, nrec=5)
+    ins = [np.float64(d[k]) for k in ("vp", "vs", "rho", "stf", "x0", "mt")]
+    do = oracle.elastic_forward(_geom(d), *ins)
+    obs = (np.random.default_rng(55).standard_normal(do.shape) * np.abs(do).max() * 0.3).astype(np.float32)
+    vp, vs, rho = (_cuda(d[k]) for k in ("vp", "vs", "rho"))
+    stf = _cuda(d["stf"], True)
+    J = elastic_misfit(vp, vs, rho, stf, _cuda(d["x0"]), _cuda(d["mt"]), _cuda(obs), _cuda(d["rec_iz"]),
+                       _cuda(d["rec_ix"]), **_kw(d, 30))
+    J.backward()
+    _, _, _, _, gso, _ = oracle.elastic_misfit_grad(_geom(d), *ins, np.float64(obs))
+    assert vp.grad is None
+    assert rel(stf.grad.cpu().numpy(), gso) <= GRAD_TOL

@@ -120,3 +120,18 @@ def test_elastic_sources():
     assert r.status() == EINVAL
     r = Req(elastic=True, kind=fwi.FWI_SRC_LINE)
     assert r.status() == EINVAL  # line sources are acoustic only
+
+
+# fwi_forward_noalloc checks the padded grid in 64-bit arithmetic before any
+# device work or pointer query, so these refusals need no GPU.
+@pytest.mark.parametrize("field,value", [("npml", 0x7FFFFFFF), ("npml", 0x40000000), ("nz", 1 << 21),
+                                         ("nx", (1 << 20) - 9)])
+def test_noalloc_grid_bound(field, value):
+    r = Req()
+    setattr(r.model, field, value)
+    seis = np.zeros((2, 4, r.nt), np.float32)
+    L = fwi.library()
+    st = L.fwi_forward_noalloc(ctypes.byref(r.model), ctypes.byref(r.src), ctypes.byref(r.rec), r.nt, 1e-3,
+                               ctypes.c_void_p(seis.ctypes.data), None)
+    assert st == EINVAL
+    assert b"grid too large" in L.fwi_last_error()

@@ -55,13 +55,13 @@ def test_workspace_grows_by_the_documented_fields(physics):
     assert ws(*args, ckpt_every=0, **kw) < min(W.values())  # the forward call holds no gradient fields
 
 
-def _brute(W, nt, budget, elastic):
+def _brute(W, nt, budget):
     best = None
     for K, w in W.items():
         if w > budget:
             continue
         nseg = math.ceil(nt / K)
-        key = (nt if elastic else (nseg - 1) * K, nseg, w)
+        key = ((nseg - 1) * K, nseg, w)  # both physics store the last segment in the forward sweep
         if best is None or key < best[0]:
             best = (key, K)
     return None if best is None else best[1]
@@ -81,7 +81,7 @@ def test_choose_ckpt_is_the_best_interval_that_fits(physics):
     assert choose(*args, budget_bytes=W[nt], **kw) == nt  # one segment fits: no checkpoint but the start
     budgets = [hi, W[nt], W[nt] - 1, lo, lo + 1] + [int(b) for b in np.linspace(lo, hi, 9)]
     for b in budgets:
-        want = _brute(W, nt, b, physics == "elastic")
+        want = _brute(W, nt, b)
         if want is None:
             continue
         got = choose(*args, budget_bytes=b, **kw)

@@ -1,15 +1,21 @@
-"""fwi_forward_noalloc, the allocation-free forward call, against fwi_forward.
+"""fwi_forward_noalloc, the allocation-free forward call, against fwi_forward
+and the FP64 oracle.
 
 Some callers cannot let a library call cudaMalloc (their device memory is
 owned by their own allocator, or their loop cannot afford the synchronisation
 an allocation may cause). fwi_forward_noalloc runs the same forward modelling
-in a fixed device array inside the library. This file is collected last so
-that a failure here comes after every other test has run.
+in a fixed device array inside the library. It launches the same kernels on
+the same inputs as fwi_forward, so its seismograms must be identical bit for
+bit; a slip in its scratch layout would show as a difference. This file is
+collected last so that a failure here comes after every other test has run.
 """
+
+import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2003_06027_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -32,6 +38,12 @@ def _run(fwi, d, fn):
     return out.cpu().numpy()
 
 
+def _geom(d):
+    return dict(nz=d["nz"], nx=d["nx"], npml=d["npml"], order=d["order"], nt=d["nt"], dz=d["dz"],
+                dx=d["dx"], dt=d["dt"], src_kind=d["src_kind"], pml_R=d["pml_R"],
+                pml_vmax=d["pml_vmax"], pml_f0=d["pml_f0"], rec_iz=d["rec_iz"], rec_ix=d["rec_ix"])
+
+
 def test_noalloc_matches_forward_on_two_calls(fwi_lib):
     from paper_2003_06027_gb300 import fwi
 
@@ -43,7 +55,19 @@ def test_noalloc_matches_forward_on_two_calls(fwi_lib):
         ref = _run(fwi, d, fwi.forward)
         got = _run(fwi, d, fwi.forward_noalloc)
         assert np.abs(ref).max() > 0
-        assert _rel(got, ref) <= SEIS_TOL, _rel(got, ref)
+        assert np.array_equal(got, ref), _rel(got, ref)
+        # and the second call on the same (now dirty) scratch repeats it exactly
+        assert np.array_equal(_run(fwi, d, fwi.forward_noalloc), ref)
+
+
+def test_noalloc_matches_oracle(fwi_lib):
+    from paper_2003_06027_gb300 import fwi
+
+    d = synth.random_acoustic(73, 33, 57, 200, 2, 8, 9, src_kind=1, nrec=7)
+    got = _run(fwi, d, fwi.forward_noalloc)
+    want = oracle.acoustic_forward(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert np.abs(want).max() > 0
+    assert _rel(got, want) <= SEIS_TOL, _rel(got, want)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(fwi_lib):
@@ -53,3 +77,23 @@ def test_noalloc_rejects_problems_beyond_its_scratch(fwi_lib):
     with pytest.raises(fwi.FwiError) as e:
         _run(fwi, d, fwi.forward_noalloc)
     assert e.value.status == 1 and "bytes" in str(e.value)
+
+
+def test_noalloc_rejects_host_pointers(fwi_lib):
+    from paper_2003_06027_gb300 import fwi
+
+    d = synth.random_acoustic(74, 30, 26, 50, 1, 4, 6, src_kind=0, nrec=3)
+    host = lambda a: np.ascontiguousarray(a)
+    c, stf, x0, iz, ix = (host(d[k]) for k in ("c", "stf", "x0", "rec_iz", "rec_ix"))
+    seis = np.zeros((1, 3, d["nt"]), np.float32)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    model = fwi._Model(fwi.FWI_ACOUSTIC, d["nz"], d["nx"], d["dz"], d["dx"], d["order"], d["npml"], d["pml_R"],
+                       d["pml_vmax"], d["pml_f0"], p(c), None, None, fwi.FWI_OP_DIVERGENCE)
+    src = fwi._Sources(1, fwi.FWI_SRC_POINT, p(x0), p(stf), None, 0)
+    rec = fwi._Receivers(3, p(iz), p(ix))
+    L = fwi.library()
+    st = L.fwi_forward_noalloc(ctypes.byref(model), ctypes.byref(src), ctypes.byref(rec), d["nt"],
+                               float(d["dt"]), ctypes.c_void_p(seis.ctypes.data), None)
+    assert st == 1 and b"device pointers" in L.fwi_last_error()
+    # the library stays usable
+    assert np.abs(_run(fwi, d, fwi.forward_noalloc)).max() > 0
