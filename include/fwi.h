@@ -253,6 +253,49 @@ fwi_status fwi_graph_launch(fwi_graph *graph, void *cuda_stream);
 fwi_status fwi_graph_status(fwi_graph *graph, void *cuda_stream);
 fwi_status fwi_graph_destroy(fwi_graph *graph);
 
+/* Batched gradients of many independent acoustic inversion instances of
+ * uneven size (different grids, time lengths, shot and receiver counts): the
+ * shot-parallel execution of the paper's Performance Benchmarking section,
+ * carried across instances. Each instance's result is exactly what
+ * fwi_misfit_grad(model_i, ..., nt_i, dt, observed_i, ckpt_every) computes
+ * (J_i and dJ_i/dc_i, Eqs. adjoint-backward and adjoint-gradient), bit for bit.
+ * Execution: every time step is ONE persistent launch whose CTAs walk a device
+ * work table of (instance, shot, tile) items, each item carrying its
+ * instance's grid and tensor maps; the whole sweep (inputs, preparation,
+ * forward sweep with checkpoints, misfits, recompute and adjoint segments,
+ * folds, outputs) is recorded once as a CUDA graph and replayed per launch.
+ *
+ * fwi_batch_create: n instances; models[i], srcs[i], recs[i], nt[i] as for
+ *   fwi_misfit_grad (acoustic, divergence form, point or Gaussian sources);
+ *   the instances share order, dx, dz and dt. observed[i] [S_i][nrec_i][nt_i],
+ *   grads[i] [nz_i][nx_i] (dJ_i/dc_i), misfit [n] (J_i, double); every
+ *   buffer is DEVICE memory owned by the caller, kept alive and in place while
+ *   the batch exists, and read again at every launch (an FWI loop updates the
+ *   models in place). ckpt_every (>= 1) is common to all instances; an
+ *   instance with nt_i < ckpt_every keeps all its steps. Allocates one device
+ *   workspace (the sum of the instances' fwi_workspace_bytes plus small
+ *   tables) on `device`, runs the sweep once (its results are left in the
+ *   outputs) and records it. FWI_EINVAL on a bad argument (the message names
+ *   the instance), FWI_ENOTIMPL for other operators or source kinds,
+ *   FWI_ENOMEM if the workspace does not fit.
+ * fwi_batch_launch: enqueue one sweep on cuda_stream (asynchronous). Two
+ *   launches of the same batch must not overlap.
+ * fwi_batch_status: wait for cuda_stream and decode the instances' status
+ *   words (the codes of fwi_misfit_grad); *instance (may be NULL) receives
+ *   the first failing instance or -1.
+ * fwi_batch_launches: kernels enqueued by one sweep.
+ * fwi_batch_destroy: free the graph and the workspace. */
+typedef struct fwi_batch fwi_batch;
+fwi_status fwi_batch_create(int32_t device, int32_t n, const fwi_model *models,
+                            const fwi_sources *srcs, const fwi_receivers *recs,
+                            const int32_t *nt, float dt, const float *const *observed,
+                            int32_t ckpt_every, double *misfit, float *const *grads,
+                            fwi_batch **batch);
+fwi_status fwi_batch_launch(fwi_batch *batch, void *cuda_stream);
+fwi_status fwi_batch_status(fwi_batch *batch, void *cuda_stream, int32_t *instance);
+int64_t fwi_batch_launches(const fwi_batch *batch);
+fwi_status fwi_batch_destroy(fwi_batch *batch);
+
 /* Forward modelling that allocates no device memory, for callers that cannot
  * let a library call cudaMalloc: applications that hand all device memory to
  * their own allocator and account for every byte, and latency-sensitive loops

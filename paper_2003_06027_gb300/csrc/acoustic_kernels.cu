@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -165,6 +166,71 @@ struct AdjSmem {
   float red[32];
   uint64_t bar;
 };
+// Multi-instance launches keep the current tile's step parameters after the
+// kernel's own shared memory.
+constexpr size_t FWD_SMEM_MAIN = (sizeof(FwdSmem) + 15) / 16 * 16;
+constexpr size_t ADJ_SMEM_MAIN = (sizeof(AdjSmem) + 15) / 16 * 16;
+
+// Multi-instance launches: the instance of tile t (the last i with tile_start[i] <= t).
+__device__ __forceinline__ int batch_instance(const BatchArgs& b, int t) {
+  int lo = 0, hi = b.n_active - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(b.tile_start + mid) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// Orders the host's writes of a tensor map in global memory before the TMA
+// unit reads it.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+               : "memory");
+}
+// Step parameters of instance i at step b.n, copied into shared memory by warp 0
+// (then one barrier). KIND: 0 forward sweep (stores the fluxes from the
+// instance's last segment on), 1 recompute (stores), 2 adjoint.
+template <int KIND>
+__device__ __forceinline__ void batch_load_step(const BatchArgs& b, int i, AcuStep& dst) {
+  if (threadIdx.x < 32) {
+    const AcuInst* in = b.inst + i;
+    const int* src = reinterpret_cast<const int*>(&in->p);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int w = threadIdx.x; w < (int)(sizeof(AcuStep) / 4); w += 32) d[w] = __ldg(src + w);
+    __syncwarp();
+    if (threadIdx.x == 0) {
+      const int n = b.n;
+      const long long f = in->field;
+      float* slot = in->slot + (long long)(n - (n / b.K) * b.K) * 2 * f;
+      dst.n = n;
+      if (KIND == 2) {
+        dst.cur = (n + 1) & 1;  // lambda_{n+1}; lambda_{n+2} -> lambda_n in the other half
+        dst.slot_px = slot;
+        dst.slot_pz = slot + f;
+        dst.zx_in = in->zx[(n + 1) & 1];
+        dst.zx_out = in->zx[n & 1];
+        dst.zz_in = in->zz[(n + 1) & 1];
+        dst.zz_out = in->zz[n & 1];
+        dst.px_in = in->px[(n + 1) & 1];
+        dst.px_out = in->px[n & 1];
+        dst.pz_in = in->pz[(n + 1) & 1];
+        dst.pz_out = in->pz[n & 1];
+        dst.hx_out = in->hxp + (n & 1) * f;
+        dst.hz_out = in->hzp + (n & 1) * f;
+      } else {
+        dst.cur = n & 1;
+        dst.psix_in = in->psix[n & 1];
+        dst.psix_out = in->psix[(n + 1) & 1];
+        dst.psiz_in = in->psiz[n & 1];
+        dst.psiz_out = in->psiz[(n + 1) & 1];
+        const bool keep = KIND == 1 || n >= in->nlast;
+        dst.slot_px = keep ? slot : nullptr;
+        dst.slot_pz = keep ? slot + f : nullptr;
+      }
+    }
+  }
+  __syncthreads();
+}
 
 }  // namespace
 
@@ -173,16 +239,34 @@ struct AdjSmem {
 // per axis, with psi <- b_h psi + a_h D+u and zeta <- b zeta + a D-(q) (zeta is
 // kept multiplied by dt^2). RECORD writes the receiver samples; STORE keeps
 // p = D+u + psi of every half point (the operand of the gradient correlation).
-template <int N, bool RECORD, bool STORE>
+//
+// MULTI: one launch over the tiles of several instances (BatchArgs); each tile
+// takes its instance's parameters and tensor maps from the device table, and a
+// forward-sweep launch (RECORD and STORE) stores the fluxes only for the
+// instances in their last segment (a null slot otherwise).
+template <int N, bool RECORD, bool STORE, bool MULTI>
 __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     acu_fwd_step(const __grid_constant__ CUtensorMap tmap_u, const __grid_constant__ CUtensorMap tmap_m,
-                 const AcuStep p) {
+                 const __grid_constant__ AcuStep p0, const AcuCoef cf, const BatchArgs b) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FwdSmem& sh = *reinterpret_cast<FwdSmem*>(smem_raw);
-  const Grid& g = p.g;
+  AcuStep& shp = *reinterpret_cast<AcuStep*>(smem_raw + FWD_SMEM_MAIN);  // MULTI only
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int pitch = g.pitch;
   const uint64_t pol = STORE ? l2_evict_first() : 0ull;  // segment slots stream through L2
+  const int ntiles = MULTI ? b.ntiles : p0.ntiles;
+  // TMA fetch of tile tt (one thread)
+  auto fetch_next = [&](int tt) {
+    if (MULTI) {
+      const int i = batch_instance(b, tt);
+      const AcuInst* in = b.inst + i;
+      const Grid gi = in->p.g;
+      tensormap_acquire(&in->mu);
+      tensormap_acquire(&in->mm);
+      fetch_tile(&in->mu, &in->mm, gi, (b.n & 1) * in->p.S, tt - __ldg(b.tile_start + i), sh.u, sh.m, &sh.bar);
+    } else {
+      fetch_tile(&tmap_u, &tmap_m, p0.g, p0.cur * p0.S_pair + p0.s0, tt, sh.u, sh.m, &sh.bar);
+    }
+  };
 
   // one operand buffer: the next tile's fetch is issued once stage 1 of this
   // tile (its last reader) is done, and overlaps stage 2
@@ -191,13 +275,21 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < p.ntiles)
-    fetch_tile(&tmap_u, &tmap_m, g, p.cur * p.S_pair + p.s0, blockIdx.x, sh.u, sh.m, &sh.bar);
+  if (tid == 0 && (int)blockIdx.x < ntiles) fetch_next(blockIdx.x);
 
   int it = 0;
-  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
     const int tn = t + gridDim.x;
-    const TileId id = tile_decode(g, t);
+    int tl = t;  // tile index within its instance
+    if (MULTI) {
+      const int i = batch_instance(b, t);
+      tl = t - __ldg(b.tile_start + i);
+      batch_load_step<RECORD ? 0 : 1>(b, i, shp);  // after the previous tile's closing barrier
+    }
+    const AcuStep& p = MULTI ? shp : p0;
+    const Grid& g = p.g;
+    const int pitch = g.pitch;
+    const TileId id = tile_decode(g, tl);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
     float* __restrict__ uprev = p.u + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
@@ -242,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       for (int e = 0; e < 4; e++) {
         float gx = 0.f;
 #pragma unroll
-        for (int k = 1; k <= N; k++) gx += p.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
+        for (int k = 1; k <= N; k++) gx += cf.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
         pp[e] = gx;
       }
       const long long id0 = base + (long long)z * pitch + hb;
@@ -264,7 +356,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       for (int e = 0; e < 4; e++) q[e] = (rowok && hb + e >= 0 && hb + e < g.Nx - 1) ? (mv[e] + mv[e + 1]) * pp[e] : 0.f;
       st4(sh.qx + r * QXW + 4 * gq, make_float4(q[0], q[1], q[2], q[3]));
       // every own row is written (zero beyond the grid): the adjoint multiplies these by zero there
-      if (STORE && own)
+      if (STORE && own && (!MULTI || p.slot_px))
         st4_stream(p.slot_px + id0, rowok ? make_float4(pp[0], pp[1], pp[2], pp[3]) : make_float4(0.f, 0.f, 0.f, 0.f), pol);
     };
     // ---- stage 1b: z fluxes at one half row (the tile's halo rows)
@@ -273,7 +365,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int k = 1; k <= N; k++)
-        acc4(acc, p.c1z[k - 1], ld4(su + (hr + 4 + k) * UW + 8 + 4 * c), ld4(su + (hr + 5 - k) * UW + 8 + 4 * c));
+        acc4(acc, cf.c1z[k - 1], ld4(su + (hr + 4 + k) * UW + 8 + 4 * c), ld4(su + (hr + 5 - k) * UW + 8 + 4 * c));
       float pp[4];
       f4a(acc, pp);
       if (pmlz && layer_h(hz, hz, g.npml, g.nz)) {
@@ -304,8 +396,8 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
 #pragma unroll
       for (int k = 1; k <= N; k++) {
-        acc4(a0, p.c1z[k - 1], w[k + N - 1], w[N - k]);
-        acc4(a1, p.c1z[k - 1], w[k + N], w[N - k + 1]);
+        acc4(a0, cf.c1z[k - 1], w[k + N - 1], w[N - k]);
+        acc4(a1, cf.c1z[k - 1], w[k + N], w[N - k + 1]);
       }
       float pp[2][4];
       f4a(a0, pp[0]);
@@ -339,7 +431,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         q[2] = (hv && xb + 2 < g.Nx) ? (ma.z + mb.z) * pp[rr][2] : 0.f;
         q[3] = (hv && xb + 3 < g.Nx) ? (ma.w + mb.w) * pp[rr][3] : 0.f;
         st4(sh.qz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(q[0], q[1], q[2], q[3]));
-        if (STORE)
+        if (STORE && (!MULTI || p.slot_pz))
           st4_stream(p.slot_pz + idz, hz < g.Nz ? make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3])
                                                 : make_float4(0.f, 0.f, 0.f, 0.f), pol);
       }
@@ -356,7 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     ucur[0] = ld4(su + (2 * ty + H) * UW + 4 * tx + H);
     ucur[1] = ld4(su + (2 * ty + 1 + H) * UW + 4 * tx + H);
     __syncthreads();
-    if (tid == 0 && tn < p.ntiles) fetch_tile(&tmap_u, &tmap_m, g, p.cur * p.S_pair + p.s0, tn, sh.u, sh.m, &sh.bar);
+    if (tid == 0 && tn < ntiles) fetch_next(tn);
 
     // ---- stage 2: divergence + CPML zeta + leapfrog + source + receivers
     cp_async_wait_all();  // this thread's own u^{n-1} copies
@@ -368,8 +460,8 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
 #pragma unroll
       for (int k = 1; k <= N; k++) {
-        acc4(a0, p.c2z[k - 1], w[k + N - 1], w[N - k]);
-        acc4(a1, p.c2z[k - 1], w[k + N], w[N - k + 1]);
+        acc4(a0, cf.c2z[k - 1], w[k + N - 1], w[N - k]);
+        acc4(a1, cf.c2z[k - 1], w[k + N], w[N - k + 1]);
       }
       f4a(a0, hzv[0]);
       f4a(a1, hzv[1]);
@@ -392,7 +484,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       for (int e = 0; e < 4; e++) {
         float hx = 0.f;
 #pragma unroll
-        for (int k = 1; k <= N; k++) hx += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
+        for (int k = 1; k <= N; k++) hx += cf.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
         hxv[e] = hx;
         rv[e] = hx + hzv[rr][e];
       }
@@ -427,7 +519,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       if (srcbox) {
         const int di = z - i0;
         if (di >= 0 && di < nb) {
-          const float amp = p.dt2 * stf_n;
+          const float amp = cf.dt2 * stf_n;
 #pragma unroll
           for (int e = 0; e < 4; e++) {
             const int dj = xb + e - j0;
@@ -466,30 +558,52 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
 // Hx = (1 + a_x) lambda + a_x Zx and Hz likewise at its own cells, and a CPML
 // tile fetches its x (z) stencil operand from Hx (Hz) instead of lambda. Z is
 // then read and written only by the thread that owns the cell.
-template <int N>
+// MULTI: one launch over the tiles of several instances, as for the forward step.
+template <int N, bool MULTI>
 __global__ void __launch_bounds__(NTHREADS, 3)
     acu_adj_step(const __grid_constant__ CUtensorMap tmap_lx, const __grid_constant__ CUtensorMap tmap_lz,
                  const __grid_constant__ CUtensorMap tmap_hx, const __grid_constant__ CUtensorMap tmap_hz,
-                 const __grid_constant__ CUtensorMap tmap_m, const AcuStep p) {
+                 const __grid_constant__ CUtensorMap tmap_m, const __grid_constant__ AcuStep p0, const AcuCoef cf,
+                 const BatchArgs b) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   AdjSmem& sh = *reinterpret_cast<AdjSmem*>(smem_raw);
-  const Grid& g = p.g;
+  AcuStep& shp = *reinterpret_cast<AcuStep*>(smem_raw + ADJ_SMEM_MAIN);  // MULTI only
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int pitch = g.pitch;
   const uint64_t pol = l2_evict_first();  // the stored fluxes are read once: evict them first
+  const int ntiles = MULTI ? b.ntiles : p0.ntiles;
 
   // one operand buffer: the next tile's fetch is issued once stage 1 of this
   // tile (its last reader) is done, and overlaps stage 2
   auto fetch = [&](int tt) {
-    const TileId f = tile_decode(g, tt);
-    const int plane = p.cur * p.S_pair + p.s0 + f.s;
-    const CUtensorMap* xm = tile_pml_x(g, f.x0) ? &tmap_hx : &tmap_lx;
-    const CUtensorMap* zm = tile_pml_z(g, f.z0) ? &tmap_hz : &tmap_lz;
+    const CUtensorMap *mlx = &tmap_lx, *mlz = &tmap_lz, *mhx = &tmap_hx, *mhz = &tmap_hz, *mm = &tmap_m;
+    Grid gf = p0.g;
+    int plane0 = p0.cur * p0.S_pair + p0.s0, tl = tt;
+    if (MULTI) {
+      const int i = batch_instance(b, tt);
+      const AcuInst* in = b.inst + i;
+      gf = in->p.g;
+      plane0 = ((b.n + 1) & 1) * in->p.S;
+      tl = tt - __ldg(b.tile_start + i);
+      mlx = &in->lx;
+      mlz = &in->lz;
+      mhx = &in->hx;
+      mhz = &in->hz;
+      mm = &in->mm;
+    }
+    const TileId f = tile_decode(gf, tl);
+    const int plane = plane0 + f.s;
+    const CUtensorMap* xm = tile_pml_x(gf, f.x0) ? mhx : mlx;
+    const CUtensorMap* zm = tile_pml_z(gf, f.z0) ? mhz : mlz;
+    if (MULTI) {
+      tensormap_acquire(xm);
+      tensormap_acquire(zm);
+      tensormap_acquire(mm);
+    }
     fence_proxy_async();
     mbar_expect_tx(&sh.bar, XS_BYTES + ZS_BYTES + M_BYTES);
     tma_3d(sh.xs, xm, f.x0 - H + APRON, f.z0 + APRON, plane, &sh.bar);
     tma_3d(sh.zs, zm, f.x0 + APRON, f.z0 - H + APRON, plane, &sh.bar);
-    tma_2d(sh.m, &tmap_m, f.x0 - 4 + APRON, f.z0 - 4 + APRON, &sh.bar);
+    tma_2d(sh.m, mm, f.x0 - 4 + APRON, f.z0 - 4 + APRON, &sh.bar);
   };
 
   if (tid == 0) {
@@ -497,12 +611,21 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < p.ntiles) fetch(blockIdx.x);
+  if (tid == 0 && (int)blockIdx.x < ntiles) fetch(blockIdx.x);
 
   int it = 0;
-  for (int t = blockIdx.x; t < p.ntiles; t += gridDim.x, it++) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
     const int tn = t + gridDim.x;
-    const TileId id = tile_decode(g, t);
+    int tl = t;  // tile index within its instance
+    if (MULTI) {
+      const int i = batch_instance(b, t);
+      tl = t - __ldg(b.tile_start + i);
+      batch_load_step<2>(b, i, shp);  // after the previous tile's closing barrier
+    }
+    const AcuStep& p = MULTI ? shp : p0;
+    const Grid& g = p.g;
+    const int pitch = g.pitch;
+    const TileId id = tile_decode(g, tl);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
@@ -557,7 +680,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         for (int e = 0; e < 4; e++) {
           float dq = 0.f;
   #pragma unroll
-          for (int k = 1; k <= N; k++) dq += p.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
+          for (int k = 1; k <= N; k++) dq += cf.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
           const bool inh = !EDGE || (rowok && hb + e >= 0 && hb + e < g.Nx - 1);
           const float qb = inh ? dq : 0.f;
           const float pb = (mv[e] + mv[e + 1]) * qb;
@@ -585,7 +708,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   #pragma unroll
         for (int k = 1; k <= N; k++)
-          acc4(acc, p.c1z[k - 1], ld4(sz + (hr + 4 + k) * TILE_X + 4 * c), ld4(sz + (hr + 5 - k) * TILE_X + 4 * c));
+          acc4(acc, cf.c1z[k - 1], ld4(sz + (hr + 4 + k) * TILE_X + 4 * c), ld4(sz + (hr + 5 - k) * TILE_X + 4 * c));
         float dq[4];
         f4a(acc, dq);
         const bool hv = !EDGE || (hz >= 0 && hz < g.Nz - 1);
@@ -626,8 +749,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
   #pragma unroll
         for (int k = 1; k <= N; k++) {
-          acc4(a0, p.c1z[k - 1], w[k + N - 1], w[N - k]);
-          acc4(a1, p.c1z[k - 1], w[k + N], w[N - k + 1]);
+          acc4(a0, cf.c1z[k - 1], w[k + N - 1], w[N - k]);
+          acc4(a1, cf.c1z[k - 1], w[k + N], w[N - k + 1]);
         }
         float dq[2][4];
         f4a(a0, dq[0]);
@@ -681,7 +804,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         else lc[rr] = ldg4(p.lam + (long long)(p.cur * p.S_pair + p.s0) * g.slice + base + (long long)(z0 + r) * pitch + xb);
       }
       __syncthreads();
-      if (tid == 0 && tn < p.ntiles) fetch(tn);  // the operand buffer is free
+      if (tid == 0 && tn < ntiles) fetch(tn);  // the operand buffer is free
 
       // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
       float* __restrict__ lprev = p.lam + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
@@ -702,8 +825,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
   #pragma unroll
         for (int k = 1; k <= N; k++) {
-          acc4(a0, p.c2z[k - 1], w[k + N - 1], w[N - k]);
-          acc4(a1, p.c2z[k - 1], w[k + N], w[N - k + 1]);
+          acc4(a0, cf.c2z[k - 1], w[k + N - 1], w[N - k]);
+          acc4(a1, cf.c2z[k - 1], w[k + N], w[N - k + 1]);
         }
         f4a(a0, dzv[0]);
         f4a(a1, dzv[1]);
@@ -732,7 +855,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         for (int e = 0; e < 4; e++) {
           float dxv = 0.f;
   #pragma unroll
-          for (int k = 1; k <= N; k++) dxv += p.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
+          for (int k = 1; k <= N; k++) dxv += cf.c2x[k - 1] * (v[e + k + 3] - v[e - k + 4]);
           const bool valid = !EDGE || (z < g.Nz && xb + e < g.Nx);
           lnew[rr][e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[rr][e]) : 0.f;
           const float ixl = e == 0 ? imxl[rr] : imx[rr][e - 1];
@@ -861,7 +984,9 @@ namespace {
 
 std::mutex g_init_mu;
 unsigned long long g_inited = 0;  // bit per device
-int g_grid_fwd[64][2][4], g_grid_adj[64][2];
+// resident-CTA grids: single-instance forward variants (record, store), adjoint,
+// and the multi-instance forward sweep / recompute and adjoint
+int g_grid_fwd[64][2][4], g_grid_adj[64][2], g_grid_fwd_m[64][2][2], g_grid_adj_m[64][2];
 
 template <typename K>
 cudaError_t setup_kernel(K k, int smem, int* grid) {
@@ -875,6 +1000,25 @@ cudaError_t setup_kernel(K k, int smem, int* grid) {
   return cudaSuccess;
 }
 
+constexpr int FWD_SMEM_M = (int)(FWD_SMEM_MAIN + sizeof(AcuStep));
+constexpr int ADJ_SMEM_M = (int)(ADJ_SMEM_MAIN + sizeof(AcuStep));
+
+template <int N>
+cudaError_t setup_order(int dev, int o) {
+  const int fs = (int)sizeof(FwdSmem), as = (int)sizeof(AdjSmem);
+  cudaError_t e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, false, false>, fs, &g_grid_fwd[dev][o][0])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, false, false>, fs, &g_grid_fwd[dev][o][1])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, true, false>, fs, &g_grid_fwd[dev][o][2])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, true, false>, fs, &g_grid_fwd[dev][o][3])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, true, true>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][0])) != cudaSuccess)
+    return e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, true, true>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][1])) != cudaSuccess)
+    return e;
+  if ((e = setup_kernel(acu_adj_step<N, false>, as, &g_grid_adj[dev][o])) != cudaSuccess) return e;
+  return setup_kernel(acu_adj_step<N, true>, ADJ_SMEM_M, &g_grid_adj_m[dev][o]);
+}
+
 cudaError_t ensure_init(int* dev_out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -883,19 +1027,22 @@ cudaError_t ensure_init(int* dev_out) {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_init_mu);
   if (g_inited & (1ull << dev)) return cudaSuccess;
-  const int fs = (int)sizeof(FwdSmem), as = (int)sizeof(AdjSmem);
-  if ((e = setup_kernel(acu_fwd_step<2, false, false>, fs, &g_grid_fwd[dev][0][0])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<2, true, false>, fs, &g_grid_fwd[dev][0][1])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<2, false, true>, fs, &g_grid_fwd[dev][0][2])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<2, true, true>, fs, &g_grid_fwd[dev][0][3])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<4, false, false>, fs, &g_grid_fwd[dev][1][0])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<4, true, false>, fs, &g_grid_fwd[dev][1][1])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<4, false, true>, fs, &g_grid_fwd[dev][1][2])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<4, true, true>, fs, &g_grid_fwd[dev][1][3])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_adj_step<2>, as, &g_grid_adj[dev][0])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_adj_step<4>, as, &g_grid_adj[dev][1])) != cudaSuccess) return e;
+  if ((e = setup_order<2>(dev, 0)) != cudaSuccess) return e;
+  if ((e = setup_order<4>(dev, 1)) != cudaSuccess) return e;
   g_inited |= 1ull << dev;
   return cudaSuccess;
+}
+
+AcuCoef coef_of(const AcuStep& p) {
+  AcuCoef c;
+  for (int k = 0; k < 4; k++) {
+    c.c1x[k] = p.c1x[k];
+    c.c1z[k] = p.c1z[k];
+    c.c2x[k] = p.c2x[k];
+    c.c2z[k] = p.c2z[k];
+  }
+  c.dt2 = p.dt2;
+  return c;
 }
 
 }  // namespace
@@ -932,17 +1079,48 @@ cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, b
   const int o = p.N == 2 ? 0 : 1;
   const int grid = std::min(p.ntiles, g_grid_fwd[dev][o][v]);
   const size_t smem = sizeof(FwdSmem);
+  const AcuCoef cf = coef_of(p);
+  BatchArgs nb;
+  memset(&nb, 0, sizeof nb);
+#define FWD_LAUNCH(NN, R, S) acu_fwd_step<NN, R, S, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p, cf, nb)
   if (p.N == 2) {
-    if (record && store) acu_fwd_step<2, true, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
-    else if (record) acu_fwd_step<2, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
-    else if (store) acu_fwd_step<2, false, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
-    else acu_fwd_step<2, false, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    if (record && store) FWD_LAUNCH(2, true, true);
+    else if (record) FWD_LAUNCH(2, true, false);
+    else if (store) FWD_LAUNCH(2, false, true);
+    else FWD_LAUNCH(2, false, false);
   } else {
-    if (record && store) acu_fwd_step<4, true, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
-    else if (record) acu_fwd_step<4, true, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
-    else if (store) acu_fwd_step<4, false, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
-    else acu_fwd_step<4, false, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p);
+    if (record && store) FWD_LAUNCH(4, true, true);
+    else if (record) FWD_LAUNCH(4, true, false);
+    else if (store) FWD_LAUNCH(4, false, true);
+    else FWD_LAUNCH(4, false, false);
   }
+#undef FWD_LAUNCH
+  return cudaGetLastError();
+}
+
+// Multi-instance forward step b.n over the tiles of instances [0, b.n_active):
+// the forward sweep (record: receivers recorded, fluxes stored by instances in
+// their last segment) or the recompute of a segment (fluxes stored).
+cudaError_t launch_acu_fwd_batch(const BatchArgs& b, const AcuCoef& cf, int N, bool record, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ensure_init(&dev);
+  if (e != cudaSuccess) return e;
+  if (b.ntiles <= 0) return cudaSuccess;
+  const int o = N == 2 ? 0 : 1;
+  const int grid = std::min(b.ntiles, g_grid_fwd_m[dev][o][record ? 0 : 1]);
+  CUtensorMap none;
+  memset(&none, 0, sizeof none);
+  AcuStep p0;
+  memset(&p0, 0, sizeof p0);
+#define FWD_LAUNCH(NN, R) acu_fwd_step<NN, R, true, true><<<grid, NTHREADS, FWD_SMEM_M, st>>>(none, none, p0, cf, b)
+  if (N == 2) {
+    if (record) FWD_LAUNCH(2, true);
+    else FWD_LAUNCH(2, false);
+  } else {
+    if (record) FWD_LAUNCH(4, true);
+    else FWD_LAUNCH(4, false);
+  }
+#undef FWD_LAUNCH
   return cudaGetLastError();
 }
 
@@ -967,8 +1145,29 @@ cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t s
   if (e != cudaSuccess) return e;
   const int grid = std::min(p.ntiles, g_grid_adj[dev][p.N == 2 ? 0 : 1]);
   const size_t smem = sizeof(AdjSmem);
-  if (p.N == 2) acu_adj_step<2><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p);
-  else acu_adj_step<4><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p);
+  const AcuCoef cf = coef_of(p);
+  BatchArgs nb;
+  memset(&nb, 0, sizeof nb);
+  if (p.N == 2)
+    acu_adj_step<2, false><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p, cf, nb);
+  else
+    acu_adj_step<4, false><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p, cf, nb);
+  return cudaGetLastError();
+}
+
+// Multi-instance adjoint step b.n over the tiles of instances [0, b.n_active).
+cudaError_t launch_acu_adj_batch(const BatchArgs& b, const AcuCoef& cf, int N, cudaStream_t st) {
+  int dev;
+  cudaError_t e = ensure_init(&dev);
+  if (e != cudaSuccess) return e;
+  if (b.ntiles <= 0) return cudaSuccess;
+  const int grid = std::min(b.ntiles, g_grid_adj_m[dev][N == 2 ? 0 : 1]);
+  CUtensorMap none;
+  memset(&none, 0, sizeof none);
+  AcuStep p0;
+  memset(&p0, 0, sizeof p0);
+  if (N == 2) acu_adj_step<2, true><<<grid, NTHREADS, ADJ_SMEM_M, st>>>(none, none, none, none, none, p0, cf, b);
+  else acu_adj_step<4, true><<<grid, NTHREADS, ADJ_SMEM_M, st>>>(none, none, none, none, none, p0, cf, b);
   return cudaGetLastError();
 }
 

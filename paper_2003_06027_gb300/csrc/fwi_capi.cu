@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -22,6 +23,9 @@
 namespace fwi {
 cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
 cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st);
+cudaError_t launch_acu_fwd_batch(const BatchArgs& b, const AcuCoef& cf, int N, bool record, cudaStream_t st);
+cudaError_t launch_acu_adj_batch(const BatchArgs& b, const AcuCoef& cf, int N, cudaStream_t st);
+cudaError_t launch_copy_table(const CopyDesc* d, int n, cudaStream_t st);
 cudaError_t acu_kernels_init();
 cudaError_t ela_kernels_init();
 cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, const float* mh);
@@ -286,6 +290,8 @@ fwi_status ensure_arena(fwi_ctx* ctx, Plan& P, cudaStream_t st) {
   return FWI_OK;
 }
 
+void fill_step(const Plan& P, const fwi_model* M, float dt, AcuStep& p);
+
 // Copy inputs into the workspace and build m, CPML tables, source weights,
 // receiver lists; queue the model checks.
 fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
@@ -317,7 +323,19 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
     LK(1, launch_src_prep(P.S, P.kind, P.x0, g, M->dx, M->dz, P.src_box, P.src_w, P.status, st));
   LK(1, launch_rec_csr(P.nrec, P.rec_in, P.rec_in + P.nrec, g, P.rec_cell, P.rec_key, P.tstart, P.tcursor, P.tlist,
                        P.status, st));
+  fill_step(P, M, dt, p);
+  (void)ctx;
+  return FWI_OK;
+}
 
+// The step parameters of a call (everything but the fields of one time step),
+// from the plan's layout alone: no device work.
+void fill_step(const Plan& P, const fwi_model* M, float dt, AcuStep& p) {
+  const Grid& g = P.g;
+  float a[4];
+  fd_coeffs(M->order, a);
+  const int L = P.tablen;
+  float* T = P.tab;
   memset(&p, 0, sizeof p);
   p.g = g;
   p.S = P.S;
@@ -354,8 +372,6 @@ fwi_status prepare(fwi_ctx* ctx, Plan& P, const fwi_model* M, const fwi_sources*
   p.x0 = P.x0;
   p.dx = M->dx;
   p.dz = M->dz;
-  (void)ctx;
-  return FWI_OK;
 }
 
 // Adjoint weights: stage 1 -a_k dt^2/dx (qbar = -dt^2 D+ hhat), stage 2 a_k/dx.
@@ -519,13 +535,17 @@ fwi_status fwi::arena_acquire(fwi_ctx* ctx, size_t bytes, const std::string& key
 fwi_status fwi::finish_status_dev(fwi_ctx* ctx, const int* d_status, cudaStream_t st) {
   CK(cudaMemcpyAsync(ctx->h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  const int s = *ctx->h_status;
-  if (s & ST_TIMEOUT) return fail(FWI_ETIMEOUT, "a step kernel gave up waiting for its tile fetch");  // first: later results are invalid
-  if (s & ST_BADMODEL) return fail(FWI_EINVAL, "the medium must be finite with vp > 0, rho > 0, vp^2 >= 2 vs^2");
-  if (s & ST_BADREC) return fail(FWI_EINVAL, "a receiver lies outside the physical grid");
-  if (s & ST_BADSRC) return fail(FWI_EINVAL, "a source (or its 7x7 Gaussian support) lies outside the grid");
-  if (s & ST_CFL) return fail(FWI_ECFL, "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
-  if (s & ST_NONFINITE) return fail(FWI_EUNSTABLE, "non-finite value in the seismograms or the misfit");
+  return decode_status(*ctx->h_status, "");
+}
+
+// The status code of a device status word (FWI_OK when no bit is set).
+fwi_status fwi::decode_status(int s, const std::string& where) {
+  if (s & ST_TIMEOUT) return fail(FWI_ETIMEOUT, where + "a step kernel gave up waiting for its tile fetch");  // first: later results are invalid
+  if (s & ST_BADMODEL) return fail(FWI_EINVAL, where + "the medium must be finite with vp > 0, rho > 0, vp^2 >= 2 vs^2");
+  if (s & ST_BADREC) return fail(FWI_EINVAL, where + "a receiver lies outside the physical grid");
+  if (s & ST_BADSRC) return fail(FWI_EINVAL, where + "a source (or its 7x7 Gaussian support) lies outside the grid");
+  if (s & ST_CFL) return fail(FWI_ECFL, where + "CFL condition violated: c_max dt sqrt(1/dx^2+1/dz^2) sum|a_k| > 1");
+  if (s & ST_NONFINITE) return fail(FWI_EUNSTABLE, where + "non-finite value in the seismograms or the misfit");
   return FWI_OK;
 }
 
@@ -1176,6 +1196,381 @@ fwi_status fwi_graph_destroy(fwi_graph* g) {
   cudaSetDevice(g->ctx->device);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   delete g;
+  return FWI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched gradients of several acoustic instances (fwi_batch_*). Every
+// instance keeps the layout of its own single call (one plan per instance in
+// one arena); a device table describes the instances, and each time step is
+// ONE persistent launch over the tiles of all instances that take part in it.
+// Instances are sorted by nt, longest first, so that at any step those that
+// take part form a prefix. The checkpoint interval K is common, so segment
+// boundaries line up across instances: every instance recomputes, stores and
+// runs the adjoint of a segment in the same launches. The whole sweep (inputs,
+// preparation, forward sweep, misfits, reverse sweep, folds, outputs) is
+// recorded as one CUDA graph.
+struct fwi_batch {
+  fwi_ctx* ctx = nullptr;
+  int n = 0, K = 0, N = 0, max_nt = 0;
+  float dt = 0.f;
+  std::vector<int> order;  // sorted position -> caller's index
+  std::vector<Plan> P;
+  std::vector<fwi_model> M;
+  std::vector<fwi_sources> Sv;
+  std::vector<fwi_receivers> R;
+  std::vector<const float*> obs;
+  std::vector<float*> grad;  // caller's order
+  double* misfit = nullptr;  // device [n], caller's order
+  std::vector<int> ts;       // first tile of each sorted instance, [n + 1]
+  AcuCoef cf_fwd{}, cf_adj{};
+  AcuInst* d_inst = nullptr;
+  int* d_ts = nullptr;
+  CopyDesc* d_copy = nullptr;
+  std::vector<int> sv0, sv1, rs0, rs1;  // per checkpoint index: descriptor ranges of the saves and restores
+  int* h_status = nullptr;              // pinned [n]
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+};
+
+namespace {
+
+void batch_free(fwi_batch* B) {
+  if (!B) return;
+  if (B->ctx) cudaSetDevice(B->ctx->device);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->h_status) cudaFreeHost(B->h_status);
+  if (B->ctx) fwi_destroy(B->ctx);
+  delete B;
+}
+
+// Instances taking part in step n (nt > n): a prefix of the sorted list.
+int batch_active(const fwi_batch* B, int n) {
+  int a = 0;
+  while (a < B->n && B->P[a].nt > n) a++;
+  return a;
+}
+
+// Enqueue one whole sweep on `st` (the recorded graph is this, captured).
+fwi_status batch_enqueue(fwi_batch* B, cudaStream_t st) {
+  fwi_ctx* ctx = B->ctx;
+  const int n = B->n, K = B->K;
+  ctx->launches = 0;
+  for (int i = 0; i < n; i++) {
+    Plan& P = B->P[i];
+    char* base = reinterpret_cast<char*>(P.status);  // the plan's layout starts with its status word
+    CK(cudaMemsetAsync(base, 0, 64, st));
+    CK(cudaMemsetAsync(base + P.zero_lo, 0, P.zero_hi - P.zero_lo, st));
+    AcuStep p;
+    fwi_status v = prepare(ctx, P, &B->M[i], &B->Sv[i], &B->R[i], B->dt, st, p);
+    if (v != FWI_OK) return v;
+    const long long ns = (long long)P.S * P.nrec * P.nt;
+    if (ns > 0) CK(cudaMemcpyAsync(P.res, B->obs[i], (size_t)ns * 4, cudaMemcpyDefault, st));
+  }
+  BatchArgs b;
+  memset(&b, 0, sizeof b);
+  b.inst = B->d_inst;
+  b.tile_start = B->d_ts;
+  b.K = K;
+  // forward sweep: checkpoints at segment starts, one launch per step
+  for (int nn = 0; nn < B->max_nt; nn++) {
+    if (nn % K == 0) {
+      const int k = nn / K;
+      LK(1, launch_copy_table(B->d_copy + B->sv0[k], B->sv1[k] - B->sv0[k], st));
+    }
+    b.n = nn;
+    b.n_active = batch_active(B, nn);
+    b.ntiles = B->ts[b.n_active];
+    LK(1, launch_acu_fwd_batch(b, B->cf_fwd, B->N, true, st));
+  }
+  for (int i = 0; i < n; i++) {
+    Plan& P = B->P[i];
+    const long long ns = (long long)P.S * P.nrec * P.nt;
+    if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, false, st));
+    else CK(cudaMemsetAsync(P.J, 0, 8, st));
+  }
+  // reverse sweep, segment by segment
+  const int max_nseg = (B->max_nt + K - 1) / K;
+  for (int seg = max_nseg - 1; seg >= 0; seg--) {
+    const int n0 = seg * K, n1 = std::min(B->max_nt, n0 + K);
+    int r = 0;  // instances with a later segment: they recompute this one (the forward sweep kept their last)
+    while (r < n && B->P[r].nt > n0 + K) r++;
+    if (r > 0) {
+      LK(1, launch_copy_table(B->d_copy + B->rs0[seg], B->rs1[seg] - B->rs0[seg], st));
+      for (int nn = n0; nn < n0 + K; nn++) {
+        b.n = nn;
+        b.n_active = r;
+        b.ntiles = B->ts[r];
+        LK(1, launch_acu_fwd_batch(b, B->cf_fwd, B->N, false, st));
+      }
+    }
+    for (int nn = n1 - 1; nn >= n0; nn--) {
+      for (int i = 0; i < n; i++) {
+        Plan& P = B->P[i];
+        if (P.nt - 1 != nn) continue;
+        // adjoint seed of instance i: lambda_nt = residual of its last sample
+        AcuStep pa;
+        fill_step(P, &B->M[i], B->dt, pa);
+        pa.res = P.res;
+        pa.gpart = P.gpart;
+        pa.src_part = nullptr;
+        const size_t field = (size_t)P.S * P.g.slice;
+        LK(1, launch_adj_init(pa, P.lam + (P.nt & 1) * field, P.hx + (P.nt & 1) * field, P.hz + (P.nt & 1) * field,
+                              st));
+      }
+      b.n = nn;
+      b.n_active = batch_active(B, nn);
+      b.ntiles = B->ts[b.n_active];
+      LK(1, launch_acu_adj_batch(b, B->cf_adj, B->N, st));
+    }
+    for (int i = 0; i < n; i++)
+      if (B->P[i].nt > n0) LK(1, launch_fold(B->P[i].gpart, B->P[i].S, B->P[i].g.slice, B->P[i].G, st));
+  }
+  for (int i = 0; i < n; i++) {
+    Plan& P = B->P[i];
+    LK(1, launch_grad_c(P.G, P.g, P.c, P.grad_c, st));
+    CK(cudaMemcpyAsync(B->grad[B->order[i]], P.grad_c, (size_t)P.g.nz * P.g.nx * 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(B->misfit + B->order[i], P.J, 8, cudaMemcpyDeviceToDevice, st));
+  }
+  return FWI_OK;
+}
+
+// Read every instance's status word (one synchronisation); the first failing
+// instance (caller's index) in *bad.
+fwi_status batch_read_status(fwi_batch* B, cudaStream_t st, int32_t* bad) {
+  for (int i = 0; i < B->n; i++)
+    CK(cudaMemcpyAsync(B->h_status + i, B->P[i].status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) *bad = -1;
+  int first = -1, word = 0;
+  for (int i = 0; i < B->n; i++)
+    if (B->h_status[i] && (first < 0 || B->order[i] < first)) {
+      first = B->order[i];
+      word = B->h_status[i];
+    }
+  if (first < 0) return FWI_OK;
+  if (bad) *bad = first;
+  return decode_status(word, "instance " + std::to_string(first) + ": ");
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_batch_create(int32_t device, int32_t n, const fwi_model* models, const fwi_sources* srcs,
+                            const fwi_receivers* recs, const int32_t* nts, float dt, const float* const* observed,
+                            int32_t K, double* misfit, float* const* grads, fwi_batch** out) {
+  if (!out) return fail(FWI_EINVAL, "batch must not be NULL");
+  *out = nullptr;
+  if (n < 1 || !models || !srcs || !recs || !nts || !observed || !grads || !misfit)
+    return fail(FWI_EINVAL, "a batch needs n >= 1 and non-NULL arrays");
+  if (K < 1) return fail(FWI_EINVAL, "ckpt_every must be >= 1");
+  for (int i = 0; i < n; i++) {
+    const fwi_model* M = &models[i];
+    fwi_status v = validate(M, &srcs[i], &recs[i], nts[i], dt);
+    if (v != FWI_OK) return fail(v, "instance " + std::to_string(i) + ": " + g_err);
+    if (M->op != FWI_OP_DIVERGENCE || srcs[i].kind == FWI_SRC_LINE)
+      return fail(FWI_ENOTIMPL, "a batch takes the divergence-form operator with point or Gaussian sources");
+    if (M->order != models[0].order || M->dx != models[0].dx || M->dz != models[0].dz)
+      return fail(FWI_EINVAL, "the instances of a batch share order, dx and dz");
+    if (recs[i].nrec > 0 && !observed[i]) return fail(FWI_EINVAL, "observed must not be NULL");
+    if (!grads[i]) return fail(FWI_EINVAL, "every instance needs a gradient buffer");
+    const void* ptrs[] = {M->vp, srcs[i].x0, srcs[i].stf, recs[i].iz, recs[i].ix, observed[i], grads[i]};
+    for (const void* p : ptrs)
+      if (!is_device_ptr(p)) return fail(FWI_EINVAL, "every buffer of a batch must be device memory");
+  }
+  if (!is_device_ptr(misfit)) return fail(FWI_EINVAL, "every buffer of a batch must be device memory");
+  fwi_batch* B = new fwi_batch;
+  fwi_status v = fwi_create(&B->ctx, device);
+  if (v != FWI_OK) {
+    delete B;
+    return v;
+  }
+  auto bail = [&](fwi_status st) {
+    const std::string msg = g_err;
+    batch_free(B);
+    g_err = msg;
+    return st;
+  };
+#define BCK(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return bail(fail(FWI_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  BCK(cudaSetDevice(device));
+  BCK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  B->n = n;
+  B->K = K;
+  B->N = models[0].order / 2;
+  B->dt = dt;
+  B->misfit = misfit;
+  B->order.resize(n);
+  for (int i = 0; i < n; i++) B->order[i] = i;
+  std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int c) { return nts[a] > nts[c]; });
+  B->P.resize(n);
+  size_t off = 0;
+  std::vector<size_t> offs(n);
+  for (int i = 0; i < n; i++) {
+    const int j = B->order[i];
+    B->M.push_back(models[j]);
+    B->Sv.push_back(srcs[j]);
+    B->R.push_back(recs[j]);
+    B->obs.push_back(observed[j]);
+    Plan& P = B->P[i];
+    make_plan(P, &models[j], &srcs[j], &recs[j], nts[j], std::min(K, nts[j]), true);
+    layout(P, nullptr);
+    offs[i] = off;
+    off += (P.bytes + 255) & ~size_t(255);
+  }
+  for (int i = 0; i < n; i++) B->grad.push_back(grads[i]);
+  B->max_nt = B->P[0].nt;
+  // tables after the plans: instances, tile starts, copy descriptors
+  const int max_nseg = (B->max_nt + K - 1) / K;
+  std::vector<CopyDesc> cp;
+  B->sv0.assign(max_nseg, 0);
+  B->sv1.assign(max_nseg, 0);
+  B->rs0.assign(max_nseg, 0);
+  B->rs1.assign(max_nseg, 0);
+  const size_t o_inst = off;
+  off += (sizeof(AcuInst) * n + 255) & ~size_t(255);
+  const size_t o_ts = off;
+  off += ((size_t)(n + 1) * 4 + 255) & ~size_t(255);
+  const size_t o_copy = off;
+  size_t ncopy = 0;
+  for (int i = 0; i < n; i++) ncopy += 12 * (size_t)std::max(0, B->P[i].nseg - 1);
+  off += (sizeof(CopyDesc) * std::max<size_t>(ncopy, 1) + 255) & ~size_t(255);
+  v = arena_acquire(B->ctx, off, "batch", 0, 0, B->cap);
+  if (v != FWI_OK) return bail(v);
+  char* arena = B->ctx->arena;
+  std::vector<AcuInst> inst(n);
+  B->ts.assign(n + 1, 0);
+  for (int i = 0; i < n; i++) {
+    Plan& P = B->P[i];
+    layout(P, arena + offs[i]);
+    AcuInst& in = inst[i];
+    memset(&in, 0, sizeof in);
+    AcuMaps mp;
+    BCK(acu_make_maps(&mp, P.g, P.S, P.u, P.m));
+    BCK(acu_make_adj_maps(&mp, P.g, P.S, P.lam, P.hx, P.hz));
+    in.mu = mp.u;
+    in.mm = mp.m;
+    in.lx = mp.lx;
+    in.lz = mp.lz;
+    in.hx = mp.hx;
+    in.hz = mp.hz;
+    fill_step(P, &B->M[i], dt, in.p);
+    in.p.res = P.res;
+    in.p.gpart = P.gpart;
+    in.p.src_part = nullptr;
+    for (int k = 0; k < 2; k++) {
+      in.psix[k] = P.psix[k];
+      in.psiz[k] = P.psiz[k];
+      in.zx[k] = P.zx[k];
+      in.zz[k] = P.zz[k];
+      in.px[k] = P.px[k];
+      in.pz[k] = P.pz[k];
+    }
+    in.hxp = P.hx;
+    in.hzp = P.hz;
+    in.slot = P.slot;
+    in.field = (long long)P.S * P.g.slice;
+    in.nt = P.nt;
+    in.nlast = (P.nseg - 1) * P.K;
+    B->ts[i + 1] = B->ts[i] + P.S * P.g.ntx * P.g.ntz;
+    if (i == 0) {
+      B->cf_fwd = AcuCoef{};
+      for (int k = 0; k < 4; k++) {
+        B->cf_fwd.c1x[k] = in.p.c1x[k];
+        B->cf_fwd.c1z[k] = in.p.c1z[k];
+        B->cf_fwd.c2x[k] = in.p.c2x[k];
+        B->cf_fwd.c2z[k] = in.p.c2z[k];
+        // adjoint: stage 1 -a_k dt^2/dx, stage 2 a_k/dx
+        B->cf_adj.c1x[k] = -in.p.c2x[k];
+        B->cf_adj.c1z[k] = -in.p.c2z[k];
+        B->cf_adj.c2x[k] = in.p.c1x[k];
+        B->cf_adj.c2z[k] = in.p.c1z[k];
+      }
+      B->cf_fwd.dt2 = B->cf_adj.dt2 = in.p.dt2;
+    }
+  }
+  // checkpoint k (step kK) of every instance whose last segment starts later
+  for (int k = 0; k < max_nseg; k++) {
+    for (int pass = 0; pass < 2; pass++) {  // 0: saves, 1: restores
+      (pass == 0 ? B->sv0 : B->rs0)[k] = (int)cp.size();
+      const int nn = k * K;
+      for (int i = 0; i < n; i++) {
+        const Plan& P = B->P[i];
+        if (nn >= (P.nseg - 1) * P.K) continue;
+        const size_t field = (size_t)P.S * P.g.slice;
+        float* ck = P.ckpt + (size_t)k * 6 * field;
+        float* st6[6] = {P.u + (nn & 1) * field, P.u + ((nn + 1) & 1) * field, P.psix[nn & 1], P.psiz[nn & 1], P.zetx,
+                         P.zetz};
+        for (int f = 0; f < 6; f++) {
+          CopyDesc d;
+          d.src = reinterpret_cast<const float4*>(pass == 0 ? st6[f] : ck + f * field);
+          d.dst = reinterpret_cast<float4*>(pass == 0 ? ck + f * field : st6[f]);
+          d.n4 = (long long)field / 4;
+          cp.push_back(d);
+        }
+      }
+      (pass == 0 ? B->sv1 : B->rs1)[k] = (int)cp.size();
+    }
+  }
+  B->d_inst = reinterpret_cast<AcuInst*>(arena + o_inst);
+  B->d_ts = reinterpret_cast<int*>(arena + o_ts);
+  B->d_copy = reinterpret_cast<CopyDesc*>(arena + o_copy);
+  BCK(cudaMemcpyAsync(B->d_inst, inst.data(), sizeof(AcuInst) * n, cudaMemcpyHostToDevice, B->cap));
+  BCK(cudaMemcpyAsync(B->d_ts, B->ts.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, B->cap));
+  if (!cp.empty())
+    BCK(cudaMemcpyAsync(B->d_copy, cp.data(), sizeof(CopyDesc) * cp.size(), cudaMemcpyHostToDevice, B->cap));
+  BCK(cudaStreamSynchronize(B->cap));  // the host tables are released below
+  BCK(cudaMallocHost((void**)&B->h_status, sizeof(int) * n));
+  // one ordinary sweep validates the inputs on the device, then the sweep is recorded
+  if ((v = batch_enqueue(B, B->cap)) != FWI_OK) return bail(v);
+  int32_t bad = -1;
+  if ((v = batch_read_status(B, B->cap, &bad)) != FWI_OK) return bail(v);
+  BCK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeRelaxed));
+  v = batch_enqueue(B, B->cap);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+  if (v == FWI_OK && e != cudaSuccess) v = fail(FWI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (v == FWI_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&B->exec, graph, 0);
+    if (ei != cudaSuccess) v = fail(FWI_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (v != FWI_OK) {
+    cudaGetLastError();
+    return bail(v);
+  }
+#undef BCK
+  *out = B;
+  g_err.clear();
+  return FWI_OK;
+}
+
+fwi_status fwi_batch_launch(fwi_batch* B, void* stream) {
+  if (!B) return fail(FWI_EINVAL, "batch must not be NULL");
+  CK(cudaSetDevice(B->ctx->device));
+  CK(cudaGraphLaunch(B->exec, (cudaStream_t)stream));
+  return FWI_OK;
+}
+
+fwi_status fwi_batch_status(fwi_batch* B, void* stream, int32_t* instance) {
+  if (!B) return fail(FWI_EINVAL, "batch must not be NULL");
+  CK(cudaSetDevice(B->ctx->device));
+  fwi_status v = batch_read_status(B, (cudaStream_t)stream, instance);
+  if (v == FWI_OK) g_err.clear();
+  return v;
+}
+
+int64_t fwi_batch_launches(const fwi_batch* B) { return B ? B->ctx->launches : 0; }
+
+fwi_status fwi_batch_destroy(fwi_batch* B) {
+  batch_free(B);
   return FWI_OK;
 }
 

@@ -39,6 +39,7 @@ fwi_status host_fail(fwi_status st, const std::string& msg);
 fwi_status arena_acquire(fwi_ctx* ctx, size_t bytes, const std::string& key, size_t zero_lo, size_t zero_hi,
                          cudaStream_t st);
 fwi_status finish_status_dev(fwi_ctx* ctx, const int* d_status, cudaStream_t st);
+fwi_status decode_status(int status_word, const std::string& where);
 void ensure_events(fwi_ctx* ctx, size_t nseg);
 }  // namespace fwi
 

@@ -131,6 +131,53 @@ struct AcuStep {
   int* status;
 };
 
+// One inversion instance of a multi-instance launch (fwi_batch_*): one work
+// table, in device memory, lists the tiles of every instance taking part, and
+// each tile finds its instance here. `p` holds the instance's static step
+// parameters (all shots, S_pair = S, s0 = 0); the fields that depend on the
+// time step n (pair halves, segment slots) are filled in by the kernel from
+// the buffers below. Instances of one launch share the discretisation (order,
+// dx, dz, dt), so the stencil weights come from the launch arguments.
+struct AcuInst {
+  CUtensorMap mu, mm;          // forward: wavefield pair, m/2
+  CUtensorMap lx, lz, hx, hz;  // adjoint operand maps (lambda pair, hhat pairs)
+  AcuStep p;
+  float *psix[2], *psiz[2];    // forward CPML memory pairs
+  float *zx[2], *zz[2], *px[2], *pz[2];  // adjoint CPML memory pairs
+  float *hxp, *hzp;            // hhat pairs [2][S][slice]
+  float* slot;                 // [K][2][S][slice] stored fluxes of one segment
+  long long field;             // S * slice
+  int nt;                      // time steps of this instance
+  int nlast;                   // first step of its last segment (the forward sweep stores from there on)
+};
+
+// Arguments of one multi-instance launch. Instances are sorted by nt (longest
+// first), so the ones taking part in any step form a prefix [0, n_active).
+struct BatchArgs {
+  const AcuInst* inst;    // [n_inst] device table
+  const int* tile_start;  // [n_inst + 1] first tile of each instance (S * ntx * ntz tiles each)
+  int n_active;           // instances of this launch
+  int ntiles;             // tile_start[n_active]
+  int n;                  // time step
+  int K;                  // checkpoint interval: segment slot of step n is n - (n / K) * K
+};
+
+// One device-to-device copy of a batched copy launch (checkpoint saves and
+// restores of several instances at once): n4 float4 from src to dst.
+struct CopyDesc {
+  const float4* src;
+  float4* dst;
+  long long n4;
+};
+
+// Stencil weights of a step launch (kernel parameters, so they stay in the
+// constant bank): forward stage 1 a_k/dx (flux) and stage 2 a_k dt^2/dx
+// (divergence); adjoint stage 1 -a_k dt^2/dx and stage 2 a_k/dx.
+struct AcuCoef {
+  float c1x[4], c1z[4], c2x[4], c2z[4];
+  float dt2;
+};
+
 // Everything one elastic step kernel needs (passed by value). Node sets on the
 // padded grid (index (i, j) of each field's storage): normal stresses and
 // lambda, lambda+2mu at (i, j); vx and bx at (i, j+1/2); vz and bz at

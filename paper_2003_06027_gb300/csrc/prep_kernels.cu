@@ -485,6 +485,17 @@ cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, 
   k_adj_init<<<p.S, 32, 0, st>>>(p, lam, hx, hz);
   return cudaGetLastError();
 }
+// Copies of a descriptor table: block row y copies descriptor y.
+__global__ void k_copy_table(const CopyDesc* __restrict__ d) {
+  const CopyDesc c = d[blockIdx.y];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < c.n4; i += (long long)gridDim.x * blockDim.x)
+    c.dst[i] = c.src[i];
+}
+cudaError_t launch_copy_table(const CopyDesc* d, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_copy_table<<<dim3(64, n), 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
 cudaError_t launch_fold(float* gpart, int S, long long slice, double* G, cudaStream_t st) {
   k_fold<<<608, 256, 0, st>>>(gpart, S, slice, G);
   return cudaGetLastError();

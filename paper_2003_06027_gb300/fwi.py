@@ -55,7 +55,8 @@ _ctx = threading.local()
 EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_last_timing",
            "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout",
            "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy",
-           "fwi_set_shot_groups", "fwi_workspace_bytes", "fwi_choose_ckpt", "fwi_forward_vjp", "fwi_last_error"]
+           "fwi_set_shot_groups", "fwi_workspace_bytes", "fwi_choose_ckpt", "fwi_forward_vjp", "fwi_batch_create",
+           "fwi_batch_launch", "fwi_batch_status", "fwi_batch_destroy", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -80,6 +81,13 @@ def library(build_if_missing: bool = True):
                                           ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
                                           ctypes.c_int32, P, P, P, P, P, P]
             L.fwi_forward_vjp.argtypes = L.fwi_misfit_grad.argtypes
+            L.fwi_batch_create.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_float, P,
+                                           ctypes.c_int32, P, P, ctypes.POINTER(P)]
+            L.fwi_batch_launch.argtypes = [P, P]
+            L.fwi_batch_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int32)]
+            L.fwi_batch_launches.argtypes = [P]
+            L.fwi_batch_launches.restype = ctypes.c_int64
+            L.fwi_batch_destroy.argtypes = [P]
             L.fwi_last_timing.argtypes = [P, P, P, P]
             L.fwi_forward_noalloc.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
                                               ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
@@ -363,6 +371,75 @@ class GradGraph:
         if getattr(self, "ctx", None):
             self._L.fwi_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """fwi_batch_*: J_i and dJ_i/dc_i of several acoustic instances of uneven
+    size in one recorded sweep, each time step one persistent launch over the
+    tiles of all instances (shared order, dx, dz, dt).
+
+    ``instances``: sequence of (c, stf, x0, rec_iz, rec_ix, observed, kw) with
+    CUDA tensors (kept referenced, read again at every launch: update ``c`` in
+    place and launch again) and kw the geometry keywords of misfit_grad.
+    Results: ``self.misfit`` [n] float64, ``self.grads`` (one [nz][nx] tensor
+    per instance). Creation runs the sweep once and records it."""
+
+    def __init__(self, instances, *, ckpt_every=100, device=None):
+        import torch
+
+        if not instances:
+            raise ValueError("a batch needs at least one instance")
+        self._calls, self._obs = [], []
+        dts = set()
+        for c, stf, x0, iz, ix, obs, kw in instances:
+            for t in (c, stf, x0, iz, ix, obs):
+                if not (_is_torch(t) and t.is_cuda):
+                    raise ValueError("Batch takes CUDA tensors only")
+            a = _Call(c, stf, x0, iz, ix, kw["dx"], kw["dz"], kw.get("order", 4), kw.get("npml", 20),
+                      kw.get("pml_R", 1e-3), kw.get("pml_vmax", 4500.0), kw.get("pml_f0", 10.0),
+                      kw.get("src_kind", FWI_SRC_POINT), kw.get("op", FWI_OP_DIVERGENCE))
+            self._calls.append(a)
+            self._obs.append(_arr(obs, np.float32))
+            dts.add(float(kw["dt"]))
+        if len(dts) != 1:
+            raise ValueError("the instances of a batch share dt")
+        n = len(self._calls)
+        ref = self._calls[0].c
+        self.device = _device(ref, device)
+        self.misfit = torch.zeros(n, dtype=torch.float64, device=ref.device)
+        self.grads = [torch.empty_like(a.c) for a in self._calls]
+        M = (_Model * n)(*[a.model for a in self._calls])
+        S = (_Sources * n)(*[a.src for a in self._calls])
+        R = (_Receivers * n)(*[a.rec for a in self._calls])
+        nts = (ctypes.c_int32 * n)(*[a.nt for a in self._calls])
+        obs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self._obs])
+        grads = (ctypes.c_void_p * n)(*[g.data_ptr() for g in self.grads])
+        self._keep = (M, S, R, nts, obs, grads)
+        self._L = library()
+        self.handle = ctypes.c_void_p()
+        _check(self._L.fwi_batch_create(self.device, n, M, S, R, nts, dts.pop(), obs, int(ckpt_every),
+                                        ctypes.c_void_p(self.misfit.data_ptr()), grads, ctypes.byref(self.handle)))
+        self.launches = int(self._L.fwi_batch_launches(self.handle))
+
+    def launch(self, stream=None):
+        """Enqueue one sweep on ``stream`` (default: the current stream)."""
+        _check(self._L.fwi_batch_launch(self.handle, _stream(self._calls[0].c, stream)))
+
+    def check(self, stream=None):
+        """Wait for ``stream`` and raise if an instance reported an error."""
+        bad = ctypes.c_int32(-1)
+        _check(self._L.fwi_batch_status(self.handle, _stream(self._calls[0].c, stream), ctypes.byref(bad)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._L.fwi_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

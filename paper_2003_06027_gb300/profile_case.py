@@ -18,6 +18,8 @@ CASES = {
     # shots, time steps, checkpoint interval
     "fwi48-nt20": (48, 20, 10),
     "fwi16-nt20": (16, 20, 10),
+    # the HBM-bound regime: 128 shots, one step's fields (~0.45 GB) far exceed L2 (~3.7 GB arena)
+    "fwi128-nt8": (128, 8, 4),
     # the same with the c^2 Laplacian operator (plain per-point kernels)
     "lap16-nt20": (16, 20, 10),
     # elastic 300 x 800 discretisation (4th order, 32 CPML cells), 8 shots

@@ -163,3 +163,100 @@ def test_autotune_over_launch_shapes(fwi_lib):
     for i in range(len(inst)):
         assert float(Jg[i][0]) == float(Jb[i][0])
     batch.close_graphs()
+
+
+# ----------------------------------------------- one persistent launch per step
+def _oracle_instances():
+    """Three small uneven instances (different grids, nt, shots, receivers;
+    one shorter than the checkpoint interval, one not a multiple of it) with the
+    same discretisation (8th order, dx = dz = 10 m, dt = 1 ms)."""
+    shapes = [(34, 71, 230, 3, 7, 1), (27, 45, 160, 2, 5, 0), (41, 38, 70, 1, 4, 1)]
+    out = []
+    for k, (nz, nx, nt, S, nrec, kind) in enumerate(shapes):
+        d = synth.random_acoustic(90 + k, nz, nx, nt, S, 8, 6, src_kind=kind, nrec=nrec)
+        rng = np.random.default_rng(190 + k)
+        d["c_obs"] = (d["c"] * (1.0 + 0.03 * rng.standard_normal(d["c"].shape))).astype(np.float32)
+        out.append(d)
+    return out
+
+
+def _geom(d):
+    return dict(nz=d["nz"], nx=d["nx"], npml=d["npml"], order=d["order"], nt=d["nt"], dz=d["dz"], dx=d["dx"],
+                dt=d["dt"], src_kind=d["src_kind"], pml_R=d["pml_R"], pml_vmax=d["pml_vmax"], pml_f0=d["pml_f0"],
+                rec_iz=d["rec_iz"], rec_ix=d["rec_ix"])
+
+
+def _device_instance(fwi, d, obs):
+    import torch
+
+    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    return (cu(d["c"]), cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"]), cu(obs), fwi.problem_kwargs(d))
+
+
+def test_persistent_batch_matches_oracle_and_single_calls(fwi_lib):
+    """fwi_batch_* (one launch per step over every instance's tiles, recorded as
+    one graph) against the FP64 oracle, and bit for bit against fwi_misfit_grad
+    of each instance alone (the same per-cell arithmetic and fold order)."""
+    import oracle
+    from paper_2003_06027_gb300 import fwi
+
+    ds = _oracle_instances()
+    K = 100
+    obs = [oracle.acoustic_forward(_geom(d), np.float64(d["c_obs"]), np.float64(d["stf"]),
+                                   np.float64(d["x0"])).astype(np.float32) for d in ds]
+    inst = [_device_instance(fwi, d, o) for d, o in zip(ds, obs)]
+    B = fwi.Batch(inst, ckpt_every=K)
+    for rep in range(2):  # the creation sweep, then a replay of the recorded graph
+        if rep:
+            B.misfit.zero_()
+            for g in B.grads:
+                g.zero_()
+            B.launch()
+            B.check()
+        for i, (d, o) in enumerate(zip(ds, obs)):
+            Jo, go, _, _ = oracle.acoustic_misfit_grad(_geom(d), np.float64(d["c"]), np.float64(d["stf"]),
+                                                       np.float64(d["x0"]), np.float64(o))
+            Jb, gb = float(B.misfit[i].cpu()), B.grads[i].cpu().numpy()
+            assert Jo > 0 and abs(Jb - Jo) <= 1e-4 * Jo, (i, Jb, Jo)
+            assert rel(gb, go) <= 1e-3, (i, rel(gb, go))
+            c, stf, x0, iz, ix, ob, kw = inst[i]
+            Js, gs, _, _, _ = fwi.misfit_grad(c, stf, x0, iz, ix, ob, ckpt_every=min(K, d["nt"]), want_src=False, **kw)
+            assert float(Js.cpu()[0]) == Jb
+            assert np.array_equal(gs.cpu().numpy(), gb), i
+    B.close()
+
+
+def test_persistent_batch_follows_model_updates(fwi_lib):
+    """The recorded sweep reads the models again at every launch."""
+    from paper_2003_06027_gb300 import fwi
+
+    ds = _oracle_instances()[:2]
+    inst = [_device_instance(fwi, d, np.zeros((d["stf"].shape[0], len(d["rec_iz"]), d["nt"]), np.float32))
+            for d in ds]
+    B = fwi.Batch(inst, ckpt_every=50)
+    inst[1][0].mul_(1.01)  # update instance 1's model in place
+    B.launch()
+    B.check()
+    c, stf, x0, iz, ix, ob, kw = inst[1]
+    Js, gs, _, _, _ = fwi.misfit_grad(c, stf, x0, iz, ix, ob, ckpt_every=50, want_src=False, **kw)
+    assert float(Js.cpu()[0]) == float(B.misfit[1].cpu())
+    assert np.array_equal(gs.cpu().numpy(), B.grads[1].cpu().numpy())
+    B.close()
+
+
+def test_persistent_batch_refusals(fwi_lib):
+    from paper_2003_06027_gb300 import fwi
+
+    ds = _oracle_instances()[:2]
+    inst = [_device_instance(fwi, d, np.zeros((d["stf"].shape[0], len(d["rec_iz"]), d["nt"]), np.float32))
+            for d in ds]
+    bad = list(inst[1])
+    bad[6] = dict(bad[6], dx=12.0, dz=12.0)  # another spacing than instance 0
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.Batch([inst[0], tuple(bad)])
+    assert e.value.status == 1
+    fast = list(inst[1])
+    fast[0] = fast[0] * 4.0  # CFL violated in instance 1
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.Batch([inst[0], tuple(fast)])
+    assert e.value.status == 2 and "instance 1" in str(e.value)
