@@ -317,31 +317,62 @@ def laplacian_op_measure(peak, steps=2):
     return {"workload": d["name"] + "-c2laplacian-ckpt100", "kernels": "plain per-point (acoustic_lap.cu)", **res}
 
 
-def batched_measure(n_inst=8):
+def batched_measure(n_inst=16):
     """Batched vs plain per-shot gradient sweeps over the first ``n_inst``
     instances of the seeded uneven workload (seed 4; grids 128..512 x
-    128..1024, nt 1000..4000, 4..16 shots). The batched sweep's (mode: host
-    threads or recorded CUDA graphs, streams, checkpoint interval) comes from the
-    autotuner run on the same instances."""
+    128..1024, nt 1000..4000, 4..16 shots). The batched sweep's mode (one
+    persistent launch per step over all instances in one recorded graph, one
+    recorded graph per instance on W streams, or host threads on W streams),
+    streams and checkpoint interval come from the autotuner run on the same
+    instances."""
     from paper_2003_06027_gb300 import batch, synth
 
     inst = batch.prepare([synth.uneven_instance(4, i) for i in range(n_inst)])
     cells = sum(i.cell_steps for i in inst)
-    best, table = batch.autotune(inst, workers=(2, 4, 8), ckpt=(100,), modes=("batched", "graph"))
+    modes = ("persistent", "graph", "batched")
+    best, table = batch.autotune(inst, workers=(1, 2, 4, 8), ckpt=(100,), modes=modes)
     _, _, tb = batch.sweep(inst, best[0], best[1], best[2])
+    batch.close_graphs()
+    batch.close_pools()
     batch.sweep(inst, "plain", ckpt_every=100)
     _, _, tp = batch.sweep(inst, "plain", ckpt_every=100)
-    best_of = {m: min(t for (mm, _, _), t in table.items() if mm == m) for m in ("batched", "graph")}
+    best_of = {m: min(t for (mm, _, _), t in table.items() if mm == m) for m in modes}
     batch.close_graphs()
     return {"workload": f"uneven-seed4-{n_inst}-instances", "cell_steps_per_sweep": cells,
             "batched": {"value": cells / tb / 1e9, "unit": UNIT, "s_per_sweep": tb, "mode": best[0],
                         "streams": best[1], "ckpt_every": best[2]},
-            "threads_best": {"value": cells / best_of["batched"] / 1e9, "s_per_sweep": best_of["batched"]},
+            "persistent": {"value": cells / best_of["persistent"] / 1e9, "s_per_sweep": best_of["persistent"],
+                           "launches": "W groups of instances, each one graph whose time steps are one persistent "
+                                       "launch over the group's instances (W = 1: all instances in every launch)"},
             "graphs_best": {"value": cells / best_of["graph"] / 1e9, "s_per_sweep": best_of["graph"]},
+            "threads_best": {"value": cells / best_of["batched"] / 1e9, "s_per_sweep": best_of["batched"]},
             "plain_per_shot": {"value": cells / tp / 1e9, "unit": UNIT, "s_per_sweep": tp},
             "speedup": tp / tb,
             "autotune_s": {f"{m}-{w}x{k}": t for (m, w, k), t in table.items()},
             "timing": "host wall time per sweep, device idle before and after (each sweep ends synchronised)"}
+
+
+def uneven_all_measure(mode="graph", workers=2, waves=2):
+    """The whole 64-instance uneven workload (seed 4, 479 G cell-steps per
+    gradient sweep) in a batched mode. Its workspace at K = 100 (300 GB)
+    exceeds the GPU's memory, so it runs as `waves` sets of consecutive
+    instances, one after the other; the time is the sum of their sweeps."""
+    from paper_2003_06027_gb300 import batch, synth
+
+    per = (64 + waves - 1) // waves
+    cells, secs = 0, 0.0
+    for w in range(waves):
+        inst = batch.prepare([synth.uneven_instance(4, i) for i in range(w * per, min(64, (w + 1) * per))])
+        cells += sum(i.cell_steps for i in inst)
+        batch.sweep(inst, mode, workers, ckpt_every=100)  # creation: the first sweep (and recording)
+        _, _, t = batch.sweep(inst, mode, workers, ckpt_every=100)
+        secs += t
+        batch.close_graphs()
+        batch.close_pools()
+        del inst
+    return {"workload": "uneven-seed4-64-instances", "cell_steps_per_sweep": cells, "mode": mode,
+            "streams": workers, "waves": waves, "value": cells / secs / 1e9, "unit": UNIT, "s_per_sweep": secs,
+            "timing": "host wall time per sweep, each wave's sweep timed after its creation sweep"}
 
 
 def learned_measure():
@@ -532,6 +563,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the elastic and 256-shot measurements")
+    ap.add_argument("--uneven-all", action="store_true",
+                    help="also time the whole 64-instance uneven workload (persistent mode, two waves)")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -651,6 +684,9 @@ def main():
         res["laplacian_op"] = laplacian_op_measure(peak)
         res["store_all"] = store_all_measure(d, (c, stf, x0, iz, ix), obs, kw, value)
         res["batched_uneven"] = batched_measure()
+        if args.uneven_all:
+            b = res["batched_uneven"]["batched"]
+            res["uneven_all"] = uneven_all_measure(b["mode"], b["streams"])
         res["learned"] = learned_measure()
     if ws == 1 and not args.no_cpu_baseline:
         import oracle

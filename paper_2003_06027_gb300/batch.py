@@ -16,6 +16,14 @@ Two ways to run the same gradient sweep (J_i and dJ_i/dc_i of every instance i):
   launch per instance, spread over W streams from a single host thread, so the
   host issues one launch per instance instead of tens of thousands of step
   kernels.
+* ``persistent``: the instances split into W groups (round robin over the
+  instances sorted by size), each group one fwi.Batch on its own stream: each
+  time step of a group is ONE persistent launch whose CTAs walk the (instance,
+  shot, tile) work items of every instance of the group, and a group's whole
+  sweep is one recorded CUDA graph. W = 1 puts every instance into each
+  step's launch; larger W trades launch count for L2 locality (a step of one
+  launch touches all its instances' fields). Results equal the per-instance
+  calls bit for bit.
 
 ``autotune`` measures a sweep on the instances themselves for each candidate
 (mode, W, checkpoint interval K) and keeps the fastest. Both modes compute the same
@@ -102,10 +110,26 @@ def _graph_of(inst: Instance, K: int, groups=(0, 0)) -> fwi.GradGraph:
     return g
 
 
+_batches = {}
+
+
+def _batch_of(instances, K: int) -> fwi.Batch:
+    key = (tuple(id(i) for i in instances), K)
+    b = _batches.get(key)
+    if b is None or any(b._calls[k].c.data_ptr() != inst.c.data_ptr() for k, inst in enumerate(instances)):
+        if b is not None:
+            b.close()
+        b = fwi.Batch([(i.c, i.stf, i.x0, i.rec_iz, i.rec_ix, i.observed, i.kw) for i in instances], ckpt_every=K)
+        _batches[key] = b
+    return b
+
+
 def close_graphs():
-    """Free the recorded graphs and their contexts."""
+    """Free the recorded graphs, batches and their contexts."""
     for k in list(_graphs):
         _graphs.pop(k).close()
+    for k in list(_batches):
+        _batches.pop(k).close()
 
 
 def _streams(W: int, device: int):
@@ -208,10 +232,36 @@ def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 
         for k, i in enumerate(order):
             graphs[i].check(streams[k % len(streams)])
             Js[i], gs[i] = graphs[i].misfit.clone(), graphs[i].grad.clone()
+    elif mode == "persistent":
+        W = max(1, min(workers, n))
+        order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first, dealt round robin
+        groups = [order[k::W] for k in range(W)]
+        batches = [_batch_of([instances[i] for i in grp], ckpt_every) for grp in groups]
+        streams = _streams(W, torch.cuda.current_device())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()  # creation (the first sweep and its recording) is not part of a sweep
+        for b, st in zip(batches, streams):
+            b.launch(st)
+        for b, st, grp in zip(batches, streams, groups):
+            b.check(st)
+            for j, i in enumerate(grp):
+                Js[i], gs[i] = b.misfit[j:j + 1].clone(), b.grads[j].clone()
     else:
         raise ValueError(f"unknown mode {mode!r}")
     torch.cuda.synchronize()
     return Js, gs, time.perf_counter() - t0
+
+
+def _close_batches_but(instances, best):
+    """Free the persistent-mode batches except those of the candidate `best`."""
+    keep = set()
+    if best is not None and best[0] == "persistent":
+        W = max(1, min(best[1], len(instances)))
+        order = sorted(range(len(instances)), key=lambda i: -instances[i].cell_steps)
+        keep = {(tuple(id(instances[i]) for i in order[k::W]), best[2]) for k in range(W)}
+    for key in [k for k in _batches if k not in keep]:
+        _batches.pop(key).close()
+    torch.cuda.synchronize()
 
 
 def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batched",), groups=((0, 0),)):
@@ -237,6 +287,7 @@ def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batch
                     table[key] = t
                     if best is None or t < table[best]:
                         best = key
+                    _close_batches_but(instances, best)  # each grouping holds every instance's workspace
             if mode == "batched":  # keep at most the best pool alive between candidates
                 bw = best[1] if best[0] == "batched" else None
                 loser = W if bw != W else (prev[1] if prev is not None and prev[0] == "batched" and prev[1] != W
@@ -246,6 +297,7 @@ def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batch
     bgrp = tuple(best[3]) if len(best) > 3 else (0, 0)
     for key in [k for k in _graphs if not (best[0] == "graph" and k[1] == best[2] and k[2] == bgrp)]:
         _graphs.pop(key).close()  # graphs the winner does not use
+    _close_batches_but(instances, best)
     return best, table
 
 

@@ -277,14 +277,17 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < ntiles) fetch_next(blockIdx.x);
 
-  int it = 0;
+  int it = 0, inst_loaded = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
     const int tn = t + gridDim.x;
     int tl = t;  // tile index within its instance
     if (MULTI) {
       const int i = batch_instance(b, t);
       tl = t - __ldg(b.tile_start + i);
-      batch_load_step<RECORD ? 0 : 1>(b, i, shp);  // after the previous tile's closing barrier
+      if (i != inst_loaded) {  // the parameters stay in shared memory while the instance does not change
+        batch_load_step<RECORD ? 0 : 1>(b, i, shp);  // after the previous tile's closing barrier
+        inst_loaded = i;
+      }
     }
     const AcuStep& p = MULTI ? shp : p0;
     const Grid& g = p.g;
@@ -613,14 +616,17 @@ __global__ void __launch_bounds__(NTHREADS, 3)
   __syncthreads();
   if (tid == 0 && (int)blockIdx.x < ntiles) fetch(blockIdx.x);
 
-  int it = 0;
+  int it = 0, inst_loaded = -1;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
     const int tn = t + gridDim.x;
     int tl = t;  // tile index within its instance
     if (MULTI) {
       const int i = batch_instance(b, t);
       tl = t - __ldg(b.tile_start + i);
-      batch_load_step<2>(b, i, shp);  // after the previous tile's closing barrier
+      if (i != inst_loaded) {  // the parameters stay in shared memory while the instance does not change
+        batch_load_step<2>(b, i, shp);  // after the previous tile's closing barrier
+        inst_loaded = i;
+      }
     }
     const AcuStep& p = MULTI ? shp : p0;
     const Grid& g = p.g;

@@ -260,3 +260,24 @@ def test_persistent_batch_refusals(fwi_lib):
     with pytest.raises(fwi.FwiError) as e:
         fwi.Batch([inst[0], tuple(fast)])
     assert e.value.status == 2 and "instance 1" in str(e.value)
+
+
+def test_persistent_sweep_and_fwi_history(fwi_lib):
+    """batch.sweep in the persistent mode gives the batched mode's misfits and
+    gradients, and an FWI loop on it follows the plain per-shot history."""
+    from paper_2003_06027_gb300 import batch
+
+    problems = _small_instances(3)
+    a = batch.prepare(problems)
+    Jp, gp, _ = batch.sweep(a, "persistent")
+    Jb, gb, _ = batch.sweep(a, "batched", workers=2)
+    for i in range(len(a)):
+        assert float(Jp[i][0]) == float(Jb[i][0])
+        assert np.array_equal(gp[i].cpu().numpy(), gb[i].cpu().numpy())
+    b = batch.prepare(problems[:2])
+    c = batch.prepare(problems[:2])
+    hp = batch.fwi_iterations(b, 3, "persistent")
+    hq = batch.fwi_iterations(c, 3, "plain")
+    np.testing.assert_allclose([h[0] for h in hp], [h[0] for h in hq], rtol=1e-4)
+    batch.close_graphs()
+    batch.close_pools()
