@@ -143,7 +143,7 @@ __device__ __forceinline__ void cpml_adj_x4(bool on, const float* ta, const floa
   if (!any4(a4)) return;
   const float4 b4 = ldg4(tb + j + TAB_OFF);
   float M[4], a[4], b[4];
-  f4a(ld4(Min + id), M);
+  f4a(ldg4(Min + id), M);  // read-only in this kernel (the pair's other half is written)
   f4a(a4, a);
   f4a(b4, b);
   float Mn[4];
@@ -163,7 +163,7 @@ __device__ __forceinline__ void cpml_adj_z4(bool on, const float* ta, const floa
   if (a == 0.f) return;
   const float b = __ldg(tb + z + TAB_OFF);
   float M[4], Mn[4];
-  f4a(ld4(Min + id), M);
+  f4a(ldg4(Min + id), M);  // read-only in this kernel (the pair's other half is written)
 #pragma unroll
   for (int e = 0; e < 4; e++) {
     const float u = M[e] + t[e];
@@ -497,57 +497,68 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
   constexpr int NA = TILE_Z * (W72 / 4), NB = H40 * (TILE_X / 4);
-  for (int k4 = tid; k4 < 2 * NA + 2 * NB; k4 += NTHREADS) {
-    if (k4 < NA) {  // (a) strain-x adjoint at normal nodes, own rows, columns [x0-4, x0+68)
-      const int r = k4 / (W72 / 4), gq = k4 - r * (W72 / 4);
-      const int z = z0 + r, j = x0 - 4 + 4 * gq;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float sx[4], sz[4], la[4], lp[4], t[4], d[4];
-      f4a(ld4(s_Sxx + (r + 4) * W72 + 4 * gq), sx);
-      f4a(ld4(s_Szz + (r + 4) * W72 + 4 * gq), sz);
-      f4a(ldg4(p.lam + im), la);
-      f4a(ldg4(p.lp2m + im), lp);
+  // the four item kinds run as separate loops, each unrolled so that a thread's
+  // items have their global loads (medium, CPML tables and memory) in flight together
+  auto item_a = [&](int k) {  // (a) strain-x adjoint at normal nodes, own rows, columns [x0-4, x0+68)
+    const int r = k / (W72 / 4), gq = k - r * (W72 / 4);
+    const int z = z0 + r, j = x0 - 4 + 4 * gq;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float sx[4], sz[4], la[4], lp[4], t[4], d[4];
+    f4a(ld4(s_Sxx + (r + 4) * W72 + 4 * gq), sx);
+    f4a(ld4(s_Szz + (r + 4) * W72 + 4 * gq), sz);
+    f4a(ldg4(p.lam + im), la);
+    f4a(ldg4(p.lp2m + im), lp);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * (lp[e] * sx[e] + la[e] * sz[e]);
-      cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[4], p.Mout[4], id, gq >= 1 && gq <= 16, t, d);
-      st4(d_vx + r * W72 + 4 * gq, a4f(d));
-    } else if (k4 < NA + NB) {  // (b) strain-z adjoint at normal nodes, rows [z0-4, z0+36), own cols
-      const int k = k4 - NA, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
-      const int z = z0 - 4 + hr, j = x0 + 4 * c;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float sx[4], sz[4], la[4], lp[4], t[4], d[4];
-      f4a(ld4(s_Sxx + hr * W72 + 4 * c + 4), sx);
-      f4a(ld4(s_Szz + hr * W72 + 4 * c + 4), sz);
-      f4a(ldg4(p.lam + im), la);
-      f4a(ldg4(p.lp2m + im), lp);
+    for (int e = 0; e < 4; e++) t[e] = dt * (lp[e] * sx[e] + la[e] * sz[e]);
+    cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[4], p.Mout[4], id, gq >= 1 && gq <= 16, t, d);
+    st4(d_vx + r * W72 + 4 * gq, a4f(d));
+  };
+  auto item_b = [&](int k) {  // (b) strain-z adjoint at normal nodes, rows [z0-4, z0+36), own cols
+    const int hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    const int z = z0 - 4 + hr, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float sx[4], sz[4], la[4], lp[4], t[4], d[4];
+    f4a(ld4(s_Sxx + hr * W72 + 4 * c + 4), sx);
+    f4a(ld4(s_Szz + hr * W72 + 4 * c + 4), sz);
+    f4a(ldg4(p.lam + im), la);
+    f4a(ldg4(p.lp2m + im), lp);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * (la[e] * sx[e] + lp[e] * sz[e]);
-      cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[5], p.Mout[5], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
-      st4(d_vz + hr * TILE_X + 4 * c, a4f(d));
-    } else if (k4 < NA + 2 * NB) {  // (c) shear strain adjoint (z part) at shear nodes, all rows, own cols
-      const int k = k4 - NA - NB, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
-      const int z = z0 - 4 + hr, j = x0 + 4 * c;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float sh[4], mx[4], t[4], d[4];
-      f4a(ld4(s_Sxz + hr * W72 + 4 * c + 4), sh);
-      f4a(ldg4(p.mxz + im), mx);
+    for (int e = 0; e < 4; e++) t[e] = dt * (la[e] * sx[e] + lp[e] * sz[e]);
+    cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[5], p.Mout[5], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
+    st4(d_vz + hr * TILE_X + 4 * c, a4f(d));
+  };
+  auto item_c = [&](int k) {  // (c) shear strain adjoint (z part) at shear nodes, all rows, own cols
+    const int hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    const int z = z0 - 4 + hr, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float sh[4], mx[4], t[4], d[4];
+    f4a(ld4(s_Sxz + hr * W72 + 4 * c + 4), sh);
+    f4a(ldg4(p.mxz + im), mx);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * mx[e] * sh[e];
-      cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[6], p.Mout[6], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
-      st4(d_vxz + hr * TILE_X + 4 * c, a4f(d));
-    } else {  // (d) shear strain adjoint (x part) at shear nodes, own rows, columns [x0-4, x0+68)
-      const int k = k4 - NA - 2 * NB, r = k / (W72 / 4), gq = k - r * (W72 / 4);
-      const int z = z0 + r, j = x0 - 4 + 4 * gq;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float sh[4], mx[4], t[4], d[4];
-      f4a(ld4(s_Sxz + (r + 4) * W72 + 4 * gq), sh);
-      f4a(ldg4(p.mxz + im), mx);
+    for (int e = 0; e < 4; e++) t[e] = dt * mx[e] * sh[e];
+    cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[6], p.Mout[6], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
+    st4(d_vxz + hr * TILE_X + 4 * c, a4f(d));
+  };
+  auto item_d = [&](int k) {  // (d) shear strain adjoint (x part) at shear nodes, own rows, columns [x0-4, x0+68)
+    const int r = k / (W72 / 4), gq = k - r * (W72 / 4);
+    const int z = z0 + r, j = x0 - 4 + 4 * gq;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float sh[4], mx[4], t[4], d[4];
+    f4a(ld4(s_Sxz + (r + 4) * W72 + 4 * gq), sh);
+    f4a(ldg4(p.mxz + im), mx);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * mx[e] * sh[e];
-      cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[7], p.Mout[7], id, gq >= 1 && gq <= 16, t, d);
-      st4(d_vzx + r * W72 + 4 * gq, a4f(d));
-    }
-  }
+    for (int e = 0; e < 4; e++) t[e] = dt * mx[e] * sh[e];
+    cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[7], p.Mout[7], id, gq >= 1 && gq <= 16, t, d);
+    st4(d_vzx + r * W72 + 4 * gq, a4f(d));
+  };
+#pragma unroll 3
+  for (int k = tid; k < NA; k += NTHREADS) item_a(k);
+#pragma unroll 3
+  for (int k = tid; k < NB; k += NTHREADS) item_b(k);
+#pragma unroll 3
+  for (int k = tid; k < NB; k += NTHREADS) item_c(k);
+#pragma unroll 3
+  for (int k = tid; k < NA; k += NTHREADS) item_d(k);
   __syncthreads();
   float zx[2][4], zz[2][4];
   {
@@ -699,53 +710,64 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
   constexpr int NA = TILE_Z * (W72 / 4), NB = H40 * (TILE_X / 4);
-  for (int k4 = tid; k4 < 2 * NA + 2 * NB; k4 += NTHREADS) {
-    if (k4 < NA) {  // (a) at vx nodes, own rows, columns [x0-4, x0+68): psi1 adjoint (x)
-      const int r = k4 / (W72 / 4), gq = k4 - r * (W72 / 4);
-      const int z = z0 + r, j = x0 - 4 + 4 * gq;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float v[4], b[4], t[4], d[4];
-      f4a(ld4(s_Vx + (r + 4) * W72 + 4 * gq), v);
-      f4a(ldg4(p.bx + im), b);
+  // the four item kinds run as separate loops, each unrolled so that a thread's
+  // items have their global loads (medium, CPML tables and memory) in flight together
+  auto item_a = [&](int k) {  // (a) at vx nodes, own rows, columns [x0-4, x0+68): psi1 adjoint (x)
+    const int r = k / (W72 / 4), gq = k - r * (W72 / 4);
+    const int z = z0 + r, j = x0 - 4 + 4 * gq;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float v[4], b[4], t[4], d[4];
+    f4a(ld4(s_Vx + (r + 4) * W72 + 4 * gq), v);
+    f4a(ldg4(p.bx + im), b);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
-      cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[0], p.Mout[0], id, gq >= 1 && gq <= 16, t, d);
-      st4(d_sxx + r * W72 + 4 * gq, a4f(d));
-    } else if (k4 < NA + NB) {  // (b) at vx nodes, rows [z0-4, z0+36), own cols: psi2 adjoint (z)
-      const int k = k4 - NA, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
-      const int z = z0 - 4 + hr, j = x0 + 4 * c;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float v[4], b[4], t[4], d[4];
-      f4a(ld4(s_Vx + hr * W72 + 4 * c + 4), v);
-      f4a(ldg4(p.bx + im), b);
+    for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
+    cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[0], p.Mout[0], id, gq >= 1 && gq <= 16, t, d);
+    st4(d_sxx + r * W72 + 4 * gq, a4f(d));
+  };
+  auto item_b = [&](int k) {  // (b) at vx nodes, rows [z0-4, z0+36), own cols: psi2 adjoint (z)
+    const int hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    const int z = z0 - 4 + hr, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float v[4], b[4], t[4], d[4];
+    f4a(ld4(s_Vx + hr * W72 + 4 * c + 4), v);
+    f4a(ldg4(p.bx + im), b);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
-      cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[1], p.Mout[1], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
-      st4(d_sxz + hr * TILE_X + 4 * c, a4f(d));
-    } else if (k4 < NA + 2 * NB) {  // (c) at vz nodes, rows [z0-4, z0+36), own cols: psi4 adjoint (z)
-      const int k = k4 - NA - NB, hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
-      const int z = z0 - 4 + hr, j = x0 + 4 * c;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float v[4], b[4], t[4], d[4];
-      f4a(ld4(s_Vz + hr * W72 + 4 * c + 4), v);
-      f4a(ldg4(p.bz + im), b);
+    for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
+    cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[1], p.Mout[1], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
+    st4(d_sxz + hr * TILE_X + 4 * c, a4f(d));
+  };
+  auto item_c = [&](int k) {  // (c) at vz nodes, rows [z0-4, z0+36), own cols: psi4 adjoint (z)
+    const int hr = k / (TILE_X / 4), c = k - hr * (TILE_X / 4);
+    const int z = z0 - 4 + hr, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float v[4], b[4], t[4], d[4];
+    f4a(ld4(s_Vz + hr * W72 + 4 * c + 4), v);
+    f4a(ldg4(p.bz + im), b);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
-      cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[3], p.Mout[3], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
-      st4(d_szz + hr * TILE_X + 4 * c, a4f(d));
-    } else {  // (d) at vz nodes, own rows, columns [x0-4, x0+68): psi3 adjoint (x)
-      const int k = k4 - NA - 2 * NB, r = k / (W72 / 4), gq = k - r * (W72 / 4);
-      const int z = z0 + r, j = x0 - 4 + 4 * gq;
-      const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
-      float v[4], b[4], t[4], d[4];
-      f4a(ld4(s_Vz + (r + 4) * W72 + 4 * gq), v);
-      f4a(ldg4(p.bz + im), b);
+    for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
+    cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[3], p.Mout[3], id, hr >= 4 && hr < 4 + TILE_Z, t, d);
+    st4(d_szz + hr * TILE_X + 4 * c, a4f(d));
+  };
+  auto item_d = [&](int k) {  // (d) at vz nodes, own rows, columns [x0-4, x0+68): psi3 adjoint (x)
+    const int r = k / (W72 / 4), gq = k - r * (W72 / 4);
+    const int z = z0 + r, j = x0 - 4 + 4 * gq;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float v[4], b[4], t[4], d[4];
+    f4a(ld4(s_Vz + (r + 4) * W72 + 4 * gq), v);
+    f4a(ldg4(p.bz + im), b);
 #pragma unroll
-      for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
-      cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[2], p.Mout[2], id, gq >= 1 && gq <= 16, t, d);
-      st4(d_sxzx + r * W72 + 4 * gq, a4f(d));
-    }
-  }
+    for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
+    cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[2], p.Mout[2], id, gq >= 1 && gq <= 16, t, d);
+    st4(d_sxzx + r * W72 + 4 * gq, a4f(d));
+  };
+#pragma unroll 3
+  for (int k = tid; k < NA; k += NTHREADS) item_a(k);
+#pragma unroll 3
+  for (int k = tid; k < NB; k += NTHREADS) item_b(k);
+#pragma unroll 3
+  for (int k = tid; k < NB; k += NTHREADS) item_c(k);
+#pragma unroll 3
+  for (int k = tid; k < NA; k += NTHREADS) item_d(k);
   __syncthreads();
   float zs[2][4], zh[2][4];
   {
