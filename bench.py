@@ -419,6 +419,33 @@ def learned_measure():
                          "frac": tfl / peak if peak else None, "peak_source": "measured sustained bf16"}}
 
 
+def learned_fwi_measure(n_train=3072, epochs=12, n_models=4, iters=20):
+    """The learned start against plain FWI, live and small: the start-model
+    network trained on `n_train` solver-generated surveys, then FWI (L-BFGS,
+    `iters` iterations, every evaluation one replay of the recorded gradient) on
+    `n_models` held-out models from the smoothed true model (plain start), the
+    network's prediction and the mean training model (no survey information).
+    Reports the GPU time each start needs to reach the plain start's final
+    misfit."""
+    import torch
+
+    from paper_2003_06027_gb300 import learned as L
+
+    t0 = time.perf_counter()
+    X, Y, _ = L.make_dataset(n_train, seed=5)
+    net = L.Net(0, seed=0)
+    log = L.train(net, X, Y, epochs=epochs, batch=32, lr=1e-3)
+    mean_model = (L.V_MID + L.V_HALF * Y[0].mean(dim=0)).contiguous()
+    del X, Y
+    torch.cuda.empty_cache()
+    _, s = L.compare_fwi(net, n_models=n_models, seed=1005, iters=iters, mean_model=mean_model)
+    s = {k: v for k, v in s.items()}
+    s.update(train_samples=n_train, epochs=epochs, params=net.nparams, train_seconds=log.seconds,
+             total_seconds=time.perf_counter() - t0,
+             timing="GPU seconds of the misfit/gradient evaluations of each FWI run (recorded graphs)")
+    return s
+
+
 def dist_setup(backend: str = "nccl"):
     """(world size, rank, local rank) from the torchrun environment; joins the
     process group when there is more than one rank (NCCL on GPUs; the host-side
@@ -688,6 +715,7 @@ def main():
             b = res["batched_uneven"]["batched"]
             res["uneven_all"] = uneven_all_measure(b["mode"], b["streams"])
         res["learned"] = learned_measure()
+        res["learned"]["fwi"] = learned_fwi_measure()
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
 

@@ -10,11 +10,11 @@ stays the fallback and the yardstick: `compare_fwi` runs both from the same data
 
 Network (activations channel-major [C][B][H][W]; H = time or depth, W = receivers
 or x; every conv 3x3, pad 1, ReLU except the last):
-  encoder  16 -> 32 (stride 4,1) -> 32 -> 64 (2,2) -> 64 -> 128 (2,1) -> 192 (2,1) -> 256 (2,1)
+  encoder  16 -> 32 (stride 4,1) -> 32 -> 64 (2,2) -> 64 -> 128 (2,1) -> 192 (2,1) -> 256 (2,1) -> 256
            i.e. 1000 x 64 -> 250 x 64 -> 125 x 32 -> 63 x 32 -> 32 x 32 -> 16 x 32
-  decoder  3 x (2x nearest upsampling, conv): 256 -> 128 -> 64 -> 32 at 32x64, 64x128, 128x256,
+  decoder  3 x (2x nearest upsampling, conv): 256 -> 192 -> 64 -> 32 at 32x64, 64x128, 128x256,
            then conv 32 -> 1 (no ReLU); velocity = 3000 + 1500 * output (m/s).
-About 1.2 M parameters. Weights are FP32 with a BF16 copy for the tensor-core
+About 2.0 M parameters (1 969 217). Weights are FP32 with a BF16 copy for the tensor-core
 GEMMs (BF16 operands, FP32 accumulation); every layer runs in libfwi's kernels
 (include/fwi_cnn.h); torch only holds the device memory.
 """
@@ -38,8 +38,8 @@ V_MID, V_HALF = 3000.0, 1500.0  # output scaling: v = V_MID + V_HALF * out
 
 # encoder layers (C_in, C_out, stride_h, stride_w); decoder layers (C_in, C_out), each after a 2x upsampling
 ENCODER = [(16, 32, 4, 1), (32, 32, 1, 1), (32, 64, 2, 2), (64, 64, 1, 1), (64, 128, 2, 1), (128, 192, 2, 1),
-           (192, 256, 2, 1)]
-DECODER = [(256, 128), (128, 64), (64, 32)]
+           (192, 256, 2, 1), (256, 256, 1, 1)]
+DECODER = [(256, 192), (192, 64), (64, 32)]
 
 
 def _lib():
@@ -275,8 +275,13 @@ def gathers_to_input(seis: torch.Tensor) -> torch.Tensor:
     return g.permute(0, 2, 1).contiguous()
 
 
-def make_dataset(n: int, seed: int, device=0):
-    """(inputs [16][n][1000][64], targets [1][n][128][256] normalised, models [n][128][256])."""
+def make_dataset(n: int, seed: int, device=0, workers: int = 4):
+    """(inputs [16][n][1000][64], targets [1][n][128][256] normalised, models [n][128][256]).
+    The surveys are modelled by `workers` host threads, each with its own CUDA
+    stream and library context (one forward call per sample is launch-bound, so
+    concurrent calls keep the GPU busy); sample i depends only on its seed."""
+    import threading
+
     dev = torch.device("cuda", device)
     X = torch.empty((NSHOT, n, NT, NREC), dtype=torch.float32, device=dev)
     Y = torch.empty((1, n, NZ, NX), dtype=torch.float32, device=dev)
@@ -285,14 +290,35 @@ def make_dataset(n: int, seed: int, device=0):
     kw = fwi.problem_kwargs(d)
     cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
     stf, x0, iz, ix = cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
-    out = torch.empty((NSHOT, NREC, NT), dtype=torch.float32, device=dev)
-    for i in range(n):
-        c = random_model(seed * 1000003 + i)
-        models[i] = c
-        ct = cu(c)
-        fwi.forward(ct, stf, x0, iz, ix, out=out, **kw)
-        X[:, i] = gathers_to_input(out)
-        Y[0, i] = (ct - V_MID) / V_HALF
+    torch.cuda.synchronize(dev)
+    errors = []
+
+    def work(w):
+        try:
+            torch.cuda.set_device(dev)
+            st = torch.cuda.Stream(dev)
+            with torch.cuda.stream(st):
+                out = torch.empty((NSHOT, NREC, NT), dtype=torch.float32, device=dev)
+                for i in range(w, n, workers):
+                    c = random_model(seed * 1000003 + i)
+                    models[i] = c
+                    ct = cu(c)
+                    fwi.forward(ct, stf, x0, iz, ix, out=out, device=device, **kw)
+                    X[:, i] = gathers_to_input(out)
+                    Y[0, i] = (ct - V_MID) / V_HALF
+            st.synchronize()
+            fwi.release_context(device)
+        except Exception as e:  # re-raised below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(w,)) for w in range(max(1, workers))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise errors[0]
+    torch.cuda.synchronize(dev)
     return X, Y, models
 
 
@@ -341,42 +367,67 @@ def network_flops_per_sample() -> float:
     return fl
 
 
-# ---------------------------------------------------------------- FWI from the two starts
-def fwi_run(c0: torch.Tensor, observed: torch.Tensor, d: dict, c_true: torch.Tensor, iters: int = 50,
-            step: float = 40.0, decay: float = 0.97):
-    """Plain FWI (normalised steepest descent: at most `step` m/s per cell, shrinking
-    by `decay` per iteration) from c0; returns [(misfit, relative model error,
-    seconds so far)] per iteration, the first entry being the start."""
-    kw = fwi.problem_kwargs(d)
-    dev = c0.device
-    cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
-    stf, x0, iz, ix = cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"])
-    c = c0.clone()
-    nrm = float(torch.linalg.vector_norm(c_true))
-    hist = []
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(iters + 1):
-        J, g, _, _, _ = fwi.misfit_grad(c, stf, x0, iz, ix, observed, ckpt_every=d["ckpt_every"], want_src=False,
-                                        **kw)
-        err = float(torch.linalg.vector_norm(c - c_true)) / nrm
-        hist.append((float(J[0]), err, time.perf_counter() - t0))
-        if k == iters:
-            break
+# ---------------------------------------------------------------- FWI from the starts
+class _Evaluator:
+    """Misfit and gradient of one survey as a recorded graph (fwi.GradGraph):
+    each evaluation copies the model into the recorded buffer and replays the
+    whole fwi_misfit_grad call, so host launch overhead stays out of the timing."""
+
+    def __init__(self, d: dict, observed: torch.Tensor, c_init: torch.Tensor):
+        kw = fwi.problem_kwargs(d)
+        dev = c_init.device
+        cu = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+        self.c = c_init.clone().contiguous()
+        self._keep = (cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"]), observed.contiguous())
+        self.g = fwi.GradGraph(self.c, *self._keep, ckpt_every=d["ckpt_every"], **kw)
+
+    def __call__(self, c: torch.Tensor):
         with torch.no_grad():
-            c.sub_(step * decay ** k * g / g.abs().max().clamp_min(1e-30)).clamp_(1400.0, 4600.0)
-    return hist
+            self.c.copy_(c)
+        self.g.launch()
+        self.g.check()
+        return float(self.g.misfit[0]), self.g.grad.clone()
+
+    def close(self):
+        self.g.close()
+
+
+def fwi_run(ev: _Evaluator, c0: torch.Tensor, c_true: torch.Tensor, iters: int = 50, step0: float = 40.0,
+            vmin: float = 1400.0, vmax: float = 4600.0):
+    """FWI from c0 with the project's L-BFGS (optim.lbfgs: memory 5, box bounds,
+    first step at most `step0` m/s per cell), every evaluation one replay of the
+    recorded gradient. Returns [(misfit, relative model error, GPU seconds so
+    far)] per accepted iterate, the first entry being the start. The seconds
+    are wall time of the evaluations (each ends with a device synchronisation),
+    so they are the GPU time the run took."""
+    from . import optim
+
+    nrm = float(torch.linalg.vector_norm(c_true))
+    clock = [0.0]
+    evals = []  # (misfit, model error, GPU seconds so far) of every evaluation
+
+    def tracked(c):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, g = ev(c)
+        clock[0] += time.perf_counter() - t0
+        evals.append((J, float(torch.linalg.vector_norm(c - c_true)) / nrm, clock[0]))
+        return J, g
+
+    _, log = optim.lbfgs(tracked, c0, iters, m=5, step0=step0, lower=vmin, upper=vmax)
+    # log.evals[k]: evaluations made when iterate k was accepted
+    return [evals[ne - 1] for ne in log.evals]
 
 
 def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, sigma: float = 10.0, device=0,
                 mean_model=None):
-    """For held-out random models: FWI from the Gaussian-smoothed true model
-    (sigma cells, the plain start), from the network's prediction, and (if
-    given) from `mean_model`, a start that knows nothing of the survey (the mean
-    of the training models). Returns the per-model histories and a summary (mean
-    start / final misfit and model error of each start, and the GPU time the
-    learned start needs to reach the plain start's final misfit, or None where
-    it does not)."""
+    """For held-out random models: FWI (L-BFGS) from the Gaussian-smoothed true
+    model (sigma cells, the plain start), from the network's prediction, and (if
+    given) from `mean_model`, the start available without any survey
+    information (the mean of the training models). Returns the per-model
+    histories and a summary: mean start / final misfit and model error of each
+    start, and the GPU time each start needs to reach the plain start's final
+    misfit (None where it does not within `iters` iterations)."""
     from . import synth
 
     dev = torch.device("cuda", device)
@@ -390,15 +441,19 @@ def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, s
         obs = fwi.forward(c_true, cu(d["stf"]), cu(d["x0"]), cu(d["rec_iz"]), cu(d["rec_ix"]), **kw)
         plain0 = cu(synth.smooth(c_np, sigma))
         learned0 = net.predict(gathers_to_input(obs).unsqueeze(1))[0].contiguous()
-        hp = fwi_run(plain0, obs, d, c_true, iters)
-        hl = fwi_run(learned0, obs, d, c_true, iters)
-        hm = fwi_run(mean_model.clone(), obs, d, c_true, iters) if mean_model is not None else None
+        ev = _Evaluator(d, obs, plain0)
+        hp = fwi_run(ev, plain0, c_true, iters)
+        hl = fwi_run(ev, learned0, c_true, iters)
+        hm = fwi_run(ev, mean_model.clone(), c_true, iters) if mean_model is not None else None
+        ev.close()
         target = hp[-1][0]
-        reach = next((h[2] for h in hl if h[0] <= target), None)
-        runs.append(dict(plain=hp, learned=hl, mean=hm, learned_time_to_plain_final=reach, plain_time=hp[-1][2]))
+        reach = lambda h: next((e[2] for e in h if e[0] <= target), None)
+        runs.append(dict(plain=hp, learned=hl, mean=hm, learned_time_to_plain_final=reach(hl),
+                         mean_time_to_plain_final=reach(hm) if hm is not None else None, plain_time=hp[-1][2]))
     mean = lambda xs: float(np.mean(xs))
+    reached = [r for r in runs if r["learned_time_to_plain_final"] is not None]
     summary = dict(
-        models=n_models, iters=iters, smooth_sigma_cells=sigma,
+        models=n_models, iters=iters, smooth_sigma_cells=sigma, optimiser="L-BFGS (optim.lbfgs, m=5)",
         plain_start_model_error=mean([r["plain"][0][1] for r in runs]),
         learned_start_model_error=mean([r["learned"][0][1] for r in runs]),
         plain_final_misfit=mean([r["plain"][-1][0] for r in runs]),
@@ -408,18 +463,23 @@ def compare_fwi(net: Net, n_models: int = 8, seed: int = 777, iters: int = 50, s
         plain_start_misfit=mean([r["plain"][0][0] for r in runs]),
         learned_start_misfit=mean([r["learned"][0][0] for r in runs]),
         plain_fwi_seconds=mean([r["plain_time"] for r in runs]),
-        learned_reaches_plain_final=sum(r["learned_time_to_plain_final"] is not None for r in runs),
+        learned_reaches_plain_final=len(reached),
         learned_seconds_to_plain_final=[r["learned_time_to_plain_final"] for r in runs],
+        learned_faster_than_plain=sum(r["learned_time_to_plain_final"] < r["plain_time"] for r in reached),
+        learned_over_plain_time_where_reached=(mean([r["learned_time_to_plain_final"] / r["plain_time"]
+                                                     for r in reached]) if reached else None),
     )
     if mean_model is not None:
         summary.update(mean_start_model_error=mean([r["mean"][0][1] for r in runs]),
                        mean_start_misfit=mean([r["mean"][0][0] for r in runs]),
                        mean_final_misfit=mean([r["mean"][-1][0] for r in runs]),
-                       mean_final_model_error=mean([r["mean"][-1][1] for r in runs]))
+                       mean_final_model_error=mean([r["mean"][-1][1] for r in runs]),
+                       mean_reaches_plain_final=sum(r["mean_time_to_plain_final"] is not None for r in runs),
+                       learned_over_mean_final_misfit=mean([r["learned"][-1][0] / r["mean"][-1][0] for r in runs]))
     return runs, summary
 
 
-def experiment(n_train=8000, epochs=12, batch=32, n_test=8, iters=50, device=0, seed=5):
+def experiment(n_train=20000, epochs=12, batch=32, n_test=64, iters=50, device=0, seed=5):
     """The whole learned-start experiment: data generation, training, FWI
     comparison. Returns a JSON-able report."""
     torch.cuda.set_device(device)
@@ -444,9 +504,9 @@ if __name__ == "__main__":
     import json
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=8000)
+    ap.add_argument("--train", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=12)
-    ap.add_argument("--test", type=int, default=8)
+    ap.add_argument("--test", type=int, default=64)
     ap.add_argument("--iters", type=int, default=50)
     a = ap.parse_args()
     print(json.dumps(experiment(a.train, a.epochs, n_test=a.test, iters=a.iters), indent=1))

@@ -169,3 +169,25 @@ def test_network_learns_layered_models(fwi_lib):
         err_net = float(((pred - Yt) ** 2).mean())
         err_const = float(((Yt.mean() - Yt) ** 2).mean())
     assert err_net < err_const, (err_net, err_const)
+
+
+def test_learned_start_gains_over_the_start_without_it(fwi_lib):
+    """What the trained network gains: on held-out surveys, FWI (L-BFGS, same
+    iteration budget) from the network's prediction against FWI from the start
+    available without the network (the mean of the training models, which uses
+    no survey information). The learned start must be closer to the true model
+    and end at a clearly lower misfit. The comparison with the smoothed true
+    model (which is built from the answer) is reported, not asserted."""
+    from paper_2003_06027_gb300 import learned as L
+
+    X, Y, _ = L.make_dataset(3072, seed=303)
+    net = L.Net(0, seed=3)
+    L.train(net, X, Y, epochs=12, batch=32, lr=1e-3)
+    mean_model = (L.V_MID + L.V_HALF * Y[0].mean(dim=0)).contiguous()
+    del X, Y
+    _, s = L.compare_fwi(net, n_models=3, seed=404, iters=12, mean_model=mean_model)
+    print("\nlearned start vs mean-model start:", {k: s[k] for k in (
+        "learned_start_model_error", "mean_start_model_error", "learned_final_misfit", "mean_final_misfit",
+        "plain_final_misfit", "learned_seconds_to_plain_final", "plain_fwi_seconds")})
+    assert s["learned_start_model_error"] < s["mean_start_model_error"]
+    assert s["learned_final_misfit"] < 0.5 * s["mean_final_misfit"]
