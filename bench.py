@@ -716,6 +716,33 @@ def main():
             res["uneven_all"] = uneven_all_measure(b["mode"], b["streams"])
         res["learned"] = learned_measure()
         res["learned"]["fwi"] = learned_fwi_measure()
+    # a compact summary of the extra measurements, placed right after the contract keys so that it
+    # survives a capture that keeps only the head of this long line
+    summ = {}
+    if "elastic" in res:
+        e = res["elastic"]
+        summ["elastic"] = {"gradient": round(e["value"], 2), "forward": round(e["forward"]["value"], 2),
+                           "adj_pair_frac": round(e["kernels"]["adj"]["frac"], 3),
+                           "fwd_pair_frac": round(e["kernels"]["fwd"]["frac"], 3)}
+    if "acoustic_xl" in res:
+        summ["acoustic_xl_frac"] = {k: round(res["acoustic_xl"][k]["frac"], 3) for k in ("fwd", "store", "adj")}
+    if "batched_uneven" in res:
+        b = res["batched_uneven"]
+        summ["batched_uneven"] = {"best": round(b["batched"]["value"], 2), "mode": b["batched"]["mode"],
+                                  "persistent": round(b["persistent"]["value"], 2),
+                                  "plain_per_shot": round(b["plain_per_shot"]["value"], 2)}
+    if "learned" in res:
+        lf = res["learned"].get("fwi", {})
+        summ["learned"] = {"train_step_ms": round(res["learned"]["ms_per_step"], 2),
+                           "bf16_frac": res["learned"]["roofline"]["frac"],
+                           "learned_over_mean_final_misfit": lf.get("learned_over_mean_final_misfit"),
+                           "learned_reaches_plain_final": lf.get("learned_reaches_plain_final")}
+    if "store_all" in res:
+        summ["store_all"] = round(res["store_all"]["value"], 2)
+    if summ:
+        head = list(res.items())
+        k = [i for i, (key, _) in enumerate(head) if key == "config"][0] + 1
+        res = dict(head[:k] + [("summary", summ)] + head[k:])
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
 
