@@ -329,18 +329,21 @@ def batched_measure(n_inst=16):
 
     inst = batch.prepare([synth.uneven_instance(4, i) for i in range(n_inst)])
     cells = sum(i.cell_steps for i in inst)
-    modes = ("persistent", "graph", "batched")
-    best, table = batch.autotune(inst, workers=(1, 2, 4, 8), ckpt=(100,), modes=modes)
-    _, _, tb = batch.sweep(inst, best[0], best[1], best[2])
+    modes, tiles = ("persistent", "graph", "batched"), (32, 64)
+    best, table = batch.autotune(inst, workers=(1, 2, 4, 8), ckpt=(100,), modes=modes, tiles=tiles)
+    mode, W, K, _, tile = batch.candidate(best, tiles=tiles)
+    _, _, tb = batch.sweep(inst, mode, W, K, tile_rows=tile)
     batch.close_graphs()
     batch.close_pools()
     batch.sweep(inst, "plain", ckpt_every=100)
     _, _, tp = batch.sweep(inst, "plain", ckpt_every=100)
-    best_of = {m: min(t for (mm, _, _), t in table.items() if mm == m) for m in modes}
+    best_of = {m: min(t for key, t in table.items() if key[0] == m) for m in modes}
+    best_tile = {tt: min(t for key, t in table.items() if key[0] != "persistent" and key[-1] == tt) for tt in tiles}
     batch.close_graphs()
     return {"workload": f"uneven-seed4-{n_inst}-instances", "cell_steps_per_sweep": cells,
-            "batched": {"value": cells / tb / 1e9, "unit": UNIT, "s_per_sweep": tb, "mode": best[0],
-                        "streams": best[1], "ckpt_every": best[2]},
+            "batched": {"value": cells / tb / 1e9, "unit": UNIT, "s_per_sweep": tb, "mode": mode,
+                        "streams": W, "ckpt_every": K, "forward_tile_rows": tile},
+            "tile_rows_best": {str(tt): {"value": cells / v / 1e9, "s_per_sweep": v} for tt, v in best_tile.items()},
             "persistent": {"value": cells / best_of["persistent"] / 1e9, "s_per_sweep": best_of["persistent"],
                            "launches": "W groups of instances, each one graph whose time steps are one persistent "
                                        "launch over the group's instances (W = 1: all instances in every launch)"},
@@ -348,11 +351,11 @@ def batched_measure(n_inst=16):
             "threads_best": {"value": cells / best_of["batched"] / 1e9, "s_per_sweep": best_of["batched"]},
             "plain_per_shot": {"value": cells / tp / 1e9, "unit": UNIT, "s_per_sweep": tp},
             "speedup": tp / tb,
-            "autotune_s": {f"{m}-{w}x{k}": t for (m, w, k), t in table.items()},
+            "autotune_s": {"-".join(str(x) for x in key): t for key, t in table.items()},
             "timing": "host wall time per sweep, device idle before and after (each sweep ends synchronised)"}
 
 
-def uneven_all_measure(mode="graph", workers=2, waves=2):
+def uneven_all_measure(mode="graph", workers=2, waves=2, tile_rows=0):
     """The whole 64-instance uneven workload (seed 4, 479 G cell-steps per
     gradient sweep) in a batched mode. Its workspace at K = 100 (300 GB)
     exceeds the GPU's memory, so it runs as `waves` sets of consecutive
@@ -364,14 +367,14 @@ def uneven_all_measure(mode="graph", workers=2, waves=2):
     for w in range(waves):
         inst = batch.prepare([synth.uneven_instance(4, i) for i in range(w * per, min(64, (w + 1) * per))])
         cells += sum(i.cell_steps for i in inst)
-        batch.sweep(inst, mode, workers, ckpt_every=100)  # creation: the first sweep (and recording)
-        _, _, t = batch.sweep(inst, mode, workers, ckpt_every=100)
+        batch.sweep(inst, mode, workers, ckpt_every=100, tile_rows=tile_rows)  # creation: the first sweep
+        _, _, t = batch.sweep(inst, mode, workers, ckpt_every=100, tile_rows=tile_rows)
         secs += t
         batch.close_graphs()
         batch.close_pools()
         del inst
     return {"workload": "uneven-seed4-64-instances", "cell_steps_per_sweep": cells, "mode": mode,
-            "streams": workers, "waves": waves, "value": cells / secs / 1e9, "unit": UNIT, "s_per_sweep": secs,
+            "streams": workers, "forward_tile_rows": tile_rows, "waves": waves, "value": cells / secs / 1e9, "unit": UNIT, "s_per_sweep": secs,
             "timing": "host wall time per sweep, each wave's sweep timed after its creation sweep"}
 
 
@@ -713,7 +716,7 @@ def main():
         res["batched_uneven"] = batched_measure()
         if args.uneven_all:
             b = res["batched_uneven"]["batched"]
-            res["uneven_all"] = uneven_all_measure(b["mode"], b["streams"])
+            res["uneven_all"] = uneven_all_measure(b["mode"], b["streams"], tile_rows=b["forward_tile_rows"])
         res["learned"] = learned_measure()
         res["learned"]["fwi"] = learned_fwi_measure()
     # a compact summary of the extra measurements, placed right after the contract keys so that it

@@ -188,7 +188,8 @@ fwi_status fwi_forward_vjp(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
  * ckpt_every (1..nt), for the given model, sources, receivers and nt; sized
  * by the layout the call itself uses, so a context whose arena is at least
  * this large allocates nothing for that call. The dominant terms are fields
- * of nshots x R x P floats, R = ceil(Nz/32)*32 + 16 rows and
+ * of nshots x R x P floats, R = ceil(Nz/64)*64 + 16 rows (acoustic; elastic
+ * ceil(Nz/32)*32 + 16) and
  * P = ceil(Nx/64)*64 + 16 columns (the padded grid Nz x Nx, tile-aligned,
  * with an 8-cell apron): per gradient call 6 per checkpoint (ceil(nt/K) of
  * them, acoustic; 13 elastic) and 2 per step of a segment (K of them,
@@ -210,6 +211,15 @@ fwi_status fwi_workspace_bytes(const fwi_model *model, const fwi_sources *src,
 fwi_status fwi_choose_ckpt(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
                            const fwi_receivers *rec, int32_t nt, uint64_t budget_bytes,
                            int32_t *ckpt_every);
+
+/* Tile shape of the acoustic forward steps of ctx's calls (forward sweep and
+ * segment recompute): tiles of 64 columns x forward_tile_rows rows, 32 (256
+ * threads per CTA) or 64 (512 threads; half the z-halo flux recompute per cell,
+ * fewer and larger CTAs). 0 keeps the library's default (32). Results do not
+ * depend on it (each cell's arithmetic is the same). Takes effect for later
+ * calls and recordings; FWI_EINVAL for other values. The batched autotuner
+ * picks it per workload. */
+fwi_status fwi_set_tile_shape(fwi_ctx *ctx, int32_t forward_tile_rows);
 
 /* Launch shape of the acoustic calls on ctx: the shots of a call are split
  * into forward_groups (forward and recompute steps) and adjoint_groups

@@ -78,8 +78,9 @@ def prepare(problems, device=0) -> list:
     return out
 
 
-def _grad_batched(inst: Instance, K: int, groups=(0, 0)):
+def _grad_batched(inst: Instance, K: int, groups=(0, 0), tile_rows: int = 0):
     fwi.set_shot_groups(*groups, device=inst.c.device.index)
+    fwi.set_tile_shape(tile_rows, device=inst.c.device.index)
     J, g, _, _, _ = fwi.misfit_grad(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed,
                                     ckpt_every=K, want_src=False, **inst.kw)
     return J, g
@@ -100,12 +101,12 @@ _graphs = {}
 _graph_streams = {}
 
 
-def _graph_of(inst: Instance, K: int, groups=(0, 0)) -> fwi.GradGraph:
-    key = (id(inst), K, tuple(groups))
+def _graph_of(inst: Instance, K: int, groups=(0, 0), tile_rows: int = 0) -> fwi.GradGraph:
+    key = (id(inst), K, tuple(groups), tile_rows)
     g = _graphs.get(key)
     if g is None or g._a.c.data_ptr() != inst.c.data_ptr():
         g = fwi.GradGraph(inst.c, inst.stf, inst.x0, inst.rec_iz, inst.rec_ix, inst.observed, ckpt_every=K,
-                          groups=groups, **inst.kw)
+                          groups=groups, tile_rows=tile_rows, **inst.kw)
         _graphs[key] = g
     return g
 
@@ -200,10 +201,13 @@ def close_pools():
         _pools.pop(k).close()
 
 
-def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 100, groups=(0, 0)):
+def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 100, groups=(0, 0),
+          tile_rows: int = 0):
     """One gradient sweep over all instances; returns ([J_i], [g_i], seconds).
     The time is host wall time with the device idle on both sides (every
-    library call ends with a stream synchronisation)."""
+    library call ends with a stream synchronisation). ``tile_rows``: tile
+    height of the forward steps (fwi_set_tile_shape; the persistent mode runs
+    32-row tiles)."""
     n = len(instances)
     Js, gs = [None] * n, [None] * n
     torch.cuda.synchronize()
@@ -215,14 +219,15 @@ def sweep(instances, mode: str = "batched", workers: int = 4, ckpt_every: int = 
         def job(i):
             def fn():
                 inst = instances[i]
-                Js[i], gs[i] = _grad_batched(inst, min(ckpt_every, int(inst.stf.shape[1])), groups)
+                Js[i], gs[i] = _grad_batched(inst, min(ckpt_every, int(inst.stf.shape[1])), groups, tile_rows)
             return fn
 
         order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
         pool(max(1, min(workers, n)), torch.cuda.current_device()).run([job(i) for i in order])
     elif mode == "graph":
         order = sorted(range(n), key=lambda i: -instances[i].cell_steps)  # largest first
-        graphs = {i: _graph_of(instances[i], min(ckpt_every, int(instances[i].stf.shape[1])), groups) for i in order}
+        graphs = {i: _graph_of(instances[i], min(ckpt_every, int(instances[i].stf.shape[1])), groups, tile_rows)
+                  for i in order}
         streams = _streams(max(1, min(workers, n)), torch.cuda.current_device())
         main = torch.cuda.current_stream()
         for s in streams:
@@ -264,14 +269,19 @@ def _close_batches_but(instances, best):
     torch.cuda.synchronize()
 
 
-def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batched",), groups=((0, 0),)):
-    """Pick (mode, workers, ckpt_every, shot groups) by timing one sweep per
-    candidate on the given instances (the first sweep of each candidate also
-    sizes the arenas or records the graphs, so each candidate is run twice and
-    the second run counts). ``groups`` lists (forward, adjoint) shot-group
-    counts, the step kernels' launch shape (fwi_set_shot_groups). The pools of
-    the losing worker counts are closed, and the graphs the winner does not use
-    are freed."""
+def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batched",), groups=((0, 0),),
+             tiles=(0,)):
+    """Pick (mode, workers, ckpt_every, shot groups, tile height) by timing one
+    sweep per candidate on the given instances (the first sweep of each
+    candidate also sizes the arenas or records the graphs, so each candidate is
+    run twice and the second run counts). ``groups`` lists (forward, adjoint)
+    shot-group counts, the step kernels' launch shape (fwi_set_shot_groups);
+    ``tiles`` lists forward tile heights (fwi_set_tile_shape: 0 or 32, 64; the
+    persistent mode runs 32-row tiles only). A candidate's key is (mode, W, K),
+    followed by the shot groups if more than one is listed and by the tile
+    height if more than one is listed (`candidate` unpacks it). The pools of
+    the losing worker counts are closed, and the graphs and batches the winner
+    does not use are freed."""
     best = None
     table = {}
     dev = torch.cuda.current_device()
@@ -281,24 +291,34 @@ def autotune(instances, workers=(1, 2, 4, 8), ckpt=(50, 100, 200), modes=("batch
             for K in ckpt:
                 for grp in groups:
                     grp = tuple(grp)
-                    sweep(instances, mode, W, K, grp)
-                    _, _, t = sweep(instances, mode, W, K, grp)
-                    key = (mode, W, K) if len(groups) == 1 else (mode, W, K, grp)
-                    table[key] = t
-                    if best is None or t < table[best]:
-                        best = key
-                    _close_batches_but(instances, best)  # each grouping holds every instance's workspace
+                    for tile in (tiles if mode != "persistent" else tiles[:1]):
+                        sweep(instances, mode, W, K, grp, tile)
+                        _, _, t = sweep(instances, mode, W, K, grp, tile)
+                        key = (mode, W, K) + ((grp,) if len(groups) > 1 else ()) + ((tile,) if len(tiles) > 1 else ())
+                        table[key] = t
+                        if best is None or t < table[best]:
+                            best = key
+                        _close_batches_but(instances, best)  # each grouping holds every instance's workspace
             if mode == "batched":  # keep at most the best pool alive between candidates
                 bw = best[1] if best[0] == "batched" else None
                 loser = W if bw != W else (prev[1] if prev is not None and prev[0] == "batched" and prev[1] != W
                                            else None)
                 if loser is not None and (loser, dev) in _pools:
                     _pools.pop((loser, dev)).close()
-    bgrp = tuple(best[3]) if len(best) > 3 else (0, 0)
-    for key in [k for k in _graphs if not (best[0] == "graph" and k[1] == best[2] and k[2] == bgrp)]:
+    _, _, bK, bgrp, btile = candidate(best, groups, tiles)
+    for key in [k for k in _graphs if not (best[0] == "graph" and k[1:] == (bK, bgrp, btile))]:
         _graphs.pop(key).close()  # graphs the winner does not use
     _close_batches_but(instances, best)
     return best, table
+
+
+def candidate(key, groups=((0, 0),), tiles=(0,)):
+    """(mode, workers, ckpt_every, shot groups, tile height) of an autotune key."""
+    mode, W, K = key[:3]
+    rest = list(key[3:])
+    grp = tuple(rest.pop(0)) if len(groups) > 1 else tuple(groups[0])
+    tile = rest.pop(0) if len(tiles) > 1 else tiles[0]
+    return mode, W, K, grp, tile
 
 
 def fwi_iterations(instances, iters: int, mode: str = "batched", workers: int = 4, ckpt_every: int = 100,

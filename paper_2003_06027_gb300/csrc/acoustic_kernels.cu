@@ -45,7 +45,6 @@ constexpr int MW = TILE_X + 12;          // 76: m tile cols [x0-4, x0+TX+8)
 constexpr int MH = TILE_Z + 9;           // 41: m tile rows [z0-4, z0+TZ+5)
 constexpr int QXW = TILE_X + 8;          // 72: half cols [x0-4, x0+TX+4)
 constexpr int QZH = TILE_Z + 8;          // 40: half rows [z0-4, z0+TZ+4)
-constexpr int U_BYTES = UW * UH * 4;     // 15360
 constexpr int M_BYTES = MW * MH * 4;     // 12464
 constexpr int M_SLOT = (M_BYTES + 127) / 128 * 128;
 #ifndef FWI_FWD_CTAS
@@ -53,6 +52,18 @@ constexpr int M_SLOT = (M_BYTES + 127) / 128 * 128;
 #endif
 constexpr int FWD_CTAS = FWI_FWD_CTAS;     // resident forward CTAs per SM the registers are sized for
 constexpr int XS_BYTES = TILE_Z * UW * 4;  // 10240: adjoint x operand tile
+// Geometry of a forward tile of TZ rows (TZ = 32 or 64) and TILE_X columns: 16
+// columns of threads, each thread owning 2 rows x 4 columns (so 8 * TZ threads).
+template <int TZ>
+struct FwdGeo {
+  static constexpr int NT = 8 * TZ;           // threads per CTA
+  static constexpr int UHT = TZ + 2 * H;      // wavefield tile height
+  static constexpr int MHT = TZ + 9;          // m tile rows [z0-4, z0+TZ+5)
+  static constexpr int QZHT = TZ + 8;         // half rows [z0-4, z0+TZ+4)
+  static constexpr int UB = UW * UHT * 4;
+  static constexpr int MB = MW * MHT * 4;
+  static constexpr int MSLOT = (MB + 127) / 128 * 128;
+};
 constexpr int ZS_BYTES = UH * TILE_X * 4;  // 12288: adjoint z operand tile
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -83,8 +94,23 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ bool tile_pml_x(const Grid& g, int x0) {
   return g.npml > 0 && (x0 - H < g.npml || x0 + TILE_X + H > g.npml + g.nx - 1);
 }
+template <int TZ = TILE_Z>
 __device__ __forceinline__ bool tile_pml_z(const Grid& g, int z0) {
-  return g.npml > 0 && (z0 - H < g.npml || z0 + TILE_Z + H > g.npml + g.nz - 1);
+  return g.npml > 0 && (z0 - H < g.npml || z0 + TZ + H > g.npml + g.nz - 1);
+}
+// Tile t of a walk over TZ-row tiles (the 32-row walk is tile_decode).
+template <int TZ>
+__device__ __forceinline__ TileId tile_decode_t(const Grid& g, int t) {
+  if (TZ == TILE_Z) return tile_decode(g, t);
+  const int ntz = (g.Nz + TZ - 1) / TZ;
+  TileId r;
+  r.tx = t % g.ntx;
+  const int q = t / g.ntx;
+  r.tz = q % ntz;
+  r.s = q / ntz;
+  r.x0 = r.tx * TILE_X;
+  r.z0 = r.tz * TZ;
+  return r;
 }
 
 // Points of one axis where the CPML coefficients can be nonzero (the tables are
@@ -133,28 +159,31 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* red) {
   __syncthreads();
 }
 
-// Issue the TMA fetches of tile t into one buffer (one elected thread).
+// Issue the TMA fetches of tile t (TZ rows) into one buffer (one elected thread).
 // plane0: the pair plane of this launch's first shot.
+template <int TZ = TILE_Z>
 __device__ __forceinline__ void fetch_tile(const CUtensorMap* fmap, const CUtensorMap* mmap, const Grid& g, int plane0,
                                            int t, float* dst_u, float* dst_m, uint64_t* bar) {
-  const TileId id = tile_decode(g, t);
+  const TileId id = tile_decode_t<TZ>(g, t);
   fence_proxy_async();
-  mbar_expect_tx(bar, U_BYTES + M_BYTES);
+  mbar_expect_tx(bar, FwdGeo<TZ>::UB + FwdGeo<TZ>::MB);
   // allocation coordinates: padded (i, j) -> (i + APRON, j + APRON)
   tma_3d(dst_u, fmap, id.x0 - H + APRON, id.z0 - H + APRON, plane0 + id.s, bar);
   tma_2d(dst_m, mmap, id.x0 - 4 + APRON, id.z0 - 4 + APRON, bar);
 }
 
 // Shared memory of the step kernels (every array a multiple of 128 bytes).
-struct FwdSmem {
-  float u[UH * UW];
-  float m[M_SLOT / 4];
-  float qx[TILE_Z * QXW];
-  float qz[QZH * TILE_X];
-  float4 up4[2 * NTHREADS];  // u^{n-1} of the own cells, [row][thread] (cp.async)
+template <int TZ>
+struct FwdSmemT {
+  float u[FwdGeo<TZ>::UHT * UW];
+  float m[FwdGeo<TZ>::MSLOT / 4];
+  float qx[TZ * QXW];
+  float qz[FwdGeo<TZ>::QZHT * TILE_X];
+  float4 up4[2 * FwdGeo<TZ>::NT];  // u^{n-1} of the own cells, [row][thread] (cp.async)
   float red[32];
   uint64_t bar;
 };
+using FwdSmem = FwdSmemT<TILE_Z>;
 struct AdjSmem {
   float xs[TILE_Z * UW];     // x stencil operand (lambda or Hx): own rows, cols [x0-H, x0+TX+H)
   float zs[UH * TILE_X];     // z stencil operand (lambda or Hz): rows [z0-H, z0+TZ+H), own cols
@@ -244,12 +273,18 @@ __device__ __forceinline__ void batch_load_step(const BatchArgs& b, int i, AcuSt
 // takes its instance's parameters and tensor maps from the device table, and a
 // forward-sweep launch (RECORD and STORE) stores the fluxes only for the
 // instances in their last segment (a null slot otherwise).
-template <int N, bool RECORD, bool STORE, bool MULTI>
-__global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
+//
+// TZ: the tile height, 32 (256 threads) or 64 (512 threads, a compile-time
+// variant for the autotuner: half the z-halo recompute per cell, the same
+// per-thread work); multi-instance launches use 32.
+template <int N, bool RECORD, bool STORE, bool MULTI, int TZ>
+__global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
     acu_fwd_step(const __grid_constant__ CUtensorMap tmap_u, const __grid_constant__ CUtensorMap tmap_m,
                  const __grid_constant__ AcuStep p0, const AcuCoef cf, const BatchArgs b) {
+  static_assert(TZ == TILE_Z || (TZ == 2 * TILE_Z && !MULTI), "tile heights: 32, or 64 for single-instance launches");
+  constexpr int NT = FwdGeo<TZ>::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  FwdSmem& sh = *reinterpret_cast<FwdSmem*>(smem_raw);
+  FwdSmemT<TZ>& sh = *reinterpret_cast<FwdSmemT<TZ>*>(smem_raw);
   AcuStep& shp = *reinterpret_cast<AcuStep*>(smem_raw + FWD_SMEM_MAIN);  // MULTI only
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const uint64_t pol = STORE ? l2_evict_first() : 0ull;  // segment slots stream through L2
@@ -264,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       tensormap_acquire(&in->mm);
       fetch_tile(&in->mu, &in->mm, gi, (b.n & 1) * in->p.S, tt - __ldg(b.tile_start + i), sh.u, sh.m, &sh.bar);
     } else {
-      fetch_tile(&tmap_u, &tmap_m, p0.g, p0.cur * p0.S_pair + p0.s0, tt, sh.u, sh.m, &sh.bar);
+      fetch_tile<TZ>(&tmap_u, &tmap_m, p0.g, p0.cur * p0.S_pair + p0.s0, tt, sh.u, sh.m, &sh.bar);
     }
   };
 
@@ -292,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     const AcuStep& p = MULTI ? shp : p0;
     const Grid& g = p.g;
     const int pitch = g.pitch;
-    const TileId id = tile_decode(g, tl);
+    const TileId id = tile_decode_t<TZ>(g, tl);
     const int x0 = id.x0, z0 = id.z0, s = id.s;
     const long long base = (long long)s * g.slice + g.off0;
     float* __restrict__ uprev = p.u + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
@@ -300,14 +335,18 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     // tile is fetched and stage 1 runs
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
 #pragma unroll
-    for (int rr = 0; rr < 2; rr++) cp_async16(&sh.up4[rr * NTHREADS + tid], uprev + (long long)(zr0 + rr) * pitch + xb);
+    for (int rr = 0; rr < 2; rr++) cp_async16(&sh.up4[rr * NT + tid], uprev + (long long)(zr0 + rr) * pitch + xb);
     cp_async_commit();
     // small per-tile operands, fetched before the wait as well
     const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
     const float stf_n = __ldg(p.stf + (long long)s * p.nt + p.n);
-    const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
+    // receivers: the lists are kept per thread of a 32-row tile; a thread of a
+    // 64-row tile owns the same 2 x 4 cells as thread (ty % 16, tx) of 32-row
+    // tile 2 tz + ty / 16 (beyond the grid's last 32-row tile: no receivers)
+    const int tz32 = id.tz * (TZ / TILE_Z) + ty / 16;
     int rb = 0, re = 0;
-    if (RECORD) {
+    if (RECORD && tz32 < g.ntz) {
+      const int key = (tz32 * g.ntx + id.tx) * NTHREADS + (ty % 16) * 16 + tx;
       rb = __ldg(p.thr_rec_start + key);
       re = __ldg(p.thr_rec_start + key + 1);
     }
@@ -323,7 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
     }
     const float* su = sh.u;
     const float* sm = sh.m;
-    const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z(g, z0);
+    const bool pmlx = tile_pml_x(g, x0), pmlz = tile_pml_z<TZ>(g, z0);
 
     // ---- stage 1a: x fluxes q = m_half (D+u + psi) at 4 half columns of row r
     auto qx_item = [&](int r, int gq, bool own) {
@@ -374,10 +413,13 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       if (pmlz && layer_h(hz, hz, g.npml, g.nz)) {
         const float aa = __ldg(p.azh + hz + TAB_OFF);
         if (aa != 0.f) {
+          // psi' = b psi + a g, then p = g + psi': the same operations, in the same
+          // order, as the owner's update, so a half row computed here as halo and by
+          // its owner tile agrees bit for bit (whatever the tile height)
           const float bb = __ldg(p.bzh + hz + TAB_OFF);
           const float4 po = *reinterpret_cast<const float4*>(p.psiz_in + base + (long long)hz * pitch + xc);
-          pp[0] += bb * po.x + aa * pp[0]; pp[1] += bb * po.y + aa * pp[1];
-          pp[2] += bb * po.z + aa * pp[2]; pp[3] += bb * po.w + aa * pp[3];
+          pp[0] += fmaf(aa, pp[0], bb * po.x); pp[1] += fmaf(aa, pp[1], bb * po.y);
+          pp[2] += fmaf(aa, pp[2], bb * po.z); pp[3] += fmaf(aa, pp[3], bb * po.w);
         }
       }
       const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
@@ -414,9 +456,9 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
           if (aa != 0.f) {
             const float bb = __ldg(p.bzh + hz + TAB_OFF);
             const float4 po = *reinterpret_cast<const float4*>(p.psiz_in + idz);
-            float4 pn;
-            pn.x = bb * po.x + aa * pp[rr][0]; pn.y = bb * po.y + aa * pp[rr][1];
-            pn.z = bb * po.z + aa * pp[rr][2]; pn.w = bb * po.w + aa * pp[rr][3];
+            float4 pn;  // the operations of the halo items' update, in the same order
+            pn.x = fmaf(aa, pp[rr][0], bb * po.x); pn.y = fmaf(aa, pp[rr][1], bb * po.y);
+            pn.z = fmaf(aa, pp[rr][2], bb * po.z); pn.w = fmaf(aa, pp[rr][3], bb * po.w);
             if (xb + 0 >= g.Nx) pn.x = 0.f;
             if (xb + 1 >= g.Nx) pn.y = 0.f;
             if (xb + 2 >= g.Nx) pn.z = 0.f;
@@ -439,10 +481,10 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
                                                 : make_float4(0.f, 0.f, 0.f, 0.f), pol);
       }
     }
-    if (tid < 128) {
+    if (tid < 128) {  // the 8 halo half rows, 16 items each
       const int hr0 = tid >> 4;
-      qz_item(hr0 < 4 ? hr0 : hr0 + 32, tid & 15);
-    } else if (tid < 192) {
+      qz_item(hr0 < 4 ? hr0 : hr0 + TZ, tid & 15);
+    } else if (tid < 128 + 2 * TZ) {  // the two halo column groups of every row
       const int k = tid - 128;
       qx_item(k >> 1, (k & 1) ? QXW / 4 - 1 : 0, false);
     }
@@ -470,7 +512,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
       f4a(a1, hzv[1]);
     }
     const int i0 = box.x, j0 = box.y, nb = p.src_n;
-    const bool srcbox = i0 >= 0 && i0 < z0 + TILE_Z && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0;
+    const bool srcbox = i0 >= 0 && i0 < z0 + TZ && i0 + nb > z0 && j0 < x0 + TILE_X && j0 + nb > x0;
     float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
     if (pmlx && layer_c(xb, xb + 3, g.npml, g.nx)) ax4 = ldg4(p.ax + xb + TAB_OFF);
     const bool zx_on = ax4.x != 0.f || ax4.y != 0.f || ax4.z != 0.f || ax4.w != 0.f;
@@ -514,7 +556,7 @@ __global__ void __launch_bounds__(NTHREADS, FWD_CTAS)
         }
       }
       const float4 uc = ucur[rr];
-      const float4 upv = sh.up4[rr * NTHREADS + tid];
+      const float4 upv = sh.up4[rr * NT + tid];
       un[rr][0] = 2.f * uc.x - upv.x + rv[0];
       un[rr][1] = 2.f * uc.y - upv.y + rv[1];
       un[rr][2] = 2.f * uc.z - upv.z + rv[2];
@@ -993,15 +1035,16 @@ unsigned long long g_inited = 0;  // bit per device
 // resident-CTA grids: single-instance forward variants (record, store), adjoint,
 // and the multi-instance forward sweep / recompute and adjoint
 int g_grid_fwd[64][2][4], g_grid_adj[64][2], g_grid_fwd_m[64][2][2], g_grid_adj_m[64][2];
+int g_grid_fwd64[64][2][4];  // the 64-row forward variants
 
 template <typename K>
-cudaError_t setup_kernel(K k, int smem, int* grid) {
+cudaError_t setup_kernel(K k, int smem, int* grid, int threads = NTHREADS) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, nb = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, NTHREADS, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem)) != cudaSuccess) return e;
   *grid = (nb < 1 ? 1 : nb) * nsm;
   return cudaSuccess;
 }
@@ -1011,15 +1054,24 @@ constexpr int ADJ_SMEM_M = (int)(ADJ_SMEM_MAIN + sizeof(AcuStep));
 
 template <int N>
 cudaError_t setup_order(int dev, int o) {
-  const int fs = (int)sizeof(FwdSmem), as = (int)sizeof(AdjSmem);
+  const int fs = (int)sizeof(FwdSmem), as = (int)sizeof(AdjSmem), f64 = (int)sizeof(FwdSmemT<64>);
+  constexpr int T64 = FwdGeo<64>::NT;
   cudaError_t e;
-  if ((e = setup_kernel(acu_fwd_step<N, false, false, false>, fs, &g_grid_fwd[dev][o][0])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<N, true, false, false>, fs, &g_grid_fwd[dev][o][1])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<N, false, true, false>, fs, &g_grid_fwd[dev][o][2])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<N, true, true, false>, fs, &g_grid_fwd[dev][o][3])) != cudaSuccess) return e;
-  if ((e = setup_kernel(acu_fwd_step<N, true, true, true>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][0])) != cudaSuccess)
+  if ((e = setup_kernel(acu_fwd_step<N, false, false, false, 32>, fs, &g_grid_fwd[dev][o][0])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, false, false, 32>, fs, &g_grid_fwd[dev][o][1])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, true, false, 32>, fs, &g_grid_fwd[dev][o][2])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, true, false, 32>, fs, &g_grid_fwd[dev][o][3])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, false, false, 64>, f64, &g_grid_fwd64[dev][o][0], T64)) != cudaSuccess)
     return e;
-  if ((e = setup_kernel(acu_fwd_step<N, false, true, true>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][1])) != cudaSuccess)
+  if ((e = setup_kernel(acu_fwd_step<N, true, false, false, 64>, f64, &g_grid_fwd64[dev][o][1], T64)) != cudaSuccess)
+    return e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, true, false, 64>, f64, &g_grid_fwd64[dev][o][2], T64)) != cudaSuccess)
+    return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, true, false, 64>, f64, &g_grid_fwd64[dev][o][3], T64)) != cudaSuccess)
+    return e;
+  if ((e = setup_kernel(acu_fwd_step<N, true, true, true, 32>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][0])) != cudaSuccess)
+    return e;
+  if ((e = setup_kernel(acu_fwd_step<N, false, true, true, 32>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][1])) != cudaSuccess)
     return e;
   if ((e = setup_kernel(acu_adj_step<N, false>, as, &g_grid_adj[dev][o])) != cudaSuccess) return e;
   return setup_kernel(acu_adj_step<N, true>, ADJ_SMEM_M, &g_grid_adj_m[dev][o]);
@@ -1074,21 +1126,51 @@ cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, co
   const cuuint32_t b2[2] = {(cuuint32_t)MW, (cuuint32_t)MH};
   if (!tma_host::encode(&maps->u, u_pair, 3, d3, s3, b3)) return cudaErrorInvalidValue;
   if (!tma_host::encode(&maps->m, const_cast<float*>(mh), 2, d2, s2, b2)) return cudaErrorInvalidValue;
+  // the 64-row forward tiles (the layout's rows are padded to 64, so these boxes fit)
+  const cuuint32_t b3t[3] = {(cuuint32_t)UW, (cuuint32_t)FwdGeo<64>::UHT, 1};
+  const cuuint32_t b2t[2] = {(cuuint32_t)MW, (cuuint32_t)FwdGeo<64>::MHT};
+  if (!tma_host::encode(&maps->u64, u_pair, 3, d3, s3, b3t)) return cudaErrorInvalidValue;
+  if (!tma_host::encode(&maps->m64, const_cast<float*>(mh), 2, d2, s2, b2t)) return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
-cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st) {
+// Forward step on tiles of tz rows (32 or 64; 64 needs the 64-row boxes of
+// acu_make_maps and is for single-instance launches).
+cudaError_t launch_acu_fwd_tz(const AcuStep& p_in, const AcuMaps& maps, bool record, bool store, int tz,
+                              cudaStream_t st) {
   int dev;
   cudaError_t e = ensure_init(&dev);
   if (e != cudaSuccess) return e;
   const int v = (record ? 1 : 0) + (store ? 2 : 0);
-  const int o = p.N == 2 ? 0 : 1;
-  const int grid = std::min(p.ntiles, g_grid_fwd[dev][o][v]);
-  const size_t smem = sizeof(FwdSmem);
-  const AcuCoef cf = coef_of(p);
+  const int o = p_in.N == 2 ? 0 : 1;
+  const AcuCoef cf = coef_of(p_in);
   BatchArgs nb;
   memset(&nb, 0, sizeof nb);
-#define FWD_LAUNCH(NN, R, S) acu_fwd_step<NN, R, S, false><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p, cf, nb)
+  if (tz == 64) {
+    AcuStep p = p_in;
+    p.ntiles = p.S * p.g.ntx * ((p.g.Nz + 63) / 64);
+    const int grid = std::min(p.ntiles, g_grid_fwd64[dev][o][v]);
+    const size_t smem = sizeof(FwdSmemT<64>);
+    constexpr int T = FwdGeo<64>::NT;
+#define FWD_LAUNCH(NN, R, S) acu_fwd_step<NN, R, S, false, 64><<<grid, T, smem, st>>>(maps.u64, maps.m64, p, cf, nb)
+    if (p.N == 2) {
+      if (record && store) FWD_LAUNCH(2, true, true);
+      else if (record) FWD_LAUNCH(2, true, false);
+      else if (store) FWD_LAUNCH(2, false, true);
+      else FWD_LAUNCH(2, false, false);
+    } else {
+      if (record && store) FWD_LAUNCH(4, true, true);
+      else if (record) FWD_LAUNCH(4, true, false);
+      else if (store) FWD_LAUNCH(4, false, true);
+      else FWD_LAUNCH(4, false, false);
+    }
+#undef FWD_LAUNCH
+    return cudaGetLastError();
+  }
+  const AcuStep& p = p_in;
+  const int grid = std::min(p.ntiles, g_grid_fwd[dev][o][v]);
+  const size_t smem = sizeof(FwdSmem);
+#define FWD_LAUNCH(NN, R, S) acu_fwd_step<NN, R, S, false, 32><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p, cf, nb)
   if (p.N == 2) {
     if (record && store) FWD_LAUNCH(2, true, true);
     else if (record) FWD_LAUNCH(2, true, false);
@@ -1102,6 +1184,10 @@ cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, b
   }
 #undef FWD_LAUNCH
   return cudaGetLastError();
+}
+
+cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st) {
+  return launch_acu_fwd_tz(p, maps, record, store, TILE_Z, st);
 }
 
 // Multi-instance forward step b.n over the tiles of instances [0, b.n_active):
@@ -1118,7 +1204,7 @@ cudaError_t launch_acu_fwd_batch(const BatchArgs& b, const AcuCoef& cf, int N, b
   memset(&none, 0, sizeof none);
   AcuStep p0;
   memset(&p0, 0, sizeof p0);
-#define FWD_LAUNCH(NN, R) acu_fwd_step<NN, R, true, true><<<grid, NTHREADS, FWD_SMEM_M, st>>>(none, none, p0, cf, b)
+#define FWD_LAUNCH(NN, R) acu_fwd_step<NN, R, true, true, 32><<<grid, NTHREADS, FWD_SMEM_M, st>>>(none, none, p0, cf, b)
   if (N == 2) {
     if (record) FWD_LAUNCH(2, true);
     else FWD_LAUNCH(2, false);

@@ -22,6 +22,7 @@
 
 namespace fwi {
 cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
+cudaError_t launch_acu_fwd_tz(const AcuStep& p, const AcuMaps& maps, bool record, bool store, int tz, cudaStream_t st);
 cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st);
 cudaError_t launch_acu_fwd_batch(const BatchArgs& b, const AcuCoef& cf, int N, bool record, cudaStream_t st);
 cudaError_t launch_acu_adj_batch(const BatchArgs& b, const AcuCoef& cf, int N, cudaStream_t st);
@@ -259,7 +260,7 @@ void make_plan(Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_rec
   g.ntx = (g.Nx + TILE_X - 1) / TILE_X;
   g.ntz = (g.Nz + TILE_Z - 1) / TILE_Z;
   g.pitch = g.ntx * TILE_X + 2 * APRON;
-  g.rows = g.ntz * TILE_Z + 2 * APRON;
+  g.rows = (g.Nz + ROW_ALIGN - 1) / ROW_ALIGN * ROW_ALIGN + 2 * APRON;
   g.slice = (long long)g.rows * g.pitch;
   g.off0 = (long long)APRON * g.pitch + APRON;
   P.S = Sv->nshots;
@@ -271,7 +272,7 @@ void make_plan(Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_rec
   P.grad = grad;
   P.K = grad ? K : 0;
   P.nseg = grad ? (nt + K - 1) / K : 0;
-  P.tablen = std::max(g.ntx * TILE_X, g.ntz * TILE_Z) + 2 * APRON + 2 * TAB_OFF;
+  P.tablen = std::max(g.ntx * TILE_X, g.rows - 2 * APRON) + 2 * APRON + 2 * TAB_OFF;
 }
 
 std::string plan_key(const Plan& P) {
@@ -449,6 +450,9 @@ fwi_status join(fwi_ctx* ctx, const Groups& gr, cudaStream_t main) {
   }
   return FWI_OK;
 }
+
+// Tile height of the context's acoustic forward steps.
+int fwd_tz(const fwi_ctx* ctx) { return ctx->fwd_tile_rows == 64 ? 64 : TILE_Z; }
 
 // The step parameters of one group: shots [s0, s0 + Sg). Per-shot arrays are
 // offset to the group's first shot; the u and lambda pairs keep their base and
@@ -637,6 +641,15 @@ fwi_status fwi_set_shot_groups(fwi_ctx* ctx, int32_t forward_groups, int32_t adj
     return fail(FWI_EINVAL, "shot groups must be in [0, " + std::to_string(MAX_GROUPS) + "] (0: default)");
   ctx->fwd_groups = forward_groups;
   ctx->adj_groups = adjoint_groups;
+  return FWI_OK;
+}
+
+fwi_status fwi_set_tile_shape(fwi_ctx* ctx, int32_t forward_tile_rows) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (forward_tile_rows != 0 && forward_tile_rows != 32 && forward_tile_rows != 64)
+    return fail(FWI_EINVAL, "forward_tile_rows must be 0, 32 or 64");
+  ctx->fwd_tile_rows = forward_tile_rows;
+  g_err.clear();
   return FWI_OK;
 }
 
@@ -864,7 +877,7 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   for (int n = 0; n < nt; n++) {
     set_fwd_state(P, p, n);
     for (int g = 0; g < gr.G; g++) {
-      LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, gr.st[g]));
+      LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, fwd_tz(ctx), gr.st[g]));
       if (P.L > 0)
         LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                  P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * fieldf + gr.s0[g] * P.g.slice,
@@ -960,7 +973,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       p.slot_pz = p.slot_px + field;
     }
     for (int g = 0; g < gr.G; g++) {
-      LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, keep, gr.st[g]));
+      LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, keep, fwd_tz(ctx), gr.st[g]));
       if (P.L > 0)
         LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                  P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
@@ -999,7 +1012,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
         p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
         p.slot_pz = p.slot_px + field;
         for (int g = 0; g < gr.G; g++) {
-          LK(1, launch_acu_fwd(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, gr.st[g]));
+          LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, fwd_tz(ctx), gr.st[g]));
           if (P.L > 0)
             LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                      P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,

@@ -28,6 +28,7 @@ struct fwi_ctx {
   // graph (fwi_misfit_grad_graph) is valid only for the epoch it was captured in
   unsigned long long arena_epoch = 0;
   int fwd_groups = 0, adj_groups = 0;  // shot groups of the acoustic step launches (0: the library's default)
+  int fwd_tile_rows = 0;               // tile height of the acoustic forward steps: 32 or 64 (0: 32)
   cudaStream_t cap_stream = nullptr;  // stream the graphs are captured on
   // set for the duration of an fwi_forward_vjp call: the "observed" buffer holds
   // the cotangent, which seeds the adjoint sweep as it stands

@@ -22,6 +22,10 @@ constexpr int NTHREADS = 256;
 constexpr int TAB_OFF = 8;   // 1D CPML tables are indexed [h + TAB_OFF]
 constexpr int SRC_W = 7;     // Gaussian source support (7 x 7)
 constexpr int SRC_SLOTS = 4; // a 7 x 7 box touches at most 2 x 2 tiles
+// Rows of the acoustic field layout are padded to a multiple of the tallest
+// tile of its step kernels (the forward step also runs on 64 x 64 tiles), so
+// that every tile of either height, with its halo, lies inside the allocation.
+constexpr int ROW_ALIGN = 64;
 
 // status bits written by device kernels
 enum : int { ST_CFL = 1, ST_BADREC = 2, ST_BADSRC = 4, ST_NONFINITE = 8, ST_BADMODEL = 16, ST_TIMEOUT = 32 };
@@ -84,6 +88,7 @@ struct EleMaps {
 struct AcuMaps {
   CUtensorMap u;
   CUtensorMap m;
+  CUtensorMap u64, m64;  // the same fields with the boxes of 64-row forward tiles
   CUtensorMap lx, lz;   // adjoint: lambda pair, x-operand and z-operand boxes
   CUtensorMap hx, hz;   // adjoint: hhat pairs (CPML tiles)
 };

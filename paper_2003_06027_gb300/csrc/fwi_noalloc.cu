@@ -153,11 +153,11 @@ extern "C" fwi_status fwi_forward_noalloc(const fwi_model* M, const fwi_sources*
   g.ntx = (g.Nx + TILE_X - 1) / TILE_X;
   g.ntz = (g.Nz + TILE_Z - 1) / TILE_Z;
   g.pitch = g.ntx * TILE_X + 2 * APRON;
-  g.rows = g.ntz * TILE_Z + 2 * APRON;
+  g.rows = (g.Nz + ROW_ALIGN - 1) / ROW_ALIGN * ROW_ALIGN + 2 * APRON;
   g.slice = (long long)g.rows * g.pitch;
   g.off0 = (long long)APRON * g.pitch + APRON;
   const int S = Sv->nshots, nrec = R->nrec, ntiles = g.ntx * g.ntz;
-  const int tablen = std::max(g.ntx * TILE_X, g.ntz * TILE_Z) + 2 * APRON + 2 * TAB_OFF;
+  const int tablen = std::max(g.ntx * TILE_X, g.rows - 2 * APRON) + 2 * APRON + 2 * TAB_OFF;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     off = (off + 255) & ~size_t(255);

@@ -56,7 +56,7 @@ EXPORTS = ["fwi_create", "fwi_destroy", "fwi_forward", "fwi_misfit_grad", "fwi_l
            "fwi_forward_noalloc", "fwi_elastic_velocity_grad", "fwi_selftest_wait_timeout",
            "fwi_misfit_grad_graph", "fwi_graph_launch", "fwi_graph_status", "fwi_graph_destroy",
            "fwi_set_shot_groups", "fwi_workspace_bytes", "fwi_choose_ckpt", "fwi_forward_vjp", "fwi_batch_create",
-           "fwi_batch_launch", "fwi_batch_status", "fwi_batch_destroy", "fwi_last_error"]
+           "fwi_batch_launch", "fwi_batch_status", "fwi_batch_destroy", "fwi_set_tile_shape", "fwi_last_error"]
 
 
 def library_path() -> str:
@@ -84,6 +84,7 @@ def library(build_if_missing: bool = True):
             L.fwi_batch_create.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_float, P,
                                            ctypes.c_int32, P, P, ctypes.POINTER(P)]
             L.fwi_batch_launch.argtypes = [P, P]
+            L.fwi_set_tile_shape.argtypes = [P, ctypes.c_int32]
             L.fwi_batch_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int32)]
             L.fwi_batch_launches.argtypes = [P]
             L.fwi_batch_launches.restype = ctypes.c_int64
@@ -156,6 +157,12 @@ def set_shot_groups(forward_groups: int = 0, adjoint_groups: int = 0, device: in
     the forward/recompute steps and of the adjoint steps (0: the library's
     default; fwi_set_shot_groups)."""
     _check(library().fwi_set_shot_groups(context(device), int(forward_groups), int(adjoint_groups)))
+
+
+def set_tile_shape(forward_tile_rows: int = 0, device: int = 0):
+    """Tile height (32 or 64 rows; 0: the default) of the acoustic forward steps
+    of this thread's context (fwi_set_tile_shape)."""
+    _check(library().fwi_set_tile_shape(context(device), int(forward_tile_rows)))
 
 
 def last_timing(device: int = 0) -> Timing:
@@ -324,7 +331,7 @@ class GradGraph:
     def __init__(self, c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
                  pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, ckpt_every=100,
                  want_src=False,
-                 groups=(0, 0)):
+                 groups=(0, 0), tile_rows=0):
         for t in (c, stf, x0, rec_iz, rec_ix, observed):
             if not (_is_torch(t) and t.is_cuda):
                 raise ValueError("GradGraph takes CUDA tensors only")
@@ -342,6 +349,8 @@ class GradGraph:
         _check(L.fwi_create(ctypes.byref(self.ctx), int(self.device)))
         self.groups = tuple(groups)
         st = L.fwi_set_shot_groups(self.ctx, int(groups[0]), int(groups[1]))
+        if st == 0:
+            st = L.fwi_set_tile_shape(self.ctx, int(tile_rows))
         if st != 0:
             L.fwi_destroy(self.ctx)
             self.ctx = None

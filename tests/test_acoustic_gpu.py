@@ -415,3 +415,48 @@ def test_laplacian_operator_graph_replay_and_noalloc(fwi_lib):
     with pytest.raises(fwi.FwiError) as e:
         fwi.forward_noalloc(*args, **kw)
     assert e.value.status == 7
+
+
+# ------------------------------------------------ forward tile shapes (32 / 64 rows)
+@pytest.mark.parametrize("shape", [(37, 71, 4, 1), (98, 45, 8, 0), (150, 130, 8, 1)])
+def test_forward_tile_shapes_agree_bit_for_bit(fwi_lib, shape):
+    """The 64 x 64 forward tiles (512 threads) against the 64 x 32 default:
+    seismograms, misfit and gradients must be identical (each cell's arithmetic
+    is the same), on grids whose padded height is not a multiple of either tile
+    (the last tile row ragged), with receivers in the bottom rows; and the same
+    as the oracle."""
+    import torch
+
+    from paper_2003_06027_gb300 import fwi
+
+    nz, nx, order, kind = shape
+    d = synth.random_acoustic(300 + nz, nz, nx, 140, 2, order, 9, src_kind=kind, nrec=9)
+    d["rec_iz"][:3] = [nz - 1, nz - 2, 0]
+    d["x0"][1, 1] = (nz - 4) * d["dz"]  # a source near the bottom edge
+    rng = np.random.default_rng(nz)
+    obs = (rng.standard_normal((2, 9, 140)) * 1e-7).astype(np.float32)
+    out = {}
+    for rows in (32, 64):
+        fwi.set_tile_shape(rows)
+        try:
+            seis = gpu_forward(d)
+            out[rows] = (seis,) + gpu_misfit_grad(d, obs, K=50)
+        finally:
+            fwi.set_tile_shape(0)
+    a, b = out[32], out[64]
+    assert np.array_equal(a[0], b[0])
+    assert a[1] == b[1]
+    for x, y in zip(a[2:], b[2:]):
+        assert np.array_equal(x, y)
+    do = oracle.acoustic_forward(_geom(d), np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(b[0], do) <= SEIS_TOL
+    Jo, go, _, _ = oracle_misfit_grad(d, obs)
+    assert abs(b[1] - Jo) <= SEIS_TOL * Jo and rel(b[2], go) <= GRAD_TOL
+
+
+def test_tile_shape_refusal(fwi_lib):
+    from paper_2003_06027_gb300 import fwi
+
+    with pytest.raises(fwi.FwiError) as e:
+        fwi.set_tile_shape(48)
+    assert e.value.status == 1

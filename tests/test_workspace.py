@@ -12,15 +12,15 @@ import pytest
 from paper_2003_06027_gb300 import fwi, synth
 
 
-def _field_bytes(d, S):
+def _field_bytes(d, S, row_align):
     Nz, Nx = d["nz"] + 2 * d["npml"], d["nx"] + 2 * d["npml"]
-    rows = math.ceil(Nz / 32) * 32 + 16
+    rows = math.ceil(Nz / row_align) * row_align + 16
     pitch = math.ceil(Nx / 64) * 64 + 16
     return S * rows * pitch * 4
 
 
 def _acoustic(nt=60, S=3):
-    d = synth.random_acoustic(5, 40, 90, nt, S, 8, 12, nrec=7)
+    d = synth.random_acoustic(5, 45, 90, nt, S, 8, 12, nrec=7)  # 69 padded rows: 128 with the 64-row padding
     args = [d["c"], d["stf"], d["x0"], d["rec_iz"], d["rec_ix"]]
     return d, args, fwi.problem_kwargs(d)
 
@@ -41,12 +41,12 @@ def test_workspace_grows_by_the_documented_fields(physics):
     shots on the tile-aligned slice (to the 256-byte alignment of the layout)."""
     if physics == "acoustic":
         d, args, kw = _acoustic()
-        ws, per_step, per_ckpt, S = fwi.workspace_bytes, 2, 6, d["stf"].shape[0]
+        ws, per_step, per_ckpt, S, align = fwi.workspace_bytes, 2, 6, d["stf"].shape[0], 64
     else:
         d, args, kw = _elastic()
-        ws, per_step, per_ckpt, S = fwi.workspace_bytes_elastic, 5, 13, d["stf"].shape[0]
+        ws, per_step, per_ckpt, S, align = fwi.workspace_bytes_elastic, 5, 13, d["stf"].shape[0], 32
     nt = d["stf"].shape[1]
-    F = _field_bytes(d, S)
+    F = _field_bytes(d, S, align)
     W = {K: ws(*args, ckpt_every=K, **kw) for K in range(1, nt + 1)}
     for K in range(1, nt):
         dseg = math.ceil(nt / (K + 1)) - math.ceil(nt / K)
