@@ -281,8 +281,8 @@ def store_all_measure(d, args_dev, obs, kw, value_k, steps=3):
 
 
 def laplacian_op_measure(peak, steps=2):
-    """The c^2 Laplacian operator variant (FWI_OP_LAPLACIAN, plain per-point
-    kernels) on the headline workload: gradient and forward throughput, with
+    """The c^2 Laplacian operator variant (FWI_OP_LAPLACIAN, the persistent
+    TMA step kernels' Laplacian instantiation) on the headline workload: gradient and forward throughput, with
     whole-path fractions by the same per-cell-step byte model as the
     divergence form (48 and 16 B)."""
     import torch
@@ -314,7 +314,7 @@ def laplacian_op_measure(peak, steps=2):
         v = cs / (ms / 1e3) / 1e9
         res[name] = {"value": v, "unit": UNIT, "ms_per_step": ms, "bytes_per_cell_step": b,
                      "path_frac": b * v / peak}
-    return {"workload": d["name"] + "-c2laplacian-ckpt100", "kernels": "plain per-point (acoustic_lap.cu)", **res}
+    return {"workload": d["name"] + "-c2laplacian-ckpt100", "kernels": "acu_fwd_step / acu_adj_step, Laplacian variant", **res}
 
 
 def batched_measure(n_inst=16):

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfwi.so")
 SOURCES = ["acoustic_kernels.cu", "elastic_kernels.cu", "prep_kernels.cu", "fwi_capi.cu", "fwi_elastic.cu",
-           "fwi_noalloc.cu", "cnn.cu", "tc_gemm.cu", "acoustic_lap.cu"]
+           "fwi_noalloc.cu", "cnn.cu", "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

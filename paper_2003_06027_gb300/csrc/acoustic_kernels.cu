@@ -277,11 +277,17 @@ __device__ __forceinline__ void batch_load_step(const BatchArgs& b, int i, AcuSt
 // TZ: the tile height, 32 (256 threads) or 64 (512 threads, a compile-time
 // variant for the autotuner: half the z-halo recompute per cell, the same
 // per-thread work); multi-instance launches use 32.
-template <int N, bool RECORD, bool STORE, bool MULTI, int TZ>
+// LAP: the c^2 Laplacian operator instead of the divergence form: the fluxes
+// carry no coefficient (q = D+u + psi), the update is
+// u^{n+1} = 2u^n - u^{n-1} + m dt^2 (D-q + zeta) + dt^2 w g(t_n) with m = c^2 at
+// the cell, and STORE keeps r = dt^2 (D-q + zeta) at the cells (the operand of
+// its gradient correlation dJ/dm = sum_n lambda_{n+1} r^n) instead of the fluxes.
+template <int N, bool RECORD, bool STORE, bool MULTI, int TZ, bool LAP = false>
 __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
     acu_fwd_step(const __grid_constant__ CUtensorMap tmap_u, const __grid_constant__ CUtensorMap tmap_m,
                  const __grid_constant__ AcuStep p0, const AcuCoef cf, const BatchArgs b) {
   static_assert(TZ == TILE_Z || (TZ == 2 * TILE_Z && !MULTI), "tile heights: 32, or 64 for single-instance launches");
+  static_assert(!LAP || (TZ == TILE_Z && !MULTI), "the Laplacian operator runs on 32-row single-instance launches");
   constexpr int NT = FwdGeo<TZ>::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FwdSmemT<TZ>& sh = *reinterpret_cast<FwdSmemT<TZ>*>(smem_raw);
@@ -395,10 +401,11 @@ __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
       }
       const bool rowok = z < g.Nz;
 #pragma unroll
-      for (int e = 0; e < 4; e++) q[e] = (rowok && hb + e >= 0 && hb + e < g.Nx - 1) ? (mv[e] + mv[e + 1]) * pp[e] : 0.f;
+      for (int e = 0; e < 4; e++)
+        q[e] = (rowok && hb + e >= 0 && hb + e < g.Nx - 1) ? (LAP ? pp[e] : (mv[e] + mv[e + 1]) * pp[e]) : 0.f;
       st4(sh.qx + r * QXW + 4 * gq, make_float4(q[0], q[1], q[2], q[3]));
       // every own row is written (zero beyond the grid): the adjoint multiplies these by zero there
-      if (STORE && own && (!MULTI || p.slot_px))
+      if (STORE && !LAP && own && (!MULTI || p.slot_px))
         st4_stream(p.slot_px + id0, rowok ? make_float4(pp[0], pp[1], pp[2], pp[3]) : make_float4(0.f, 0.f, 0.f, 0.f), pol);
     };
     // ---- stage 1b: z fluxes at one half row (the tile's halo rows)
@@ -424,10 +431,10 @@ __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
       }
       const float4 ma = ld4(sm + hr * MW + 4 * c + 4), mb = ld4(sm + (hr + 1) * MW + 4 * c + 4);
       const bool hv = hz >= 0 && hz < g.Nz - 1;
-      const float q0 = (hv && xc + 0 < g.Nx) ? (ma.x + mb.x) * pp[0] : 0.f;
-      const float q1 = (hv && xc + 1 < g.Nx) ? (ma.y + mb.y) * pp[1] : 0.f;
-      const float q2 = (hv && xc + 2 < g.Nx) ? (ma.z + mb.z) * pp[2] : 0.f;
-      const float q3 = (hv && xc + 3 < g.Nx) ? (ma.w + mb.w) * pp[3] : 0.f;
+      const float q0 = (hv && xc + 0 < g.Nx) ? (LAP ? pp[0] : (ma.x + mb.x) * pp[0]) : 0.f;
+      const float q1 = (hv && xc + 1 < g.Nx) ? (LAP ? pp[1] : (ma.y + mb.y) * pp[1]) : 0.f;
+      const float q2 = (hv && xc + 2 < g.Nx) ? (LAP ? pp[2] : (ma.z + mb.z) * pp[2]) : 0.f;
+      const float q3 = (hv && xc + 3 < g.Nx) ? (LAP ? pp[3] : (ma.w + mb.w) * pp[3]) : 0.f;
       st4(sh.qz + hr * TILE_X + 4 * c, make_float4(q0, q1, q2, q3));
     };
 
@@ -471,12 +478,12 @@ __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
         const float4 mb = ld4(sm + (2 * ty + 5 + rr) * MW + 4 * tx + 4);
         const bool hv = hz < g.Nz - 1;
         float q[4];
-        q[0] = (hv && xb + 0 < g.Nx) ? (ma.x + mb.x) * pp[rr][0] : 0.f;
-        q[1] = (hv && xb + 1 < g.Nx) ? (ma.y + mb.y) * pp[rr][1] : 0.f;
-        q[2] = (hv && xb + 2 < g.Nx) ? (ma.z + mb.z) * pp[rr][2] : 0.f;
-        q[3] = (hv && xb + 3 < g.Nx) ? (ma.w + mb.w) * pp[rr][3] : 0.f;
+        q[0] = (hv && xb + 0 < g.Nx) ? (LAP ? pp[rr][0] : (ma.x + mb.x) * pp[rr][0]) : 0.f;
+        q[1] = (hv && xb + 1 < g.Nx) ? (LAP ? pp[rr][1] : (ma.y + mb.y) * pp[rr][1]) : 0.f;
+        q[2] = (hv && xb + 2 < g.Nx) ? (LAP ? pp[rr][2] : (ma.z + mb.z) * pp[rr][2]) : 0.f;
+        q[3] = (hv && xb + 3 < g.Nx) ? (LAP ? pp[rr][3] : (ma.w + mb.w) * pp[rr][3]) : 0.f;
         st4(sh.qz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(q[0], q[1], q[2], q[3]));
-        if (STORE && (!MULTI || p.slot_pz))
+        if (STORE && !LAP && (!MULTI || p.slot_pz))
           st4_stream(p.slot_pz + idz, hz < g.Nz ? make_float4(pp[rr][0], pp[rr][1], pp[rr][2], pp[rr][3])
                                                 : make_float4(0.f, 0.f, 0.f, 0.f), pol);
       }
@@ -488,10 +495,15 @@ __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
       const int k = tid - 128;
       qx_item(k >> 1, (k & 1) ? QXW / 4 - 1 : 0, false);
     }
-    // u^n at the own cells, read before the operand buffer is refilled
-    float4 ucur[2];
+    // u^n at the own cells (and, for the Laplacian operator, m/2 there), read
+    // before the operand buffer is refilled
+    float4 ucur[2], mown[2];
     ucur[0] = ld4(su + (2 * ty + H) * UW + 4 * tx + H);
     ucur[1] = ld4(su + (2 * ty + 1 + H) * UW + 4 * tx + H);
+    if (LAP) {
+      mown[0] = ld4(sm + (2 * ty + 4) * MW + 4 * tx + 4);
+      mown[1] = ld4(sm + (2 * ty + 5) * MW + 4 * tx + 4);
+    }
     __syncthreads();
     if (tid == 0 && tn < ntiles) fetch_next(tn);
 
@@ -557,6 +569,19 @@ __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
       }
       const float4 uc = ucur[rr];
       const float4 upv = sh.up4[rr * NT + tid];
+      if (LAP) {
+        // r^n (dt^2-scaled) is the gradient operand; the update takes m r, m = 2 (m/2)
+        if (STORE) {
+          float r4[4];
+#pragma unroll
+          for (int e = 0; e < 4; e++) r4[e] = (z < g.Nz && xb + e < g.Nx) ? rv[e] : 0.f;  // zero off the grid
+          st4_stream(p.slot_px + idc0, make_float4(r4[0], r4[1], r4[2], r4[3]), pol);
+        }
+        rv[0] *= 2.f * mown[rr].x;
+        rv[1] *= 2.f * mown[rr].y;
+        rv[2] *= 2.f * mown[rr].z;
+        rv[3] *= 2.f * mown[rr].w;
+      }
       un[rr][0] = 2.f * uc.x - upv.x + rv[0];
       un[rr][1] = 2.f * uc.y - upv.y + rv[1];
       un[rr][2] = 2.f * uc.z - upv.z + rv[2];
@@ -604,12 +629,18 @@ __global__ void __launch_bounds__(FwdGeo<TZ>::NT, TZ == TILE_Z ? FWD_CTAS : 2)
 // tile fetches its x (z) stencil operand from Hx (Hz) instead of lambda. Z is
 // then read and written only by the thread that owns the cell.
 // MULTI: one launch over the tiles of several instances, as for the forward step.
-template <int N, bool MULTI>
+// LAP: the adjoint of the c^2 Laplacian step: rbar = dt^2 m lambda_{n+1}, so
+// m lambda takes lambda's place in Z and hhat (written by every tile, and every
+// tile fetches its operands from Hx and Hz), pbar = qbar (no half-point
+// coefficient), and the gradient correlation is 2 dJ/dm += 2 lambda_{n+1} r^n at
+// the cells, with r^n (dt^2-scaled) stored by the forward step.
+template <int N, bool MULTI, bool LAP = false>
 __global__ void __launch_bounds__(NTHREADS, 3)
     acu_adj_step(const __grid_constant__ CUtensorMap tmap_lx, const __grid_constant__ CUtensorMap tmap_lz,
                  const __grid_constant__ CUtensorMap tmap_hx, const __grid_constant__ CUtensorMap tmap_hz,
                  const __grid_constant__ CUtensorMap tmap_m, const __grid_constant__ AcuStep p0, const AcuCoef cf,
                  const BatchArgs b) {
+  static_assert(!LAP || !MULTI, "the Laplacian operator runs on single-instance launches");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   AdjSmem& sh = *reinterpret_cast<AdjSmem*>(smem_raw);
   AcuStep& shp = *reinterpret_cast<AcuStep*>(smem_raw + ADJ_SMEM_MAIN);  // MULTI only
@@ -637,8 +668,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     }
     const TileId f = tile_decode(gf, tl);
     const int plane = plane0 + f.s;
-    const CUtensorMap* xm = tile_pml_x(gf, f.x0) ? mhx : mlx;
-    const CUtensorMap* zm = tile_pml_z(gf, f.z0) ? mhz : mlz;
+    const CUtensorMap* xm = (LAP || tile_pml_x(gf, f.x0)) ? mhx : mlx;
+    const CUtensorMap* zm = (LAP || tile_pml_z(gf, f.z0)) ? mhz : mlz;
     if (MULTI) {
       tensormap_acquire(xm);
       tensormap_acquire(zm);
@@ -679,10 +710,15 @@ __global__ void __launch_bounds__(NTHREADS, 3)
     const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
     // stored fluxes p^n of this thread's own half points (x and z), fetched before the wait
     float4 pfx[2], pfz[2];
+    // (LAP: pfx holds r^n of the own cells and pfz is not used)
     pfx[0] = ld4_stream(p.slot_px + base + (long long)zr0 * pitch + xb, pol);
     pfx[1] = ld4_stream(p.slot_px + base + (long long)(zr0 + 1) * pitch + xb, pol);
-    pfz[0] = ld4_stream(p.slot_pz + base + (long long)zr0 * pitch + xb, pol);
-    pfz[1] = ld4_stream(p.slot_pz + base + (long long)(zr0 + 1) * pitch + xb, pol);
+    if (!LAP) {
+      pfz[0] = ld4_stream(p.slot_pz + base + (long long)zr0 * pitch + xb, pol);
+      pfz[1] = ld4_stream(p.slot_pz + base + (long long)(zr0 + 1) * pitch + xb, pol);
+    } else {
+      pfz[0] = pfz[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     const bool ok = mbar_wait(&sh.bar, it & 1);
     if (__syncthreads_or(!ok)) {
@@ -710,8 +746,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         const float4 m4 = ld4(sm + (r + 4) * MW + 4 * gq);
         const float mv[5] = {m4.x, m4.y, m4.z, m4.w, sm[(r + 4) * MW + 4 * gq + 4]};
         float pf[4] = {0.f, 0.f, 0.f, 0.f};
-        if (pre) f4a(*pre, pf);
-        else if (image && (!EDGE || hb >= 0)) f4a(ld4_stream(p.slot_px + id0, pol), pf);  // the apron holds no flux
+        if (!LAP && pre) f4a(*pre, pf);
+        else if (!LAP && image && (!EDGE || hb >= 0)) f4a(ld4_stream(p.slot_px + id0, pol), pf);  // the apron holds no flux
         const bool rowok = !EDGE || z < g.Nz;
         float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f), b4 = a4, P4 = a4;
         if (pmlx && layer_h(hb, hb + 3, g.npml, g.nx)) {  // one round trip: tables and P together
@@ -731,11 +767,11 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           for (int k = 1; k <= N; k++) dq += cf.c1x[k - 1] * (v[e + 4 + k] - v[e + 5 - k]);
           const bool inh = !EDGE || (rowok && hb + e >= 0 && hb + e < g.Nx - 1);
           const float qb = inh ? dq : 0.f;
-          const float pb = (mv[e] + mv[e + 1]) * qb;
+          const float pb = LAP ? qb : (mv[e] + mv[e + 1]) * qb;
           const float tt = Pv[e] + pb;
           gb[e] = inh ? pb + av[e] * tt : 0.f;
           Pn[e] = av[e] != 0.f ? bv[e] * tt : 0.f;  // P stays zero outside the layer
-          im[e] = qb * pf[e];
+          im[e] = LAP ? 0.f : qb * pf[e];
         }
         if (pmlx && own && rowok && (av[0] != 0.f || av[1] != 0.f || av[2] != 0.f || av[3] != 0.f))
           st4(p.px_out + id0, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
@@ -746,7 +782,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         const int hz = z0 - 4 + hr, xc = x0 + 4 * c;
         const long long idz = base + (long long)hz * pitch + xc;
         float pf[4] = {0.f, 0.f, 0.f, 0.f};
-        if (image && (!EDGE || hz >= 0)) f4a(ld4_stream(p.slot_pz + idz, pol), pf);
+        if (!LAP && image && (!EDGE || hz >= 0)) f4a(ld4_stream(p.slot_pz + idz, pol), pf);
         float aa = 0.f;
         float Pv[4] = {0.f, 0.f, 0.f, 0.f};
         if (pmlz && layer_h(hz, hz, g.npml, g.nz)) {
@@ -767,9 +803,9 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         for (int e = 0; e < 4; e++) {
           const bool inh = !EDGE || (hv && xc + e < g.Nx);
           const float qb = inh ? dq[e] : 0.f;
-          const float pb = mhv[e] * qb;
+          const float pb = LAP ? qb : mhv[e] * qb;
           gb[e] = inh ? pb + aa * (Pv[e] + pb) : 0.f;
-          im[e] = qb * pf[e];
+          im[e] = LAP ? 0.f : qb * pf[e];
         }
         st4(sh.gz + hr * TILE_X + 4 * c, make_float4(gb[0], gb[1], gb[2], gb[3]));
         if (image) st4(sh.imz + 4 * c, make_float4(im[0], im[1], im[2], im[3]));
@@ -819,11 +855,11 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           for (int e = 0; e < 4; e++) {
             const bool inh = !EDGE || (hv && xb + e < g.Nx);
             const float qb = inh ? dq[rr][e] : 0.f;
-            const float pb = mhv[e] * qb;
+            const float pb = LAP ? qb : mhv[e] * qb;
             const float tt = Pv[e] + pb;
             gb[e] = inh ? pb + aa[rr] * tt : 0.f;
             Pn[e] = inh ? bb[rr] * tt : 0.f;
-            imz[rr][e] = qb * pf[e];
+            imz[rr][e] = LAP ? 0.f : qb * pf[e];
           }
           if (aa[rr] != 0.f && (!EDGE || hz < g.Nz)) st4(p.pz_out + idz, make_float4(Pn[0], Pn[1], Pn[2], Pn[3]));
           st4(sh.gz + (2 * ty + 4 + rr) * TILE_X + 4 * tx, make_float4(gb[0], gb[1], gb[2], gb[3]));
@@ -843,13 +879,19 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         if (left) sh.imx[k >> 1] = im[3];
       }
       // lambda_{n+1} at the own cells, from a stencil tile that holds lambda itself
-      float4 lc[2];
+      // (the Laplacian operator's tiles hold m lambda: lambda from memory, m = 2 (m/2)
+      // of the own cells from the coefficient tile)
+      float4 lc[2], m2[2];
   #pragma unroll
       for (int rr = 0; rr < 2; rr++) {
         const int r = 2 * ty + rr;
-        if (!pmlx) lc[rr] = ld4(sx + r * UW + H + 4 * tx);
-        else if (!pmlz) lc[rr] = ld4(sz + (r + H) * TILE_X + 4 * tx);
+        if (!LAP && !pmlx) lc[rr] = ld4(sx + r * UW + H + 4 * tx);
+        else if (!LAP && !pmlz) lc[rr] = ld4(sz + (r + H) * TILE_X + 4 * tx);
         else lc[rr] = ldg4(p.lam + (long long)(p.cur * p.S_pair + p.s0) * g.slice + base + (long long)(z0 + r) * pitch + xb);
+        if (LAP) {
+          const float4 mh = ld4(sm + (r + 4) * MW + 4 * tx + 4);
+          m2[rr] = make_float4(2.f * mh.x, 2.f * mh.y, 2.f * mh.z, 2.f * mh.w);
+        }
       }
       __syncthreads();
       if (tid == 0 && tn < ntiles) fetch(tn);  // the operand buffer is free
@@ -880,13 +922,15 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         f4a(a1, dzv[1]);
       }
       // image of the half row above (2ty-1) and of the half column left of the thread (xb-1/2)
-      float imzu[4];
-      f4a(ld4(sh.imz + ty * TILE_X + 4 * tx), imzu);
-      float imxl[2];
+      float imzu[4] = {0.f, 0.f, 0.f, 0.f};
+      float imxl[2] = {0.f, 0.f};
+      if (!LAP) {
+        f4a(ld4(sh.imz + ty * TILE_X + 4 * tx), imzu);
   #pragma unroll
-      for (int rr = 0; rr < 2; rr++) {
-        const float up = __shfl_up_sync(0xffffffffu, imx[rr][3], 1, 16);
-        imxl[rr] = tx == 0 ? sh.imx[2 * ty + rr] : up;
+        for (int rr = 0; rr < 2; rr++) {
+          const float up = __shfl_up_sync(0xffffffffu, imx[rr][3], 1, 16);
+          imxl[rr] = tx == 0 ? sh.imx[2 * ty + rr] : up;
+        }
       }
       float lnew[2][4];
   #pragma unroll
@@ -908,7 +952,11 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           lnew[rr][e] = valid ? 2.f * lcv[e] - lov[e] - (dxv + dzv[rr][e]) : 0.f;
           const float ixl = e == 0 ? imxl[rr] : imx[rr][e - 1];
           const float izu = rr == 0 ? imzu[e] : imz[0][e];
-          gn[e] = valid ? gov[e] + (ixl + imx[rr][e] + izu + imz[rr][e]) : 0.f;
+          float rst[4];
+          f4a(pfx[rr], rst);
+          // divergence form: the four half-point images; Laplacian: 2 lambda_{n+1} r^n at the cell
+          const float inc = LAP ? 2.f * lcv[e] * rst[e] : (ixl + imx[rr][e] + izu + imz[rr][e]);
+          gn[e] = valid ? gov[e] + inc : 0.f;
         }
         st4(gp + (long long)z * pitch + xb, make_float4(gn[0], gn[1], gn[2], gn[3]));
       }
@@ -925,7 +973,7 @@ __global__ void __launch_bounds__(NTHREADS, 3)
               if (r2 == rr && e2 == e) lnew[r2][e2] += rv;
         }
       }
-      const bool wx = tile_writes_hx(g, id.tx), wz = tile_writes_hz(g, id.tz);
+      const bool wx = LAP || tile_writes_hx(g, id.tx), wz = LAP || tile_writes_hz(g, id.tz);
       float4 ax4 = make_float4(0.f, 0.f, 0.f, 0.f), bx4 = ax4;
       if (pmlx && layer_c(xb, xb + 3, g.npml, g.nx)) {
         ax4 = ldg4(p.ax + xb + TAB_OFF);
@@ -938,14 +986,19 @@ __global__ void __launch_bounds__(NTHREADS, 3)
         const long long idc0 = base + (long long)z * pitch + xb;
         const float4 l4 = make_float4(lnew[rr][0], lnew[rr][1], lnew[rr][2], lnew[rr][3]);
         st4(lprev + (long long)z * pitch + xb, l4);
+        // what rbar / dt^2 is made of: lambda (divergence form) or m lambda (Laplacian)
+        const float4 lcm = LAP ? make_float4(m2[rr].x * lc[rr].x, m2[rr].y * lc[rr].y, m2[rr].z * lc[rr].z,
+                                             m2[rr].w * lc[rr].w)
+                               : lc[rr];
+        const float4 l4m = LAP ? make_float4(m2[rr].x * l4.x, m2[rr].y * l4.y, m2[rr].z * l4.z, m2[rr].w * l4.w) : l4;
         // CPML Z (divided by dt^2) <- b (Z + lambda_{n+1}); zero outside the layer and the grid
         float4 Zx = make_float4(0.f, 0.f, 0.f, 0.f), Zz = Zx;
         if (zx_on) {
           const float4 Zo = ld4(p.zx_in + idc0);
-          Zx.x = ax4.x != 0.f && (!EDGE || z < g.Nz) ? bx4.x * (Zo.x + lc[rr].x) : 0.f;
-          Zx.y = ax4.y != 0.f && (!EDGE || z < g.Nz) ? bx4.y * (Zo.y + lc[rr].y) : 0.f;
-          Zx.z = ax4.z != 0.f && (!EDGE || z < g.Nz) ? bx4.z * (Zo.z + lc[rr].z) : 0.f;
-          Zx.w = ax4.w != 0.f && (!EDGE || z < g.Nz) ? bx4.w * (Zo.w + lc[rr].w) : 0.f;
+          Zx.x = ax4.x != 0.f && (!EDGE || z < g.Nz) ? bx4.x * (Zo.x + lcm.x) : 0.f;
+          Zx.y = ax4.y != 0.f && (!EDGE || z < g.Nz) ? bx4.y * (Zo.y + lcm.y) : 0.f;
+          Zx.z = ax4.z != 0.f && (!EDGE || z < g.Nz) ? bx4.z * (Zo.z + lcm.z) : 0.f;
+          Zx.w = ax4.w != 0.f && (!EDGE || z < g.Nz) ? bx4.w * (Zo.w + lcm.w) : 0.f;
           st4(p.zx_out + idc0, Zx);
         }
         float az = 0.f;
@@ -954,20 +1007,20 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           if (az != 0.f) {
             const float bz = __ldg(p.bz + z + TAB_OFF);
             const float4 Zo = ld4(p.zz_in + idc0);
-            Zz.x = (!EDGE || xb + 0 < g.Nx) ? bz * (Zo.x + lc[rr].x) : 0.f;
-            Zz.y = (!EDGE || xb + 1 < g.Nx) ? bz * (Zo.y + lc[rr].y) : 0.f;
-            Zz.z = (!EDGE || xb + 2 < g.Nx) ? bz * (Zo.z + lc[rr].z) : 0.f;
-            Zz.w = (!EDGE || xb + 3 < g.Nx) ? bz * (Zo.w + lc[rr].w) : 0.f;
+            Zz.x = (!EDGE || xb + 0 < g.Nx) ? bz * (Zo.x + lcm.x) : 0.f;
+            Zz.y = (!EDGE || xb + 1 < g.Nx) ? bz * (Zo.y + lcm.y) : 0.f;
+            Zz.z = (!EDGE || xb + 2 < g.Nx) ? bz * (Zo.z + lcm.z) : 0.f;
+            Zz.w = (!EDGE || xb + 3 < g.Nx) ? bz * (Zo.w + lcm.w) : 0.f;
             st4(p.zz_out + idc0, Zz);
           }
         }
-        // hhat of step n-1 (lambda_n with the updated Z); equal to lambda_n outside the layer
+        // hhat of step n-1 (lambda_n, or m lambda_n, with the updated Z); equal to that outside the layer
         if (wx)
-          st4(p.hx_out + idc0, make_float4(l4.x + ax4.x * (Zx.x + l4.x), l4.y + ax4.y * (Zx.y + l4.y),
-                                           l4.z + ax4.z * (Zx.z + l4.z), l4.w + ax4.w * (Zx.w + l4.w)));
+          st4(p.hx_out + idc0, make_float4(l4m.x + ax4.x * (Zx.x + l4m.x), l4m.y + ax4.y * (Zx.y + l4m.y),
+                                           l4m.z + ax4.z * (Zx.z + l4m.z), l4m.w + ax4.w * (Zx.w + l4m.w)));
         if (wz)
-          st4(p.hz_out + idc0, make_float4(l4.x + az * (Zz.x + l4.x), l4.y + az * (Zz.y + l4.y),
-                                           l4.z + az * (Zz.z + l4.z), l4.w + az * (Zz.w + l4.w)));
+          st4(p.hz_out + idc0, make_float4(l4m.x + az * (Zz.x + l4m.x), l4m.y + az * (Zz.y + l4m.y),
+                                           l4m.z + az * (Zz.z + l4m.z), l4m.w + az * (Zz.w + l4m.w)));
       }
       // source-parameter partials from lambda_n (index n-1): sum w lambda,
       // sum w lambda (x_i - x0), sum w lambda (z_i - z0); at most 4 tiles touch a box
@@ -1036,6 +1089,7 @@ unsigned long long g_inited = 0;  // bit per device
 // and the multi-instance forward sweep / recompute and adjoint
 int g_grid_fwd[64][2][4], g_grid_adj[64][2], g_grid_fwd_m[64][2][2], g_grid_adj_m[64][2];
 int g_grid_fwd64[64][2][4];  // the 64-row forward variants
+int g_grid_fwd_lap[64][2][4], g_grid_adj_lap[64][2];  // the c^2 Laplacian operator
 
 template <typename K>
 cudaError_t setup_kernel(K k, int smem, int* grid, int threads = NTHREADS) {
@@ -1074,6 +1128,12 @@ cudaError_t setup_order(int dev, int o) {
   if ((e = setup_kernel(acu_fwd_step<N, false, true, true, 32>, FWD_SMEM_M, &g_grid_fwd_m[dev][o][1])) != cudaSuccess)
     return e;
   if ((e = setup_kernel(acu_adj_step<N, false>, as, &g_grid_adj[dev][o])) != cudaSuccess) return e;
+  if ((e = setup_kernel(acu_adj_step<N, false, true>, as, &g_grid_adj_lap[dev][o])) != cudaSuccess) return e;
+  for (int v = 0; v < 4; v++) {
+    auto k = v == 0 ? acu_fwd_step<N, false, false, false, 32, true> : v == 1 ? acu_fwd_step<N, true, false, false, 32, true>
+           : v == 2 ? acu_fwd_step<N, false, true, false, 32, true> : acu_fwd_step<N, true, true, false, 32, true>;
+    if ((e = setup_kernel(k, fs, &g_grid_fwd_lap[dev][o][v])) != cudaSuccess) return e;
+  }
   return setup_kernel(acu_adj_step<N, true>, ADJ_SMEM_M, &g_grid_adj_m[dev][o]);
 }
 
@@ -1137,7 +1197,7 @@ cudaError_t acu_make_maps(AcuMaps* maps, const Grid& g, int S, float* u_pair, co
 // Forward step on tiles of tz rows (32 or 64; 64 needs the 64-row boxes of
 // acu_make_maps and is for single-instance launches).
 cudaError_t launch_acu_fwd_tz(const AcuStep& p_in, const AcuMaps& maps, bool record, bool store, int tz,
-                              cudaStream_t st) {
+                              cudaStream_t st, bool lap) {
   int dev;
   cudaError_t e = ensure_init(&dev);
   if (e != cudaSuccess) return e;
@@ -1146,6 +1206,26 @@ cudaError_t launch_acu_fwd_tz(const AcuStep& p_in, const AcuMaps& maps, bool rec
   const AcuCoef cf = coef_of(p_in);
   BatchArgs nb;
   memset(&nb, 0, sizeof nb);
+  if (lap) {  // the c^2 Laplacian operator: 32-row tiles
+    const AcuStep& p = p_in;
+    const int grid = std::min(p.ntiles, g_grid_fwd_lap[dev][o][v]);
+    const size_t smem = sizeof(FwdSmem);
+#define FWD_LAUNCH(NN, R, S) \
+  acu_fwd_step<NN, R, S, false, 32, true><<<grid, NTHREADS, smem, st>>>(maps.u, maps.m, p, cf, nb)
+    if (p.N == 2) {
+      if (record && store) FWD_LAUNCH(2, true, true);
+      else if (record) FWD_LAUNCH(2, true, false);
+      else if (store) FWD_LAUNCH(2, false, true);
+      else FWD_LAUNCH(2, false, false);
+    } else {
+      if (record && store) FWD_LAUNCH(4, true, true);
+      else if (record) FWD_LAUNCH(4, true, false);
+      else if (store) FWD_LAUNCH(4, false, true);
+      else FWD_LAUNCH(4, false, false);
+    }
+#undef FWD_LAUNCH
+    return cudaGetLastError();
+  }
   if (tz == 64) {
     AcuStep p = p_in;
     p.ntiles = p.S * p.g.ntx * ((p.g.Nz + 63) / 64);
@@ -1187,7 +1267,7 @@ cudaError_t launch_acu_fwd_tz(const AcuStep& p_in, const AcuMaps& maps, bool rec
 }
 
 cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st) {
-  return launch_acu_fwd_tz(p, maps, record, store, TILE_Z, st);
+  return launch_acu_fwd_tz(p, maps, record, store, TILE_Z, st, false);
 }
 
 // Multi-instance forward step b.n over the tiles of instances [0, b.n_active):
@@ -1231,15 +1311,22 @@ cudaError_t acu_make_adj_maps(AcuMaps* maps, const Grid& g, int S, float* lam_pa
   return ok ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st) {
+cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st, bool lap) {
   int dev;
   cudaError_t e = ensure_init(&dev);
   if (e != cudaSuccess) return e;
-  const int grid = std::min(p.ntiles, g_grid_adj[dev][p.N == 2 ? 0 : 1]);
+  const int grid = std::min(p.ntiles, (lap ? g_grid_adj_lap : g_grid_adj)[dev][p.N == 2 ? 0 : 1]);
   const size_t smem = sizeof(AdjSmem);
   const AcuCoef cf = coef_of(p);
   BatchArgs nb;
   memset(&nb, 0, sizeof nb);
+  if (lap) {
+    if (p.N == 2)
+      acu_adj_step<2, false, true><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p, cf, nb);
+    else
+      acu_adj_step<4, false, true><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p, cf, nb);
+    return cudaGetLastError();
+  }
   if (p.N == 2)
     acu_adj_step<2, false><<<grid, NTHREADS, smem, st>>>(maps.lx, maps.lz, maps.hx, maps.hz, maps.m, p, cf, nb);
   else

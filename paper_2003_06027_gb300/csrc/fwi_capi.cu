@@ -22,8 +22,9 @@
 
 namespace fwi {
 cudaError_t launch_acu_fwd(const AcuStep& p, const AcuMaps& maps, bool record, bool store, cudaStream_t st);
-cudaError_t launch_acu_fwd_tz(const AcuStep& p, const AcuMaps& maps, bool record, bool store, int tz, cudaStream_t st);
-cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st);
+cudaError_t launch_acu_fwd_tz(const AcuStep& p, const AcuMaps& maps, bool record, bool store, int tz, cudaStream_t st,
+                              bool lap);
+cudaError_t launch_acu_adj(const AcuStep& p, const AcuMaps& maps, cudaStream_t st, bool lap);
 cudaError_t launch_acu_fwd_batch(const BatchArgs& b, const AcuCoef& cf, int N, bool record, cudaStream_t st);
 cudaError_t launch_acu_adj_batch(const BatchArgs& b, const AcuCoef& cf, int N, cudaStream_t st);
 cudaError_t launch_copy_table(const CopyDesc* d, int n, cudaStream_t st);
@@ -46,28 +47,7 @@ cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaSt
 cudaError_t launch_selftest_wait(int* status, unsigned long long* waited_ns, cudaStream_t st);
 cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
                                      float* gout, long long n, cudaStream_t st);
-cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st);
-struct LapStep {
-  Grid g;
-  int N;
-  float c1x[4], c1z[4];
-  float dt2;
-  const float* mh;
-  const float *ax, *bx, *axh, *bxh, *az, *bz, *azh, *bzh;
-};
-cudaError_t launch_lap_forward_step(const LapStep& p, int S, const float* u, float* uprev, float* psix, float* psiz,
-                                    float* qx, float* qz, float* zetx, float* zetz, const int* box, const float* w,
-                                    int nb, const float* stf, int nt, int n, float* rstore, cudaStream_t st);
-cudaError_t launch_lap_record(const float* u, const Grid& g, int S, int nrec, int nt, int n, const int* rec_cell,
-                              float* seis, cudaStream_t st);
-cudaError_t launch_lap_inject_res(float* lam, const Grid& g, int S, int nrec, int nt, int n, const int* rec_cell,
-                                  const float* res, cudaStream_t st);
-cudaError_t launch_lap_adjoint_step(const LapStep& p, int S, const float* lam1, float* lam2, const float* rst,
-                                    float* gpart, float* Zx, float* Zz, float* Px, float* Pz, float* hbx, float* hbz,
-                                    float* gbx, float* gbz, cudaStream_t st);
-cudaError_t launch_lap_src_part(const float* lam1, const Grid& g, int S, int nt, int n, const int* box,
-                                const float* w, int nb, const float* x0, float dx, float dz, float* part,
-                                cudaStream_t st);
+cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st, bool lap = false);
 cudaError_t launch_line_prep(int S, int L, const float* x0, const Grid& g, float dx, float dz, int* line_cell,
                              int* box, int* status, cudaStream_t st);
 cudaError_t launch_line_inject(int S, int L, int n, int nt, float scale, const float* amp, const int* line_cell,
@@ -663,190 +643,6 @@ fwi_status fwi_last_timing(const fwi_ctx* ctx, float* phase_ms3, float* kernel_m
   return FWI_OK;
 }
 
-}  // extern "C"
-
-namespace {
-
-// ---------------------------------------------------------------------------
-// The c^2 Laplacian operator (FWI_OP_LAPLACIAN, acoustic_lap.cu): plain
-// per-point kernels on one stream, the same arena layout, checkpoints and folds
-// as the divergence form. Buffers: psix[0], psiz[0] the CPML memory of the
-// fluxes, psix[1], psiz[1] the fluxes of the current step; adjoint Z in zx[0],
-// zz[0], P in px[0], pz[0], the cell and half-point adjoint temporaries in the
-// hhat pairs; the segment slot keeps r^n (its first field per step).
-LapStep lap_params(const Plan& P, const fwi_model* M, float dt) {
-  LapStep q;
-  memset(&q, 0, sizeof q);
-  q.g = P.g;
-  q.N = P.N;
-  float a[4];
-  fd_coeffs(M->order, a);
-  for (int k = 0; k < 4; k++) {
-    q.c1x[k] = a[k] / M->dx;
-    q.c1z[k] = a[k] / M->dz;
-  }
-  q.dt2 = dt * dt;
-  q.mh = P.m;
-  const int L = P.tablen;
-  const float* T = P.tab;
-  q.ax = T; q.bx = T + L; q.axh = T + 2 * L; q.bxh = T + 3 * L;
-  q.az = T + 4 * L; q.bz = T + 5 * L; q.azh = T + 6 * L; q.bzh = T + 7 * L;
-  return q;
-}
-
-// One forward step n of all shots (fluxes, update, line source, receivers).
-fwi_status lap_step(fwi_ctx* ctx, const Plan& P, const LapStep& q, int n, float lscale, bool record, float* rstore,
-                    cudaStream_t st) {
-  const size_t field = (size_t)P.S * P.g.slice;
-  const float* u = P.u + (n & 1) * field;
-  float* un = P.u + ((n + 1) & 1) * field;  // u^{n-1} in, u^{n+1} out
-  const int nb = P.kind == FWI_SRC_GAUSSIAN ? SRC_W : 1;
-  LK(2, launch_lap_forward_step(q, P.S, u, un, P.psix[0], P.psiz[0], P.psix[1], P.psiz[1], P.zetx, P.zetz,
-                                P.src_box, P.src_w, nb, P.stf, P.nt, n, rstore, st));
-  // the receivers are sampled after the line injection, so no seismogram fix-up is needed here
-  if (P.L > 0)
-    LK(1, launch_line_inject(P.S, P.L, n, P.nt, lscale, P.stf, P.line_cell, un, P.g, P.rec_cell, P.nrec, nullptr, st));
-  if (record) LK(1, launch_lap_record(un, P.g, P.S, P.nrec, P.nt, n, P.rec_cell, P.seis, st));
-  return FWI_OK;
-}
-
-fwi_status lap_save(const Plan& P, int n, float* ck, cudaStream_t st) {
-  const size_t field = (size_t)P.S * P.g.slice;
-  const float* src[6] = {P.u + (n & 1) * field, P.u + ((n + 1) & 1) * field, P.psix[0], P.psiz[0], P.zetx, P.zetz};
-  for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(ck + f * field, src[f], field * 4, cudaMemcpyDeviceToDevice, st));
-  return FWI_OK;
-}
-fwi_status lap_restore(const Plan& P, int n, const float* ck, cudaStream_t st) {
-  const size_t field = (size_t)P.S * P.g.slice;
-  float* dst[6] = {P.u + (n & 1) * field, P.u + ((n + 1) & 1) * field, P.psix[0], P.psiz[0], P.zetx, P.zetz};
-  for (int f = 0; f < 6; f++) CK(cudaMemcpyAsync(dst[f], ck + f * field, field * 4, cudaMemcpyDeviceToDevice, st));
-  return FWI_OK;
-}
-
-fwi_status lap_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int32_t nt,
-                       float dt, float* seis, cudaStream_t st) {
-  Plan P;
-  make_plan(P, M, Sv, R, nt, 0, false);
-  fwi_status v = ensure_arena(ctx, P, st);
-  if (v != FWI_OK) return v;
-  AcuStep p;
-  ctx->launches = 0;
-  if ((v = prepare(ctx, P, M, Sv, R, dt, st, p)) != FWI_OK) return v;
-  const LapStep q = lap_params(P, M, dt);
-  const float lscale = (float)((double)dt * dt / ((double)M->dx * M->dz));
-  ensure_events(ctx, 0);
-  CK(cudaEventRecord(ctx->ev[0], st));
-  for (int n = 0; n < nt; n++)
-    if ((v = lap_step(ctx, P, q, n, lscale, true, nullptr, st)) != FWI_OK) return v;
-  CK(cudaEventRecord(ctx->ev[1], st));
-  const long long ns = (long long)P.S * P.nrec * nt;
-  if (ns > 0) {
-    LK(1, launch_finite_check(P.seis, ns, P.status, st));
-    CK(cudaMemcpyAsync(seis, P.seis, (size_t)ns * 4, cudaMemcpyDefault, st));
-  }
-  CK(cudaEventRecord(ctx->ev[3], st));
-  v = finish_status(ctx, P, st);
-  float t = 0.f;
-  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
-  ctx->phase_ms[0] = t;
-  ctx->phase_ms[1] = 0.f;
-  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3]);
-  ctx->phase_ms[2] = t;
-  ctx->kernel_ms[0] = ctx->phase_ms[0] / nt;
-  ctx->kernel_ms[1] = ctx->kernel_ms[2] = 0.f;
-  if (v == FWI_OK) g_err.clear();
-  return v;
-}
-
-fwi_status lap_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R, int32_t nt,
-                           float dt, const float* observed, int32_t K, double* misfit, float* grad, float* grad_stf,
-                           float* grad_x0, float* seis_out, cudaStream_t st, bool capture, int** status_out) {
-  Plan P;
-  make_plan(P, M, Sv, R, nt, K, true);
-  fwi_status v = ensure_arena(ctx, P, st);
-  if (v != FWI_OK) return v;
-  AcuStep p;
-  ctx->launches = 0;
-  if ((v = prepare(ctx, P, M, Sv, R, dt, st, p)) != FWI_OK) return v;
-  const long long ns = (long long)P.S * P.nrec * nt;
-  if (ns > 0) CK(cudaMemcpyAsync(P.res, observed, (size_t)ns * 4, cudaMemcpyDefault, st));
-  const LapStep q = lap_params(P, M, dt);
-  const float lscale = (float)((double)dt * dt / ((double)M->dx * M->dz));
-  const size_t field = (size_t)P.S * P.g.slice;
-  ensure_events(ctx, P.nseg);
-  // the forward sweep keeps r^n of the last segment itself, so that segment is never recomputed
-  const int nlast = (P.nseg - 1) * K;
-  CK(cudaEventRecord(ctx->ev[0], st));
-  for (int n = 0; n < nt; n++) {
-    if (n % K == 0 && n < nlast && (v = lap_save(P, n, P.ckpt + (size_t)(n / K) * 6 * field, st)) != FWI_OK)
-      return v;
-    float* keep = n >= nlast ? P.slot + (size_t)(n - nlast) * 2 * field : nullptr;
-    if ((v = lap_step(ctx, P, q, n, lscale, true, keep, st)) != FWI_OK) return v;
-  }
-  CK(cudaEventRecord(ctx->ev[1], st));
-  if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, ctx->vjp, st));
-  else CK(cudaMemsetAsync(P.J, 0, 8, st));
-  // adjoint seed: lambda_nt = residual of the last sample; lambda_{nt+1} = 0 (zeroed)
-  if (ns > 0) LK(1, launch_lap_inject_res(P.lam + (nt & 1) * field, P.g, P.S, P.nrec, nt, nt - 1, P.rec_cell, P.res, st));
-  const int nb = P.kind == FWI_SRC_GAUSSIAN ? SRC_W : 1;
-  for (int seg = P.nseg - 1; seg >= 0; seg--) {
-    const int n0 = seg * K, n1 = std::min(nt, n0 + K);
-    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
-    if (seg < P.nseg - 1) {
-      if ((v = lap_restore(P, n0, P.ckpt + (size_t)seg * 6 * field, st)) != FWI_OK) return v;
-      for (int n = n0; n < n1; n++)
-        if ((v = lap_step(ctx, P, q, n, lscale, false, P.slot + (size_t)(n - n0) * 2 * field, st)) != FWI_OK)
-          return v;
-    }
-    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
-    for (int n = n1 - 1; n >= n0; n--) {
-      const float* lam1 = P.lam + ((n + 1) & 1) * field;  // lambda_{n+1}, complete
-      float* lam2 = P.lam + (n & 1) * field;               // lambda_{n+2} in, lambda_n out
-      if (P.L > 0) LK(1, launch_line_grad(P.S, P.L, n, nt, lscale, P.line_cell, lam1, P.g, P.gstf, st));
-      else LK(1, launch_lap_src_part(lam1, P.g, P.S, nt, n, P.src_box, P.src_w, nb, P.x0, M->dx, M->dz, P.src_part, st));
-      LK(3, launch_lap_adjoint_step(q, P.S, lam1, lam2, P.slot + (size_t)(n - n0) * 2 * field, P.gpart, P.zx[0],
-                                    P.zz[0], P.px[0], P.pz[0], P.hx, P.hx + field, P.hz, P.hz + field, st));
-      if (n >= 1 && ns > 0) LK(1, launch_lap_inject_res(lam2, P.g, P.S, P.nrec, nt, n - 1, P.rec_cell, P.res, st));
-    }
-    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
-    LK(1, launch_fold(P.gpart, P.S, P.g.slice, P.G, st));
-  }
-  CK(cudaEventRecord(ctx->ev[2], st));
-  if (grad) {
-    LK(1, launch_grad_c(P.G, P.g, P.c, P.grad_c, st));
-    CK(cudaMemcpyAsync(grad, P.grad_c, (size_t)P.g.nz * P.g.nx * 4, cudaMemcpyDefault, st));
-  }
-  if (P.L > 0) {
-    if (grad_stf) CK(cudaMemcpyAsync(grad_stf, P.gstf, (size_t)P.S * nt * P.L * 4, cudaMemcpyDefault, st));
-  } else if (grad_stf || grad_x0) {
-    LK(1, launch_src_grad(P.src_part, P.S, nt, SRC_SLOTS, (double)dt * dt, P.stf, 1.0 / (0.25 * (double)M->dx * M->dx),
-                          P.kind, P.gstf, P.gx0, st));
-    if (grad_stf) CK(cudaMemcpyAsync(grad_stf, P.gstf, (size_t)P.S * nt * 4, cudaMemcpyDefault, st));
-    if (grad_x0) CK(cudaMemcpyAsync(grad_x0, P.gx0, (size_t)P.S * 2 * 4, cudaMemcpyDefault, st));
-  }
-  if (seis_out && ns > 0) CK(cudaMemcpyAsync(seis_out, P.seis, (size_t)ns * 4, cudaMemcpyDefault, st));
-  CK(cudaMemcpyAsync(misfit, P.J, 8, cudaMemcpyDefault, st));
-  CK(cudaEventRecord(ctx->ev[3], st));
-  if (status_out) *status_out = P.status;
-  if (capture) return FWI_OK;
-  v = finish_status(ctx, P, st);
-  float t = 0.f;
-  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
-  ctx->phase_ms[0] = t;
-  cudaEventElapsedTime(&t, ctx->ev[1], ctx->ev[2]);
-  ctx->phase_ms[1] = t;
-  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3]);
-  ctx->phase_ms[2] = t;
-  ctx->kernel_ms[0] = ctx->phase_ms[0] / nt;
-  ctx->kernel_ms[1] = ctx->kernel_ms[2] = 0.f;
-  if (v == FWI_OK) g_err.clear();
-  return v;
-}
-
-}  // namespace
-
-extern "C" {
-
 fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,
                        int32_t nt, float dt, float* seis, void* stream) {
   if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
@@ -856,7 +652,7 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   if (!seis && R->nrec > 0) return fail(FWI_EINVAL, "seis must not be NULL");
   CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  if (M->op == FWI_OP_LAPLACIAN) return lap_forward(ctx, M, Sv, R, nt, dt, seis, st);
+  const bool lap = M->op == FWI_OP_LAPLACIAN;
   Plan P;
   make_plan(P, M, Sv, R, nt, 0, false);
   v = ensure_arena(ctx, P, st);
@@ -877,7 +673,7 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
   for (int n = 0; n < nt; n++) {
     set_fwd_state(P, p, n);
     for (int g = 0; g < gr.G; g++) {
-      LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, fwd_tz(ctx), gr.st[g]));
+      LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, false, fwd_tz(ctx), gr.st[g], lap));
       if (P.L > 0)
         LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                  P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * fieldf + gr.s0[g] * P.g.slice,
@@ -925,9 +721,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   if (K < 1 || K > nt) return fail(FWI_EINVAL, "ckpt_every must be in [1, nt]");
   if (Sv->kind == FWI_SRC_LINE && grad_x0) return fail(FWI_EINVAL, "a line source has no position gradient");
   CK(cudaSetDevice(ctx->device));
-  if (M->op == FWI_OP_LAPLACIAN)
-    return lap_misfit_grad(ctx, M, Sv, R, nt, dt, observed, K, misfit, grad, grad_stf, grad_x0, seis_out, st, capture,
-                           status_out);
+  const bool lap = M->op == FWI_OP_LAPLACIAN;
   const float lscale = (float)((double)dt * dt / ((double)M->dx * M->dz));
   Plan P;
   make_plan(P, M, Sv, R, nt, K, true);
@@ -973,7 +767,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       p.slot_pz = p.slot_px + field;
     }
     for (int g = 0; g < gr.G; g++) {
-      LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, keep, fwd_tz(ctx), gr.st[g]));
+      LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, keep, fwd_tz(ctx), gr.st[g], lap));
       if (P.L > 0)
         LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                  P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
@@ -991,7 +785,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   p.src_part = P.src_part;
   AcuStep pa = p;
   set_adjoint_weights(pa, p);
-  LK(1, launch_adj_init(pa, P.lam + (nt & 1) * field, P.hx + (nt & 1) * field, P.hz + (nt & 1) * field, st));
+  LK(1, launch_adj_init(pa, P.lam + (nt & 1) * field, P.hx + (nt & 1) * field, P.hz + (nt & 1) * field, st, lap));
   if (P.L > 0) LK(1, launch_line_grad(P.S, P.L, nt - 1, nt, lscale, P.line_cell, P.lam + (nt & 1) * field, P.g, P.gstf, st));
   for (int seg = P.nseg - 1; seg >= 0; seg--) {
     const int n0 = seg * K, n1 = std::min(nt, n0 + K);
@@ -1012,7 +806,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
         p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
         p.slot_pz = p.slot_px + field;
         for (int g = 0; g < gr.G; g++) {
-          LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, fwd_tz(ctx), gr.st[g]));
+          LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, fwd_tz(ctx), gr.st[g], lap));
           if (P.L > 0)
             LK(1, launch_line_inject(gr.n[g], P.L, n, nt, lscale, P.stf + (size_t)gr.s0[g] * nt * P.L,
                                      P.line_cell + 2 * gr.s0[g], P.u + ((n + 1) & 1) * field + gr.s0[g] * sl, P.g,
@@ -1039,7 +833,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       pa.hx_out = P.hx + (n & 1) * field;
       pa.hz_out = P.hz + (n & 1) * field;
       for (int g = 0; g < gra.G; g++) {
-        LK(1, launch_acu_adj(group_view(pa, P, gra.s0[g], gra.n[g]), maps, gra.st[g]));
+        LK(1, launch_acu_adj(group_view(pa, P, gra.s0[g], gra.n[g]), maps, gra.st[g], lap));
         if (P.L > 0 && n >= 1)  // lambda_n is complete: the derivative for amp[n - 1]
           LK(1, launch_line_grad(gra.n[g], P.L, n - 1, nt, lscale, P.line_cell + 2 * gra.s0[g],
                                  P.lam + (n & 1) * field + gra.s0[g] * sl, P.g, P.gstf + (size_t)gra.s0[g] * nt * P.L,

@@ -259,7 +259,7 @@ __global__ void k_finite_check(const float* __restrict__ a, long long n, int* st
 
 // Adjoint initial condition: lambda_{nt} = residual of the last sample at the
 // receivers (in receiver order), and its source-parameter partial (index nt-1).
-__global__ void k_adj_init(AcuStep p, float* lam, float* hx, float* hz) {
+__global__ void k_adj_init(AcuStep p, float* lam, float* hx, float* hz, bool lap) {
   const int s = blockIdx.x;
   if (threadIdx.x != 0) return;
   const long long sh = (long long)s * p.g.slice + p.g.off0;
@@ -268,9 +268,12 @@ __global__ void k_adj_init(AcuStep p, float* lam, float* hx, float* hz) {
     if (ri < 0) continue;
     const long long c = sh + (long long)ri * p.g.pitch + rj;
     const float rv = p.res[((long long)s * p.nrec + r) * p.nt + p.nt - 1];
+    // hhat = lambda at a receiver (never inside the CPML layer); m lambda for the
+    // Laplacian operator (m = 2 (m/2) at the cell)
+    const float hv = lap ? 2.f * p.mh[p.g.off0 + (long long)ri * p.g.pitch + rj] * rv : rv;
     lam[c] += rv;
-    hx[c] += rv;  // hhat = lambda at a receiver (never inside the CPML layer)
-    hz[c] += rv;
+    hx[c] += hv;
+    hz[c] += hv;
   }
   if (p.src_part == nullptr) return;
   const int i0 = p.src_box[2 * s], j0 = p.src_box[2 * s + 1], nb = p.src_n;
@@ -481,8 +484,8 @@ cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaSt
   k_finite_check<<<304, 256, 0, st>>>(a, n, status);
   return cudaGetLastError();
 }
-cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st) {
-  k_adj_init<<<p.S, 32, 0, st>>>(p, lam, hx, hz);
+cudaError_t launch_adj_init(const AcuStep& p, float* lam, float* hx, float* hz, cudaStream_t st, bool lap) {
+  k_adj_init<<<p.S, 32, 0, st>>>(p, lam, hx, hz, lap);
   return cudaGetLastError();
 }
 // Copies of a descriptor table: block row y copies descriptor y.

@@ -20,7 +20,7 @@ CASES = {
     "fwi16-nt20": (16, 20, 10),
     # the HBM-bound regime: 128 shots, one step's fields (~0.45 GB) far exceed L2 (~3.7 GB arena)
     "fwi128-nt8": (128, 8, 4),
-    # the same with the c^2 Laplacian operator (plain per-point kernels)
+    # the same with the c^2 Laplacian operator
     "lap16-nt20": (16, 20, 10),
     # elastic 300 x 800 discretisation (4th order, 32 CPML cells), 8 shots
     "ela8-nt20": (8, 20, 10),

@@ -328,6 +328,7 @@ def test_line_source_errors(fwi_lib):
 LAP_CASES = [  # nz, nx, nt, shots, order, npml, kind, seed, K
     (37, 71, 150, 2, 4, 10, 0, 41, 50),
     (30, 44, 140, 3, 8, 9, 1, 42, 47),
+    (80, 200, 120, 2, 8, 10, 1, 45, 40),  # 4 x 4 tiles with interior ones and a ragged tail
 ]
 
 
