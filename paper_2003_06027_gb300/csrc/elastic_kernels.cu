@@ -228,6 +228,40 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* red) {
   __syncthreads();     \
   }
 
+// Single-buffer walk (the adjoint kernels): one operand buffer and one barrier;
+// the fetch of the next tile is issued by ELA_PREFETCH1 once every thread has
+// read what it needs of the buffer, so the copy overlaps the rest of the tile
+// and the other CTAs on the SM cover its latency. On a timeout the CTA lets a
+// late copy land (bounded wait) before it returns.
+#define ELA_WALK1_BEGIN(FETCH)                                      \
+  const int ntiles = p.S * g.ntx * g.ntz;                           \
+  if (tid == 0) {                                                   \
+    mbar_init(&bar[0], 1);                                          \
+    fence_mbar_init();                                              \
+  }                                                                 \
+  __syncthreads();                                                  \
+  if (tid == 0 && (int)blockIdx.x < ntiles) FETCH(blockIdx.x);      \
+  int it = 0;                                                       \
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {      \
+    const TileId id = tile_decode(g, t);                            \
+    const int s = id.s, x0 = id.x0, z0 = id.z0;                     \
+    const long long base = (long long)s * g.slice + g.off0;
+
+#define ELA_WAIT1()                                      \
+  {                                                      \
+    const bool ok_ = mbar_wait(&bar[0], it & 1);         \
+    if (__syncthreads_or(!ok_)) {                        \
+      if (tid == 0) {                                    \
+        atomicOr(p.status, ST_TIMEOUT);                  \
+        mbar_wait(&bar[0], it & 1);                      \
+      }                                                  \
+      return;                                            \
+    }                                                    \
+  }
+
+#define ELA_PREFETCH1(FETCH) \
+  if (tid == 0 && t + (int)gridDim.x < ntiles) FETCH(t + (int)gridDim.x);
+
 // Velocity half step: v^{n+1/2} = v^{n-1/2} + dt b (div sigma^n + CPML).
 // Tile buffer: sxx rows [z0, z0+32) cols [x0-4, x0+68); szz rows [z0-4, z0+36)
 // cols [x0, x0+64); sxz rows [z0-4, z0+36) cols [x0-4, x0+68).
@@ -457,11 +491,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 constexpr int ADJA_BUF = 3 * H40 * W72;  // Sbar xx, zz, xz: rows [z0-4, z0+36), cols [x0-4, x0+68)
 constexpr int ADJA_SCR = 2 * TILE_Z * W72 + 2 * H40 * TILE_X + 32;
 template <int N>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at 4th order (80 registers)
     ela_str_adj(const __grid_constant__ CUtensorMap m_Sxx, const __grid_constant__ CUtensorMap m_Szz,
                 const __grid_constant__ CUtensorMap m_Sxz, const EleStep p) {
   extern __shared__ __align__(128) float smem_e[];
-  float* d_vx = smem_e + 2 * ADJA_BUF;        // [TILE_Z][W72] normal nodes, own rows
+  float* d_vx = smem_e + ADJA_BUF;            // [TILE_Z][W72] normal nodes, own rows
   float* d_vz = d_vx + TILE_Z * W72;          // [H40][TILE_X] normal nodes, own cols
   float* d_vxz = d_vz + H40 * TILE_X;         // [H40][TILE_X] shear nodes, own cols
   float* d_vzx = d_vxz + H40 * TILE_X;        // [TILE_Z][W72] shear nodes, own rows
@@ -470,16 +504,15 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
-  auto fetch = [&](int tt, int bb) {
+  auto fetch = [&](int tt) {
     const TileId f = tile_decode(g, tt);
-    float* d = smem_e + bb * ADJA_BUF;
     fence_proxy_async();
-    mbar_expect_tx(&bar[bb], ADJA_BUF * 4);
-    tma_3d(d, &m_Sxx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
-    tma_3d(d + H40 * W72, &m_Szz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
-    tma_3d(d + 2 * H40 * W72, &m_Sxz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    mbar_expect_tx(&bar[0], ADJA_BUF * 4);
+    tma_3d(smem_e, &m_Sxx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[0]);
+    tma_3d(smem_e + H40 * W72, &m_Szz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[0]);
+    tma_3d(smem_e + 2 * H40 * W72, &m_Sxz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[0]);
   };
-  ELA_WALK_BEGIN(fetch)
+  ELA_WALK1_BEGIN(fetch)
   const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
   float4 vpre[2][2];
 #pragma unroll
@@ -490,8 +523,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   }
   const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
   const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
-  ELA_WAIT()
-  const float* s_Sxx = smem_e + b * ADJA_BUF;
+  ELA_WAIT1()
+  const float* s_Sxx = smem_e;
   const float* s_Szz = s_Sxx + H40 * W72;
   const float* s_Sxz = s_Szz + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
@@ -559,7 +592,17 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   for (int k = tid; k < NB; k += NTHREADS) item_c(k);
 #pragma unroll 3
   for (int k = tid; k < NA; k += NTHREADS) item_d(k);
+  // the own nodes' adjoint stresses, read before the buffer is refilled
+  float Sx_own[2][4], Sz_own[2][4], Sh_own[2][4];
+#pragma unroll
+  for (int rr = 0; rr < 2; rr++) {
+    const int o = (2 * ty + rr + 4) * W72 + 4 * tx + 4;
+    f4a(ld4(s_Sxx + o), Sx_own[rr]);
+    f4a(ld4(s_Szz + o), Sz_own[rr]);
+    f4a(ld4(s_Sxz + o), Sh_own[rr]);
+  }
   __syncthreads();
+  ELA_PREFETCH1(fetch)
   float zx[2][4], zz[2][4];
   {
     float4 W[2 * N + 1];
@@ -568,7 +611,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     load_win<N, TILE_X>(d_vz, 2 * ty + 5 - N, 4 * tx, W);   // D-z^T at vz half rows
     zwin<N>(p.cz, W, zz[0], zz[1]);
   }
-  float Sx_own[2][4], Sz_own[2][4], Sh_own[2][4];
 #pragma unroll
   for (int rr = 0; rr < 2; rr++) {
     const int r = 2 * ty + rr, z = z0 + r;
@@ -608,9 +650,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     f4a(ld4_stream(p.slot[2] + id, l2_evict_first()), ex);
     f4a(ld4_stream(p.slot[3] + id, l2_evict_first()), ez);
     f4a(ld4_stream(p.slot[4] + id, l2_evict_first()), exz);
-    f4a(ld4(s_Sxx + (r + 4) * W72 + 4 * tx + 4), Sx_own[rr]);
-    f4a(ld4(s_Szz + (r + 4) * W72 + 4 * tx + 4), Sz_own[rr]);
-    f4a(ld4(s_Sxz + (r + 4) * W72 + 4 * tx + 4), Sh_own[rr]);
     f4a(ld4(p.g_lam + id), gl);
     f4a(ld4(p.g_mu + id), gm);
     f4a(ld4(p.g_mxz + id), gx);
@@ -675,10 +714,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 constexpr int ADJB_BUF = 2 * H40 * W72;  // Vbar x, z: rows [z0-4, z0+36), cols [x0-4, x0+68)
 constexpr int ADJB_SCR = 2 * TILE_Z * W72 + 2 * H40 * TILE_X;
 template <int N>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at 4th order (80 registers)
     ela_vel_adj(const __grid_constant__ CUtensorMap m_Vx, const __grid_constant__ CUtensorMap m_Vz, const EleStep p) {
   extern __shared__ __align__(128) float smem_e[];
-  float* d_sxx = smem_e + 2 * ADJB_BUF;       // [TILE_Z][W72] vx nodes, own rows
+  float* d_sxx = smem_e + ADJB_BUF;           // [TILE_Z][W72] vx nodes, own rows
   float* d_sxz = d_sxx + TILE_Z * W72;        // [H40][TILE_X] vx nodes, own cols
   float* d_szz = d_sxz + H40 * TILE_X;        // [H40][TILE_X] vz nodes, own cols
   float* d_sxzx = d_szz + H40 * TILE_X;       // [TILE_Z][W72] vz nodes, own rows
@@ -686,15 +725,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   const Grid& g = p.g;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int pitch = g.pitch;
-  auto fetch = [&](int tt, int bb) {
+  auto fetch = [&](int tt) {
     const TileId f = tile_decode(g, tt);
-    float* d = smem_e + bb * ADJB_BUF;
     fence_proxy_async();
-    mbar_expect_tx(&bar[bb], ADJB_BUF * 4);
-    tma_3d(d, &m_Vx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
-    tma_3d(d + H40 * W72, &m_Vz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[bb]);
+    mbar_expect_tx(&bar[0], ADJB_BUF * 4);
+    tma_3d(smem_e, &m_Vx, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[0]);
+    tma_3d(smem_e + H40 * W72, &m_Vz, f.x0 - 4 + APRON, f.z0 - 4 + APRON, f.s, &bar[0]);
   };
-  ELA_WALK_BEGIN(fetch)
+  ELA_WALK1_BEGIN(fetch)
   const int xb = x0 + 4 * tx, zr0 = z0 + 2 * ty;
   float4 spre[2][3];
 #pragma unroll
@@ -704,8 +742,8 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     spre[rr][1] = ld4(p.Szz + id);
     spre[rr][2] = ld4(p.Sxz + id);
   }
-  ELA_WAIT()
-  const float* s_Vx = smem_e + b * ADJB_BUF;
+  ELA_WAIT1()
+  const float* s_Vx = smem_e;
   const float* s_Vz = s_Vx + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
@@ -768,7 +806,16 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   for (int k = tid; k < NB; k += NTHREADS) item_c(k);
 #pragma unroll 3
   for (int k = tid; k < NA; k += NTHREADS) item_d(k);
+  // the own nodes' adjoint velocities, read before the buffer is refilled
+  float vx_own[2][4], vz_own[2][4];
+#pragma unroll
+  for (int rr = 0; rr < 2; rr++) {
+    const int o = (2 * ty + rr + 4) * W72 + 4 * tx + 4;
+    f4a(ld4(s_Vx + o), vx_own[rr]);
+    f4a(ld4(s_Vz + o), vz_own[rr]);
+  }
   __syncthreads();
+  ELA_PREFETCH1(fetch)
   float zs[2][4], zh[2][4];
   {
     float4 W[2 * N + 1];
@@ -803,11 +850,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     st4(p.Szz + id, a4f(sz));
     st4(p.Sxz + id, a4f(sh));
     // buoyancy correlations
-    float fx[4], fz[4], vx_[4], vz_[4], gbx[4], gbz[4];
+    float fx[4], fz[4], gbx[4], gbz[4];
+    const float* vx_ = vx_own[rr];
+    const float* vz_ = vz_own[rr];
     f4a(ld4_stream(p.slot[0] + id, l2_evict_first()), fx);
     f4a(ld4_stream(p.slot[1] + id, l2_evict_first()), fz);
-    f4a(ld4(s_Vx + (r + 4) * W72 + 4 * tx + 4), vx_);
-    f4a(ld4(s_Vz + (r + 4) * W72 + 4 * tx + 4), vz_);
     f4a(ld4(p.g_bx + id), gbx);
     f4a(ld4(p.g_bz + id), gbz);
 #pragma unroll
@@ -1035,8 +1082,8 @@ __global__ void k_ela_velocity_grad(const float* __restrict__ vp, const float* _
 namespace {
 constexpr size_t VEL_SMEM = sizeof(float) * 2 * VEL_BUF + 2 * sizeof(uint64_t);
 constexpr size_t STR_SMEM = sizeof(float) * 2 * STR_BUF + 2 * sizeof(uint64_t);
-constexpr size_t ADJ_A_SMEM = sizeof(float) * (2 * ADJA_BUF + ADJA_SCR) + 2 * sizeof(uint64_t);
-constexpr size_t ADJ_B_SMEM = sizeof(float) * (2 * ADJB_BUF + ADJB_SCR) + 2 * sizeof(uint64_t);
+constexpr size_t ADJ_A_SMEM = sizeof(float) * (ADJA_BUF + ADJA_SCR) + sizeof(uint64_t);  // one operand buffer
+constexpr size_t ADJ_B_SMEM = sizeof(float) * (ADJB_BUF + ADJB_SCR) + sizeof(uint64_t);
 
 std::mutex g_ela_mu;
 unsigned long long g_ela_inited = 0;  // bit per device
