@@ -12,10 +12,12 @@
 // Every update is a first-order staggered stencil (memory bound, no tensor
 // cores). Persistent CTAs walk the 64 x 32 tiles of all shots; the fields a
 // tile needs with a halo are fetched by TMA (cp.async.bulk.tensor, one box per
-// field) into one of two shared-memory buffers, so the next tile's fetch
-// overlaps the current tile's work (bounded mbarrier waits report a timeout);
-// per-node operands without a halo are loaded before the wait. Each thread
-// updates 2 rows x 4 columns. CPML memory variables are node-local in the
+// field). The forward kernels use two shared-memory buffers, so the next
+// tile's fetch overlaps the current tile's work; the adjoint kernels, whose
+// halo-item scratch is larger, use one buffer, refilled once stage 1 has read
+// it. Bounded mbarrier waits report a timeout. Per-node operands without a
+// halo are loaded before the wait. At 4th order every kernel runs 3 CTAs of
+// 256 threads per SM (80 registers). Each thread updates 2 rows x 4 columns. CPML memory variables are node-local in the
 // forward (updated in place) and double-buffered in the adjoint, where their
 // values are needed at halo nodes.
 #include <cuda_runtime.h>
@@ -267,7 +269,7 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* red) {
 // cols [x0, x0+64); sxz rows [z0-4, z0+36) cols [x0-4, x0+68).
 constexpr int VEL_BUF = TILE_Z * W72 + H40 * TILE_X + H40 * W72;
 template <int N, bool RECORD, bool STORE>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at 4th order (80 registers)
     ela_vel_step(const __grid_constant__ CUtensorMap m_xx, const __grid_constant__ CUtensorMap m_zz,
                  const __grid_constant__ CUtensorMap m_xz, const EleStep p) {
   extern __shared__ __align__(128) float smem_e[];
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 // Tile buffer: vx and vz, rows [z0-4, z0+36), cols [x0-4, x0+68).
 constexpr int STR_BUF = 2 * H40 * W72;
 template <int N, bool STORE>
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at 4th order (80 registers)
     ela_str_step(const __grid_constant__ CUtensorMap m_vx, const __grid_constant__ CUtensorMap m_vz, const EleStep p) {
   extern __shared__ __align__(128) float smem_e[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_e + 2 * STR_BUF);
