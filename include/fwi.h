@@ -252,7 +252,10 @@ fwi_status fwi_set_shot_groups(fwi_ctx *ctx, int32_t forward_groups, int32_t adj
  *   launches of graphs of the SAME context must not overlap (they share the
  *   workspace); graphs of different contexts may run concurrently.
  * fwi_graph_status: wait for cuda_stream and decode the device status word of
- *   the last evaluation (the codes of fwi_misfit_grad).
+ *   the last evaluation (the codes of fwi_misfit_grad). The recording keeps the
+ *   call's phase marks as event-record nodes, so afterwards fwi_last_timing(ctx)
+ *   reports that replay's phase and per-step kernel times and its launch count,
+ *   as for a direct call.
  * fwi_graph_destroy: free the graph (not the context). */
 typedef struct fwi_graph fwi_graph;
 fwi_status fwi_misfit_grad_graph(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
@@ -339,7 +342,8 @@ fwi_status fwi_forward_noalloc(const fwi_model *model, const fwi_sources *src,
  * groups whose launches run concurrently on internal streams (forked from and
  * joined to the call's stream), so one step is one launch per group, and the
  * step time includes launch gaps. launches: number of kernels the call
- * launched. Any pointer may be NULL. */
+ * launched. After fwi_graph_status, the values of the last graph replay on
+ * ctx. Any pointer may be NULL. */
 fwi_status fwi_last_timing(const fwi_ctx *ctx, float *phase_ms3, float *kernel_ms3,
                            int64_t *launches);
 

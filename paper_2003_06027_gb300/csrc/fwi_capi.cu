@@ -706,6 +706,39 @@ fwi_status fwi_forward(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, 
 
 namespace {
 
+// A phase mark: a plain event record on a direct call; inside a recording, an
+// external event-record node, so that every replay of the graph records it
+// and the replay's phases can be timed like a direct call's.
+cudaError_t mark(cudaEvent_t e, cudaStream_t st, bool capture) {
+  return capture ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal) : cudaEventRecord(e, st);
+}
+
+// Phase and per-step kernel times of the last gradient call (or graph replay)
+// of nt steps with a checkpoint every K steps, from its completed phase marks:
+// ev[0..3] (forward sweep start and end, reverse sweep end, call end) and per
+// segment seg_ev[4 seg + 0..2] (recompute start, adjoint start, adjoint end).
+void grad_timings(fwi_ctx* ctx, int nt, int K) {
+  const int nseg = (nt + K - 1) / K, nlast = (nseg - 1) * K;
+  float t = 0.f;
+  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
+  ctx->phase_ms[0] = t;
+  cudaEventElapsedTime(&t, ctx->ev[1], ctx->ev[2]);
+  ctx->phase_ms[1] = t;
+  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3]);
+  ctx->phase_ms[2] = t;
+  ctx->kernel_ms[0] = ctx->phase_ms[0] / nt;
+  float rec = 0.f, adj = 0.f;
+  for (int seg = 0; seg < nseg; seg++) {
+    float ta = 0.f;
+    cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 0], ctx->seg_ev[4 * seg + 1]);
+    rec += ta;
+    cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 1], ctx->seg_ev[4 * seg + 2]);
+    adj += ta;
+  }
+  ctx->kernel_ms[1] = nlast > 0 ? rec / nlast : 0.f;  // per recomputed step
+  ctx->kernel_ms[2] = adj / nt;
+}
+
 // The acoustic misfit/gradient call. With `capture` the device work is being
 // recorded into a graph: the arena is already sized and laid out by an earlier
 // call with the same problem, and the ending synchronisation (status read,
@@ -748,7 +781,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   // but the last: the sweep itself keeps the last segment's fluxes (recording
   // and storing in one launch), so that segment is never recomputed
   const int nlast = (P.nseg - 1) * K;
-  CK(cudaEventRecord(ctx->ev[0], st));
+  CK(mark(ctx->ev[0], st, capture));
   if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
   for (int n = 0; n < nt; n++) {
     if (n % K == 0 && n < nlast) {
@@ -775,7 +808,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     }
   }
   if ((v = join(ctx, gr, st)) != FWI_OK) return v;
-  CK(cudaEventRecord(ctx->ev[1], st));
+  CK(mark(ctx->ev[1], st, capture));
   if (ns > 0) LK(2, launch_misfit(P.seis, P.res, ns, P.Jpart, MISFIT_BLOCKS, P.J, P.status, ctx->vjp, st));
   else CK(cudaMemsetAsync(P.J, 0, 8, st));
 
@@ -794,7 +827,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
                      P.zetz};
     // recompute (from the checkpoint) on the group streams; the last segment's
     // fluxes are already stored by the forward sweep
-    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 0], st));
+    CK(mark(ctx->seg_ev[4 * seg + 0], st, capture));
     if (seg < P.nseg - 1) {
       if ((v = fork(ctx, gr, st)) != FWI_OK) return v;
       for (int g = 0; g < gr.G; g++)
@@ -815,7 +848,7 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       }
       if ((v = join(ctx, gr, st)) != FWI_OK) return v;
     }
-    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 1], st));
+    CK(mark(ctx->seg_ev[4 * seg + 1], st, capture));
     if ((v = fork(ctx, gra, st)) != FWI_OK) return v;
     for (int n = n1 - 1; n >= n0; n--) {
       pa.n = n;
@@ -841,10 +874,10 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
       }
     }
     if ((v = join(ctx, gra, st)) != FWI_OK) return v;
-    CK(cudaEventRecord(ctx->seg_ev[4 * seg + 2], st));
+    CK(mark(ctx->seg_ev[4 * seg + 2], st, capture));
     LK(1, launch_fold(P.gpart, P.S, P.g.slice, P.G, st));
   }
-  CK(cudaEventRecord(ctx->ev[2], st));
+  CK(mark(ctx->ev[2], st, capture));
   if (grad) {
     LK(1, launch_grad_c(P.G, P.g, P.c, P.grad_c, st));
     CK(cudaMemcpyAsync(grad, P.grad_c, (size_t)P.g.nz * P.g.nx * 4, cudaMemcpyDefault, st));
@@ -859,28 +892,11 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   }
   if (seis_out && ns > 0) CK(cudaMemcpyAsync(seis_out, P.seis, (size_t)ns * 4, cudaMemcpyDefault, st));
   CK(cudaMemcpyAsync(misfit, P.J, 8, cudaMemcpyDefault, st));
-  CK(cudaEventRecord(ctx->ev[3], st));
+  CK(mark(ctx->ev[3], st, capture));
   if (status_out) *status_out = P.status;
   if (capture) return FWI_OK;
   v = finish_status(ctx, P, st);
-  float t = 0.f;
-  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
-  ctx->phase_ms[0] = t;
-  cudaEventElapsedTime(&t, ctx->ev[1], ctx->ev[2]);
-  ctx->phase_ms[1] = t;
-  cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[3]);
-  ctx->phase_ms[2] = t;
-  ctx->kernel_ms[0] = ctx->phase_ms[0] / nt;
-  float rec = 0.f, adj = 0.f;
-  for (int seg = 0; seg < P.nseg; seg++) {
-    float ta = 0.f;
-    cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 0], ctx->seg_ev[4 * seg + 1]);
-    rec += ta;
-    cudaEventElapsedTime(&ta, ctx->seg_ev[4 * seg + 1], ctx->seg_ev[4 * seg + 2]);
-    adj += ta;
-  }
-  ctx->kernel_ms[1] = nlast > 0 ? rec / nlast : 0.f;  // per recomputed step
-  ctx->kernel_ms[2] = adj / nt;
+  grad_timings(ctx, nt, K);
   if (v == FWI_OK) g_err.clear();
   return v;
 }
@@ -902,6 +918,8 @@ struct fwi_graph {
   cudaGraphExec_t exec = nullptr;
   int* status = nullptr;  // device status word inside ctx's arena
   unsigned long long epoch = 0;
+  int nt = 0, K = 1;       // the recorded call's steps and checkpoint interval (for its phase times)
+  long long launches = 0;  // kernels of one replay
 };
 
 extern "C" {
@@ -976,6 +994,9 @@ fwi_status fwi_misfit_grad_graph(fwi_ctx* ctx, const fwi_model* M, const fwi_sou
   g->exec = exec;
   g->status = dstatus;
   g->epoch = epoch;
+  g->nt = nt;
+  g->K = K;
+  g->launches = ctx->launches;
   *out = g;
   g_err.clear();
   return FWI_OK;
@@ -994,6 +1015,9 @@ fwi_status fwi_graph_status(fwi_graph* g, void* stream) {
   if (!g) return fail(FWI_EINVAL, "graph must not be NULL");
   CK(cudaSetDevice(g->ctx->device));
   fwi_status v = finish_status_dev(g->ctx, g->status, (cudaStream_t)stream);
+  // the replay's phase marks are complete: its timings replace the context's
+  grad_timings(g->ctx, g->nt, g->K);
+  g->ctx->launches = g->launches;
   if (v == FWI_OK) g_err.clear();
   return v;
 }

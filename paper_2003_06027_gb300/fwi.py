@@ -373,6 +373,15 @@ class GradGraph:
         """Wait for ``stream`` and raise if the last evaluation reported an error."""
         _check(self._L.fwi_graph_status(self.graph, _stream(self._a.c, stream)))
 
+    def timing(self) -> Timing:
+        """Phase and per-step kernel times of the replay that the last ``check``
+        waited for (the recording keeps the library's phase marks)."""
+        ph = (ctypes.c_float * 3)()
+        km = (ctypes.c_float * 3)()
+        n = ctypes.c_int64()
+        _check(self._L.fwi_last_timing(self.ctx, ph, km, ctypes.byref(n)))
+        return Timing(ph[0], ph[1], ph[2], km[0], km[1], km[2], int(n.value))
+
     def close(self):
         if getattr(self, "graph", None):
             self._L.fwi_graph_destroy(self.graph)

@@ -89,6 +89,34 @@ def test_graph_sweep_equals_batched(fwi_lib):
     batch.close_graphs()
 
 
+def test_graph_replay_reports_phase_times(fwi_lib):
+    """A recorded gradient keeps the call's phase marks as event-record nodes:
+    after each replay the context reports positive phase and per-step kernel
+    times that add up like a direct call's, and the direct call's launch count;
+    the replay's results are the direct call's bit for bit."""
+    import torch
+
+    from paper_2003_06027_gb300 import batch, fwi
+
+    (a,) = batch.prepare(_small_instances(1))
+    J1, g1, _, _, _ = fwi.misfit_grad(a.c, a.stf, a.x0, a.rec_iz, a.rec_ix, a.observed, ckpt_every=100,
+                                      want_src=False, **a.kw)
+    td = fwi.last_timing(a.c.device.index)
+    g = fwi.GradGraph(a.c, a.stf, a.x0, a.rec_iz, a.rec_ix, a.observed, ckpt_every=100, **a.kw)
+    try:
+        for _ in range(2):
+            g.launch()
+            g.check()
+            t = g.timing()
+            assert t.launches == td.launches > 0
+            assert t.forward_ms > 0 and t.reverse_ms > 0 and t.total_ms >= 0.999 * (t.forward_ms + t.reverse_ms)
+            assert t.fwd_step_ms > 0 and t.adj_step_ms > 0
+            assert t.store_step_ms > 0  # the instance has more than one checkpoint segment
+            assert float(g.misfit[0]) == float(J1[0]) and torch.equal(g.grad, g1)
+    finally:
+        g.close()
+
+
 def test_graph_refuses_a_relaid_workspace(fwi_lib):
     """A graph is tied to its context's workspace: after a call with another
     problem layout on the same context, launching it fails with FWI_EINVAL."""
