@@ -297,16 +297,39 @@ __global__ void k_adj_init(AcuStep p, float* lam, float* hx, float* hz, bool lap
 }
 
 // Segment fold: G (FP64, per padded cell) += sum over shots of the FP32
-// segment partials, which are reset for the next segment.
-__global__ void k_fold(float* gpart, int S, long long slice, double* G) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < slice;
+// segment partials (in shot order), which are reset for the next segment. A
+// thread takes 4 consecutive cells (the slice is a multiple of 4 floats) and
+// has the partials of 8 shots in flight before it adds them.
+__global__ void k_fold(float* __restrict__ gpart, int S, long long slice, double* __restrict__ G) {
+  const long long n4 = slice / 4;
+  float4* __restrict__ p4 = reinterpret_cast<float4*>(gpart);
+  double2* __restrict__ G2 = reinterpret_cast<double2*>(G);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int s = 0; s < S; s++) {
-      acc += (double)gpart[(long long)s * slice + i];
-      gpart[(long long)s * slice + i] = 0.f;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int s0 = 0; s0 < S; s0 += 8) {
+      const int m = min(8, S - s0);
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++)
+        if (u < m) v[u] = p4[(long long)(s0 + u) * n4 + i];
+#pragma unroll
+      for (int u = 0; u < 8; u++)
+        if (u < m) {
+          a0 += (double)v[u].x;
+          a1 += (double)v[u].y;
+          a2 += (double)v[u].z;
+          a3 += (double)v[u].w;
+          p4[(long long)(s0 + u) * n4 + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
-    G[i] += acc;
+    double2 g0 = G2[2 * i], g1 = G2[2 * i + 1];
+    g0.x += a0;
+    g0.y += a1;
+    g1.x += a2;
+    g1.y += a3;
+    G2[2 * i] = g0;
+    G2[2 * i + 1] = g1;
   }
 }
 
