@@ -241,9 +241,12 @@ fwi_status fwi_set_shot_groups(fwi_ctx *ctx, int32_t forward_groups, int32_t adj
  * place and launches again.
  *
  * fwi_misfit_grad_graph: arguments as fwi_misfit_grad (no seis_out, no stream);
- *   every buffer must be device memory (FWI_EINVAL otherwise) and stays owned
+ *   every buffer must be device memory or page-locked host memory
+ *   (cudaMallocHost / cudaHostRegister; FWI_EINVAL otherwise) and stays owned
  *   by the caller, who keeps it alive and at the same address while the graph
- *   exists. Runs the call once on the context's own stream (its results are
+ *   exists. Host buffers are read and written by the graph's own copy nodes at
+ *   every launch (inputs copied in at its start, results copied out at its
+ *   end), as a direct call with host buffers does. Runs the call once on the context's own stream (its results are
  *   left in the outputs), then records it. FWI_ENOTIMPL for elastic models.
  *   The graph uses ctx's workspace: it is valid until a call on ctx needs a
  *   larger workspace or a different problem layout, after which

@@ -901,14 +901,15 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   return v;
 }
 
-bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p, bool or_pinned_host = false) {
   if (!p) return true;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+         (or_pinned_host && a.type == cudaMemoryTypeHost);
 }
 
 }  // namespace
@@ -961,7 +962,8 @@ fwi_status fwi_misfit_grad_graph(fwi_ctx* ctx, const fwi_model* M, const fwi_sou
   if (v != FWI_OK) return v;
   const void* ptrs[] = {M->vp, Sv->x0, Sv->stf, R->iz, R->ix, observed, misfit, grad, grad_stf, grad_x0};
   for (const void* p : ptrs)
-    if (!is_device_ptr(p)) return fail(FWI_EINVAL, "every buffer of a recorded call must be device memory");
+    if (!is_device_ptr(p, true))
+      return fail(FWI_EINVAL, "every buffer of a recorded call must be device memory or page-locked host memory");
   CK(cudaSetDevice(ctx->device));
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   cudaStream_t cs = ctx->cap_stream;

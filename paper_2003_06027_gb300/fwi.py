@@ -322,27 +322,52 @@ class GradGraph:
     """One acoustic misfit/gradient evaluation recorded as a CUDA graph
     (fwi_misfit_grad_graph) on a library context of its own.
 
-    All arguments must be device tensors; they are kept referenced and are read
-    again at every launch, so an inversion updates ``c`` in place and launches
-    again. Outputs live in ``self.misfit``, ``self.grad`` (and ``grad_stf``,
-    ``grad_x0`` when ``want_src``). ``groups`` = (forward, adjoint) shot groups
-    of the recorded launches (0: default). Recording runs the evaluation once."""
+    The arguments are either all CUDA tensors or all page-locked (pinned) host
+    tensors of the call's own dtypes (float32; int32 receiver indices) on the
+    CUDA device ``device`` (default: the current one). They are kept referenced
+    and are read again at every launch, so an inversion updates ``c`` in place
+    and launches again; with host tensors the graph's copy nodes move the inputs
+    in and the results out at every launch. Outputs live in ``self.misfit``,
+    ``self.grad`` (and ``grad_stf``, ``grad_x0`` when ``want_src``), in the
+    inputs' memory kind. ``groups`` = (forward, adjoint) shot groups of the
+    recorded launches (0: default). Recording runs the evaluation once."""
 
     def __init__(self, c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
                  pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_POINT, op=FWI_OP_DIVERGENCE, ckpt_every=100,
                  want_src=False,
-                 groups=(0, 0), tile_rows=0):
-        for t in (c, stf, x0, rec_iz, rec_ix, observed):
-            if not (_is_torch(t) and t.is_cuda):
-                raise ValueError("GradGraph takes CUDA tensors only")
+                 groups=(0, 0), tile_rows=0, device=None):
+        import torch
+
+        ts = (c, stf, x0, rec_iz, rec_ix, observed)
+        if not all(_is_torch(t) for t in ts):
+            raise ValueError("GradGraph takes torch tensors")
+        host = not c.is_cuda
+        if host:
+            # a converted copy would not see the caller's in-place updates: the
+            # host tensors must already be pinned, contiguous and of the call's dtypes
+            want = (torch.float32, torch.float32, torch.float32, torch.int32, torch.int32, torch.float32)
+            for t, dt_ in zip(ts, want):
+                if t.is_cuda or not t.is_pinned() or t.dtype != dt_ or not t.is_contiguous():
+                    raise ValueError("GradGraph host inputs must all be pinned, contiguous, float32 "
+                                     "(int32 receiver indices)")
+        elif not all(t.is_cuda for t in ts):
+            raise ValueError("GradGraph takes CUDA tensors, or pinned host tensors, not a mix")
         self._a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
         a = self._a
         self._obs = _arr(observed, np.float32)
-        self.device = a.c.device.index
-        self.misfit = _empty_like_place(a.c, (1,), np.float64)
-        self.grad = _empty_like_place(a.c, tuple(a.c.shape))
-        self.grad_stf = _empty_like_place(a.c, (a.S, a.nt)) if want_src else None
-        self.grad_x0 = _empty_like_place(a.c, (a.S, 2)) if want_src else None
+        if host:
+            self.device = torch.cuda.current_device() if device is None else int(device)
+            place = lambda shape, dtype=torch.float32: torch.empty(shape, dtype=dtype).pin_memory()
+            self.misfit = place((1,), torch.float64)
+            self.grad = place(tuple(a.c.shape))
+            self.grad_stf = place((a.S, a.nt)) if want_src else None
+            self.grad_x0 = place((a.S, 2)) if want_src else None
+        else:
+            self.device = a.c.device.index
+            self.misfit = _empty_like_place(a.c, (1,), np.float64)
+            self.grad = _empty_like_place(a.c, tuple(a.c.shape))
+            self.grad_stf = _empty_like_place(a.c, (a.S, a.nt)) if want_src else None
+            self.grad_x0 = _empty_like_place(a.c, (a.S, 2)) if want_src else None
         L = library()
         self._L = L
         self.ctx = ctypes.c_void_p()

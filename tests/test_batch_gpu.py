@@ -117,6 +117,41 @@ def test_graph_replay_reports_phase_times(fwi_lib):
         g.close()
 
 
+def test_graph_on_pinned_host_buffers(fwi_lib):
+    """A gradient recorded on page-locked host tensors copies its inputs in and
+    its results out at every replay: it gives the device-buffer call's misfit
+    and gradients bit for bit, follows an in-place update of the host model on
+    the next replay, and refuses pageable or mixed inputs."""
+    import torch
+
+    from paper_2003_06027_gb300 import batch, fwi
+
+    (a,) = batch.prepare(_small_instances(1))
+    pin = lambda t: t.detach().cpu().contiguous().pin_memory()
+    h = [pin(a.c), pin(a.stf), pin(a.x0), pin(a.rec_iz.to(torch.int32)), pin(a.rec_ix.to(torch.int32)),
+         pin(a.observed)]
+    g = fwi.GradGraph(*h, ckpt_every=100, want_src=True, **a.kw)
+    try:
+        assert not g.grad.is_cuda and g.grad.is_pinned()
+        for scale in (1.0, 1.01):
+            if scale != 1.0:
+                h[0].mul_(scale)  # the next replay reads the updated host model
+            st = torch.cuda.current_stream()
+            g.launch(st)
+            g.check(st)
+            J, gc, gs, gx, _ = fwi.misfit_grad(h[0].cuda(), a.stf, a.x0, a.rec_iz, a.rec_ix, a.observed,
+                                               ckpt_every=100, **a.kw)
+            assert float(g.misfit[0]) == float(J[0])
+            assert torch.equal(g.grad, gc.cpu()) and torch.equal(g.grad_stf, gs.cpu())
+            assert torch.equal(g.grad_x0, gx.cpu())
+    finally:
+        g.close()
+    with pytest.raises(ValueError):
+        fwi.GradGraph(a.c.cpu(), *h[1:], ckpt_every=100, **a.kw)  # pageable model
+    with pytest.raises(ValueError):
+        fwi.GradGraph(a.c, *h[1:], ckpt_every=100, **a.kw)  # device and host mixed
+
+
 def test_graph_refuses_a_relaid_workspace(fwi_lib):
     """A graph is tied to its context's workspace: after a call with another
     problem layout on the same context, launching it fails with FWI_EINVAL."""
