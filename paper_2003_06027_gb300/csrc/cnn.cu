@@ -119,13 +119,18 @@ __global__ void __launch_bounds__(256) k_im2col_t(const float* __restrict__ x, c
 // pixel's 144 taps of the chunk as 18 runs of 16 bytes (288 bytes, whole
 // 32-byte sectors when the row stride is a multiple of 288 bytes, as for 16
 // channels or a multiple: no sector is shared between two blocks' writes).
-// Taps in [K9, ldk) are written as zeros. Dynamic shared memory:
-// IM_CC * 3 * (64 sw + 2) floats.
+// Thread (run v, pixel group g) of the 288 writes run v of pixels g, g+16,
+// g+32, g+48: the 8 taps of its run, and so their shared-memory offsets, are
+// the same for all four, computed once. Taps in [K9, ldk) are written as zeros
+// (their staged channels are zero). Dynamic shared memory: IM_CC * 3 * (64 sw +
+// 2) floats.
 constexpr int IM_CC = 16;   // channels per block
 constexpr int IM_VPP = IM_CC * 9 / 8;  // 16-byte runs per pixel
 constexpr int IM_PIX = 64;  // output columns per block
-__global__ void __launch_bounds__(256) k_im2col_rows_t(const float* __restrict__ x, const ConvDims d, int ldk,
-                                                       uint16_t* __restrict__ colT) {
+constexpr int IM_GRP = 16;  // pixel groups: IM_VPP x IM_GRP threads
+constexpr int IM_T_THREADS = IM_VPP * IM_GRP;
+__global__ void __launch_bounds__(IM_T_THREADS) k_im2col_rows_t(const float* __restrict__ x, const ConvDims d, int ldk,
+                                                                uint16_t* __restrict__ colT) {
   extern __shared__ float xs[];  // [IM_CC][3][JW]
   const int row = blockIdx.x;    // b * Ho + i
   const int j0 = blockIdx.y * IM_PIX, c0 = blockIdx.z * IM_CC;
@@ -133,30 +138,38 @@ __global__ void __launch_bounds__(256) k_im2col_rows_t(const float* __restrict__
   const int i = row - (int)b * d.Ho;
   const int JW = IM_PIX * d.sw + 2, s0 = d.sw * j0 - 1;
   const long long plane = (long long)d.B * d.H * d.W;
-  for (int e = threadIdx.x; e < IM_CC * 3 * JW; e += 256) {  // all staging loads independent
-    const int cp = e / JW, col = e - cp * JW;
-    const int cc = cp / 3, p = cp - 3 * cc, c = c0 + cc, r = d.sh * i + p - 1, s = s0 + col;
-    xs[e] = (c < d.C && r >= 0 && r < d.H && s >= 0 && s < d.W)
-                ? __ldg(x + c * plane + ((long long)b * d.H + r) * d.W + s)
-                : 0.f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int cp = warp; cp < IM_CC * 3; cp += IM_T_THREADS / 32) {  // staged row (channel, tap row)
+    const int cc = cp / 3, p = cp - 3 * cc, c = c0 + cc, r = d.sh * i + p - 1;
+    const bool rok = c < d.C && r >= 0 && r < d.H;
+    const float* src = rok ? x + c * plane + ((long long)b * d.H + r) * d.W : x;
+    for (int col = lane; col < JW; col += 32) {
+      const int sc = s0 + col;
+      xs[cp * JW + col] = (rok && sc >= 0 && sc < d.W) ? __ldg(src + sc) : 0.f;
+    }
   }
   __syncthreads();
+  const int vv = threadIdx.x % IM_VPP, grp = threadIdx.x / IM_VPP;
+  const int k0 = c0 * 9 + 8 * vv;
+  if (k0 >= ldk) return;
+  int off[8];
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    const int t = 8 * vv + u;  // tap within the chunk: (cc, p, q)
+    const int cc = t / 9, pq = t - 9 * cc, p = pq / 3, q = pq - 3 * p;
+    off[u] = (3 * cc + p) * JW + q;
+  }
   const long long pix0 = (long long)row * d.Wo;
-  for (int v = threadIdx.x; v < IM_PIX * IM_VPP; v += 256) {
-    const int jl = v / IM_VPP, vv = v - IM_VPP * jl, j = j0 + jl;
-    const int k0 = c0 * 9 + 8 * vv;
-    if (j >= d.Wo || k0 >= ldk) continue;
+#pragma unroll
+  for (int k = 0; k < IM_PIX / IM_GRP; k++) {
+    const int jl = grp + IM_GRP * k, j = j0 + jl;
+    if (j >= d.Wo) break;
+    const float* xl = xs + d.sw * jl;
     uint32_t w[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      uint32_t h2[2];
-#pragma unroll
-      for (int e = 0; e < 2; e++) {
-        const int t = 8 * vv + 2 * u + e;  // tap within the chunk: (cc, p, q)
-        const int cc = t / 9, pq = t - 9 * cc, p = pq / 3, q = pq - 3 * p;
-        h2[e] = to_bf16_bits(xs[(3 * cc + p) * JW + d.sw * jl + q]);
-      }
-      w[u] = h2[0] | (h2[1] << 16);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(xl[off[2 * u]], xl[off[2 * u + 1]]);
+      w[u] = *reinterpret_cast<const uint32_t*>(&h);
     }
     *reinterpret_cast<uint4*>(colT + (pix0 + j) * ldk + k0) = make_uint4(w[0], w[1], w[2], w[3]);
   }
@@ -202,6 +215,48 @@ __global__ void __launch_bounds__(256) k_im2col_rows_n(const float* __restrict__
     } else {
       for (int u = 0; u < 4 && 4 * jq + u < d.Wo; u++) dst[u] = v[u];
     }
+  }
+}
+
+// The row-staged tap-major im2col for output rows of a multiple of 8 pixels
+// (Wo = 8 W8): the staging of k_im2col_rows_n, then item e = (row rl, tap kk,
+// 8-pixel group j8) with j8 fastest, decoded by multiply-shift, writes 8
+// pixels of one tap row as one 16-byte store (consecutive threads, consecutive
+// 16-byte runs of the row).
+__global__ void __launch_bounds__(256) k_im2col_rows_n8(const float* __restrict__ x, const ConvDims d, int R,
+                                                        long long ldn, FastDiv fW8, uint16_t* __restrict__ col) {
+  extern __shared__ float xs[];  // [R][3][JW]
+  const int c = blockIdx.y, row0 = blockIdx.x * R;
+  const int nrows = min(R, d.B * d.Ho - row0);
+  const int JW = d.sw * d.Wo + 2;
+  const float* xc = x + (long long)c * d.B * d.H * d.W;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rp = warp; rp < nrows * 3; rp += 8) {  // staged row (output row, tap row)
+    const int rl = rp / 3, p = rp - 3 * rl, row = row0 + rl;
+    const uint32_t b = d.fHo.div((uint32_t)row);
+    const int i = row - (int)b * d.Ho, r = d.sh * i + p - 1;
+    const bool rok = r >= 0 && r < d.H;
+    const float* src = rok ? xc + ((long long)b * d.H + r) * d.W : xc;
+    for (int colx = lane; colx < JW; colx += 32) {
+      const int sc = colx - 1;
+      xs[rp * JW + colx] = (rok && sc >= 0 && sc < d.W) ? __ldg(src + sc) : 0.f;
+    }
+  }
+  __syncthreads();
+  const int W8 = (int)fW8.d;
+  for (int e = threadIdx.x; e < nrows * 9 * W8; e += 256) {
+    const uint32_t t = fW8.div((uint32_t)e);
+    const int j8 = e - (int)t * W8, rl = (int)t / 9, kk = (int)t - 9 * rl;
+    const int p = kk / 3, q = kk - 3 * p;
+    const float* xr = xs + (3 * rl + p) * JW + q + 8 * d.sw * j8;
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(xr[d.sw * (2 * u)], xr[d.sw * (2 * u + 1)]);
+      w[u] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const long long n0 = (long long)(row0 + rl) * d.Wo + 8 * j8;
+    *reinterpret_cast<uint4*>(col + (long long)(9 * c + kk) * ldn + n0) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -510,7 +565,7 @@ cudaError_t im2col_t(const float* x, const fwi::ConvDims& d, int ldk, uint16_t* 
   if (smem <= 48 * 1024 && d.C <= 65535 * fwi::IM_CC) {
     const dim3 grid((unsigned)rows, (unsigned)((d.Wo + fwi::IM_PIX - 1) / fwi::IM_PIX),
                     (unsigned)((d.C + fwi::IM_CC - 1) / fwi::IM_CC));
-    fwi::k_im2col_rows_t<<<grid, 256, smem, st>>>(x, d, ldk, colT);
+    fwi::k_im2col_rows_t<<<grid, fwi::IM_T_THREADS, smem, st>>>(x, d, ldk, colT);
   } else {
     fwi::k_im2col_t<<<dim3((d.Npix + 63) / 64, (ldk + 63) / 64), 256, 0, st>>>(x, d, ldk, colT);
   }
@@ -520,7 +575,10 @@ cudaError_t im2col_n(const float* x, const fwi::ConvDims& d, long long ldn, uint
   const int R = std::max(1, std::min(16, 1024 / std::max(1, d.Wo)));
   const size_t smem = (size_t)R * 3 * (d.sw * d.Wo + 2) * sizeof(float);
   const int rows = d.B * d.Ho;
-  if (smem <= 48 * 1024 && d.C <= 65535) {
+  if (smem <= 48 * 1024 && d.C <= 65535 && d.Wo % 8 == 0) {
+    fwi::k_im2col_rows_n8<<<dim3((unsigned)((rows + R - 1) / R), (unsigned)d.C), 256, smem, st>>>(
+        x, d, R, ldn, fwi::FastDiv((uint32_t)(d.Wo / 8)), col);
+  } else if (smem <= 48 * 1024 && d.C <= 65535) {
     fwi::k_im2col_rows_n<<<dim3((unsigned)((rows + R - 1) / R), (unsigned)d.C), 256, smem, st>>>(x, d, R, ldn, col);
   } else {
     fwi::k_im2col_n<<<dim3((d.Npix + 1023) / 1024, d.K9), 256, 0, st>>>(x, d, ldn, col);

@@ -81,6 +81,7 @@ SHAPES = [  # C, B, H, W, O, sh, sw, relu
     (32, 1, 9, 33, 4, 2, 1, True),
     (64, 2, 16, 32, 32, 1, 1, True),
     (20, 3, 7, 40, 24, 1, 1, False),
+    (8, 3, 20, 64, 4, 2, 2, True),  # stride 2, 8-pixel tap-major runs over two staged row blocks
     # rows wider than the row-staged im2col's shared memory, and a column stride of 8:
     # the per-element im2col kernels
     (2, 1, 5, 4100, 3, 1, 1, True),
