@@ -193,7 +193,8 @@ fwi_status fwi_forward_vjp(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
  * P = ceil(Nx/64)*64 + 16 columns (the padded grid Nz x Nx, tile-aligned,
  * with an 8-cell apron): per gradient call 6 per checkpoint (ceil(nt/K) of
  * them, acoustic; 13 elastic) and 2 per step of a segment (K of them,
- * acoustic; 5 elastic). Host arithmetic only: no device is touched; inputs are
+ * acoustic; 1 with FWI_OP_LAPLACIAN, whose storing step keeps one field; 5
+ * elastic). Host arithmetic only: no device is touched; inputs are
  * validated as by the call (FWI_EINVAL, FWI_ENOTIMPL). */
 fwi_status fwi_workspace_bytes(const fwi_model *model, const fwi_sources *src,
                                const fwi_receivers *rec, int32_t nt, int32_t ckpt_every,

@@ -104,6 +104,7 @@ struct Plan {
   int L = 0;  // cells of a line source (FWI_SRC_LINE), else 0
   bool grad = false;
   int tablen = 0;
+  int slot_fields = 2;  // fields a segment slot keeps per step: p_x, p_z (divergence form) or r (c^2 Laplacian)
   // base
   float *m = nullptr, *tab = nullptr, *c = nullptr, *stf = nullptr, *x0 = nullptr, *src_w = nullptr;
   int *src_box = nullptr, *rec_in = nullptr, *rec_cell = nullptr, *rec_key = nullptr, *tstart = nullptr;
@@ -180,7 +181,7 @@ void layout(Plan& P, char* base) {
     P.gstf = (float*)take(stf_len * 4);
     P.gx0 = (float*)take((size_t)P.S * 2 * 4);
     P.ckpt = (float*)take(field * 6 * (size_t)P.nseg);
-    P.slot = (float*)take(field * 2 * (size_t)P.K);  // per step: p_x, p_z
+    P.slot = (float*)take(field * (size_t)P.slot_fields * (size_t)P.K);  // per step: p_x, p_z, or r
   }
   P.bytes = (off + 255) & ~size_t(255);
 }
@@ -253,12 +254,13 @@ void make_plan(Plan& P, const fwi_model* M, const fwi_sources* Sv, const fwi_rec
   P.K = grad ? K : 0;
   P.nseg = grad ? (nt + K - 1) / K : 0;
   P.tablen = std::max(g.ntx * TILE_X, g.rows - 2 * APRON) + 2 * APRON + 2 * TAB_OFF;
+  P.slot_fields = M->op == FWI_OP_LAPLACIAN ? 1 : 2;
 }
 
 std::string plan_key(const Plan& P) {
   char b[256];
-  snprintf(b, sizeof b, "%d %d %d %d %lld %d %d %d %d %d %d %d", P.g.Nz, P.g.Nx, P.g.pitch, P.g.rows, P.g.slice,
-           P.S, P.nt, P.nrec, P.K, (int)P.grad, P.tablen, P.L);
+  snprintf(b, sizeof b, "%d %d %d %d %lld %d %d %d %d %d %d %d %d", P.g.Nz, P.g.Nx, P.g.pitch, P.g.rows, P.g.slice,
+           P.S, P.nt, P.nrec, P.K, (int)P.grad, P.tablen, P.L, P.slot_fields);
   return b;
 }
 
@@ -796,8 +798,8 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     set_fwd_state(P, p, n);
     const bool keep = n >= nlast;
     if (keep) {
-      p.slot_px = P.slot + (size_t)(n - nlast) * 2 * field;
-      p.slot_pz = p.slot_px + field;
+      p.slot_px = P.slot + (size_t)(n - nlast) * P.slot_fields * field;
+      p.slot_pz = lap ? nullptr : p.slot_px + field;
     }
     for (int g = 0; g < gr.G; g++) {
       LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, true, keep, fwd_tz(ctx), gr.st[g], lap));
@@ -836,8 +838,8 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
                              cudaMemcpyDeviceToDevice, gr.st[g]));
       for (int n = n0; n < n1; n++) {
         set_fwd_state(P, p, n);
-        p.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
-        p.slot_pz = p.slot_px + field;
+        p.slot_px = P.slot + (size_t)(n - n0) * P.slot_fields * field;
+        p.slot_pz = lap ? nullptr : p.slot_px + field;
         for (int g = 0; g < gr.G; g++) {
           LK(1, launch_acu_fwd_tz(group_view(p, P, gr.s0[g], gr.n[g]), maps, false, true, fwd_tz(ctx), gr.st[g], lap));
           if (P.L > 0)
@@ -853,8 +855,8 @@ fwi_status acu_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
     for (int n = n1 - 1; n >= n0; n--) {
       pa.n = n;
       pa.cur = (n + 1) & 1;  // lambda_{n+1}; lambda_{n+2} -> lambda_n in the other buffer
-      pa.slot_px = P.slot + (size_t)(n - n0) * 2 * field;
-      pa.slot_pz = pa.slot_px + field;
+      pa.slot_px = P.slot + (size_t)(n - n0) * P.slot_fields * field;
+      pa.slot_pz = lap ? nullptr : pa.slot_px + field;
       pa.zx_in = P.zx[(n + 1) & 1];
       pa.zx_out = P.zx[n & 1];
       pa.zz_in = P.zz[(n + 1) & 1];

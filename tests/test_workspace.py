@@ -33,15 +33,19 @@ def _elastic(nt=50, S=2):
     return d, args, kw
 
 
-@pytest.mark.parametrize("physics", ["acoustic", "elastic"])
+@pytest.mark.parametrize("physics", ["acoustic", "laplacian", "elastic"])
 def test_workspace_grows_by_the_documented_fields(physics):
     """Between two intervals K and K + 1 the workspace changes by the segment
     fields of one more step, less the checkpoints of the segments saved:
-    (2 or 5) F per step and (6 or 13) F per checkpoint, F one field of all
-    shots on the tile-aligned slice (to the 256-byte alignment of the layout)."""
-    if physics == "acoustic":
+    (2, 1 for the c^2 Laplacian operator, or 5) F per step and (6 or 13) F per
+    checkpoint, F one field of all shots on the tile-aligned slice (to the
+    256-byte alignment of the layout)."""
+    if physics in ("acoustic", "laplacian"):
         d, args, kw = _acoustic()
         ws, per_step, per_ckpt, S, align = fwi.workspace_bytes, 2, 6, d["stf"].shape[0], 64
+        if physics == "laplacian":
+            kw = dict(kw, op=fwi.FWI_OP_LAPLACIAN)
+            per_step = 1
     else:
         d, args, kw = _elastic()
         ws, per_step, per_ckpt, S, align = fwi.workspace_bytes_elastic, 5, 13, d["stf"].shape[0], 32
