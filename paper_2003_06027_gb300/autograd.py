@@ -148,11 +148,12 @@ class ElasticSeismograms(torch.autograd.Function):
 
 
 def acoustic_seismograms(c, stf, x0, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3, pml_vmax=4500.0,
-                         pml_f0=10.0, src_kind=fwi.FWI_SRC_POINT, ckpt_every=100):
+                         pml_f0=10.0, src_kind=fwi.FWI_SRC_POINT, op=fwi.FWI_OP_DIVERGENCE, ckpt_every=100):
     """Differentiable acoustic seismograms [S][nrec][nt] (float32, on c's device);
-    ``ckpt_every`` is the checkpoint interval of the backward sweep."""
+    ``ckpt_every`` is the checkpoint interval of the backward sweep, ``op`` the
+    acoustic operator (divergence form or c^2 Laplacian)."""
     opts = dict(dx=dx, dz=dz, dt=dt, order=order, npml=npml, pml_R=pml_R, pml_vmax=pml_vmax, pml_f0=pml_f0,
-                src_kind=src_kind, ckpt_every=ckpt_every)
+                src_kind=src_kind, op=op, ckpt_every=ckpt_every)
     return AcousticSeismograms.apply(c, stf, x0, rec_iz, rec_ix, opts)
 
 
@@ -165,10 +166,11 @@ def elastic_seismograms(vp, vs, rho, stf, x0, mt, rec_iz, rec_ix, *, dx, dz, dt,
 
 
 def acoustic_misfit(c, stf, x0, observed, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
-                    pml_vmax=4500.0, pml_f0=10.0, src_kind=fwi.FWI_SRC_POINT, ckpt_every=100):
+                    pml_vmax=4500.0, pml_f0=10.0, src_kind=fwi.FWI_SRC_POINT, op=fwi.FWI_OP_DIVERGENCE,
+                    ckpt_every=100):
     """Differentiable acoustic misfit (a 0-d float64 tensor on c's device)."""
     opts = dict(dx=dx, dz=dz, dt=dt, order=order, npml=npml, pml_R=pml_R, pml_vmax=pml_vmax, pml_f0=pml_f0,
-                src_kind=src_kind, ckpt_every=ckpt_every)
+                src_kind=src_kind, op=op, ckpt_every=ckpt_every)
     return AcousticMisfit.apply(c, stf, x0, observed, rec_iz, rec_ix, opts)
 
 

@@ -176,6 +176,27 @@ def test_acoustic_seismogram_vjp_matches_oracle(fwi_lib):
     assert rel(c.grad.cpu().numpy(), go2) <= GRAD_TOL, rel(c.grad.cpu().numpy(), go2)
 
 
+def test_laplacian_seismogram_vjp_matches_oracle(fwi_lib):
+    """The same seismogram operator with the c^2 Laplacian operator (op 1):
+    backward with a random upstream gradient against the oracle's op-1 adjoint
+    seeded with it, on a grid of several tiles with an interior one."""
+    from paper_2003_06027_gb300.autograd import acoustic_seismograms
+
+    d = dict(synth.random_acoustic(47, 70, 150, 110, 2, 8, 10, src_kind=1, nrec=9), op=1)
+    g = dict(_geom(d), op=1)
+    c, stf, x0 = _cuda(d["c"], True), _cuda(d["stf"], True), _cuda(d["x0"], True)
+    seis = acoustic_seismograms(c, stf, x0, _cuda(d["rec_iz"]), _cuda(d["rec_ix"]), **_kw(d, 40))
+    do = oracle.acoustic_forward(g, np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]))
+    assert rel(seis.detach().cpu().numpy(), do) <= SEIS_TOL
+    v = np.random.default_rng(47).standard_normal(do.shape).astype(np.float32)
+    seis.backward(_cuda(v))
+    go, gso, gxo = oracle.acoustic_adjoint(g, np.float64(d["c"]), np.float64(d["stf"]), np.float64(d["x0"]),
+                                           np.float64(v))
+    assert rel(c.grad.cpu().numpy(), go) <= GRAD_TOL, rel(c.grad.cpu().numpy(), go)
+    assert rel(stf.grad.cpu().numpy(), gso) <= GRAD_TOL, rel(stf.grad.cpu().numpy(), gso)
+    assert rel(x0.grad.cpu().numpy(), gxo) <= GRAD_TOL, rel(x0.grad.cpu().numpy(), gxo)
+
+
 def test_forward_vjp_value_is_the_inner_product(fwi_lib):
     """fwi_forward_vjp's scalar is <d, v> in FP64, and v = d - d_obs reproduces
     fwi_misfit_grad's gradient bit for bit (the same sweep, the same seed)."""
