@@ -49,6 +49,13 @@ fwi_status fwi_cnn_destroy(fwi_cnn *h);
  * this handle gave up a bounded wait since the last check, else FWI_OK. */
 fwi_status fwi_cnn_check(fwi_cnn *h, void *cuda_stream);
 
+/* How the convolution GEMMs of the forward pass and of the stride-1 data
+ * gradient get their tap operand: on != 0 (the default) gathers it from the
+ * activations into the GEMM's shared-memory stages (no im2col matrix in device
+ * memory); 0 builds the im2col matrix first and has TMA stage it. Both give the
+ * same BF16 operand and the same results bit for bit. FWI_EINVAL if h is NULL. */
+fwi_status fwi_cnn_set_conv_gather(fwi_cnn *h, int32_t on);
+
 /* The tensor-core GEMM itself: out[n][m] = act(sum_k A[m][k] B[n][k] + bias[n]).
  * A: M rows of K BF16 values, row stride lda; B: N rows of K BF16 values, row
  * stride ldb (lda, ldb multiples of 8 and >= K; A, B 16-byte aligned).

@@ -499,6 +499,7 @@ struct fwi_cnn {
   size_t ws_bytes = 0;
   int* status = nullptr;  // device status word of the GEMMs (timeout bit)
   double* red = nullptr;  // block partials of the loss reduction
+  bool gather = true;     // forward / stride-1 data-gradient GEMMs gather their tap operand (no im2col matrix)
 };
 
 namespace {
@@ -636,6 +637,12 @@ fwi_status fwi_cnn_check(fwi_cnn* h, void* stream) {
   return FWI_OK;
 }
 
+fwi_status fwi_cnn_set_conv_gather(fwi_cnn* h, int32_t on) {
+  if (!h) return fwi::host_fail(FWI_EINVAL, "h must not be NULL");
+  h->gather = on != 0;
+  return FWI_OK;
+}
+
 fwi_status fwi_cnn_gemm_bt(fwi_cnn* h, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, int64_t M,
                            int32_t N, int64_t K, float* out, int64_t ldo, const float* bias, int32_t relu,
                            int32_t splits, void* stream) {
@@ -674,16 +681,19 @@ fwi_status fwi_cnn_conv_forward(fwi_cnn* h, const float* x, int32_t C, int32_t B
   CNN_CK(cudaSetDevice(h->device), "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
   const int ldk = (int)fwi::round8(d.K9);
+  const bool gather = h->gather;
   Carve cv;
-  const size_t o_col = cv.take((size_t)d.Npix * ldk * 2), o_wp = cv.take((size_t)O * ldk * 2);
+  const size_t o_col = cv.take(gather ? 0 : (size_t)d.Npix * ldk * 2), o_wp = cv.take((size_t)O * ldk * 2);
   if ((v = ws_reserve(h, cv.off)) != FWI_OK) return v;
   char* ws = (char*)h->ws;
   uint16_t* colT = (uint16_t*)(ws + o_col);
   uint16_t* Wp = (uint16_t*)(ws + o_wp);
   fwi::k_wprep<<<blocks_for((long long)O * d.K9), 256, 0, st>>>(w_bf16, O, d.K9, ldk, 0, Wp, nullptr);
   CNN_CK(cudaGetLastError(), "weight layout");
-  CNN_CK(im2col_t(x, d, ldk, colT, st), "im2col");
-  fwi::TcGemm g{colT, ldk, Wp, ldk, d.Npix, O, d.K9, y, d.Npix, 0, bias, relu, 1, h->status};
+  const fwi::TcConvA ca = fwi::tc_conv_a(x, C, B, H, W, sh, sw);
+  if (!gather) CNN_CK(im2col_t(x, d, ldk, colT, st), "im2col");
+  fwi::TcGemm g{gather ? nullptr : colT, ldk, Wp, ldk, d.Npix, O, d.K9, y, d.Npix, 0, bias, relu, 1, h->status,
+                gather ? &ca : nullptr};
   CNN_CK(fwi::tc_gemm(g, st), "conv forward GEMM");
   return FWI_OK;
 }
@@ -714,7 +724,7 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
   Carve cv;
   const size_t o_dyb = cv.take((size_t)O * ldn * 2), o_bp = cv.take((size_t)O * nchunk * 4);
   size_t colb_elems = (size_t)d.K9 * ldn;
-  if (dx) colb_elems = std::max(colb_elems, s1 ? (size_t)dd.Npix * ldf : (size_t)d.Npix * ldo);
+  if (dx) colb_elems = std::max(colb_elems, s1 ? (h->gather ? 0 : (size_t)dd.Npix * ldf) : (size_t)d.Npix * ldo);
   const size_t o_col = cv.take(colb_elems * 2);
   const size_t o_wt = cv.take(dx ? (size_t)(s1 ? C * ldf : d.K9 * ldo) * 2 : 0);
   const size_t o_dcol = cv.take(dx && !s1 ? (size_t)d.K9 * d.Npix * 4 : 0);
@@ -739,8 +749,10 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn* h, const float* x, int32_t C, int32_t 
     // im2col of dy (BF16, the same rounding as dyb) and one GEMM, no dcol / col2im
     fwi::k_wflip<<<blocks_for(9LL * O * C), 256, 0, st>>>(w_bf16, O, C, ldf, Wf);
     CNN_CK(cudaGetLastError(), "weight flip");
-    CNN_CK(im2col_t(dy, dd, ldf, colb, st), "im2col of dy");
-    fwi::TcGemm g{colb, ldf, Wf, ldf, dd.Npix, C, dd.K9, dx, dd.Npix, 0, nullptr, 0, 1, h->status};
+    const fwi::TcConvA ca = fwi::tc_conv_a(dy, O, B, H, W, 1, 1);
+    if (!h->gather) CNN_CK(im2col_t(dy, dd, ldf, colb, st), "im2col of dy");
+    fwi::TcGemm g{h->gather ? nullptr : colb, ldf, Wf, ldf, dd.Npix, C, dd.K9, dx, dd.Npix, 0, nullptr, 0, 1,
+                  h->status, h->gather ? &ca : nullptr};
     CNN_CK(fwi::tc_gemm(g, st), "conv data-gradient GEMM");
   } else if (dx) {
     // dcol[k][pix] = sum_o dyT[pix][o] W[o][k], then the col2im gather

@@ -20,6 +20,7 @@
 // records a timeout in the status word, the tile is written as NaN, and the
 // CTA frees its TMEM and exits.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,10 +90,97 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcArgs a) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ uint32_t mulhi_div(uint32_t n, unsigned long long m, uint32_t s) {
+  return (uint32_t)(((unsigned long long)n * m) >> s);
+}
+
+// The threads of a CTA: 128 (warp 0: TMEM and the TMA producer, warp 1: the
+// MMA issuer, all four: the epilogue); with a gathered A operand (CONV) 320:
+// warps 0-7 gather A (two threads per tile row, 32 taps each; warps 0-3 also
+// run the epilogue), warp 8 loads B by TMA, warp 9 issues the MMAs. Up to two
+// CONV CTAs share an SM, so that one's gather covers the other's load latency.
+template <bool CONV>
+struct TcRoles {
+  static constexpr int THREADS = CONV ? 320 : TC_THREADS;
+  static constexpr int GATHER = 2 * TC_BM;  // gathering threads (CONV)
+  static constexpr int B_WARP = CONV ? 8 : 0;
+  static constexpr int MMA_WARP = CONV ? 9 : 1;
+  static constexpr int CTAS = CONV ? 2 : 1;
+};
+
+// Gathered A rows (CONV): threads r and r + 128 build row r of every 128 x 64
+// stage tile, pixel m0 + r, each 32 of its taps (half h: k0 + 32 h .. k0 + 32 h
+// + 31), read from x (zero outside the image and beyond 9 C), rounded to BF16 as
+// the im2col kernels round them, and stored as four 16-byte chunks in the
+// layout TMA's 128-byte swizzle gives a K-major tile (chunk c of row r at
+// 16 (c ^ (r % 8)) within its 128-byte row).
+struct GatherRow {
+  long long base;  // x offset of (b, r0, s0) relative to channel 0, if m is a pixel
+  uint32_t mask;   // bit 3p + q: tap (p, q) inside the image
+  bool live;
+};
+__device__ __forceinline__ GatherRow gather_row(const TcConvA& c, long long m, long long M) {
+  GatherRow g{0, 0u, m < M};
+  if (!g.live) return g;
+  const uint32_t bi = mulhi_div((uint32_t)m, c.wo_m, c.wo_s);
+  const int j = (int)((uint32_t)m - bi * (uint32_t)c.Wo);
+  const uint32_t b = mulhi_div(bi, c.ho_m, c.ho_s);
+  const int i = (int)(bi - b * (uint32_t)c.Ho);
+  const int r0 = c.sh * i - 1, s0 = c.sw * j - 1;
+  g.base = ((long long)b * c.H + r0) * c.W + s0;
+#pragma unroll
+  for (int p = 0; p < 3; p++)
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+      if (r0 + p >= 0 && r0 + p < c.H && s0 + q >= 0 && s0 + q < c.W) g.mask |= 1u << (3 * p + q);
+  return g;
+}
+constexpr int GATHER_K = TC_BK / 2;  // taps of a row built by one gathering thread per stage
+// Tap table of a CONV CTA (shared memory, built once): for tap k < 9 C the x
+// offset of (channel c, tap row p, tap column q) relative to a pixel's base,
+// c B H W + p W + q, and its tap index 3 p + q (bit of the pixel's mask).
+struct TapTab {
+  int* off;
+  unsigned char* tap;
+};
+// Loads (into registers) the GATHER_K taps of half `half` of k-block kb for the thread's row.
+__device__ __forceinline__ void gather_load(const TcConvA& c, const GatherRow& g, const TapTab& tt, int kb, int half,
+                                            float v[GATHER_K]) {
+  const int k0 = kb * TC_BK + GATHER_K * half, K9 = 9 * c.C;
+  const float* xb = c.x + g.base;
+#pragma unroll
+  for (int kk = 0; kk < GATHER_K; kk++) {
+    const int k = min(k0 + kk, K9 - 1);  // table reads stay inside the table
+    const bool ok = g.live && k0 + kk < K9 && ((g.mask >> tt.tap[k]) & 1u);
+    v[kk] = ok ? __ldg(xb + tt.off[k]) : 0.f;
+  }
+}
+// Rounds them to BF16 and stores them as chunks 4 half .. 4 half + 3 of the row.
+__device__ __forceinline__ void gather_store(const float v[GATHER_K], int row, int half, unsigned char* dst) {
+  unsigned char* rowp = dst + row * 128;
+#pragma unroll
+  for (int cl = 0; cl < 4; cl++) {
+    const int cc = 4 * half + cl;  // 16-byte chunk of the row
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * cl + 2 * u], v[8 * cl + 2 * u + 1]);
+      w[u] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    *reinterpret_cast<uint4*>(rowp + ((cc ^ (row & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+template <bool CONV>
+__global__ void __launch_bounds__(TcRoles<CONV>::THREADS, TcRoles<CONV>::CTAS)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcArgs a,
+              const TcConvA conv) {
+  using R = TcRoles<CONV>;
   extern __shared__ unsigned char tc_smem_raw[];
-  __shared__ uint64_t full[TC_STAGES], empty[TC_STAGES], accb;
+  __shared__ uint64_t full[TC_STAGES], empty[TC_STAGES], fulla[TC_STAGES], accb;
   __shared__ uint32_t tmem_slot;
   __shared__ int err;
   // the swizzled tiles need 1024-byte alignment
@@ -100,6 +188,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* smA = tc_smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const int B_STAGE = a.BN * TC_BK * 2;
   unsigned char* smB = smA + TC_STAGES * A_STAGE;
+  TapTab tt{nullptr, nullptr};
+  if (CONV) {  // after the stages: 9 C offsets, then 9 C tap indices
+    const int K9 = 9 * conv.C;
+    tt.off = reinterpret_cast<int*>(smB + TC_STAGES * a.BN * TC_BK * 2);
+    tt.tap = reinterpret_cast<unsigned char*>(tt.off + K9);
+    const int plane = conv.B * conv.H * conv.W;
+    for (int k = threadIdx.x; k < K9; k += blockDim.x) {
+      const int ch = k / 9, t = k - 9 * ch, p = t / 3, q = t - 3 * p;
+      tt.off[k] = ch * plane + p * conv.W + q;
+      tt.tap[k] = (unsigned char)t;
+    }
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long m0 = (long long)blockIdx.x * TC_BM;
@@ -111,6 +211,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int s = 0; s < TC_STAGES; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&fulla[s], R::GATHER);  // CONV: one arrival per gathering thread
     }
     mbar_init(&accb, 1);
     err = 0;
@@ -127,8 +228,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // producer
+  if (warp == R::B_WARP && lane == 0) {
+    // TMA producer: A and B, or B alone when A is gathered
     for (int i = 0; i < nk; i++) {
       const int s = i % TC_STAGES;
       const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
@@ -136,16 +237,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         err = 1;
         break;
       }
-      mbar_expect_tx(&full[s], (uint32_t)(A_STAGE + B_STAGE));
-      tma_2d(smA + s * A_STAGE, &ta, (kb0 + i) * TC_BK, (int)m0, &full[s]);
+      mbar_expect_tx(&full[s], (uint32_t)((CONV ? 0 : A_STAGE) + B_STAGE));
+      if (!CONV) tma_2d(smA + s * A_STAGE, &ta, (kb0 + i) * TC_BK, (int)m0, &full[s]);
       tma_2d(smB + s * B_STAGE, &tb, (kb0 + i) * TC_BK, n0, &full[s]);
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == R::MMA_WARP && lane == 0) {
     // MMA issuer
     for (int i = 0; i < nk; i++) {
       const int s = i % TC_STAGES;
       const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
+      if (!mbar_wait(&full[s], ph) || (CONV && !mbar_wait(&fulla[s], ph))) {
         err = 1;
         break;
       }
@@ -158,30 +259,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_commit(&empty[s]);
     }
     tc_commit(&accb);
+  } else if (CONV && (int)threadIdx.x < R::GATHER) {
+    // A gatherers: half threadIdx.x / 128 of row threadIdx.x % 128 of every stage tile
+    const int row = threadIdx.x % TC_BM, half = threadIdx.x / TC_BM;
+    const GatherRow g = gather_row(conv, m0 + row, a.M);
+    for (int i = 0; i < nk; i++) {
+      const int s = i % TC_STAGES;
+      const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        err = 1;
+        break;
+      }
+      float v[GATHER_K];
+      gather_load(conv, g, tt, kb0 + i, half, v);
+      gather_store(v, row, half, smA + s * A_STAGE);
+      fence_proxy_async();  // the generic-proxy writes before the tensor core reads them
+      mbar_arrive(&fulla[s]);
+    }
   }
   __syncwarp();
 
-  // epilogue: TMEM lane = tile row m, column = n
-  const bool ok = mbar_wait(&accb, 0);
-  tc_fence_after();
-  __syncwarp();
-  if (!ok && lane == 0) atomicOr(a.status, ST_TIMEOUT);
-  const int row = warp * 32 + lane;
-  const long long m = m0 + row;
-  float* outp = a.out + (long long)blockIdx.z * a.split_stride;
-  const bool bad = !ok || err;
-  for (int c0 = 0; c0 < a.BN; c0 += 16) {
-    uint32_t r[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-    if (m < a.M) {
+  // epilogue (warps 0-3): TMEM lane = tile row m, column = n
+  if (warp < 4) {
+    const bool ok = mbar_wait(&accb, 0);
+    tc_fence_after();
+    __syncwarp();
+    if (!ok && lane == 0) atomicOr(a.status, ST_TIMEOUT);
+    const int row = warp * 32 + lane;
+    const long long m = m0 + row;
+    float* outp = a.out + (long long)blockIdx.z * a.split_stride;
+    const bool bad = !ok || err;
+    for (int c0 = 0; c0 < a.BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (m < a.M) {
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        const int n = n0 + c0 + j;
-        if (n < a.N) {
-          float v = bad ? __int_as_float(0x7fc00000) : __uint_as_float(r[j]);
-          if (a.bias) v += a.bias[n];
-          if (a.relu) v = fmaxf(v, 0.f);
-          outp[(long long)n * a.ldo + m] = v;
+        for (int j = 0; j < 16; j++) {
+          const int n = n0 + c0 + j;
+          if (n < a.N) {
+            float v = bad ? __int_as_float(0x7fc00000) : __uint_as_float(r[j]);
+            if (a.bias) v += a.bias[n];
+            if (a.relu) v = fmaxf(v, 0.f);
+            outp[(long long)n * a.ldo + m] = v;
+          }
         }
       }
     }
@@ -208,6 +328,32 @@ bool encode_bf16_sw128(CUtensorMap* map, const void* base, long long inner, long
 
 }  // namespace
 
+// Multiply-shift constants for floor(n / d), n < 2^31 (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", 1994): l = ceil(log2 d),
+// m = ceil(2^(32+l) / d), floor(n / d) = (n m) >> (32 + l).
+static void div_consts(uint32_t d, unsigned long long* m, uint32_t* s) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) l++;
+  *s = 32 + l;
+  *m = ((1ull << *s) + d - 1) / d;
+}
+
+TcConvA tc_conv_a(const float* x, int C, int B, int H, int W, int sh, int sw) {
+  TcConvA c;
+  c.x = x;
+  c.C = C;
+  c.B = B;
+  c.H = H;
+  c.W = W;
+  c.sh = sh;
+  c.sw = sw;
+  c.Ho = (H - 1) / sh + 1;
+  c.Wo = (W - 1) / sw + 1;
+  div_consts((uint32_t)c.Wo, &c.wo_m, &c.wo_s);
+  div_consts((uint32_t)c.Ho, &c.ho_m, &c.ho_s);
+  return c;
+}
+
 int tc_split_count(long long K, int want) {
   const long long nkb = tc_kblocks(K);
   if (want < 1) want = 1;
@@ -216,9 +362,15 @@ int tc_split_count(long long K, int want) {
 }
 
 cudaError_t tc_gemm(const TcGemm& g, cudaStream_t st) {
-  if (!g.A || !g.B || !g.out || !g.status || g.M < 1 || g.N < 1 || g.K < 1 || g.splits < 1) return cudaErrorInvalidValue;
-  if (g.lda % 8 || g.ldb % 8 || g.lda < g.K || g.ldb < g.K) return cudaErrorInvalidValue;
-  if (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15)) return cudaErrorInvalidValue;
+  const bool conv = g.conv != nullptr;
+  if ((!conv && !g.A) || !g.B || !g.out || !g.status || g.M < 1 || g.N < 1 || g.K < 1 || g.splits < 1)
+    return cudaErrorInvalidValue;
+  if (g.ldb % 8 || g.ldb < g.K || ((uintptr_t)g.B & 15)) return cudaErrorInvalidValue;
+  if (!conv && (g.lda % 8 || g.lda < g.K || ((uintptr_t)g.A & 15))) return cudaErrorInvalidValue;
+  if (conv) {  // the gathered operand must be the one the sizes describe
+    const TcConvA& c = *g.conv;
+    if (!c.x || (long long)c.B * c.Ho * c.Wo != g.M || 9LL * c.C != g.K) return cudaErrorInvalidValue;
+  }
   if (g.M > 0x7fffff00LL || g.N > 0x7fffff00) return cudaErrorInvalidValue;
   const int BN = std::min(256, (g.N + 15) / 16 * 16);
   const long long nkb = tc_kblocks(g.K);
@@ -243,13 +395,17 @@ cudaError_t tc_gemm(const TcGemm& g, cudaStream_t st) {
   a.idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
   a.tmem_cols = cols;
   CUtensorMap ta, tb;
-  if (!encode_bf16_sw128(&ta, g.A, g.K, g.M, g.lda, TC_BM) || !encode_bf16_sw128(&tb, g.B, g.K, g.N, g.ldb, BN))
-    return cudaErrorInvalidValue;
-  const int smem = TC_STAGES * (A_STAGE + BN * TC_BK * 2) + 1024;
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  if (!encode_bf16_sw128(&tb, g.B, g.K, g.N, g.ldb, BN)) return cudaErrorInvalidValue;
+  if (conv) ta = tb;  // unused: A is gathered
+  else if (!encode_bf16_sw128(&ta, g.A, g.K, g.M, g.lda, TC_BM)) return cudaErrorInvalidValue;
+  const int smem = TC_STAGES * (A_STAGE + BN * TC_BK * 2) + 1024 + (conv ? 9 * g.conv->C * 5 + 16 : 0);
   const dim3 grid((unsigned)((g.M + TC_BM - 1) / TC_BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)splits);
-  k_tc_gemm<<<grid, TC_THREADS, smem, st>>>(ta, tb, a);
+  TcConvA c{};
+  if (conv) c = *g.conv;
+  auto kern = conv ? k_tc_gemm<true> : k_tc_gemm<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, conv ? TcRoles<true>::THREADS : TcRoles<false>::THREADS, smem, st>>>(ta, tb, a, c);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,20 @@ namespace fwi {
 //   status: device int; a bounded wait that gives up ORs 32 (timeout) into it
 // Returns cudaSuccess, or the launch / tensor-map error (cudaErrorInvalidValue
 // for sizes or alignments the kernel does not take).
+// The A operand of a 3x3 convolution (padding 1, strides sh, sw) gathered
+// on the fly instead of read from an im2col matrix: A[m][k] = BF16(x[c][b][r][s])
+// for output pixel m = (b * Ho + i) * Wo + j and tap k = 9 c + 3 p + q, with
+// r = sh i + p - 1, s = sw j + q - 1, and 0 outside the image or for k >= 9 C.
+// x is FP32, channel-major [C][B][H][W]. The divisions by Wo and Ho use the
+// multiply-shift constants filled in by tc_conv_a().
+struct TcConvA {
+  const float* x;
+  int C, B, H, W, Ho, Wo, sh, sw;
+  unsigned long long wo_m, ho_m;
+  uint32_t wo_s, ho_s;
+};
+TcConvA tc_conv_a(const float* x, int C, int B, int H, int W, int sh, int sw);
+
 struct TcGemm {
   const uint16_t* A;
   long long lda;
@@ -35,6 +49,10 @@ struct TcGemm {
   int relu;
   int splits;
   int* status;
+  // if not null, A (and lda) are ignored and A is gathered from conv->x
+  // (M = B Ho Wo pixels, K = 9 C taps); the results equal those of the
+  // im2col matrix of the same layer bit for bit
+  const TcConvA* conv = nullptr;
 };
 
 cudaError_t tc_gemm(const TcGemm& g, cudaStream_t st);

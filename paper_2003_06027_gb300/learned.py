@@ -49,6 +49,7 @@ def _lib():
         L.fwi_cnn_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
         L.fwi_cnn_destroy.argtypes = [P]
         L.fwi_cnn_check.argtypes = [P, P]
+        L.fwi_cnn_set_conv_gather.argtypes = [P, i32]
         L.fwi_cnn_gemm_bt.argtypes = [P, P, i64, P, i64, i64, i32, i64, P, i64, P, i32, i32, P]
         L.fwi_cnn_conv_forward.argtypes = [P, P, i32, i32, i32, i32, P, P, i32, i32, i32, i32, P, P]
         L.fwi_cnn_conv_backward.argtypes = [P, P, i32, i32, i32, i32, P, i32, i32, i32, i32, P, P, P, P, P, P]
@@ -89,6 +90,11 @@ class Handle:
     def check(self):
         """Wait for the current stream; raise if a GEMM wait timed out."""
         _chk(_lib().fwi_cnn_check(self.h, _st()))
+
+    def set_conv_gather(self, on: bool):
+        """Gather the convolution GEMMs' tap operand in the GEMM (default) or
+        build the im2col matrix first (fwi_cnn_set_conv_gather)."""
+        _chk(_lib().fwi_cnn_set_conv_gather(self.h, int(bool(on))))
 
     def __del__(self):
         try:

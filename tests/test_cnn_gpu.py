@@ -122,6 +122,42 @@ def test_conv_forward_backward(fwi_lib, shape):
     assert np.array_equal(dw2.cpu().numpy(), dw.cpu().numpy())
 
 
+GATHER_SHAPES = SHAPES[:-2] + [  # the gathered operand also for a full 64-channel layer of the network's size class
+    (64, 2, 64, 128, 32, 1, 1, True),
+    (1, 3, 37, 29, 16, 2, 1, True),
+]
+
+
+@pytest.mark.parametrize("shape", GATHER_SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}x{s[3]}-o{s[4]}-s{s[5]}{s[6]}"
+                                                       for s in GATHER_SHAPES])
+def test_gathered_operand_equals_im2col(fwi_lib, shape):
+    """The convolution GEMMs with their tap operand gathered from the
+    activations inside the GEMM (the default) give the forward output and the
+    stride-1 data gradient of the im2col-matrix path bit for bit: the same
+    BF16 operand, the same MMA order; every tile row, edge and padding tap."""
+    import torch
+
+    from paper_2003_06027_gb300 import learned as L
+
+    C, B, H, W, O, sh, sw, relu = shape
+    rng = np.random.default_rng(C * 31 + W)
+    x = _cuda(rng.standard_normal((C, B, H, W)).astype(np.float32))
+    wb = L.to_bf16(_cuda((rng.standard_normal((O, C, 3, 3)) * 0.3).astype(np.float32)))
+    b = _cuda(rng.standard_normal(O).astype(np.float32) * 0.1)
+    out = {}
+    for gather in (True, False):
+        h = L.Handle(0)
+        h.set_conv_gather(gather)
+        y = L.conv_forward(h, x, wb, b, sh, sw, relu)
+        dy = _cuda(np.random.default_rng(7).standard_normal(tuple(y.shape)).astype(np.float32))
+        dx, dw, db = L.conv_backward(h, x, wb, y, dy, sh, sw, relu, need_dx=True)
+        h.check()
+        out[gather] = (y, dx, dw, db)
+    for a, c in zip(out[True], out[False]):
+        assert torch.equal(a, c)
+    assert torch.isfinite(out[True][0]).all()
+
+
 def test_upsample_and_mse_and_adam(fwi_lib):
     from paper_2003_06027_gb300 import learned as L
 
