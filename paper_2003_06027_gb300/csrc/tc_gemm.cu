@@ -16,6 +16,11 @@
 //     (tile rows m) with tcgen05.ld, adds the bias, applies the ReLU and writes
 //     out[n][m]: for each column n the 32 lanes of a warp store 32 consecutive
 //     m, so the transposed write is coalesced.
+// The convolution variant (CONV) gathers A instead of loading it: 256 threads
+// build each 128 x 64 A stage from the FP32 activations of a 3x3 layer in the
+// same swizzled layout, fence their shared-memory writes for the tensor core
+// and arrive on the stage's second "full" barrier, which the MMA thread also
+// waits for; warp 8 loads B by TMA, warp 9 issues the MMAs.
 // Every mbarrier wait is bounded (2^24 polls or 1 s); a wait that gives up
 // records a timeout in the status word, the tile is written as NaN, and the
 // CTA frees its TMEM and exits.
