@@ -222,13 +222,17 @@ __global__ void __launch_bounds__(256) k_im2col_rows_n(const float* __restrict__
 // (Wo = 8 W8): the staging of k_im2col_rows_n, then item e = (row rl, tap kk,
 // 8-pixel group j8) with j8 fastest, decoded by multiply-shift, writes 8
 // pixels of one tap row as one 16-byte store (consecutive threads, consecutive
-// 16-byte runs of the row).
+// 16-byte runs of the row). A staged row is kept in 8 column classes: column
+// col at (col mod 8) JW8 + col / 8 (JW8 odd), so that the threads of a warp,
+// reading the same tap of consecutive 8-pixel groups, read consecutive words.
+// Dynamic shared memory: R * 3 * 8 * JW8 floats (im2col_n8_row).
+__host__ __device__ __forceinline__ int im2col_n8_row(int JW) { return 8 * (((JW + 7) / 8) | 1); }
 __global__ void __launch_bounds__(256) k_im2col_rows_n8(const float* __restrict__ x, const ConvDims d, int R,
                                                         long long ldn, FastDiv fW8, uint16_t* __restrict__ col) {
-  extern __shared__ float xs[];  // [R][3][JW]
+  extern __shared__ float xs[];  // [R][3][8][JW8]
   const int c = blockIdx.y, row0 = blockIdx.x * R;
   const int nrows = min(R, d.B * d.Ho - row0);
-  const int JW = d.sw * d.Wo + 2;
+  const int JW = d.sw * d.Wo + 2, JWT = im2col_n8_row(JW), JW8 = JWT / 8;
   const float* xc = x + (long long)c * d.B * d.H * d.W;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int rp = warp; rp < nrows * 3; rp += 8) {  // staged row (output row, tap row)
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(256) k_im2col_rows_n8(const float* __restrict_
     const float* src = rok ? xc + ((long long)b * d.H + r) * d.W : xc;
     for (int colx = lane; colx < JW; colx += 32) {
       const int sc = colx - 1;
-      xs[rp * JW + colx] = (rok && sc >= 0 && sc < d.W) ? __ldg(src + sc) : 0.f;
+      xs[rp * JWT + (colx & 7) * JW8 + (colx >> 3)] = (rok && sc >= 0 && sc < d.W) ? __ldg(src + sc) : 0.f;
     }
   }
   __syncthreads();
@@ -248,11 +252,18 @@ __global__ void __launch_bounds__(256) k_im2col_rows_n8(const float* __restrict_
     const uint32_t t = fW8.div((uint32_t)e);
     const int j8 = e - (int)t * W8, rl = (int)t / 9, kk = (int)t - 9 * rl;
     const int p = kk / 3, q = kk - 3 * p;
-    const float* xr = xs + (3 * rl + p) * JW + q + 8 * d.sw * j8;
+    const float* xr = xs + (3 * rl + p) * JWT;
+    const int c0 = q + 8 * d.sw * j8;  // staged column of the group's first pixel
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int cu = c0 + d.sw * u;
+      v[u] = xr[(cu & 7) * JW8 + (cu >> 3)];
+    }
     uint32_t w[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(xr[d.sw * (2 * u)], xr[d.sw * (2 * u + 1)]);
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
       w[u] = *reinterpret_cast<const uint32_t*>(&h);
     }
     const long long n0 = (long long)(row0 + rl) * d.Wo + 8 * j8;
@@ -575,9 +586,10 @@ cudaError_t im2col_t(const float* x, const fwi::ConvDims& d, int ldk, uint16_t* 
 cudaError_t im2col_n(const float* x, const fwi::ConvDims& d, long long ldn, uint16_t* col, cudaStream_t st) {
   const int R = std::max(1, std::min(16, 1024 / std::max(1, d.Wo)));
   const size_t smem = (size_t)R * 3 * (d.sw * d.Wo + 2) * sizeof(float);
+  const size_t smem8 = (size_t)R * 3 * fwi::im2col_n8_row(d.sw * d.Wo + 2) * sizeof(float);
   const int rows = d.B * d.Ho;
-  if (smem <= 48 * 1024 && d.C <= 65535 && d.Wo % 8 == 0) {
-    fwi::k_im2col_rows_n8<<<dim3((unsigned)((rows + R - 1) / R), (unsigned)d.C), 256, smem, st>>>(
+  if (smem8 <= 48 * 1024 && d.C <= 65535 && d.Wo % 8 == 0) {
+    fwi::k_im2col_rows_n8<<<dim3((unsigned)((rows + R - 1) / R), (unsigned)d.C), 256, smem8, st>>>(
         x, d, R, ldn, fwi::FastDiv((uint32_t)(d.Wo / 8)), col);
   } else if (smem <= 48 * 1024 && d.C <= 65535) {
     fwi::k_im2col_rows_n<<<dim3((unsigned)((rows + R - 1) / R), (unsigned)d.C), 256, smem, st>>>(x, d, R, ldn, col);
