@@ -87,7 +87,9 @@ fwi_status fwi_cnn_conv_backward(fwi_cnn *h, const float *x, int32_t C, int32_t 
                                  const float *y, float *dy, float *dx, float *dw, float *db, void *cuda_stream);
 
 /* Nearest-neighbour 2x upsampling of the last two axes: x [C][B][H][W] -> y [C][B][2H][2W],
- * and its gradient dx [C][B][H][W] from dy [C][B][2H][2W] (sums of 2x2 blocks). */
+ * and its gradient dx [C][B][H][W] from dy [C][B][2H][2W] (sums of 2x2 blocks, in the order
+ * (dy[2r][2s] + dy[2r][2s+1]) + (dy[2r+1][2s] + dy[2r+1][2s+1])). The 2H x 2W tensor (y, or dy) must be
+ * 8-byte aligned (FWI_EINVAL otherwise). */
 fwi_status fwi_cnn_upsample2(const float *x, int32_t C, int32_t B, int32_t H, int32_t W, float *y,
                              void *cuda_stream);
 fwi_status fwi_cnn_upsample2_backward(const float *dy, int32_t C, int32_t B, int32_t H, int32_t W, float *dx,

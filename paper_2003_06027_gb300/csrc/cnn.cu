@@ -425,24 +425,35 @@ __global__ void k_split_sum(const float* __restrict__ part, int splits, long lon
   }
 }
 
+// Input row `row` (= cb H + r) of x feeds output rows 2 row and 2 row + 1 of y
+// (cb 2H + 2r = 2 row): blocks walk the input rows, threads the columns, and
+// each thread writes its value's 2 x 2 copies as two 8-byte stores (y 8-byte
+// aligned; the launcher checks).
 __global__ void k_upsample2(const float* __restrict__ x, int CB, int H, int W, float* __restrict__ y) {
-  const int W2 = 2 * W, H2 = 2 * H;
-  const long long total = (long long)CB * H2 * W2;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(e / W2), s = (int)(e - (long long)row * W2);  // row = cb * 2H + r
-    const int cb = row / H2, r = row - cb * H2;
-    y[e] = x[((long long)cb * H + (r >> 1)) * W + (s >> 1)];
+  const long long rows = (long long)CB * H, W2 = 2LL * W;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const float* xr = x + row * W;
+    float2* y0 = reinterpret_cast<float2*>(y + 2 * row * W2);
+    float2* y1 = reinterpret_cast<float2*>(y + (2 * row + 1) * W2);
+    for (int s = threadIdx.x; s < W; s += blockDim.x) {
+      const float v = __ldg(xr + s);
+      y0[s] = make_float2(v, v);
+      y1[s] = make_float2(v, v);
+    }
   }
 }
 
+// dx[row][s] = (dy[2 row][2s] + dy[2 row][2s + 1]) + (dy[2 row + 1][2s] + dy[2 row + 1][2s + 1]),
+// blocks walking the rows and threads the columns (8-byte loads; dy 8-byte aligned).
 __global__ void k_upsample2_back(const float* __restrict__ dy, int CB, int H, int W, float* __restrict__ dx) {
-  const long long total = (long long)CB * H * W;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(e / W), s = (int)(e - (long long)row * W);  // row = cb * H + r
-    const float* d = dy + (long long)row * 4 * W + 2 * s;           // (cb * 2H + 2r) * 2W + 2s
-    dx[e] = (d[0] + d[1]) + (d[2 * W] + d[2 * W + 1]);
+  const long long rows = (long long)CB * H, W2 = 2LL * W;
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const float2* d0 = reinterpret_cast<const float2*>(dy + 2 * row * W2);
+    const float2* d1 = reinterpret_cast<const float2*>(dy + (2 * row + 1) * W2);
+    for (int s = threadIdx.x; s < W; s += blockDim.x) {
+      const float2 a = __ldg(d0 + s), b = __ldg(d1 + s);
+      dx[row * W + s] = (a.x + a.y) + (b.x + b.y);
+    }
   }
 }
 
@@ -794,8 +805,11 @@ fwi_status fwi_cnn_upsample2(const float* x, int32_t C, int32_t B, int32_t H, in
   if (!x || !y) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (bad_dims(C, B, H, W)) return fwi::host_fail(FWI_EINVAL, "bad sizes");
   if ((long long)C * B * 4 * H * W > 0x7fffff00LL) return fwi::host_fail(FWI_EINVAL, "tensor too large");
+  if ((uintptr_t)y & 7) return fwi::host_fail(FWI_EINVAL, "y must be 8-byte aligned");
   const int CB = C * B;
-  fwi::k_upsample2<<<blocks_for(4LL * CB * H * W), 256, 0, (cudaStream_t)stream>>>(x, CB, H, W, y);
+  const long long rows = (long long)CB * H;
+  fwi::k_upsample2<<<(unsigned)std::min<long long>(rows, 65535LL * 16), W >= 256 ? 256 : 128, 0,
+                     (cudaStream_t)stream>>>(x, CB, H, W, y);
   CNN_CK(cudaGetLastError(), "upsample");
   return FWI_OK;
 }
@@ -805,8 +819,11 @@ fwi_status fwi_cnn_upsample2_backward(const float* dy, int32_t C, int32_t B, int
   if (!dy || !dx) return fwi::host_fail(FWI_EINVAL, "NULL pointer");
   if (bad_dims(C, B, H, W)) return fwi::host_fail(FWI_EINVAL, "bad sizes");
   if ((long long)C * B * 4 * H * W > 0x7fffff00LL) return fwi::host_fail(FWI_EINVAL, "tensor too large");
+  if ((uintptr_t)dy & 7) return fwi::host_fail(FWI_EINVAL, "dy must be 8-byte aligned");
   const int CB = C * B;
-  fwi::k_upsample2_back<<<blocks_for((long long)CB * H * W), 256, 0, (cudaStream_t)stream>>>(dy, CB, H, W, dx);
+  const long long rows = (long long)CB * H;
+  fwi::k_upsample2_back<<<(unsigned)std::min<long long>(rows, 65535LL * 16), W >= 256 ? 256 : 128, 0,
+                          (cudaStream_t)stream>>>(dy, CB, H, W, dx);
   CNN_CK(cudaGetLastError(), "upsample backward");
   return FWI_OK;
 }

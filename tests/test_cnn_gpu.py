@@ -168,6 +168,11 @@ def test_upsample_and_mse_and_adam(fwi_lib):
     d = rng.standard_normal(u.shape).astype(np.float32)
     np.testing.assert_allclose(L.upsample2_backward(_cuda(d)).cpu().numpy(), cnn.upsample2_backward(np.float64(d)),
                                rtol=1e-6, atol=1e-6)
+    xw = rng.standard_normal((4, 2, 40, 300)).astype(np.float32)  # rows wider than a block of threads
+    np.testing.assert_array_equal(L.upsample2(_cuda(xw)).cpu().numpy(), cnn.upsample2(xw))
+    dw_ = rng.standard_normal((4, 2, 80, 600)).astype(np.float32)
+    np.testing.assert_allclose(L.upsample2_backward(_cuda(dw_)).cpu().numpy(),
+                               cnn.upsample2_backward(np.float64(dw_)), rtol=1e-6, atol=1e-6)
     h = L.Handle(0)
     for n in (5000, 1_000_003):  # one block's worth, and many blocks with a ragged tail
         p, t = rng.standard_normal(n).astype(np.float32), rng.standard_normal(n).astype(np.float32)
