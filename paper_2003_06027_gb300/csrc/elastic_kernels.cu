@@ -531,9 +531,7 @@ __global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at
   const float* s_Sxz = s_Szz + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
-  constexpr int NA = TILE_Z * (W72 / 4), NB = H40 * (TILE_X / 4);
-  // the four item kinds run as separate loops, each unrolled so that a thread's
-  // items have their global loads (medium, CPML tables and memory) in flight together
+  // the halo items of each kind (the own nodes' are merged below)
   auto item_a = [&](int k) {  // (a) strain-x adjoint at normal nodes, own rows, columns [x0-4, x0+68)
     const int r = k / (W72 / 4), gq = k - r * (W72 / 4);
     const int z = z0 + r, j = x0 - 4 + 4 * gq;
@@ -586,14 +584,57 @@ __global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at
     cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[7], p.Mout[7], id, gq >= 1 && gq <= 16, t, d);
     st4(d_vzx + r * W72 + 4 * gq, a4f(d));
   };
-#pragma unroll 3
-  for (int k = tid; k < NA; k += NTHREADS) item_a(k);
-#pragma unroll 3
-  for (int k = tid; k < NB; k += NTHREADS) item_b(k);
-#pragma unroll 3
-  for (int k = tid; k < NB; k += NTHREADS) item_c(k);
-#pragma unroll 3
-  for (int k = tid; k < NA; k += NTHREADS) item_d(k);
+  // own nodes: items (a) and (b) of a normal-node group, and (c) and (d) of a
+  // shear-node group, in one pass each, so that its medium is loaded once
+  auto item_ab = [&](int k) {
+    const int r = k >> 4, c = k & 15;
+    const int z = z0 + r, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float sx[4], sz[4], la[4], lp[4], ta[4], tb[4], d[4];
+    f4a(ld4(s_Sxx + (r + 4) * W72 + 4 * c + 4), sx);
+    f4a(ld4(s_Szz + (r + 4) * W72 + 4 * c + 4), sz);
+    f4a(ldg4(p.lam + im), la);
+    f4a(ldg4(p.lp2m + im), lp);
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      ta[e] = dt * (lp[e] * sx[e] + la[e] * sz[e]);
+      tb[e] = dt * (la[e] * sx[e] + lp[e] * sz[e]);
+    }
+    cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[4], p.Mout[4], id, true, ta, d);
+    st4(d_vx + r * W72 + 4 * (c + 1), a4f(d));
+    cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[5], p.Mout[5], id, true, tb, d);
+    st4(d_vz + (r + 4) * TILE_X + 4 * c, a4f(d));
+  };
+  auto item_cd = [&](int k) {
+    const int r = k >> 4, c = k & 15;
+    const int z = z0 + r, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float sh[4], mx[4], t[4], d[4];
+    f4a(ld4(s_Sxz + (r + 4) * W72 + 4 * c + 4), sh);
+    f4a(ldg4(p.mxz + im), mx);
+#pragma unroll
+    for (int e = 0; e < 4; e++) t[e] = dt * mx[e] * sh[e];
+    cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[6], p.Mout[6], id, true, t, d);
+    st4(d_vxz + (r + 4) * TILE_X + 4 * c, a4f(d));
+    cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[7], p.Mout[7], id, true, t, d);
+    st4(d_vzx + r * W72 + 4 * (c + 1), a4f(d));
+  };
+  constexpr int NOWN = TILE_Z * (TILE_X / 4);  // own 4-node groups: 512
+#pragma unroll 2
+  for (int k = tid; k < NOWN; k += NTHREADS) item_ab(k);
+#pragma unroll 2
+  for (int k = tid; k < NOWN; k += NTHREADS) item_cd(k);
+  // halo nodes: the two halo column groups of every own row (items a, d) and
+  // the 8 halo rows of the own columns (items b, c)
+  if (tid < 2 * TILE_Z) {
+    const int k = (tid >> 1) * (W72 / 4) + ((tid & 1) ? W72 / 4 - 1 : 0);
+    item_a(k);
+    item_d(k);
+  } else if (tid < 2 * TILE_Z + 8 * (TILE_X / 4)) {
+    const int h = (tid - 2 * TILE_Z) >> 4, c = tid & 15, hr = h < 4 ? h : h + TILE_Z;
+    item_b(hr * (TILE_X / 4) + c);
+    item_c(hr * (TILE_X / 4) + c);
+  }
   // the own nodes' adjoint stresses, read before the buffer is refilled
   float Sx_own[2][4], Sz_own[2][4], Sh_own[2][4];
 #pragma unroll
@@ -749,9 +790,7 @@ __global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at
   const float* s_Vz = s_Vx + H40 * W72;
   const bool px = pml_x(g, x0), pz = pml_z(g, z0);
   const float dt = p.dt;
-  constexpr int NA = TILE_Z * (W72 / 4), NB = H40 * (TILE_X / 4);
-  // the four item kinds run as separate loops, each unrolled so that a thread's
-  // items have their global loads (medium, CPML tables and memory) in flight together
+  // the halo items of each kind (the own nodes' are merged below)
   auto item_a = [&](int k) {  // (a) at vx nodes, own rows, columns [x0-4, x0+68): psi1 adjoint (x)
     const int r = k / (W72 / 4), gq = k - r * (W72 / 4);
     const int z = z0 + r, j = x0 - 4 + 4 * gq;
@@ -800,14 +839,52 @@ __global__ void __launch_bounds__(NTHREADS, N == 2 ? 3 : 2)  // 3 CTAs per SM at
     cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[2], p.Mout[2], id, gq >= 1 && gq <= 16, t, d);
     st4(d_sxzx + r * W72 + 4 * gq, a4f(d));
   };
-#pragma unroll 3
-  for (int k = tid; k < NA; k += NTHREADS) item_a(k);
-#pragma unroll 3
-  for (int k = tid; k < NB; k += NTHREADS) item_b(k);
-#pragma unroll 3
-  for (int k = tid; k < NB; k += NTHREADS) item_c(k);
-#pragma unroll 3
-  for (int k = tid; k < NA; k += NTHREADS) item_d(k);
+  // own nodes: items (a) and (b) of a vx-node group, and (c) and (d) of a
+  // vz-node group, in one pass each, so that its buoyancy is loaded once
+  auto item_ab = [&](int k) {
+    const int r = k >> 4, c = k & 15;
+    const int z = z0 + r, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float v[4], b[4], t[4], d[4];
+    f4a(ld4(s_Vx + (r + 4) * W72 + 4 * c + 4), v);
+    f4a(ldg4(p.bx + im), b);
+#pragma unroll
+    for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
+    cpml_adj_x4(px, p.axh, p.bxh, j, p.Min[0], p.Mout[0], id, true, t, d);
+    st4(d_sxx + r * W72 + 4 * (c + 1), a4f(d));
+    cpml_adj_z4(pz, p.az, p.bzt, z, p.Min[1], p.Mout[1], id, true, t, d);
+    st4(d_sxz + (r + 4) * TILE_X + 4 * c, a4f(d));
+  };
+  auto item_cd = [&](int k) {
+    const int r = k >> 4, c = k & 15;
+    const int z = z0 + r, j = x0 + 4 * c;
+    const long long id = base + (long long)z * pitch + j, im = g.off0 + (long long)z * pitch + j;
+    float v[4], b[4], t[4], d[4];
+    f4a(ld4(s_Vz + (r + 4) * W72 + 4 * c + 4), v);
+    f4a(ldg4(p.bz + im), b);
+#pragma unroll
+    for (int e = 0; e < 4; e++) t[e] = dt * b[e] * v[e];
+    cpml_adj_z4(pz, p.azh, p.bzh, z, p.Min[3], p.Mout[3], id, true, t, d);
+    st4(d_szz + (r + 4) * TILE_X + 4 * c, a4f(d));
+    cpml_adj_x4(px, p.ax, p.bxt, j, p.Min[2], p.Mout[2], id, true, t, d);
+    st4(d_sxzx + r * W72 + 4 * (c + 1), a4f(d));
+  };
+  constexpr int NOWN = TILE_Z * (TILE_X / 4);  // own 4-node groups: 512
+#pragma unroll 2
+  for (int k = tid; k < NOWN; k += NTHREADS) item_ab(k);
+#pragma unroll 2
+  for (int k = tid; k < NOWN; k += NTHREADS) item_cd(k);
+  // halo nodes: the two halo column groups of every own row (items a, d) and
+  // the 8 halo rows of the own columns (items b, c)
+  if (tid < 2 * TILE_Z) {
+    const int k = (tid >> 1) * (W72 / 4) + ((tid & 1) ? W72 / 4 - 1 : 0);
+    item_a(k);
+    item_d(k);
+  } else if (tid < 2 * TILE_Z + 8 * (TILE_X / 4)) {
+    const int h = (tid - 2 * TILE_Z) >> 4, c = tid & 15, hr = h < 4 ? h : h + TILE_Z;
+    item_b(hr * (TILE_X / 4) + c);
+    item_c(hr * (TILE_X / 4) + c);
+  }
   // the own nodes' adjoint velocities, read before the buffer is refilled
   float vx_own[2][4], vz_own[2][4];
 #pragma unroll
