@@ -124,12 +124,11 @@ struct TcRoles {
 // 16 (c ^ (r % 8)) within its 128-byte row).
 struct GatherRow {
   long long base;  // x offset of (b, r0, s0) relative to channel 0, if m is a pixel
-  uint32_t mask;   // bit 3p + q: tap (p, q) inside the image
-  bool live;
+  uint32_t mask;   // bit 3p + q: tap (p, q) inside the image (0 if m is not a pixel)
 };
 __device__ __forceinline__ GatherRow gather_row(const TcConvA& c, long long m, long long M) {
-  GatherRow g{0, 0u, m < M};
-  if (!g.live) return g;
+  GatherRow g{0, 0u};
+  if (m >= M) return g;
   const uint32_t bi = mulhi_div((uint32_t)m, c.wo_m, c.wo_s);
   const int j = (int)((uint32_t)m - bi * (uint32_t)c.Wo);
   const uint32_t b = mulhi_div(bi, c.ho_m, c.ho_s);
@@ -144,23 +143,19 @@ __device__ __forceinline__ GatherRow gather_row(const TcConvA& c, long long m, l
   return g;
 }
 constexpr int GATHER_K = TC_BK / 2;  // taps of a row built by one gathering thread per stage
-// Tap table of a CONV CTA (shared memory, built once): for tap k < 9 C the x
-// offset of (channel c, tap row p, tap column q) relative to a pixel's base,
-// c B H W + p W + q, and its tap index 3 p + q (bit of the pixel's mask).
-struct TapTab {
-  int* off;
-  unsigned char* tap;
-};
+// Tap table of a CONV CTA (shared memory, built once, one entry per tap of every
+// k-block): for tap k < 9 C the x offset of (channel c, tap row p, tap column q)
+// relative to a pixel's base, c B H W + p W + q, and its tap index 3 p + q (the
+// bit of the pixel's mask); beyond 9 C, offset 0 and index 9 (a bit no mask has).
 // Loads (into registers) the GATHER_K taps of half `half` of k-block kb for the thread's row.
-__device__ __forceinline__ void gather_load(const TcConvA& c, const GatherRow& g, const TapTab& tt, int kb, int half,
+__device__ __forceinline__ void gather_load(const TcConvA& c, const GatherRow& g, const int2* tab, int kb, int half,
                                             float v[GATHER_K]) {
-  const int k0 = kb * TC_BK + GATHER_K * half, K9 = 9 * c.C;
+  const int2* t = tab + kb * TC_BK + GATHER_K * half;
   const float* xb = c.x + g.base;
 #pragma unroll
   for (int kk = 0; kk < GATHER_K; kk++) {
-    const int k = min(k0 + kk, K9 - 1);  // table reads stay inside the table
-    const bool ok = g.live && k0 + kk < K9 && ((g.mask >> tt.tap[k]) & 1u);
-    v[kk] = ok ? __ldg(xb + tt.off[k]) : 0.f;
+    const int2 e = t[kk];
+    v[kk] = ((g.mask >> e.y) & 1u) ? __ldg(xb + e.x) : 0.f;
   }
 }
 // Rounds them to BF16 and stores them as chunks 4 half .. 4 half + 3 of the row.
@@ -193,16 +188,14 @@ __global__ void __launch_bounds__(TcRoles<CONV>::THREADS, TcRoles<CONV>::CTAS)
   unsigned char* smA = tc_smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const int B_STAGE = a.BN * TC_BK * 2;
   unsigned char* smB = smA + TC_STAGES * A_STAGE;
-  TapTab tt{nullptr, nullptr};
-  if (CONV) {  // after the stages: 9 C offsets, then 9 C tap indices
-    const int K9 = 9 * conv.C;
-    tt.off = reinterpret_cast<int*>(smB + TC_STAGES * a.BN * TC_BK * 2);
-    tt.tap = reinterpret_cast<unsigned char*>(tt.off + K9);
+  int2* tab = nullptr;
+  if (CONV) {  // after the stages: a.nkb k-blocks of (offset, tap index) entries
+    const int K9 = 9 * conv.C, len = a.nkb * TC_BK;
+    tab = reinterpret_cast<int2*>(smB + TC_STAGES * a.BN * TC_BK * 2);
     const int plane = conv.B * conv.H * conv.W;
-    for (int k = threadIdx.x; k < K9; k += blockDim.x) {
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
       const int ch = k / 9, t = k - 9 * ch, p = t / 3, q = t - 3 * p;
-      tt.off[k] = ch * plane + p * conv.W + q;
-      tt.tap[k] = (unsigned char)t;
+      tab[k] = k < K9 ? make_int2(ch * plane + p * conv.W + q, t) : make_int2(0, 9);
     }
   }
 
@@ -276,7 +269,7 @@ __global__ void __launch_bounds__(TcRoles<CONV>::THREADS, TcRoles<CONV>::CTAS)
         break;
       }
       float v[GATHER_K];
-      gather_load(conv, g, tt, kb0 + i, half, v);
+      gather_load(conv, g, tab, kb0 + i, half, v);
       gather_store(v, row, half, smA + s * A_STAGE);
       fence_proxy_async();  // the generic-proxy writes before the tensor core reads them
       mbar_arrive(&fulla[s]);
@@ -403,7 +396,7 @@ cudaError_t tc_gemm(const TcGemm& g, cudaStream_t st) {
   if (!encode_bf16_sw128(&tb, g.B, g.K, g.N, g.ldb, BN)) return cudaErrorInvalidValue;
   if (conv) ta = tb;  // unused: A is gathered
   else if (!encode_bf16_sw128(&ta, g.A, g.K, g.M, g.lda, TC_BM)) return cudaErrorInvalidValue;
-  const int smem = TC_STAGES * (A_STAGE + BN * TC_BK * 2) + 1024 + (conv ? 9 * g.conv->C * 5 + 16 : 0);
+  const int smem = TC_STAGES * (A_STAGE + BN * TC_BK * 2) + 1024 + (conv ? (int)nkb * TC_BK * 8 : 0);
   const dim3 grid((unsigned)((g.M + TC_BM - 1) / TC_BM), (unsigned)((g.N + BN - 1) / BN), (unsigned)splits);
   TcConvA c{};
   if (conv) c = *g.conv;
