@@ -145,8 +145,8 @@ __device__ __forceinline__ GatherRow gather_row(const TcConvA& c, long long m, l
 constexpr int GATHER_K = TC_BK / 2;  // taps of a row built by one gathering thread per stage
 // Tap table of a CONV CTA (shared memory, built once, one entry per tap of every
 // k-block): for tap k < 9 C the x offset of (channel c, tap row p, tap column q)
-// relative to a pixel's base, c B H W + p W + q, and its tap index 3 p + q (the
-// bit of the pixel's mask); beyond 9 C, offset 0 and index 9 (a bit no mask has).
+// relative to a pixel's base, c B H W + p W + q, and the mask bit of its tap,
+// 1 << (3 p + q); beyond 9 C, offset 0 and bit 1 << 9 (a bit no mask has).
 // Loads (into registers) the GATHER_K taps of half `half` of k-block kb for the thread's row.
 __device__ __forceinline__ void gather_load(const TcConvA& c, const GatherRow& g, const int2* tab, int kb, int half,
                                             float v[GATHER_K]) {
@@ -155,7 +155,7 @@ __device__ __forceinline__ void gather_load(const TcConvA& c, const GatherRow& g
 #pragma unroll
   for (int kk = 0; kk < GATHER_K; kk++) {
     const int2 e = t[kk];
-    v[kk] = ((g.mask >> e.y) & 1u) ? __ldg(xb + e.x) : 0.f;
+    v[kk] = (g.mask & (uint32_t)e.y) ? __ldg(xb + e.x) : 0.f;
   }
 }
 // Rounds them to BF16 and stores them as chunks 4 half .. 4 half + 3 of the row.
@@ -189,13 +189,13 @@ __global__ void __launch_bounds__(TcRoles<CONV>::THREADS, TcRoles<CONV>::CTAS)
   const int B_STAGE = a.BN * TC_BK * 2;
   unsigned char* smB = smA + TC_STAGES * A_STAGE;
   int2* tab = nullptr;
-  if (CONV) {  // after the stages: a.nkb k-blocks of (offset, tap index) entries
+  if (CONV) {  // after the stages: a.nkb k-blocks of (offset, tap bit) entries
     const int K9 = 9 * conv.C, len = a.nkb * TC_BK;
     tab = reinterpret_cast<int2*>(smB + TC_STAGES * a.BN * TC_BK * 2);
     const int plane = conv.B * conv.H * conv.W;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
       const int ch = k / 9, t = k - 9 * ch, p = t / 3, q = t - 3 * p;
-      tab[k] = k < K9 ? make_int2(ch * plane + p * conv.W + q, t) : make_int2(0, 9);
+      tab[k] = k < K9 ? make_int2(ch * plane + p * conv.W + q, 1 << t) : make_int2(0, 1 << 9);
     }
   }
 
