@@ -261,15 +261,20 @@ __global__ void __launch_bounds__(TcRoles<CONV>::THREADS, TcRoles<CONV>::CTAS)
     // A gatherers: half threadIdx.x / 128 of row threadIdx.x % 128 of every stage tile
     const int row = threadIdx.x % TC_BM, half = threadIdx.x / TC_BM;
     const GatherRow g = gather_row(conv, m0 + row, a.M);
+    // the loads of k-block i + 1 are issued before block i is converted and stored
+    float vn[GATHER_K];
+    if (nk > 0) gather_load(conv, g, tab, kb0, half, vn);
     for (int i = 0; i < nk; i++) {
       const int s = i % TC_STAGES;
       const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+      float v[GATHER_K];
+#pragma unroll
+      for (int kk = 0; kk < GATHER_K; kk++) v[kk] = vn[kk];
+      if (i + 1 < nk) gather_load(conv, g, tab, kb0 + i + 1, half, vn);
       if (!mbar_wait(&empty[s], ph ^ 1u)) {
         err = 1;
         break;
       }
-      float v[GATHER_K];
-      gather_load(conv, g, tab, kb0 + i, half, v);
       gather_store(v, row, half, smA + s * A_STAGE);
       fence_proxy_async();  // the generic-proxy writes before the tensor core reads them
       mbar_arrive(&fulla[s]);
