@@ -183,6 +183,25 @@ fwi_status fwi_forward_vjp(fwi_ctx *ctx, const fwi_model *model, const fwi_sourc
                            float *grad, float *grad_stf, float *grad_x0, float *seis_out,
                            void *cuda_stream);
 
+/* Misfit of sub-sources acting together (the rupture imaging of the paper's
+ * source-inversion applications): the nshots sources of src are the
+ * sub-sources of ONE event, each propagated in its own wavefield (the wave
+ * equation is linear in the source), and the event's seismograms are their sum:
+ *   J = 1/2 sum_{r,n} (sum_s d_s - observed)^2,
+ * with the gradients of the sub-sources' time functions and positions (and the
+ * model) from the adjoint sweep of every sub-source seeded with the common
+ * residual sum_s d_s - observed. The sum, the residual and J (FP64) are formed on
+ * the device. Acoustic models only (FWI_ENOTIMPL otherwise).
+ * observed   [nrec][nt] FP32, host or device (one event, not per sub-source).
+ * Other arguments, outputs and status codes as fwi_misfit_grad (grad_stf
+ * [nshots][nt], grad_x0 [nshots][2], grad [nz][nx], each may be NULL). Runs a
+ * forward call and a vector-Jacobian call on ctx; its scratch comes from the
+ * stream-ordered allocator (FWI_ENOMEM if that fails). Synchronises. */
+fwi_status fwi_superposed_misfit_grad(fwi_ctx *ctx, const fwi_model *model, const fwi_sources *src,
+                                      const fwi_receivers *rec, int32_t nt, float dt, const float *observed,
+                                      int32_t ckpt_every, double *misfit, float *grad, float *grad_stf,
+                                      float *grad_x0, void *cuda_stream);
+
 /* Device workspace (bytes) that a call allocates in its context: the forward
  * call (ckpt_every = 0) or fwi_misfit_grad with checkpoint interval
  * ckpt_every (1..nt), for the given model, sources, receivers and nt; sized

@@ -10,12 +10,11 @@ imaging).
 * ``superposed_misfit``: J = 1/2 || sum_k d_k - d_obs ||^2 for several sources
   active in ONE wavefield (a rupture: sub-sources switched on along a fault).
   The scheme is linear in its source term, so the wavefield of the sum is the
-  sum of the per-source wavefields d_k, which one batched call of the
-  differentiable seismogram operator gives (the sub-sources as shots). The
-  loss is ordinary torch code on those seismograms; its backward seeds every
-  sub-source's adjoint sweep with the common residual dJ/dd_k =
-  sum_k d_k - d_obs (fwi_forward_vjp), which gives the gradient with respect to
-  each sub-source's time function and position.
+  sum of the per-source wavefields d_k (the sub-sources as the shots of one
+  call). The library forms the sum, the residual and J on the device and seeds
+  every sub-source's adjoint sweep with the common residual dJ/dd_k =
+  sum_k d_k - d_obs (fwi_superposed_misfit_grad), which gives the gradient
+  with respect to each sub-source's time function and position.
 * ``gaussian_slip``: the rupture time / amplitude parametrisation
   g_k(t) = A_k exp(-(t - t_k)^2 / (2 s^2)), differentiable in (A_k, t_k).
 
@@ -30,18 +29,39 @@ from dataclasses import dataclass, field
 import torch
 
 from . import fwi
-from .autograd import acoustic_misfit, acoustic_seismograms
+from .autograd import acoustic_misfit
+
+
+class SuperposedMisfit(torch.autograd.Function):
+    """J(stf, x0, c) of sub-sources acting together: the library forms the sum
+    of the sub-sources' seismograms, the residual and J, and the gradients by the
+    adjoint sweep seeded with that residual (fwi_superposed_misfit_grad);
+    backward scales them by the upstream gradient."""
+
+    @staticmethod
+    def forward(ctx, stf, x0, c, observed, rec_iz, rec_ix, opts):
+        want_src = ctx.needs_input_grad[0] or ctx.needs_input_grad[1]
+        J, gc, gs, gx = fwi.superposed_misfit_grad(c, stf, x0, rec_iz, rec_ix, observed,
+                                                   want_grad=ctx.needs_input_grad[2], want_src=want_src, **opts)
+        ctx.grads = (gs, gx, gc)
+        return J.reshape(())
+
+    @staticmethod
+    def backward(ctx, gJ):
+        gs, gx, gc = ctx.grads
+        scale = lambda g: None if g is None else g * gJ.to(g.dtype)
+        return (scale(gs) if ctx.needs_input_grad[0] else None, scale(gx) if ctx.needs_input_grad[1] else None,
+                scale(gc) if ctx.needs_input_grad[2] else None, None, None, None, None)
 
 
 def superposed_misfit(stf, x0, c, observed, rec_iz, rec_ix, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
                       pml_vmax=4500.0, pml_f0=10.0, src_kind=fwi.FWI_SRC_GAUSSIAN, ckpt_every=100):
     """Differentiable misfit of the sources stf [k][nt] at x0 [k][2] acting
-    together (a 0-d float64 tensor): the seismogram operator over the k
-    sub-sources, summed, against observed [nrec][nt]."""
-    d = acoustic_seismograms(c, stf, x0, rec_iz, rec_ix, dx=dx, dz=dz, dt=dt, order=order, npml=npml, pml_R=pml_R,
-                             pml_vmax=pml_vmax, pml_f0=pml_f0, src_kind=src_kind, ckpt_every=ckpt_every)
-    r = d.sum(dim=0) - observed
-    return 0.5 * torch.sum(r.double() * r.double())
+    together (a 0-d float64 tensor): J = 1/2 sum (sum_k d_k - observed)^2 for
+    observed [nrec][nt], computed by the library."""
+    opts = dict(dx=dx, dz=dz, dt=dt, order=order, npml=npml, pml_R=pml_R, pml_vmax=pml_vmax, pml_f0=pml_f0,
+                src_kind=src_kind, ckpt_every=ckpt_every)
+    return SuperposedMisfit.apply(stf, x0, c, observed, rec_iz, rec_ix, opts)
 
 
 def gaussian_slip(A, t0, sigma, nt, dt):

@@ -44,6 +44,8 @@ cudaError_t launch_model_check(const float* c, long long n, float coef, int* sta
 cudaError_t launch_misfit(const float* seis, float* res, long long n, double* part, int nb, double* J,
                           int* status, bool vjp, cudaStream_t st);
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st);
+cudaError_t launch_superpose(const float* seis, int S, long long n, const float* obs, float* cot, double* part,
+                             int nb, double* J, int* status, cudaStream_t st);
 cudaError_t launch_selftest_wait(int* status, unsigned long long* waited_ns, cudaStream_t st);
 cudaError_t launch_ela_velocity_grad(const float* vp, const float* vs, const float* rho, const float* gin,
                                      float* gout, long long n, cudaStream_t st);
@@ -952,6 +954,58 @@ fwi_status fwi_forward_vjp(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* 
   ctx->vjp = true;
   return fwi_misfit_grad(ctx, M, Sv, R, nt, dt, cotangent, K, value ? value : &local, grad, grad_stf, grad_x0,
                          seis_out, stream);
+}
+
+fwi_status fwi_superposed_misfit_grad(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv,
+                                      const fwi_receivers* R, int32_t nt, float dt, const float* observed, int32_t K,
+                                      double* misfit, float* grad, float* grad_stf, float* grad_x0, void* stream) {
+  if (!ctx) return fail(FWI_EINVAL, "ctx must not be NULL");
+  if (M && M->physics != FWI_ACOUSTIC) return fail(FWI_ENOTIMPL, "superposed sources are acoustic only");
+  fwi_status v = validate(M, Sv, R, nt, dt);
+  if (v != FWI_OK) return v;
+  if (!misfit) return fail(FWI_EINVAL, "misfit must not be NULL");
+  if (!observed && R->nrec > 0) return fail(FWI_EINVAL, "observed must not be NULL");
+  if (K < 1 || K > nt) return fail(FWI_EINVAL, "ckpt_every must be in [1, nt]");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = Sv->nshots;
+  const long long n = (long long)R->nrec * nt;
+  // stream-ordered scratch: the S seismograms, the common residual for every
+  // sub-source, the observed data, the misfit's partial sums and status word
+  struct Scratch {
+    cudaStream_t st;
+    void* p[5] = {};
+    ~Scratch() {
+      for (void* q : p)
+        if (q) cudaFreeAsync(q, st);
+    }
+  } sc{st};
+  const size_t bytes[5] = {(size_t)S * n * 4 + 4, (size_t)S * n * 4 + 4, (size_t)n * 4 + 4,
+                           (size_t)MISFIT_BLOCKS * 8 + 8, sizeof(int)};
+  for (int k = 0; k < 5; k++)
+    if (cudaMallocAsync(&sc.p[k], bytes[k], st) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FWI_ENOMEM, "superposed misfit: scratch allocation failed");
+    }
+  float *seis = (float*)sc.p[0], *cot = (float*)sc.p[1], *obs = (float*)sc.p[2];
+  double* part = (double*)sc.p[3];
+  double* J = part + MISFIT_BLOCKS;
+  int* status = (int*)sc.p[4];
+  // the S sub-source seismograms, each in its own wavefield (the equation is linear in the source)
+  if ((v = fwi_forward(ctx, M, Sv, R, nt, dt, seis, stream)) != FWI_OK) return v;
+  CK(cudaMemsetAsync(status, 0, sizeof(int), st));
+  if (n > 0) CK(cudaMemcpyAsync(obs, observed, (size_t)n * 4, cudaMemcpyDefault, st));
+  if (n > 0) LK(2, launch_superpose(seis, S, n, obs, cot, part, MISFIT_BLOCKS, J, status, st));
+  else CK(cudaMemsetAsync(J, 0, 8, st));
+  CK(cudaMemcpyAsync(misfit, J, 8, cudaMemcpyDefault, st));
+  // the gradient: the adjoint sweep of every sub-source seeded with the common residual
+  double inner = 0.0;
+  if ((v = fwi_forward_vjp(ctx, M, Sv, R, nt, dt, cot, K, &inner, grad, grad_stf, grad_x0, nullptr, stream)) !=
+      FWI_OK)
+    return v;
+  if ((v = finish_status_dev(ctx, status, st)) != FWI_OK) return v;
+  g_err.clear();
+  return FWI_OK;
 }
 
 fwi_status fwi_misfit_grad_graph(fwi_ctx* ctx, const fwi_model* M, const fwi_sources* Sv, const fwi_receivers* R,

@@ -240,6 +240,31 @@ __global__ void k_misfit(const float* __restrict__ seis, float* res, long long n
   }
 }
 
+// Superposed sources: r = sum_s d_s - d_obs over the S seismograms (summed in
+// shot order), broadcast into cot[s] for every s (the adjoint source of each
+// sub-source is the common residual), and per-block FP64 partial sums of r^2.
+__global__ void k_superpose(const float* __restrict__ seis, int S, long long n, const float* __restrict__ obs,
+                            float* __restrict__ cot, double* part) {
+  __shared__ double sred[256 / 32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float d = 0.f;
+    for (int sh = 0; sh < S; sh++) d += seis[(long long)sh * n + i];
+    const float r = d - obs[i];
+    for (int sh = 0; sh < S; sh++) cot[(long long)sh * n + i] = r;
+    acc += (double)r * (double)r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) sum += sred[w];
+    part[blockIdx.x] = sum;
+  }
+}
+
 __global__ void k_misfit_final(const double* part, int nb, double scale, double* J, int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
@@ -501,6 +526,12 @@ cudaError_t launch_misfit(const float* seis, float* res, long long n, double* pa
   if (vjp) k_misfit<true><<<nb, 256, 0, st>>>(seis, res, n, part);
   else k_misfit<false><<<nb, 256, 0, st>>>(seis, res, n, part);
   k_misfit_final<<<1, 32, 0, st>>>(part, nb, vjp ? 1.0 : 0.5, J, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_superpose(const float* seis, int S, long long n, const float* obs, float* cot, double* part,
+                             int nb, double* J, int* status, cudaStream_t st) {
+  k_superpose<<<nb, 256, 0, st>>>(seis, S, n, obs, cot, part);
+  k_misfit_final<<<1, 32, 0, st>>>(part, nb, 0.5, J, status);
   return cudaGetLastError();
 }
 cudaError_t launch_finite_check(const float* a, long long n, int* status, cudaStream_t st) {

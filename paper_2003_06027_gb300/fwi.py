@@ -81,6 +81,9 @@ def library(build_if_missing: bool = True):
                                           ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
                                           ctypes.c_int32, P, P, P, P, P, P]
             L.fwi_forward_vjp.argtypes = L.fwi_misfit_grad.argtypes
+            L.fwi_superposed_misfit_grad.argtypes = [P, ctypes.POINTER(_Model), ctypes.POINTER(_Sources),
+                                                     ctypes.POINTER(_Receivers), ctypes.c_int32, ctypes.c_float, P,
+                                                     ctypes.c_int32, P, P, P, P, P]
             L.fwi_batch_create.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, ctypes.c_float, P,
                                            ctypes.c_int32, P, P, ctypes.POINTER(P)]
             L.fwi_batch_launch.argtypes = [P, P]
@@ -309,6 +312,26 @@ def misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, np
         _ptr(out.get("grad_stf")), _ptr(out.get("grad_x0")), _ptr(out.get("seis")),
         _stream(ref, stream)))
     return out["misfit"], out.get("grad"), out.get("grad_stf"), out.get("grad_x0"), out.get("seis")
+
+
+def superposed_misfit_grad(c, stf, x0, rec_iz, rec_ix, observed, *, dx, dz, dt, order=4, npml=20, pml_R=1e-3,
+                           pml_vmax=4500.0, pml_f0=10.0, src_kind=FWI_SRC_GAUSSIAN, op=FWI_OP_DIVERGENCE,
+                           ckpt_every=100, want_grad=True, want_src=True, stream=None, device=None):
+    """(J, dJ/dc, dJ/dstf, dJ/dx0) of J = 1/2 sum (sum_s d_s - d_obs)^2 for the
+    sub-sources stf [k][nt] at x0 [k][2] of one event, observed [nrec][nt]
+    (fwi_superposed_misfit_grad)."""
+    a = _Call(c, stf, x0, rec_iz, rec_ix, dx, dz, order, npml, pml_R, pml_vmax, pml_f0, src_kind, op)
+    obs = _arr(observed, np.float32)
+    ref = a.c
+    J = _empty_like_place(ref, (1,), np.float64)
+    gc = _empty_like_place(ref, tuple(a.c.shape)) if want_grad else None
+    gs = _empty_like_place(ref, (a.S, a.nt)) if want_src else None
+    gx = _empty_like_place(ref, (a.S, 2)) if want_src else None
+    K = max(1, min(int(ckpt_every), a.nt))
+    _check(library().fwi_superposed_misfit_grad(
+        context(_device(ref, device)), ctypes.byref(a.model), ctypes.byref(a.src), ctypes.byref(a.rec), a.nt,
+        float(dt), _ptr(obs), K, _ptr(J), _ptr(gc), _ptr(gs), _ptr(gx), _stream(ref, stream)))
+    return J, gc, gs, gx
 
 
 def forward_vjp(c, stf, x0, rec_iz, rec_ix, cotangent, **kw):
