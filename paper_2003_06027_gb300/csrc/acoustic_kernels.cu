@@ -893,10 +893,8 @@ __global__ void __launch_bounds__(NTHREADS, 3)
           m2[rr] = make_float4(2.f * mh.x, 2.f * mh.y, 2.f * mh.z, 2.f * mh.w);
         }
       }
-      __syncthreads();
-      if (tid == 0 && tn < ntiles) fetch(tn);  // the operand buffer is free
-
-      // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
+      // lambda_{n+2} and the gradient partial of the own cells: issued before the
+      // barrier, so that their latency overlaps the other warps' halo items
       float* __restrict__ lprev = p.lam + (long long)((p.cur ^ 1) * p.S_pair + p.s0) * g.slice + base;
       float* __restrict__ gp = p.gpart + base;
       float4 lo[2], go[2];
@@ -904,6 +902,10 @@ __global__ void __launch_bounds__(NTHREADS, 3)
       lo[1] = ldg4(lprev + (long long)(zr0 + 1) * pitch + xb);
       go[0] = ldg4(gp + (long long)zr0 * pitch + xb);
       go[1] = ldg4(gp + (long long)(zr0 + 1) * pitch + xb);
+      __syncthreads();
+      if (tid == 0 && tn < ntiles) fetch(tn);  // the operand buffer is free
+
+      // ---- stage 2: lambda_n, gradient, residual, Z update, hhat for step n-1, source partials
       const int2 box = __ldg(reinterpret_cast<const int2*>(p.src_box) + s);
       const int key = (id.tz * g.ntx + id.tx) * NTHREADS + tid;
       const int rb = __ldg(p.thr_rec_start + key), re = __ldg(p.thr_rec_start + key + 1);
