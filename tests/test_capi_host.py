@@ -42,3 +42,18 @@ def test_binding_fails_loudly_without_a_device():
 
     with pytest.raises(fwi.FwiError):
         fwi.context(0)
+
+
+def test_recorded_graph_refuses_pageable_or_mixed_inputs_on_the_host():
+    """GradGraph's host-side checks run before the library is touched: host
+    inputs must be page-locked, of the call's dtypes (a converted copy would not
+    see the caller's in-place model updates), and not mixed with device ones."""
+    torch = pytest.importorskip("torch")
+    from paper_2003_06027_gb300 import fwi
+
+    args = [torch.zeros(4, 4), torch.zeros(1, 5), torch.zeros(1, 2), torch.zeros(2, dtype=torch.int32),
+            torch.zeros(2, dtype=torch.int32), torch.zeros(1, 2, 5)]
+    with pytest.raises(ValueError):
+        fwi.GradGraph(*args, dx=1.0, dz=1.0, dt=0.1)  # pageable host tensors
+    with pytest.raises(ValueError):
+        fwi.GradGraph(*args[:3], args[3].long(), *args[4:], dx=1.0, dz=1.0, dt=0.1)  # int64 receivers
